@@ -1,0 +1,532 @@
+"""Pins of the CPU oracle to what the paper and the mathematics fix (no GPU).
+
+Each test names what it pins.  None of them re-types the oracle's own formula: they use printed values
+(tests/golden), closed forms, exact discrete identities, invariants, special cases and an independent
+method (a density-matrix HEOM in a truncated vibrational basis).
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import qhfpe_inputs as qi
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _model(**kw):
+    """Two-state harmonic model; keyword arguments go to qhfpe_inputs.harmonic_two_state."""
+    return qi.harmonic_two_state(**kw)
+
+
+def _relerr(a, b):
+    return np.linalg.norm(np.ravel(a - b)) / max(np.linalg.norm(np.ravel(b)), 1e-300)
+
+
+# ------------------------------------------------------------------------------------------------
+# P1: the printed upwind stencil (Sec. III) and the orders of the q- and p-differences
+# ------------------------------------------------------------------------------------------------
+def _read_stencil():
+    rows = {}
+    with open(os.path.join(GOLDEN, "upwind_stencil.txt")) as f:
+        for line in f:
+            if line.startswith("#") or not line.strip():
+                continue
+            br, d, c = line.split()
+            rows.setdefault(br, {})[int(d)] = float(c)
+    return rows
+
+
+def test_upwind_stencil_matches_printed_coefficients():
+    """Kinetic term on a unit impulse reproduces the printed coefficients for both signs of p."""
+    m = qi.single_state(lambda q: 0 * q, nq=16, n_p=8, depth=0, closure=0)
+    O = oracle.Oracle(m)
+    W = np.zeros(O.shape, complex)
+    i0 = 8
+    W[0, 0, 0, i0, :] = 1.0
+    out = O.rhs(W, oracle.KINETIC)[0, 0, 0]
+    p = qi.axis(m["np"], m["p_min"], m["p_max"])
+    dq = O.dq
+    gold = _read_stencil()
+    for l in range(m["np"]):
+        br = "p<0" if p[l] < 0 else "p>=0"
+        for d, c in gold[br].items():
+            # output row i = i0 - d sees the impulse at offset +d with coefficient c
+            got = out[i0 - d, l].real / (-p[l]) * 60 * dq if p[l] != 0 else None
+            if got is not None:
+                assert got == pytest.approx(c, abs=1e-12)
+        # rows outside the stencil's reach see nothing
+        for i in range(m["nq"]):
+            if (i0 - i) not in gold[br]:
+                assert out[i, l] == 0
+
+
+def test_upwind_stencil_order_and_first_error_term():
+    """Exact for q^k, k <= 5; for q^6 at q = 0 the error is -12 dq^5 (p >= 0) and +12 dq^5 (p < 0)
+    (the sixth moment of the printed stencil is -+720)."""
+    m = qi.single_state(lambda q: 0 * q, nq=16, n_p=4, qr=(-4.0, 4.0), depth=0, closure=0)
+    O = oracle.Oracle(m)
+    q = qi.axis(m["nq"], m["q_min"], m["q_max"])
+    p = qi.axis(m["np"], m["p_min"], m["p_max"])
+    i0 = int(np.argmin(abs(q)))
+    assert q[i0] == 0
+    for k in range(0, 7):
+        W = np.zeros(O.shape, complex)
+        W[0, 0, 0] = (q ** k)[:, None] * np.ones(m["np"])[None, :]
+        out = O.rhs(W, oracle.KINETIC)[0, 0, 0]
+        for l in range(m["np"]):
+            if p[l] == 0:
+                continue
+            dq_est = out[3:-3, l].real / (-p[l])
+            exact = k * q[3:-3] ** (k - 1) if k > 0 else 0 * q[3:-3]
+            if k <= 5:
+                assert np.allclose(dq_est, exact, atol=1e-10 * max(1, np.abs(exact).max()))
+            else:
+                err = dq_est[i0 - 3] - 0.0
+                expect = -12 * O.dq ** 5 if p[l] >= 0 else 12 * O.dq ** 5
+                assert err == pytest.approx(expect, rel=1e-9)
+
+
+def test_p_differences_order():
+    """d/dp (through the tier-up coupling) is exact for p^k, k <= 4, with error -4 dp^4 at p = 0 for
+    p^5; d^2/dp^2 (through the delta-term) exact for k <= 5 with error -8 dp^4 at p = 0 for p^6."""
+    m = qi.single_state(lambda q: 0 * q, nq=4, n_p=16, pr=(-4.0, 4.0), depth=1, closure=0,
+                        high_temperature=0, use_cdelta=1, n_matsubara=1, beta=1.0, gamma=1.0, eta=1.0)
+    O = oracle.Oracle(m)
+    co = O.coefficients()
+    assert co["cdelta"] != 0
+    h = O.hierarchy().tolist()
+    up0 = h.index([1, 0])
+    p = qi.axis(m["np"], m["p_min"], m["p_max"])
+    l0 = int(np.argmin(abs(p)))
+    for k in range(0, 7):
+        W = np.zeros(O.shape, complex)
+        W[up0, 0, 0] = np.ones(m["nq"])[:, None] * (p ** k)[None, :]
+        d1 = O.rhs(W, oracle.TIER_UP)[0, 0, 0, 1, 2:-2].real
+        ex1 = k * p[2:-2] ** (k - 1) if k else 0 * p[2:-2]
+        if k <= 4:
+            assert np.allclose(d1, ex1, atol=1e-10 * max(1, abs(ex1).max()))
+        elif k == 5:
+            assert d1[l0 - 2] == pytest.approx(-4 * O.dp ** 4, rel=1e-9)
+        W = np.zeros(O.shape, complex)
+        W[0, 0, 0] = np.ones(m["nq"])[:, None] * (p ** k)[None, :]
+        d2 = O.rhs(W, oracle.DAMPING)[0, 0, 0, 1, 2:-2].real / co["cdelta"]
+        ex2 = k * (k - 1) * p[2:-2] ** (k - 2) if k >= 2 else 0 * p[2:-2]
+        if k <= 5:
+            assert np.allclose(d2, ex2, atol=1e-9 * max(1, abs(ex2).max()))
+        elif k == 6:
+            assert d2[l0 - 2] == pytest.approx(-8 * O.dp ** 4, rel=1e-9)
+
+
+# ------------------------------------------------------------------------------------------------
+# P2: the potential kernel of Eq. (quantum-liouvillian)
+# ------------------------------------------------------------------------------------------------
+def test_potential_kernel_constant_surfaces():
+    """Constant surfaces a, b: the 10 block rotates at -i(b - a), the 01 block at -i(a - b), the
+    diagonal blocks do not move."""
+    a, b = 0.7, 3.2
+    m = _model()
+    m["U"] = [[lambda q: a + 0 * q, None], [None, lambda q: b + 0 * q]]
+    O = oracle.Oracle(m)
+    W = qi.random_state(m)
+    out = O.rhs(W, oracle.POTENTIAL)
+    assert np.abs(out[:, 0, 0]).max() < 1e-12
+    assert np.abs(out[:, 1, 1]).max() < 1e-12
+    assert _relerr(out[:, 1, 0], -1j * (b - a) * W[:, 1, 0]) < 1e-13
+    assert _relerr(out[:, 0, 1], -1j * (a - b) * W[:, 0, 1]) < 1e-13
+
+
+@pytest.mark.parametrize("surface", ["quadratic", "cubic", "anharmonic"])
+def test_potential_kernel_plane_waves(surface):
+    """A p-plane wave W = exp(i kappa p) (kappa = 2 pi k/(np dp), |k| < np/2) is an eigenfunction of
+    the single-state kernel with eigenvalue i [U(q + kappa/2) - U(q - kappa/2)]; for a quadratic
+    surface this is U'(q) d/dp, the classical force term, and for a cubic it adds the Moyal term."""
+    funcs = {
+        "quadratic": lambda q: 0.3 * q * q - 0.7 * q + 2.0,
+        "cubic": lambda q: 0.05 * q ** 3 + 0.5 * q * q,
+        "anharmonic": lambda q: 5.0 * ((q / 4.0) ** 2 - 1.0) ** 2,
+    }
+    U = funcs[surface]
+    m = qi.single_state(U, nq=8, n_p=32, depth=0, closure=0)
+    O = oracle.Oracle(m)
+    q = qi.axis(m["nq"], m["q_min"], m["q_max"])
+    lidx = np.arange(m["np"])
+    for k in (-15, -7, -1, 1, 5, 15):
+        kappa = 2 * math.pi * k / (m["np"] * O.dp)
+        W = np.zeros(O.shape, complex)
+        W[0, 0, 0] = np.exp(2j * math.pi * k * lidx / m["np"])[None, :] * np.ones((m["nq"], 1))
+        out = O.rhs(W, oracle.POTENTIAL)[0, 0, 0]
+        lam = 1j * (U(q + kappa / 2) - U(q - kappa / 2))
+        assert _relerr(out, lam[:, None] * W[0, 0, 0]) < 1e-12
+        if surface == "quadratic":
+            force = (0.6 * q - 0.7)[:, None] * (1j * kappa) * W[0, 0, 0]
+            assert _relerr(out, force) < 1e-12
+
+
+def test_potential_kernel_keeps_real_diagonal_blocks_real():
+    """With the symmetric Nyquist reading, a real W_jj gives a real potential term for any surface."""
+    m = qi.photoisomerization_two_state(nq=8, n_p=16, depth=0, n_matsubara=0)
+    m["U"][0][1] = m["U"][1][0] = None
+    O = oracle.Oracle(m)
+    W = np.zeros(O.shape, complex)
+    W[0, 0, 0] = np.random.default_rng(1).uniform(-1, 1, (8, 16))
+    out = O.rhs(W, oracle.POTENTIAL)
+    assert np.abs(out[0, 0, 0].imag).max() < 1e-12 * np.abs(out).max()
+    assert np.abs(out[0, 0, 0]).max() > 1e-3
+
+
+# ------------------------------------------------------------------------------------------------
+# P3: invariants of the full right-hand side
+# ------------------------------------------------------------------------------------------------
+@pytest.mark.parametrize("kind", ["harmonic", "photoiso"])
+def test_rhs_conserves_trace_and_hermiticity(kind):
+    if kind == "harmonic":
+        m = _model(periodic_q=1)
+    else:
+        m = qi.photoisomerization_two_state(nq=16, n_p=16, depth=2, n_matsubara=1)
+        m["periodic_q"] = 1
+    O = oracle.Oracle(m)
+    W = qi.random_state(m, hermitian=True, zero_p_edges=2)
+    L = O.rhs(W)
+    tr = sum(L[0, j, j].sum() for j in range(m["S"]))
+    assert abs(tr) < 1e-12 * np.abs(L).sum()
+    LH = np.conj(np.swapaxes(L, 1, 2))
+    assert _relerr(L, LH) < 1e-13
+
+
+# ------------------------------------------------------------------------------------------------
+# P4: R1(0) = 0 and the closed form of dR1/dt(0)
+# ------------------------------------------------------------------------------------------------
+def test_linear_response_initial_value_and_slope():
+    m = _model()
+    O = oracle.Oracle(m)
+    rng = np.random.default_rng(3)
+    W = np.zeros(O.shape, complex)
+    for e in range(O.n_elem):
+        blk = np.zeros((m["nq"], m["np"]))
+        blk[4:-4, 3:-3] = rng.uniform(0, 1, (m["nq"] - 8, m["np"] - 6))
+        W[e, 0, 0] = blk
+    X = O.apply_dipole(W, oracle.COMMUTATOR)
+    assert abs(O.trace(X)) < 1e-14
+    slope = 1j * O.trace(O.rhs(X))
+    q = qi.axis(m["nq"], m["q_min"], m["q_max"])
+    dU = m["U"][1][1](q) - m["U"][0][0](q)
+    expect = 2.0 * (dU * W[0, 0, 0].sum(axis=1)).sum() * O.dq * O.dp
+    assert slope.real == pytest.approx(expect, rel=1e-12)
+    assert abs(slope.imag) < 1e-12 * abs(expect)
+
+
+# ------------------------------------------------------------------------------------------------
+# P5: identical surfaces -- exact discrete closed form through RK4's amplification polynomial
+# ------------------------------------------------------------------------------------------------
+def _electronic_liouvillian(H):
+    S = H.shape[0]
+    I = np.eye(S)
+    # d vec(s)/dt = -i (H s - s H), row-major vec
+    return -1j * (np.kron(H, I) - np.kron(I, H.T))
+
+
+def _rk4_poly(A, dt):
+    Z = dt * A
+    P = np.eye(A.shape[0], dtype=complex)
+    term = np.eye(A.shape[0], dtype=complex)
+    for k in range(1, 5):
+        term = term @ Z / k
+        P = P + term
+    return P
+
+
+def _dip(mu, side):
+    S = mu.shape[0]
+    I = np.eye(S)
+    left = np.kron(mu, I)
+    right = np.kron(I, mu.T)
+    return {oracle.LEFT: left, oracle.RIGHT: right, oracle.COMMUTATOR: left - right}[side]
+
+
+@pytest.fixture(scope="module")
+def identical_surface_case():
+    """Periodic q and p make the trace an exact invariant, so the discrete ground problem has an exact
+    stationary state; it is reached by propagation (at a larger step, which does not change the null
+    vector of the generator) and then used with the response step dt."""
+    E, V = 3.0, 0.4
+    kw = dict(nq=24, n_p=24, qr=(-9.0, 9.0), pr=(-9.0, 9.0), displacement=0.0, eta=1.0, depth=1, periodic_q=1)
+    surf = [[lambda q: 0.5 * q * q, lambda q: V + 0 * q], [lambda q: V + 0 * q, lambda q: 0.5 * q * q + E]]
+    m_eq = _model(dt=0.04, **kw)
+    m_eq["U"] = surf
+    Weq, res = oracle.Oracle(m_eq).equilibrate(5000)
+    m = _model(dt=0.02, **kw)
+    m["U"] = surf
+    O = oracle.Oracle(m)
+    H = np.array([[0.0, V], [V, E]])
+    return m, O, Weq, res, H
+
+
+def test_identical_surfaces_linear_response(identical_surface_case):
+    m, O, Weq, res, H = identical_surface_case
+    assert res < 1e-10
+    n = 150
+    R1 = O.linear_response(Weq, n)
+    mu = m["mu"]
+    P = _rk4_poly(_electronic_liouvillian(H), m["dt"])
+    s0 = np.zeros(4, complex)
+    s0[0] = 1.0
+    x = _dip(mu, oracle.COMMUTATOR) @ s0
+    trW = Weq[0, 0, 0].sum() * O.dq * O.dp
+    ref = []
+    for _ in range(n + 1):
+        ref.append(1j * (mu.T.reshape(-1) @ x) * trW)
+        x = P @ x
+    assert _relerr(R1, np.array(ref)) < 1e-10
+
+
+def test_identical_surfaces_third_order_response(identical_surface_case):
+    """Covers the t1-stride / t2-fork / t3 bookkeeping of the third-order protocol."""
+    m, O, Weq, res, H = identical_surface_case
+    n_t1, stride, t2s, n_t3 = 3, 4, [0, 5, 9], 12
+    R3 = O.third_order_response(Weq, n_t1, stride, t2s, n_t3)
+    P = _rk4_poly(_electronic_liouvillian(H), m["dt"])
+    D = _dip(m["mu"], oracle.COMMUTATOR)
+    mu_row = m["mu"].T.reshape(-1)
+    trW = Weq[0, 0, 0].sum() * O.dq * O.dp
+    s0 = np.zeros(4, complex)
+    s0[0] = 1
+    Pn = lambda k: np.linalg.matrix_power(P, k)
+    ref = np.zeros_like(R3)
+    for b, t2 in enumerate(t2s):
+        for a in range(n_t1):
+            x = D @ Pn(t2) @ D @ Pn(a * stride) @ D @ s0
+            for c in range(n_t3 + 1):
+                ref[b, a, c] = (1j) ** 3 * (mu_row @ Pn(c) @ x) * trW
+    assert _relerr(R3, ref) < 1e-10
+
+
+# ------------------------------------------------------------------------------------------------
+# P6: harmonic single-state equilibrium (classical Boltzmann variances at high temperature)
+# ------------------------------------------------------------------------------------------------
+@pytest.mark.slow
+def test_harmonic_equilibrium_variances():
+    beta = 0.48
+    m = qi.single_state(lambda q: 0.5 * q * q, nq=48, n_p=48, qr=(-10.0, 10.0), pr=(-10.0, 10.0),
+                        beta=beta, eta=1.0, gamma=2.0, depth=4, closure=1, dt=0.02)
+    O = oracle.Oracle(m)
+    Weq, res = O.equilibrate(2500)
+    q = qi.axis(m["nq"], m["q_min"], m["q_max"])
+    p = qi.axis(m["np"], m["p_min"], m["p_max"])
+    W = Weq[0, 0, 0].real
+    Z = W.sum()
+    q2 = (W * q[:, None] ** 2).sum() / Z
+    p2 = (W * p[None, :] ** 2).sum() / Z
+    assert q2 == pytest.approx(1 / beta, rel=2e-3)
+    assert p2 == pytest.approx(1 / beta, rel=2e-3)
+
+
+# ------------------------------------------------------------------------------------------------
+# P8: independent method -- density-matrix HEOM in a truncated harmonic-oscillator basis
+# ------------------------------------------------------------------------------------------------
+class _HOBasisHEOM:
+    """The same hierarchy (Eq. (heom), linear coupling, Eq. (GMFP) terminator) written for density
+    matrices: Phi rho = i[q, rho], Lambda rho = -(1/2){p, rho}, with q, p in an n_v-level
+    oscillator basis (omega = 1) tensored with the electronic states."""
+
+    def __init__(self, S, n_v, d, E, V, co, depth, mu):
+        a = np.diag(np.sqrt(np.arange(1, n_v)), 1)
+        q = (a + a.T) / math.sqrt(2)
+        p = 1j * (a.T - a) / math.sqrt(2)
+        num = np.diag(np.arange(n_v) + 0.5)
+        Iv, Ie = np.eye(n_v), np.eye(S)
+        H = np.zeros((S * n_v, S * n_v), complex)
+        for j in range(S):
+            blk = num - d[j] * q + (0.5 * d[j] ** 2 + E[j]) * Iv
+            H[j * n_v:(j + 1) * n_v, j * n_v:(j + 1) * n_v] = blk
+            for k in range(S):
+                if k != j:
+                    H[j * n_v:(j + 1) * n_v, k * n_v:(k + 1) * n_v] = V[j][k] * Iv
+        self.H = H
+        self.Q = np.kron(Ie, q)
+        self.P = np.kron(Ie, p)
+        self.mu = np.kron(mu, Iv)
+        self.co = co
+        self.depth = depth
+        self.S, self.n_v = S, n_v
+
+    def rhs(self, R):
+        g, r, c = self.co["gamma"][0], self.co["r"][0], self.co["c"][0]
+        H, Q, P = self.H, self.Q, self.P
+        phi = lambda X: 1j * (Q @ X - X @ Q)
+        lam = lambda X: -0.5 * (P @ X + X @ P)
+        out = []
+        N = self.depth
+        for n in range(N + 1):
+            X = R[n]
+            d = -1j * (H @ X - X @ H) - n * g * X
+            if n < N:
+                d = d - phi(R[n + 1])
+            else:
+                d = d + phi(r * lam(X) + c * phi(X))
+            if n > 0:
+                d = d - n * g * (r * lam(R[n - 1]) + c * phi(R[n - 1]))
+            out.append(d)
+        return np.array(out)
+
+    def rk4(self, R, dt, n):
+        for _ in range(n):
+            k1 = self.rhs(R)
+            k2 = self.rhs(R + 0.5 * dt * k1)
+            k3 = self.rhs(R + 0.5 * dt * k2)
+            k4 = self.rhs(R + dt * k3)
+            R = R + dt / 6 * (k1 + 2 * k2 + 2 * k3 + k4)
+        return R
+
+
+@pytest.mark.slow
+def test_linear_response_against_vibrational_basis_heom():
+    beta, eta, gamma, depth = 1.0, 0.3, 1.0, 3
+    d, E, V = [0.0, 1.0], [0.0, 2.0], [[0, 0.3], [0.3, 0]]
+    m = _model(nq=48, n_p=48, qr=(-8.0, 8.0), pr=(-8.0, 8.0), displacement=d[1], gap=E[1], coupling=0.3,
+               eta=eta, gamma=gamma, beta=beta, depth=depth, dt=0.01)
+    O = oracle.Oracle(m)
+    co = O.coefficients()
+    Weq, res = O.equilibrate(4000)
+    n_t = 400
+    R1_w = O.linear_response(Weq, n_t)
+
+    n_v = 36
+    mu = m["mu"]
+    B1 = _HOBasisHEOM(1, n_v, [0.0], [0.0], [[0]], co, depth, np.array([[1.0]]))
+    rho0 = np.zeros((depth + 1, n_v, n_v), complex)
+    Hg = B1.H
+    w, U = np.linalg.eigh(Hg)
+    th = U @ np.diag(np.exp(-beta * w)) @ U.conj().T
+    rho0[0] = th / np.trace(th)
+    rho_eq = B1.rk4(rho0, 0.02, 2000)
+    B = _HOBasisHEOM(2, n_v, d, E, V, co, depth, mu)
+    R = np.zeros((depth + 1, 2 * n_v, 2 * n_v), complex)
+    R[:, :n_v, :n_v] = rho_eq
+    R = np.array([B.mu @ X - X @ B.mu for X in R])
+    R1_h = [1j * np.trace(B.mu @ R[0])]
+    for _ in range(n_t):
+        R = B.rk4(R, m["dt"], 1)
+        R1_h.append(1j * np.trace(B.mu @ R[0]))
+    R1_h = np.array(R1_h)
+    # both truncations (48x48 phase-space grid vs 36 vibrational levels) leave ~5e-4
+    assert _relerr(R1_w, R1_h) < 1e-3
+
+
+# ------------------------------------------------------------------------------------------------
+# P11: depth 0 with the terminator is the multi-state quantum Fokker-Planck equation, Eq. (heomW)
+# ------------------------------------------------------------------------------------------------
+def test_depth_zero_terminator_is_quantum_fokker_planck():
+    m = _model(depth=0)
+    O = oracle.Oracle(m)
+    W = qi.random_state(m)
+    zeta, beta = m["eta"], m["beta"]
+    p = qi.axis(m["np"], m["p_min"], m["p_max"])
+    dp = O.dp
+    # zeta d/dp (p W + (1/beta) dW/dp) with 4th-order central differences on the periodic p axis
+    d1 = np.array([1, -8, 0, 8, -1]) / (12 * dp)
+    d2 = np.array([-1, 16, -30, 16, -1]) / (12 * dp * dp)
+
+    def conv(x, c):
+        return sum(c[t] * np.roll(x, 2 - t, axis=-1) for t in range(5))
+
+    fp = zeta * conv(p * W, d1) + (zeta / beta) * conv(W, d2)
+    ref = O.rhs(W, oracle.KINETIC | oracle.POTENTIAL) + fp
+    assert _relerr(O.rhs(W), ref) < 1e-13
+
+
+# ------------------------------------------------------------------------------------------------
+# Bath coefficients against direct quadrature of Eqs. (bath-response), (bath-correlation)
+# ------------------------------------------------------------------------------------------------
+@pytest.mark.parametrize("beta,gamma", [(0.48, 1.0), (1.0, 2.0), (2.0, 1.0)])
+def test_bath_coefficients_reproduce_correlation_functions(beta, gamma):
+    from scipy.integrate import quad
+    eta, K = 0.7, 400
+    g = np.zeros(K + 1); r = np.zeros(K + 1); c = np.zeros(K + 1); cd = np.zeros(1)
+    import ctypes
+    dp = ctypes.POINTER(ctypes.c_double)
+    oracle.lib().oq_bath_coefficients(eta, gamma, beta, K, 0, 1, g.ctypes.data_as(dp), r.ctypes.data_as(dp),
+                                      c.ctypes.data_as(dp), cd.ctypes.data_as(dp))
+    J_over_w = lambda w: (eta / math.pi) * gamma ** 2 / (gamma ** 2 + w ** 2)
+    w_coth = lambda w: w / math.tanh(beta * w / 2) if w > 1e-12 else 2.0 / beta
+    for t in (0.3, 1.0, 2.5):
+        psi = 2 * quad(J_over_w, 0, np.inf, weight="cos", wvar=t)[0]
+        assert sum(r * g * np.exp(-g * t)) == pytest.approx(psi, rel=1e-8)
+        C = quad(lambda w: J_over_w(w) * w_coth(w), 0, np.inf, weight="cos", wvar=t, limlst=200)[0]
+        assert sum(c * g * np.exp(-g * t)) == pytest.approx(C, rel=1e-6, abs=1e-9)
+    # the delta-term carries the neglected Matsubara weight, which vanishes as K grows
+    assert abs(cd[0]) < 2 * eta * gamma ** 2 * beta / (4 * math.pi ** 2 * K)
+    # high-temperature limit of the zeroth coefficient (end of Sec. II)
+    oracle.lib().oq_bath_coefficients(eta, gamma, 1e-4, 0, 0, 0, g.ctypes.data_as(dp), r.ctypes.data_as(dp),
+                                      c.ctypes.data_as(dp), cd.ctypes.data_as(dp))
+    assert c[0] == pytest.approx(eta / 1e-4, rel=1e-6)
+
+
+def test_hierarchy_size_and_neighbours():
+    for K, N in [(0, 3), (2, 8), (2, 10), (3, 10)]:
+        n = oracle.lib().oq_hierarchy(K + 1, N, None)
+        assert n == math.comb(N + K + 1, K + 1)
+    m = qi.photoisomerization_two_state(nq=4, n_p=8, depth=4, n_matsubara=2)
+    O = oracle.Oracle(m)
+    h = O.hierarchy()
+    assert len({tuple(x) for x in h}) == len(h)
+    assert (h.sum(axis=1) <= 4).all() and (np.diff(h.sum(axis=1)) >= 0).all()
+
+
+# ------------------------------------------------------------------------------------------------
+# P9 / P10: spectra identities and pathway additivity
+# ------------------------------------------------------------------------------------------------
+def test_transient_absorption_two_definitions():
+    """w int dw1 I_corr(w, T, w1) over one w1 period equals 2 pi times Eq. (transient-absorption)."""
+    rng = np.random.default_rng(5)
+    n1, n3, dt1, dt3 = 9, 40, 0.08, 0.01
+    R3 = rng.normal(size=(n1, n3 + 1)) + 1j * rng.normal(size=(n1, n3 + 1))
+    om = np.linspace(-20, 20, 33)
+    a = oracle.transient_absorption_from_corr(R3, dt1, dt3, om, n_omega1=16)
+    b = oracle.transient_absorption(R3[0][None, :], dt3, om)[0]
+    assert _relerr(a, 2 * math.pi * b) < 1e-12
+
+
+def test_absorption_of_damped_oscillation():
+    """Trapezoid transform of R1 = 2 sin(Et) exp(-G t) against the closed-form Laplace transform."""
+    E, G, dt, n = 5.0, 0.5, 1e-3, 60000
+    t = np.arange(n + 1) * dt
+    R1 = 2 * np.sin(E * t) * np.exp(-G * t)
+    om = np.linspace(-10, 10, 41)
+    got = oracle.absorption(R1, dt, om)
+    ft = -1j * (1 / (G - 1j * (om + E)) - 1 / (G - 1j * (om - E)))
+    assert np.allclose(got, om * ft.imag, atol=2e-5)
+
+
+def test_pathway_split_is_additive():
+    m = _model(nq=16, n_p=16, depth=1)
+    O = oracle.Oracle(m)
+    Weq, _ = O.equilibrate(50)
+    args = (2, 3, [0, 4], 6)
+    full = O.third_order_response(Weq, *args, first=oracle.COMMUTATOR)
+    ket = O.third_order_response(Weq, *args, first=oracle.LEFT)
+    bra = O.third_order_response(Weq, *args, first=oracle.RIGHT)
+    assert _relerr(ket + bra, full) < 1e-13
+    assert np.abs(ket).max() > 1e-3 and np.abs(bra).max() > 1e-3
+
+
+# ------------------------------------------------------------------------------------------------
+# The paper's printed model parameters pin the reading of its Morse surfaces
+# ------------------------------------------------------------------------------------------------
+def test_morse_reading_reproduces_printed_resonances():
+    vals = {}
+    with open(os.path.join(GOLDEN, "morse_resonances.txt")) as f:
+        for line in f:
+            if line.strip() and not line.startswith("#"):
+                k, v = line.split()
+                vals[k] = float(v)
+    m = qi.morse_photoisomerization()
+    q0, q1 = m["q_minima"]
+    U00, U11 = m["U"][0][0], m["U"][1][1]
+    scale = vals["omega0"]
+    nu0 = (U11(q0) - U00(q0)) * scale
+    nu1 = (U00(q1) - U11(q1)) * scale
+    assert nu0 == pytest.approx(vals["nu0"], rel=1e-3)
+    assert nu1 == pytest.approx(vals["nu1"], rel=1e-3)
