@@ -1,0 +1,270 @@
+"""Benchmark of the multi-state QHFPE hot path on GB300.
+
+Workload: the two-state photoisomerization model (quartic double-well ground state, displaced
+anharmonic excited state, constant diabatic coupling 0.5) on a 96 x 128 (q x p) grid, Drude bath
+eta = 1, gamma = 1, beta = 1 with two Matsubara terms and the delta-term, hierarchy depth 8 (165
+elements x 4 electronic pairs = 8.11 M phase-space cells).  One step = one RK4 step of every cell of
+the whole hierarchy (four right-hand-side stages: upwind kinetic stencil, FFT potential kernel with
+diabatic mixing, bath and tier couplings, Horner update) plus the FP64 trace Tr{mu W^(0)} that the
+response functions record.  Metric: phase-space cell-updates per second.
+
+Prints one JSON line.  `--impl reference` times the FP64 CPU oracle instead (bounded sample).
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "phase-space cell-updates/s"
+L2_BYTES = 129 * 2 ** 20
+
+
+def _env_int(k, d):
+    try:
+        return int(os.environ.get(k, d))
+    except ValueError:
+        return d
+
+
+def workload():
+    import qhfpe_inputs as qi
+    m = qi.photoisomerization_two_state()
+    return m, qi.u_table(m)
+
+
+def cells_of(m, n_elem):
+    return n_elem * m["S"] * m["S"] * m["nq"] * m["np"]
+
+
+class Clocks:
+    """Samples SM clocks and throttle reasons with nvidia-smi during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 9:
+                self.rows.append(parts)
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.t.join(timeout=2)
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in self.rows for k in range(4) if r[5 + k].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows)}
+
+
+def cpu_baseline(m, T, seconds=15.0):
+    """The FP64 oracle as it stands, on this host's cores, over a bounded number of RK4 steps of the
+    same workload (full hierarchy, full grid)."""
+    import oracle
+    import qhfpe_inputs as qi
+    O = oracle.Oracle(m, T)
+    W = qi.random_state(m, seed=1706)
+    n = 0
+    t0 = time.perf_counter()
+    while True:
+        W, _ = O.step(W, 1)
+        n += 1
+        if time.perf_counter() - t0 > seconds or n >= 50:
+            break
+    dt = time.perf_counter() - t0
+    cells = cells_of(m, O.n_elem)
+    return {"value": cells * n / dt, "unit": METRIC, "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"{n} RK4 steps of the full 96x128 depth-8 hierarchy ({cells} cells), FP64, {dt:.1f} s"}
+
+
+def run_reference(args):
+    rank = _env_int("RANK", 0)
+    if rank != 0:
+        return 0
+    from oracle import build as ob
+    ob.build()
+    m, T = workload()
+    import oracle
+    import qhfpe_inputs as qi
+    O = oracle.Oracle(m, T)
+    W = qi.random_state(m, seed=1706)
+    for _ in range(args.warmup):
+        W, _ = O.step(W, 1)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        W, _ = O.step(W, 1)
+    dt = time.perf_counter() - t0
+    cells = cells_of(m, O.n_elem)
+    val = cells * args.steps / dt
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "cell-updates/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "photoiso_96x128_d8_K2 (2 states, 165 elements, 8.11M cells)"},
+            "cpu_baseline": {"value": val, "unit": "cell-updates/s", "cores": oracle.num_threads(), "kind": "oracle",
+                             "sample": f"{args.steps} timed RK4 steps after {args.warmup} warm-up, full workload"},
+            "e2e": {"value": val, "unit": "cell-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=40)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--precision", default="mixed", choices=["fp64", "mixed"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import numpy as np
+    import torch
+
+    world = _env_int("WORLD_SIZE", 1)
+    rank = _env_int("RANK", 0)
+    local = _env_int("LOCAL_RANK", 0)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    from paper_1706_09590_gb300 import Propagator
+    import qhfpe_inputs as qi
+
+    m, T = workload()
+    stream = torch.cuda.Stream()
+    P = Propagator(m, T, precision=args.precision, stream=stream)
+    cells = cells_of(m, P.n_elem)
+    W0 = qi.random_state(m, seed=1706 + rank)
+    W0 *= 1e-3  # keep values O(1e-3) so that repeated benchmark steps stay finite
+    P.set_state(W0)
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    # ---- device-resident throughput --------------------------------------------------------------
+    for _ in range(max(args.warmup, 3)):
+        P.step(1, record_trace=True)
+    barrier()
+    P.kernel_timing(True)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with Clocks(local) as clk:
+        barrier()
+        with torch.cuda.stream(stream):
+            ev0.record(stream)
+        tr = P.step(args.steps, record_trace=True)
+        with torch.cuda.stream(stream):
+            ev1.record(stream)
+        barrier()
+    ms = ev0.elapsed_time(ev1)
+    kt = P.kernel_timing_read()
+    P.kernel_timing(False)
+    if dist is not None:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    assert np.all(np.isfinite(tr)), "non-finite trace"
+    value = cells * args.steps * world / (ms / 1e3)
+
+    # ---- end to end through the C ABI with host buffers --------------------------------------------
+    n_e2e = max(2, min(args.steps, 10))
+    host_in = torch.from_numpy(W0.view(np.float64)).pin_memory()
+    host_out = torch.empty_like(host_in).pin_memory()
+    state_bytes = host_in.numel() * 8
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(n_e2e):
+        P.set_state(host_in.numpy().view(np.complex128).reshape(P.shape))
+        trr = P.step(1, record_trace=True)
+        P.get_state(0, out=None)
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    e2e = cells * n_e2e * world / e2e_s
+    del host_out
+
+    # ---- roofline of the dominant kernel ------------------------------------------------------------
+    import json as _j
+    peaks = {}
+    try:
+        peaks = _j.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        pass
+    hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    n_stage, ms_stage = kt["stage"]
+    n_pot, ms_pot = kt["potential"]
+    esize = 4 if args.precision == "mixed" else 8
+    # algorithmic bytes of one right-hand-side stage: the 11 state passes of a Horner RK4 step
+    # (complex values) spread over its 4 stages
+    alg_bytes_stage = 11 * 2 * esize * cells / 4
+    dom_ms = ms_stage / max(n_stage, 1)
+    pot_ms = ms_pot / max(n_pot, 1)
+    roof = {"bound": "hbm", "kernel": "stage_kernel (stencil + bath + tier couplings + Horner update)",
+            "achieved": alg_bytes_stage / (dom_ms / 1e3) / 1e9, "peak": hbm_peak, "unit": "GB/s",
+            "frac": alg_bytes_stage / (dom_ms / 1e3) / 1e9 / hbm_peak, "traffic": None,
+            "peak_source": "MEASURED_PEAKS.json hbm_gbs (burst copy)" if peaks else "fallback 6800 GB/s",
+            "stage_ms_per_launch": dom_ms, "potential_ms_per_launch": pot_ms,
+            "share_stage": ms_stage / max(ms_stage + ms_pot + kt["aux"][1], 1e-9),
+            "share_potential": ms_pot / max(ms_stage + ms_pot + kt["aux"][1], 1e-9)}
+
+    line = {"metric": METRIC, "value": value, "unit": "cell-updates/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32" if args.precision == "mixed" else "f64", "data": "synthetic",
+            "config": {"workload": "photoiso_96x128_d8_K2 (2 states, depth 8, 3 modes, 165 elements, "
+                                   f"{cells} cells per GPU)", "precision": args.precision,
+                       "l2": f"working set {4 * cells * 2 * esize / 1e6:.0f} MB per step > 129 MB L2 (no flush)",
+                       "parallelism": f"replicas x{world}"},
+            "e2e": {"value": e2e, "unit": "cell-updates/s", "h2d_bytes_per_step": state_bytes,
+                    "d2h_bytes_per_step": state_bytes + 16 * 2},
+            "gpu_launches": int(n_stage + n_pot + 2 * args.steps + 2),
+            "roofline": roof, "clocks": clk.summary()}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(m, T)
+    if rank == 0:
+        print(json.dumps(line))
+    P.close()
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,202 @@
+/*
+ * qhfpe.h -- C ABI of the GB300 (sm_103a) library for the multi-state quantum hierarchical
+ * Fokker-Planck equation (MS-QHFPE) of Ikeda & Tanimura, J. Chem. Phys. 2017 (arXiv:1706.09590).
+ *
+ * The library time-steps the hierarchy of electronic-state-resolved Wigner distributions
+ * W^(n)_jk(q, p) of Eq. (heom) on a phase-space grid, applies the dipole super-operators of Sec. III
+ * and returns the response functions of Eqs. (R1), (R3) and the spectra built from them.
+ *
+ * Units: hbar = m = omega_0 = 1 (the dimensionless q, p of Sec. III).
+ *
+ * Conventions shared by every call:
+ *   - Grid: x_i = x_min + i*dx with dx = (x_max - x_min)/n, i = 0..n-1 (end point excluded), for both
+ *     q (nq points) and p (np points, np a power of two, 8 <= np <= 512).
+ *   - Hierarchy: the index set {n in N^(K+1) : |n| <= depth} of Eq. (heom) with K = n_matsubara,
+ *     ordered by tier |n| ascending and, inside a tier, lexicographically with n_0 largest first.
+ *     qhfpe_hierarchy() returns the list.
+ *   - State layout at the ABI ("canonical"): complex128 (re, im interleaved) array
+ *     [n_elem][S][S][nq][np], element index, ket state j, bra state k, q row, p column.  One such
+ *     array per replica; replica r of a batch starts at r * state_elems(h) complex numbers.
+ *   - Potential tables: U_table[j][k][i][t] = U_jk(q_i + s_t) with s_t = (t - np/2) * pi / (np*dp),
+ *     t = 0..np (np+1 samples per q row): the surfaces at q +/- r/2 on the grid r conjugate to p,
+ *     Eq. (quantum-liouvillian).  Real, symmetric in (j, k).  The caller chooses how U continues
+ *     beyond the q box (the kernel samples up to pi/(2 dp) outside it).
+ *   - Time: one step is one RK4 step of size dt (classic RK4 = the degree-4 Taylor polynomial of the
+ *     propagator for this linear equation, the 4th-order integrator of Sec. III at fixed step).
+ *
+ * Ownership and streams: the library owns every device buffer it allocates (released by
+ * qhfpe_destroy).  Host arrays passed in are copied before the call returns.  Device pointers passed in
+ * are read/written in stream order on the handle's stream and are not retained.  Host outputs are
+ * complete when the call returns.
+ *
+ * Errors: every call returns a qhfpe_status; no exception or abort crosses the ABI.  After a CUDA
+ * failure or a device-side timeout the handle turns sticky: every later call returns QHFPE_ESTATE
+ * until qhfpe_destroy.  qhfpe_last_error() gives a one-line description of the last failure.
+ */
+#ifndef QHFPE_H
+#define QHFPE_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    QHFPE_OK = 0,
+    QHFPE_EINVAL = 1,       /* invalid argument (message in qhfpe_last_error) */
+    QHFPE_ENOMEM = 2,       /* device or host allocation failed */
+    QHFPE_ECUDA = 3,        /* CUDA runtime error */
+    QHFPE_ENUMERIC = 4,     /* NaN or Inf found where finite values are required */
+    QHFPE_ETIMEOUT = 5,     /* a device-side wait gave up (reported, never hung) */
+    QHFPE_EUNSUPPORTED = 6, /* valid request this build does not implement */
+    QHFPE_ESTATE = 7        /* handle unusable after an earlier device failure */
+} qhfpe_status;
+
+/* Arithmetic of the propagation. */
+typedef enum {
+    /* Everything in FP64; potential kernel by shared-memory FFT.  Reference form. */
+    QHFPE_FP64 = 0,
+    /* State and right-hand side in FP32 (FFT potential kernel in FP32); the zeroth tier's state and
+     * its RK4 accumulation kept in FP64; traces and response sums in FP64. */
+    QHFPE_MIXED = 1,
+    /* As QHFPE_MIXED, but the potential kernel is a DFT-as-GEMM on the tcgen05 tensor cores with
+     * split bf16 (hi + lo, three products) operands and FP32 accumulation. */
+    QHFPE_MIXED_BF16X3 = 2
+} qhfpe_precision;
+
+typedef enum {
+    QHFPE_TRUNCATE = 0,   /* W^(n + e_k) = 0 beyond the deepest tier */
+    QHFPE_TERMINATOR = 1, /* Eq. (GMFP) at the deepest tier; requires n_matsubara = 0 */
+    QHFPE_LEARNED = 2     /* learned closure (see qhfpe_closure_load) */
+} qhfpe_closure;
+
+typedef enum {
+    QHFPE_LEFT = 1,       /* mu^-> W = mu W  (ket side)   */
+    QHFPE_RIGHT = 2,      /* mu^<- W = W mu  (bra side)   */
+    QHFPE_COMMUTATOR = 3  /* mu^x W = mu W - W mu          */
+} qhfpe_side;
+
+/* Right-hand-side term mask for qhfpe_apply_rhs (test and diagnostics entry point). */
+enum {
+    QHFPE_TERM_KINETIC = 1,   /* -p dW/dq, 5th-order upwind (Sec. III)                              */
+    QHFPE_TERM_POTENTIAL = 2, /* -i [U, W] in Wigner space, Eq. (quantum-liouvillian)                */
+    QHFPE_TERM_DAMPING = 4,   /* -(sum_k n_k gamma_k) W + c_delta d2W/dp2, Eq. (heom)                */
+    QHFPE_TERM_TIER_UP = 8,   /* sum_k dW^(n+e_k)/dp, or the Eq. (GMFP) terminator                   */
+    QHFPE_TERM_TIER_DOWN = 16,/* sum_k n_k gamma_k (r_k p + c_k d/dp) W^(n-e_k), Eq. (heom)          */
+    QHFPE_TERM_ALL = 31
+};
+
+typedef struct {
+    int n_states;            /* S >= 1 (at most 4) */
+    int nq, np;              /* nq >= 1; np a power of two in [8, 512] */
+    double q_min, q_max, p_min, p_max;
+    const double *U_table;   /* host, [S][S][nq][np+1] (see conventions); copied */
+    const double *mu;        /* host, [S][S] Condon dipole matrix, real symmetric; copied */
+    double eta, gamma, beta; /* Drude coupling zeta (Eq. (Drude-J)), cutoff gamma, inverse temperature */
+    int n_matsubara;         /* K: modes k = 0..K (K <= 7) */
+    int high_temperature;    /* 1: c_0 = eta/beta, no Matsubara terms, no delta-term (end of Sec. II) */
+    int use_cdelta;          /* 1: keep the delta-term c_delta d2/dp2 (low-temperature remainder) */
+    int depth;               /* N >= 0 */
+    int closure;             /* qhfpe_closure */
+    int periodic_q;          /* 0: open q boundary (zero ghost cells); 1: periodic q */
+    int precision;           /* qhfpe_precision */
+    double dt;               /* RK4 step > 0 */
+    int n_replicas;          /* independent propagations held by the handle, >= 1 */
+} qhfpe_params;
+
+typedef struct qhfpe qhfpe_t;
+
+/* Validates params, derives the bath coefficients (Eqs. (expansion-of-bath-*) for the Drude J) and
+ * the hierarchy, uploads the tables and allocates all device buffers.  All replicas start at zero.
+ * stream: a cudaStream_t or NULL for the legacy default stream.  Errors: EINVAL (bad parameter),
+ * ENOMEM, ECUDA, EUNSUPPORTED (e.g. a precision this GPU cannot run). */
+qhfpe_status qhfpe_create(const qhfpe_params *params, void *stream, qhfpe_t **out);
+qhfpe_status qhfpe_destroy(qhfpe_t *h);
+const char *qhfpe_last_error(const qhfpe_t *h);
+
+/* Sizes: number of hierarchy elements, modes (K+1) and complex numbers per replica state. */
+qhfpe_status qhfpe_sizes(const qhfpe_t *h, int *n_elem, int *n_modes, size_t *state_elems);
+/* idx_out: host int[n_elem][n_modes], the multi-indices in storage order. */
+qhfpe_status qhfpe_hierarchy(const qhfpe_t *h, int *idx_out);
+/* Bath coefficients as used (host arrays of n_modes doubles; cdelta one double). */
+qhfpe_status qhfpe_bath_coefficients(const qhfpe_t *h, double *gamma_k, double *r_k, double *c_k, double *cdelta);
+/* Upper bound of a stable dt from a Gershgorin-type estimate of the generator's spectral radius and
+ * RK4's stability interval on the imaginary axis (2.8). */
+qhfpe_status qhfpe_max_stable_dt(const qhfpe_t *h, double *dt_out);
+
+/* Copy a canonical-layout complex128 state into / out of replica `replica` (or every replica when
+ * replica = -1 for set_state: the same state is broadcast).  is_device: the pointer is device memory.
+ * In the mixed forms the state is rounded to FP32 except the zeroth tier, which stays FP64. */
+qhfpe_status qhfpe_set_state(qhfpe_t *h, int replica, const double *src, int is_device);
+qhfpe_status qhfpe_get_state(qhfpe_t *h, int replica, double *dst, int is_device);
+/* Copy replica src onto each of dst[0..n-1] (host int array). */
+qhfpe_status qhfpe_fork(qhfpe_t *h, int src, const int *dst, int n);
+
+/* Advance every replica n_steps RK4 steps.  trace_out (host, may be NULL): complex128
+ * [n_replicas][n_steps + 1], Tr{mu W^(0)} = sum_jk mu_kj sum_il W^(0)_jk(q_i, p_l) dq dp before the
+ * first step and after each step (FP64 sums, Eqs. (R1), (R3)). */
+qhfpe_status qhfpe_step(qhfpe_t *h, long n_steps, double *trace_out);
+
+/* Dipole super-operator on every hierarchy element of the listed replicas (replicas = NULL: all),
+ * Sec. III (Condon: mu constant, so the p-convolution with mu(p, q) is a product). */
+qhfpe_status qhfpe_apply_dipole(qhfpe_t *h, int side, const int *replicas, int n);
+
+/* out (host complex128, canonical layout of one replica) = selected terms of the right-hand side of
+ * Eq. (heom) evaluated on replica `replica`, in the handle's arithmetic. */
+qhfpe_status qhfpe_apply_rhs(qhfpe_t *h, int replica, int terms, double *out);
+
+/* Tr{mu W^(0)} of every replica now: host complex128 [n_replicas]. */
+qhfpe_status qhfpe_trace(qhfpe_t *h, double *out);
+
+/* Equilibrium of Sec. III: the ground surface U_00 alone with the full hierarchy, started from the
+ * classical Boltzmann distribution exp(-beta (p^2/2 + U_00(q))) normalised to unit trace, propagated
+ * n_steps RK4 steps (FP64 always).  The result (ground block of every hierarchy element, all other
+ * blocks zero) is kept as the handle's equilibrium state and written to every replica.
+ * residual_out (may be NULL): ||L W|| / ||W|| of the final ground problem (2-norm, all elements). */
+qhfpe_status qhfpe_equilibrate(qhfpe_t *h, long n_steps, double *residual_out);
+/* Provide the equilibrium state directly (canonical layout, one replica). */
+qhfpe_status qhfpe_set_equilibrium(qhfpe_t *h, const double *src, int is_device);
+
+/* Response-function schedules (Eqs. (R1), (R3)); all delays are in steps of dt.
+ *   QHFPE_LINEAR:     R1(c dt), c = 0..n_t3.  R_out: complex128 [n_t3 + 1].
+ *   QHFPE_THIRD_ORDER: R3(c dt, t2[b] dt, a t1_stride dt), a < n_t1, b < n_t2, c <= n_t3.
+ *                     R_out: complex128 [n_paths][n_t2][n_t1][n_t3 + 1] with n_paths = 2 when
+ *                     split_pathways (first interaction mu^-> then -mu^<-; they add up to mu^x),
+ *                     else 1.  Transient absorption is n_t1 = 1.
+ * All propagations of one phase are packed as replicas of one batch and run by one captured CUDA
+ * graph per phase. */
+typedef enum { QHFPE_LINEAR = 0, QHFPE_THIRD_ORDER = 1 } qhfpe_response_kind;
+typedef struct {
+    int kind;
+    int n_t1, t1_stride;
+    int n_t2;
+    const int *t2_steps;    /* host, ascending, n_t2 entries */
+    int n_t3;
+    int split_pathways;
+} qhfpe_schedule;
+qhfpe_status qhfpe_response(qhfpe_t *h, const qhfpe_schedule *sched, double *R_out);
+
+/* Spectra by trapezoid Fourier-Laplace sums in FP64 on the device (host arrays in and out).
+ * Absorption, Eq. (I1):  out[w] = omega_w Im sum_c w_c dt e^{i omega_w c dt} R1[c].
+ * Two-dimensional, Eqs. (nonreph), (reph): R3 [n_t1][n_t3 + 1] for one waiting time;
+ *   nr[w3][w1] = Im sum_a sum_c w_a w_c dt1 dt3 e^{i omega3 t3} e^{+i omega1 t1} R3,
+ *   re[w3][w1] = same with e^{-i omega1 t1}; the correlation spectrum, Eq. (I3), is nr + re. */
+qhfpe_status qhfpe_spectrum_absorption(qhfpe_t *h, const double *R1, long n_t, double dt,
+                                       const double *omega, int n_omega, double *out);
+qhfpe_status qhfpe_spectrum_2d(qhfpe_t *h, const double *R3, int n_t1, int n_t3, double dt1, double dt3,
+                               const double *omega1, int n_omega1, const double *omega3, int n_omega3,
+                               double *nr, double *re);
+
+/* Kernel timing for measurement: when enabled, every launch of the right-hand-side stage kernels
+ * (and the separate potential kernel, if the form has one) is bracketed by CUDA events on the
+ * handle's stream.  read returns the launch count and total device milliseconds per kernel kind
+ * (index 0: stage kernel, 1: potential kernel, 2: trace/auxiliary) and resets the counters. */
+qhfpe_status qhfpe_kernel_timing(qhfpe_t *h, int enable);
+qhfpe_status qhfpe_kernel_timing_read(qhfpe_t *h, long *launches, double *total_ms, int n_kinds);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* QHFPE_H */

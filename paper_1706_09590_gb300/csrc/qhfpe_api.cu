@@ -1,0 +1,1146 @@
+// C ABI of the QHFPE library (include/qhfpe.h): validation, set-up of the model (bath coefficients,
+// hierarchy, potential tables), device buffers, the RK4 step loop with captured CUDA graphs, the
+// equilibration and response protocols of Sec. III, and spectra.
+#include "../../include/qhfpe.h"
+#include "qhfpe_internal.cuh"
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <new>
+#include <string>
+#include <vector>
+
+namespace {
+
+thread_local std::string g_create_error;  // message of the last failed qhfpe_create on this thread
+
+constexpr double kPi = 3.14159265358979323846;
+constexpr int kGraphChunk = 16;
+
+// ------------------------------------------------------------------------------------------------
+// Bath coefficients for the Drude spectral density (Eqs. (Drude-J), (bath-response),
+// (bath-correlation), (expansion-of-bath-*)).  Psi_B(t) = zeta gamma e^{-gamma t} gives
+// gamma_0 = gamma, r_0 = zeta; the poles of coth(beta w/2) J(w) give the correlation terms:
+//   c_0 = (zeta gamma / 2) cot(beta gamma / 2),
+//   gamma_k = 2 pi k / beta,  c_k = 2 zeta gamma^2 / (beta (gamma_k^2 - gamma^2)),  r_k = 0,
+//   c_delta = zeta/beta - c_0 - sum_{k<=K} c_k   (the Matsubara tail folded into a delta function).
+// High temperature (end of Sec. II): c_0 = zeta / beta and nothing else.
+// ------------------------------------------------------------------------------------------------
+struct Bath {
+    std::vector<double> gamma, r, c;
+    double cdelta = 0.0;
+};
+
+Bath drude_coefficients(double eta, double gamma, double beta, int K, bool high_t, bool use_cdelta)
+{
+    Bath b;
+    b.gamma.assign(K + 1, 0.0);
+    b.r.assign(K + 1, 0.0);
+    b.c.assign(K + 1, 0.0);
+    b.gamma[0] = gamma;
+    b.r[0] = eta;
+    if (high_t) {
+        b.c[0] = eta / beta;
+        return b;
+    }
+    b.c[0] = eta * gamma / (2.0 * std::tan(beta * gamma / 2.0));
+    double tail = eta / beta - b.c[0];
+    for (int k = 1; k <= K; ++k) {
+        const double nu = 2.0 * kPi * k / beta;
+        b.gamma[k] = nu;
+        b.c[k] = 2.0 * eta * gamma * gamma / (beta * (nu * nu - gamma * gamma));
+        tail -= b.c[k];
+    }
+    if (use_cdelta) b.cdelta = tail;
+    return b;
+}
+
+// Hierarchy {n : |n| <= N} ordered by tier, then lexicographically with n_0 largest first.
+std::vector<std::vector<int>> build_hierarchy(int modes, int depth)
+{
+    std::vector<std::vector<int>> all;
+    std::vector<int> cur(modes, 0);
+    // odometer over the box [0, depth]^modes, keeping |n| <= depth
+    while (true) {
+        int s = 0;
+        for (int v : cur) s += v;
+        if (s <= depth) all.push_back(cur);
+        int a = modes - 1;
+        while (a >= 0 && cur[a] == depth) cur[a--] = 0;
+        if (a < 0) break;
+        cur[a] += 1;
+    }
+    std::stable_sort(all.begin(), all.end(), [](const std::vector<int> &x, const std::vector<int> &y) {
+        int sx = 0, sy = 0;
+        for (int v : x) sx += v;
+        for (int v : y) sy += v;
+        if (sx != sy) return sx < sy;
+        return x > y;  // lexicographic, n_0 largest first
+    });
+    return all;
+}
+
+unsigned bitrev(unsigned x, int bits)
+{
+    unsigned r = 0;
+    for (int b = 0; b < bits; ++b) r |= ((x >> b) & 1u) << (bits - 1 - b);
+    return r;
+}
+
+struct DevBuf {
+    void *p = nullptr;
+    ~DevBuf() { if (p) cudaFree(p); }
+};
+
+}  // namespace
+
+// A model: grid, bath and hierarchy data and the potential tables for one set of surfaces.
+struct Model {
+    int S = 0, nq = 0, np = 0, log2np = 0, n_modes = 0, n_elem = 0, depth = 0, closure = 0;
+    GridInfo g{};
+    Bath bath;
+    std::vector<std::vector<int>> hier;
+    std::vector<ElemInfo> elems_host;
+    std::vector<double> mu_host;
+    ElemInfo *elems = nullptr;
+    double *mu = nullptr;
+    double *tab64 = nullptr;   // D | L | R | twiddles, FP64
+    float *tab32 = nullptr;    // same in FP32
+    size_t tab_n = 0;          // entries of one of D, L, R
+    double max_rate = 0.0;     // Gershgorin estimate of the generator's spectral radius
+
+    PotTables<double> t64() const
+    {
+        return {tab64, tab64 + tab_n, tab64 + 2 * tab_n, tab64 + 3 * tab_n};
+    }
+    PotTables<float> t32() const
+    {
+        return {tab32, tab32 + tab_n, tab32 + 2 * tab_n, tab32 + 3 * tab_n};
+    }
+    ~Model()
+    {
+        if (elems) cudaFree(elems);
+        if (mu) cudaFree(mu);
+        if (tab64) cudaFree(tab64);
+        if (tab32) cudaFree(tab32);
+    }
+};
+
+struct Timing {
+    bool enabled = false;
+    std::vector<cudaEvent_t> pool;
+    size_t used = 0;
+    std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> pending;
+    long launches[QH_KINDS] = {0, 0, 0};
+    double ms[QH_KINDS] = {0, 0, 0};
+    ~Timing()
+    {
+        for (auto e : pool) cudaEventDestroy(e);
+    }
+};
+
+// One propagator: a batch of replicas of one model in one arithmetic.
+struct Prop {
+    Model *m = nullptr;
+    GridInfo g{};
+    bool mixed = false;
+    double dt = 0.0;
+    void *y = nullptr, *vA = nullptr, *vB = nullptr, *P = nullptr;
+    double *y0 = nullptr;
+    TraceSink *sink = nullptr;
+    double *trace_buf = nullptr;
+    size_t trace_cap = 0;
+    cudaGraphExec_t graphs[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};  // [chunk][trace]
+
+    ~Prop()
+    {
+        for (auto &a : graphs)
+            for (auto &x : a)
+                if (x) cudaGraphExecDestroy(x);
+        for (void *b : {y, vA, vB, P, (void *)y0, (void *)sink, (void *)trace_buf})
+            if (b) cudaFree(b);
+    }
+};
+
+struct qhfpe {
+    qhfpe_params p{};
+    std::vector<double> U, mu;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    std::string err;
+    bool sticky = false;
+    std::unique_ptr<Model> model, ground;
+    std::unique_ptr<Prop> main;
+    std::map<int, std::unique_ptr<Prop>> batches;  // response phases, keyed by replica count
+    double *eq = nullptr;   // canonical FP64 equilibrium of one replica
+    bool have_eq = false;
+    double *scratch = nullptr;
+    size_t scratch_cap = 0;
+    Timing timing;
+
+    ~qhfpe()
+    {
+        batches.clear();
+        main.reset();
+        if (eq) cudaFree(eq);
+        if (scratch) cudaFree(scratch);
+        model.reset();
+        ground.reset();
+        if (own_stream && stream) cudaStreamDestroy(stream);
+    }
+
+    qhfpe_status fail(qhfpe_status s, const std::string &msg)
+    {
+        err = msg;
+        return s;
+    }
+    qhfpe_status cuda_fail(cudaError_t e, const char *what)
+    {
+        err = std::string("CUDA error in ") + what + ": " + cudaGetErrorString(e);
+        sticky = true;
+        return QHFPE_ECUDA;
+    }
+};
+
+#define QH_CK(h, call)                                              \
+    do {                                                            \
+        cudaError_t e_ = (call);                                    \
+        if (e_ != cudaSuccess) return (h)->cuda_fail(e_, #call);    \
+    } while (0)
+
+namespace {
+
+template <typename T>
+cudaError_t dalloc(T **p, size_t n)
+{
+    return cudaMalloc((void **)p, n * sizeof(T) + 16);
+}
+
+// Potential tables (Eq. (quantum-liouvillian) in r-space) for FFT output order, pre-scaled by 1/np.
+void build_tables(const Model &M, const double *U, std::vector<double> &out)
+{
+    const int S = M.S, nq = M.nq, N = M.np;
+    const size_t n = (size_t)S * S * nq * N;
+    out.assign(3 * n + N, 0.0);
+    auto T = [&](int j, int k, int i, int t) { return U[(((size_t)j * S + k) * nq + i) * (N + 1) + t]; };
+    auto UL = [&](int j, int s, int i, int m) {
+        return m == -N / 2 ? 0.5 * (T(j, s, i, 0) + T(j, s, i, N)) : T(j, s, i, m + N / 2);
+    };
+    auto UR = [&](int s, int k, int i, int m) {
+        return m == -N / 2 ? 0.5 * (T(s, k, i, 0) + T(s, k, i, N)) : T(s, k, i, N / 2 - m);
+    };
+    for (int j = 0; j < S; ++j)
+        for (int k = 0; k < S; ++k)
+            for (int i = 0; i < nq; ++i)
+                for (int pos = 0; pos < N; ++pos) {
+                    const int kk = (int)bitrev((unsigned)pos, M.log2np);
+                    const int m = kk < N / 2 ? kk : kk - N;
+                    const size_t o = (((size_t)j * S + k) * nq + i) * N + pos;
+                    out[o] = (UL(j, j, i, m) - UR(k, k, i, m)) / N;
+                    out[n + o] = UL(j, k, i, m) / N;
+                    out[2 * n + o] = UR(j, k, i, m) / N;
+                }
+    for (int t = 0; t < N / 2; ++t) {
+        out[3 * n + 2 * t] = std::cos(2.0 * kPi * t / N);
+        out[3 * n + 2 * t + 1] = std::sin(2.0 * kPi * t / N);
+    }
+}
+
+qhfpe_status build_model(qhfpe *h, Model &M, int S, const double *U, const double *mu)
+{
+    const qhfpe_params &p = h->p;
+    M.S = S;
+    M.nq = p.nq;
+    M.np = p.np;
+    M.log2np = 0;
+    while ((1 << M.log2np) < p.np) ++M.log2np;
+    M.n_modes = p.n_matsubara + 1;
+    M.depth = p.depth;
+    M.closure = p.closure;
+    M.bath = drude_coefficients(p.eta, p.gamma, p.beta, p.n_matsubara, p.high_temperature != 0, p.use_cdelta != 0);
+    M.hier = build_hierarchy(M.n_modes, p.depth);
+    M.n_elem = (int)M.hier.size();
+    std::map<std::vector<int>, int> index;
+    for (int e = 0; e < M.n_elem; ++e) index[M.hier[e]] = e;
+    M.elems_host.assign(M.n_elem, ElemInfo{});
+    for (int e = 0; e < M.n_elem; ++e) {
+        ElemInfo &E = M.elems_host[e];
+        const std::vector<int> &n = M.hier[e];
+        int tier = 0;
+        double ngam = 0.0;
+        for (int k = 0; k < M.n_modes; ++k) {
+            tier += n[k];
+            ngam += n[k] * M.bath.gamma[k];
+        }
+        E.ngam = ngam;
+        E.tier = tier;
+        E.terminator = (p.closure == QHFPE_TERMINATOR && tier == p.depth) ? 1 : 0;
+        for (int k = 0; k < M.n_modes; ++k) {
+            std::vector<int> v = n;
+            v[k] += 1;
+            auto it = index.find(v);
+            if (it != index.end()) E.up[E.n_up++] = it->second;
+            if (n[k] > 0) {
+                v[k] -= 2;
+                E.dn[E.n_dn] = index.at(v);
+                E.wr[E.n_dn] = n[k] * M.bath.gamma[k] * M.bath.r[k];
+                E.wc[E.n_dn] = n[k] * M.bath.gamma[k] * M.bath.c[k];
+                E.n_dn++;
+            }
+        }
+    }
+    GridInfo &g = M.g;
+    g.S = S;
+    g.nq = p.nq;
+    g.np = p.np;
+    g.log2np = M.log2np;
+    g.n_elem = M.n_elem;
+    g.n_rep = 0;
+    g.periodic_q = p.periodic_q;
+    g.q_min = p.q_min;
+    g.p_min = p.p_min;
+    g.dq = (p.q_max - p.q_min) / p.nq;
+    g.dp = (p.p_max - p.p_min) / p.np;
+    g.cdelta = M.bath.cdelta;
+    g.term_r0 = M.bath.r[0];
+    g.term_c0 = M.bath.c[0];
+    g.blk = (size_t)p.nq * p.np;
+    g.elem_stride = (size_t)S * S * 2 * g.blk;
+    g.rep_stride = (size_t)M.n_elem * g.elem_stride;
+    g.tier0_rep_stride = g.elem_stride;
+
+    M.mu_host.assign(mu, mu + S * S);
+    std::vector<double> tab;
+    build_tables(M, U, tab);
+    M.tab_n = (size_t)S * S * p.nq * p.np;
+
+    // Gershgorin-type bound of the spectral radius (for qhfpe_max_stable_dt)
+    double pmax = std::max(std::fabs(p.p_min), std::fabs(p.p_max));
+    double kin = 130.0 * pmax / (60.0 * g.dq);
+    double pot = 0.0;
+    const size_t n = M.tab_n;
+    for (int j = 0; j < S; ++j)
+        for (int k = 0; k < S; ++k)
+            for (int i = 0; i < p.nq; ++i)
+                for (int pos = 0; pos < p.np; ++pos) {
+                    const size_t row = (size_t)i * p.np + pos;
+                    double r = std::fabs(tab[((size_t)(j * S + k) * p.nq) * p.np + row]);
+                    for (int s = 0; s < S; ++s) {
+                        if (s != j) r += std::fabs(tab[n + ((size_t)(j * S + s) * p.nq) * p.np + row]);
+                        if (s != k) r += std::fabs(tab[2 * n + ((size_t)(s * S + k) * p.nq) * p.np + row]);
+                    }
+                    pot = std::max(pot, r * p.np);
+                }
+    double bathr = 0.0;
+    for (const ElemInfo &E : M.elems_host) {
+        double r = E.ngam + (std::fabs(g.cdelta) + (E.terminator ? g.term_c0 : 0.0)) * 64.0 / (12.0 * g.dp * g.dp);
+        r += E.n_up * 1.5 / g.dp + (E.terminator ? g.term_r0 * (pmax / g.dp * 1.5 + 1.0) : 0.0);
+        for (int a = 0; a < E.n_dn; ++a) r += std::fabs(E.wr[a]) * pmax + std::fabs(E.wc[a]) * 1.5 / g.dp;
+        bathr = std::max(bathr, r);
+    }
+    M.max_rate = kin + pot + bathr;
+
+    cudaStream_t st = h->stream;
+    QH_CK(h, prepare_potential((size_t)2 * S * S * 2 * p.np * sizeof(double)));
+    QH_CK(h, dalloc(&M.elems, M.n_elem));
+    QH_CK(h, cudaMemcpyAsync(M.elems, M.elems_host.data(), sizeof(ElemInfo) * M.n_elem, cudaMemcpyHostToDevice, st));
+    QH_CK(h, dalloc(&M.mu, S * S));
+    QH_CK(h, cudaMemcpyAsync(M.mu, M.mu_host.data(), sizeof(double) * S * S, cudaMemcpyHostToDevice, st));
+    QH_CK(h, dalloc(&M.tab64, tab.size()));
+    QH_CK(h, cudaMemcpyAsync(M.tab64, tab.data(), sizeof(double) * tab.size(), cudaMemcpyHostToDevice, st));
+    std::vector<float> tab32(tab.begin(), tab.end());
+    QH_CK(h, dalloc(&M.tab32, tab32.size()));
+    QH_CK(h, cudaMemcpyAsync(M.tab32, tab32.data(), sizeof(float) * tab32.size(), cudaMemcpyHostToDevice, st));
+    QH_CK(h, cudaStreamSynchronize(st));
+    return QHFPE_OK;
+}
+
+qhfpe_status make_prop(qhfpe *h, Model *M, int n_rep, bool mixed, double dt, std::unique_ptr<Prop> &out)
+{
+    std::unique_ptr<Prop> P(new (std::nothrow) Prop());
+    if (!P) return h->fail(QHFPE_ENOMEM, "host allocation failed");
+    P->m = M;
+    P->g = M->g;
+    P->g.n_rep = n_rep;
+    P->mixed = mixed;
+    P->dt = dt;
+    const size_t n = (size_t)n_rep * P->g.rep_stride;
+    const size_t es = mixed ? sizeof(float) : sizeof(double);
+    for (void **b : {&P->y, &P->vA, &P->vB, &P->P}) {
+        cudaError_t e = cudaMalloc(b, n * es + 16);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return h->fail(QHFPE_ENOMEM, "device allocation of the state buffers failed");
+        }
+        QH_CK(h, cudaMemsetAsync(*b, 0, n * es, h->stream));
+    }
+    if (mixed) {
+        cudaError_t e = cudaMalloc((void **)&P->y0, (size_t)n_rep * P->g.tier0_rep_stride * sizeof(double) + 16);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return h->fail(QHFPE_ENOMEM, "device allocation of the tier-0 buffer failed");
+        }
+        QH_CK(h, cudaMemsetAsync(P->y0, 0, (size_t)n_rep * P->g.tier0_rep_stride * sizeof(double), h->stream));
+    }
+    QH_CK(h, cudaMalloc((void **)&P->sink, sizeof(TraceSink)));
+    QH_CK(h, cudaMemsetAsync(P->sink, 0, sizeof(TraceSink), h->stream));
+    out = std::move(P);
+    return QHFPE_OK;
+}
+
+// ---- timing helpers --------------------------------------------------------------------------
+cudaEvent_t next_event(qhfpe *h)
+{
+    Timing &T = h->timing;
+    if (T.used == T.pool.size()) {
+        cudaEvent_t e;
+        if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+        T.pool.push_back(e);
+    }
+    return T.pool[T.used++];
+}
+
+struct Bracket {
+    qhfpe *h;
+    int kind;
+    cudaEvent_t a = nullptr, b = nullptr;
+    Bracket(qhfpe *h_, int k) : h(h_), kind(k)
+    {
+        if (h->timing.enabled) {
+            a = next_event(h);
+            b = next_event(h);
+            if (a) cudaEventRecord(a, h->stream);
+        }
+    }
+    ~Bracket()
+    {
+        if (a && b) {
+            cudaEventRecord(b, h->stream);
+            h->timing.pending.push_back({kind, {a, b}});
+        }
+    }
+};
+
+// ---- one RK4 step: Horner form of the degree-4 Taylor polynomial ---------------------------------
+//   v = y;  v = y + (dt/4) L v;  v = y + (dt/3) L v;  v = y + (dt/2) L v;  y = y + dt L v.
+template <typename T, bool MIXED>
+qhfpe_status step_once(qhfpe *h, Prop &P, bool record)
+{
+    cudaStream_t st = h->stream;
+    T *y = (T *)P.y, *vA = (T *)P.vA, *vB = (T *)P.vB, *Pt = (T *)P.P;
+    const Model &M = *P.m;
+    for (int k = 4; k >= 1; --k) {
+        T *in = (k == 4) ? y : (k == 3 ? vA : (k == 2 ? vB : vA));
+        T *out = (k == 1) ? y : (k == 4 ? vA : (k == 3 ? vB : vA));
+        {
+            Bracket br(h, QH_KIND_POT);
+            if (MIXED) QH_CK(h, launch_potential<float>(P.g, M.t32(), (const float *)in, (float *)Pt, 0, P.g.n_rep, st));
+            else QH_CK(h, launch_potential<double>(P.g, M.t64(), (const double *)in, (double *)Pt, 0, P.g.n_rep, st));
+        }
+        {
+            Bracket br(h, QH_KIND_STAGE);
+            QH_CK(h, (launch_stage<T, MIXED>(P.g, M.elems, in, Pt, y, P.y0, out, k == 1 ? P.y0 : nullptr, P.dt / k,
+                                             k == 1 ? 2 : 1, QHFPE_TERM_ALL, 0, P.g.n_rep, st)));
+        }
+    }
+    if (record) {
+        Bracket br(h, QH_KIND_AUX);
+        if (MIXED) QH_CK(h, launch_trace<double>(P.g, P.y0, P.g.tier0_rep_stride, M.mu, P.sink, 1, st));
+        else QH_CK(h, launch_trace<double>(P.g, (const double *)P.y, P.g.rep_stride, M.mu, P.sink, 1, st));
+    }
+    return QHFPE_OK;
+}
+
+qhfpe_status step_dispatch(qhfpe *h, Prop &P, bool record)
+{
+    return P.mixed ? step_once<float, true>(h, P, record) : step_once<double, false>(h, P, record);
+}
+
+__global__ void set_sink_kernel(TraceSink *s, double *base, long stride, long counter)
+{
+    s->base = base;
+    s->stride = stride;
+    s->counter = counter;
+}
+
+qhfpe_status run_steps(qhfpe *h, Prop &P, long n_steps, double *trace_dev, long stride)
+{
+    cudaStream_t st = h->stream;
+    const bool record = trace_dev != nullptr;
+    if (record) {
+        set_sink_kernel<<<1, 1, 0, st>>>(P.sink, trace_dev, stride, 0);
+        QH_CK(h, cudaGetLastError());
+        if (P.mixed) QH_CK(h, launch_trace<double>(P.g, P.y0, P.g.tier0_rep_stride, P.m->mu, P.sink, 1, st));
+        else QH_CK(h, launch_trace<double>(P.g, (const double *)P.y, P.g.rep_stride, P.m->mu, P.sink, 1, st));
+    }
+    if (h->timing.enabled) {
+        for (long s = 0; s < n_steps; ++s) {
+            qhfpe_status r = step_dispatch(h, P, record);
+            if (r != QHFPE_OK) return r;
+        }
+        return QHFPE_OK;
+    }
+    long done = 0;
+    while (done < n_steps) {
+        const int chunk = (n_steps - done >= kGraphChunk) ? 1 : 0;
+        const int len = chunk ? kGraphChunk : 1;
+        cudaGraphExec_t &ge = P.graphs[chunk][record ? 1 : 0];
+        if (!ge) {
+            cudaGraph_t graph;
+            QH_CK(h, cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+            qhfpe_status r = QHFPE_OK;
+            for (int s = 0; s < len && r == QHFPE_OK; ++s) r = step_dispatch(h, P, record);
+            cudaError_t e = cudaStreamEndCapture(st, &graph);
+            if (r != QHFPE_OK) return r;
+            QH_CK(h, e);
+            e = cudaGraphInstantiate(&ge, graph, 0);
+            cudaGraphDestroy(graph);
+            QH_CK(h, e);
+        }
+        QH_CK(h, cudaGraphLaunch(ge, st));
+        done += len;
+    }
+    return QHFPE_OK;
+}
+
+qhfpe_status ensure_trace(qhfpe *h, Prop &P, size_t n_complex)
+{
+    if (P.trace_cap >= n_complex) return QHFPE_OK;
+    if (P.trace_buf) cudaFree(P.trace_buf);
+    P.trace_buf = nullptr;
+    P.trace_cap = 0;
+    QH_CK(h, cudaMalloc((void **)&P.trace_buf, n_complex * 2 * sizeof(double)));
+    P.trace_cap = n_complex;
+    return QHFPE_OK;
+}
+
+qhfpe_status ensure_scratch(qhfpe *h, size_t bytes)
+{
+    if (h->scratch_cap >= bytes) return QHFPE_OK;
+    if (h->scratch) cudaFree(h->scratch);
+    h->scratch = nullptr;
+    h->scratch_cap = 0;
+    QH_CK(h, cudaMalloc((void **)&h->scratch, bytes));
+    h->scratch_cap = bytes;
+    return QHFPE_OK;
+}
+
+qhfpe_status set_from_canonical(qhfpe *h, Prop &P, const double *src_dev, int rep, int n_rep)
+{
+    if (P.mixed) QH_CK(h, launch_from_canonical<float>(P.g, src_dev, (float *)P.y, P.y0, rep, n_rep, h->stream));
+    else QH_CK(h, launch_from_canonical<double>(P.g, src_dev, (double *)P.y, nullptr, rep, n_rep, h->stream));
+    return QHFPE_OK;
+}
+
+qhfpe_status get_to_canonical(qhfpe *h, Prop &P, const void *src, const double *y0, double *dst_dev, int rep)
+{
+    if (P.mixed) QH_CK(h, launch_to_canonical<float>(P.g, (const float *)src, y0, dst_dev, rep, h->stream));
+    else QH_CK(h, launch_to_canonical<double>(P.g, (const double *)src, nullptr, dst_dev, rep, h->stream));
+    return QHFPE_OK;
+}
+
+qhfpe_status apply_dipole_prop(qhfpe *h, Prop &P, int side, const int *reps_dev, int n, double scale)
+{
+    if (P.mixed) QH_CK(h, launch_dipole<float>(P.g, (float *)P.y, P.y0, reps_dev, n, P.m->mu, side, scale, h->stream));
+    else QH_CK(h, launch_dipole<double>(P.g, (double *)P.y, nullptr, reps_dev, n, P.m->mu, side, scale, h->stream));
+    return QHFPE_OK;
+}
+
+// copy replica `src` of A into replica `dst` of B (same model and arithmetic)
+qhfpe_status copy_replica(qhfpe *h, Prop &A, int src, Prop &B, int dst)
+{
+    if (&A == &B && src == dst) return QHFPE_OK;
+    const size_t es = A.mixed ? sizeof(float) : sizeof(double);
+    QH_CK(h, cudaMemcpyAsync((char *)B.y + (size_t)dst * B.g.rep_stride * es, (char *)A.y + (size_t)src * A.g.rep_stride * es,
+                             A.g.rep_stride * es, cudaMemcpyDeviceToDevice, h->stream));
+    if (A.mixed)
+        QH_CK(h, cudaMemcpyAsync(B.y0 + (size_t)dst * B.g.tier0_rep_stride, A.y0 + (size_t)src * A.g.tier0_rep_stride,
+                                 A.g.tier0_rep_stride * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+    return QHFPE_OK;
+}
+
+bool finite_all(const double *x, size_t n)
+{
+    for (size_t i = 0; i < n; ++i)
+        if (!std::isfinite(x[i])) return false;
+    return true;
+}
+
+qhfpe_status check_handle(qhfpe *h)
+{
+    if (!h) return QHFPE_EINVAL;
+    if (h->sticky) return QHFPE_ESTATE;
+    return QHFPE_OK;
+}
+
+qhfpe_status batch_prop(qhfpe *h, int n_rep, Prop **out)
+{
+    auto it = h->batches.find(n_rep);
+    if (it == h->batches.end()) {
+        std::unique_ptr<Prop> P;
+        qhfpe_status r = make_prop(h, h->model.get(), n_rep, h->p.precision != QHFPE_FP64, h->p.dt, P);
+        if (r != QHFPE_OK) return r;
+        it = h->batches.emplace(n_rep, std::move(P)).first;
+    }
+    *out = it->second.get();
+    return QHFPE_OK;
+}
+
+}  // namespace
+
+// ================================================================================================
+//                                          C ABI
+// ================================================================================================
+extern "C" {
+
+qhfpe_status qhfpe_create(const qhfpe_params *params, void *stream, qhfpe_t **out)
+{
+    if (!params || !out) return QHFPE_EINVAL;
+    *out = nullptr;
+    const qhfpe_params &p = *params;
+    std::string &create_err = g_create_error;
+    auto bad = [&](const char *m) {
+        create_err = m;
+        return QHFPE_EINVAL;
+    };
+    if (p.n_states < 1 || p.n_states > QH_MAX_S) return bad("n_states must be in [1, 4]");
+    if (p.nq < 1) return bad("nq must be >= 1");
+    if (p.np < 8 || p.np > 512 || (p.np & (p.np - 1))) return bad("np must be a power of two in [8, 512]");
+    if (!(p.q_max > p.q_min) || !(p.p_max > p.p_min)) return bad("empty grid range");
+    if (!p.U_table || !p.mu) return bad("U_table and mu are required");
+    if (!(p.dt > 0.0) || !std::isfinite(p.dt)) return bad("dt must be positive and finite");
+    if (p.n_matsubara < 0 || p.n_matsubara + 1 > QH_MAX_MODES) return bad("n_matsubara must be in [0, 7]");
+    if (p.high_temperature && p.n_matsubara != 0) return bad("high_temperature requires n_matsubara = 0");
+    if (p.depth < 0) return bad("depth must be >= 0");
+    if (p.closure == QHFPE_TERMINATOR && p.n_matsubara != 0) return bad("the terminator closure needs n_matsubara = 0");
+    if (p.closure == QHFPE_LEARNED) {
+        create_err = "the learned closure is not available in this build";
+        return QHFPE_EUNSUPPORTED;
+    }
+    if (p.closure != QHFPE_TRUNCATE && p.closure != QHFPE_TERMINATOR) return bad("unknown closure");
+    if (p.precision != QHFPE_FP64 && p.precision != QHFPE_MIXED) {
+        if (p.precision == QHFPE_MIXED_BF16X3) {
+            create_err = "the bf16x3 tensor-core potential kernel is not available in this build";
+            return QHFPE_EUNSUPPORTED;
+        }
+        return bad("unknown precision");
+    }
+    if (p.n_replicas < 1) return bad("n_replicas must be >= 1");
+    if (!(p.beta > 0.0) || !(p.gamma > 0.0) || !(p.eta >= 0.0)) return bad("bath parameters out of range");
+    if (!p.high_temperature && std::fabs(std::sin(p.beta * p.gamma / 2.0)) < 1e-12)
+        return bad("beta*gamma/2 is a multiple of pi (cot diverges)");
+    const int S = p.n_states;
+    const size_t tn = (size_t)S * S * p.nq * (p.np + 1);
+    if (!finite_all(p.U_table, tn) || !finite_all(p.mu, (size_t)S * S)) {
+        create_err = "U_table or mu holds NaN/Inf";
+        return QHFPE_ENUMERIC;
+    }
+    for (int j = 0; j < S; ++j)
+        for (int k = 0; k < S; ++k)
+            if (p.mu[j * S + k] != p.mu[k * S + j]) return bad("mu must be symmetric");
+    const size_t smem64 = (size_t)2 * S * S * 2 * p.np * sizeof(double);
+    if (smem64 > 200 * 1024) return bad("n_states * np too large for the shared-memory potential kernel");
+
+    std::unique_ptr<qhfpe> h(new (std::nothrow) qhfpe());
+    if (!h) return QHFPE_ENOMEM;
+    h->p = p;
+    h->U.assign(p.U_table, p.U_table + tn);
+    h->mu.assign(p.mu, p.mu + S * S);
+    h->p.U_table = h->U.data();
+    h->p.mu = h->mu.data();
+    if (stream) {
+        h->stream = (cudaStream_t)stream;
+    } else {
+        cudaError_t e = cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) {
+            create_err = std::string("cudaStreamCreate: ") + cudaGetErrorString(e);
+            cudaGetLastError();
+            return QHFPE_ECUDA;
+        }
+        h->own_stream = true;
+    }
+    h->model.reset(new Model());
+    qhfpe_status r = build_model(h.get(), *h->model, S, h->U.data(), h->mu.data());
+    if (r != QHFPE_OK) {
+        create_err = h->err;
+        return r;
+    }
+    r = make_prop(h.get(), h->model.get(), p.n_replicas, p.precision != QHFPE_FP64, p.dt, h->main);
+    if (r != QHFPE_OK) {
+        create_err = h->err;
+        return r;
+    }
+    cudaError_t e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) {
+        create_err = std::string("create: ") + cudaGetErrorString(e);
+        return QHFPE_ECUDA;
+    }
+    *out = h.release();
+    return QHFPE_OK;
+}
+
+qhfpe_status qhfpe_destroy(qhfpe_t *h)
+{
+    if (!h) return QHFPE_EINVAL;
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    delete h;
+    return QHFPE_OK;
+}
+
+const char *qhfpe_last_error(const qhfpe_t *h)
+{
+    if (!h) return g_create_error.c_str();  // a failed create has no handle
+    return h->err.c_str();
+}
+
+qhfpe_status qhfpe_sizes(const qhfpe_t *h, int *n_elem, int *n_modes, size_t *state_elems)
+{
+    if (!h) return QHFPE_EINVAL;
+    const Model &M = *h->model;
+    if (n_elem) *n_elem = M.n_elem;
+    if (n_modes) *n_modes = M.n_modes;
+    if (state_elems) *state_elems = (size_t)M.n_elem * M.S * M.S * M.g.blk;
+    return QHFPE_OK;
+}
+
+qhfpe_status qhfpe_hierarchy(const qhfpe_t *h, int *idx_out)
+{
+    if (!h || !idx_out) return QHFPE_EINVAL;
+    const Model &M = *h->model;
+    for (int e = 0; e < M.n_elem; ++e)
+        for (int k = 0; k < M.n_modes; ++k) idx_out[e * M.n_modes + k] = M.hier[e][k];
+    return QHFPE_OK;
+}
+
+qhfpe_status qhfpe_bath_coefficients(const qhfpe_t *h, double *gamma_k, double *r_k, double *c_k, double *cdelta)
+{
+    if (!h) return QHFPE_EINVAL;
+    const Model &M = *h->model;
+    for (int k = 0; k < M.n_modes; ++k) {
+        if (gamma_k) gamma_k[k] = M.bath.gamma[k];
+        if (r_k) r_k[k] = M.bath.r[k];
+        if (c_k) c_k[k] = M.bath.c[k];
+    }
+    if (cdelta) *cdelta = M.bath.cdelta;
+    return QHFPE_OK;
+}
+
+qhfpe_status qhfpe_max_stable_dt(const qhfpe_t *h, double *dt_out)
+{
+    if (!h || !dt_out) return QHFPE_EINVAL;
+    *dt_out = 2.8 / h->model->max_rate;
+    return QHFPE_OK;
+}
+
+qhfpe_status qhfpe_set_state(qhfpe_t *h, int replica, const double *src, int is_device)
+{
+    qhfpe_status r = check_handle(h);
+    if (r != QHFPE_OK) return r;
+    Prop &P = *h->main;
+    if (!src || replica < -1 || replica >= P.g.n_rep) return h->fail(QHFPE_EINVAL, "set_state: bad replica or NULL source");
+    const size_t n = (size_t)P.g.n_elem * P.g.S * P.g.S * P.g.blk;
+    const double *dsrc = src;
+    if (!is_device) {
+        if (!finite_all(src, 2 * n)) return h->fail(QHFPE_ENUMERIC, "set_state: source holds NaN/Inf");
+        r = ensure_scratch(h, n * 2 * sizeof(double));
+        if (r != QHFPE_OK) return r;
+        QH_CK(h, cudaMemcpyAsync(h->scratch, src, n * 2 * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+        dsrc = h->scratch;
+    }
+    r = set_from_canonical(h, P, dsrc, replica < 0 ? 0 : replica, replica < 0 ? P.g.n_rep : 1);
+    if (r != QHFPE_OK) return r;
+    QH_CK(h, cudaStreamSynchronize(h->stream));
+    return QHFPE_OK;
+}
+
+qhfpe_status qhfpe_get_state(qhfpe_t *h, int replica, double *dst, int is_device)
+{
+    qhfpe_status r = check_handle(h);
+    if (r != QHFPE_OK) return r;
+    Prop &P = *h->main;
+    if (!dst || replica < 0 || replica >= P.g.n_rep) return h->fail(QHFPE_EINVAL, "get_state: bad replica or NULL destination");
+    const size_t n = (size_t)P.g.n_elem * P.g.S * P.g.S * P.g.blk;
+    double *ddst = dst;
+    if (!is_device) {
+        r = ensure_scratch(h, n * 2 * sizeof(double));
+        if (r != QHFPE_OK) return r;
+        ddst = h->scratch;
+    }
+    r = get_to_canonical(h, P, P.y, P.y0, ddst, replica);
+    if (r != QHFPE_OK) return r;
+    if (!is_device) QH_CK(h, cudaMemcpyAsync(dst, ddst, n * 2 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    QH_CK(h, cudaStreamSynchronize(h->stream));
+    return QHFPE_OK;
+}
+
+qhfpe_status qhfpe_fork(qhfpe_t *h, int src, const int *dst, int n)
+{
+    qhfpe_status r = check_handle(h);
+    if (r != QHFPE_OK) return r;
+    Prop &P = *h->main;
+    if (src < 0 || src >= P.g.n_rep || (n > 0 && !dst)) return h->fail(QHFPE_EINVAL, "fork: bad replica");
+    for (int a = 0; a < n; ++a) {
+        if (dst[a] < 0 || dst[a] >= P.g.n_rep) return h->fail(QHFPE_EINVAL, "fork: bad destination replica");
+        if (dst[a] == src) continue;
+        r = copy_replica(h, P, src, P, dst[a]);
+        if (r != QHFPE_OK) return r;
+    }
+    QH_CK(h, cudaStreamSynchronize(h->stream));
+    return QHFPE_OK;
+}
+
+qhfpe_status qhfpe_step(qhfpe_t *h, long n_steps, double *trace_out)
+{
+    qhfpe_status r = check_handle(h);
+    if (r != QHFPE_OK) return r;
+    if (n_steps < 0) return h->fail(QHFPE_EINVAL, "step: n_steps < 0");
+    Prop &P = *h->main;
+    double *tr = nullptr;
+    const long stride = n_steps + 1;
+    if (trace_out) {
+        r = ensure_trace(h, P, (size_t)P.g.n_rep * stride);
+        if (r != QHFPE_OK) return r;
+        tr = P.trace_buf;
+    }
+    r = run_steps(h, P, n_steps, tr, stride);
+    if (r != QHFPE_OK) return r;
+    if (trace_out)
+        QH_CK(h, cudaMemcpyAsync(trace_out, tr, (size_t)P.g.n_rep * stride * 2 * sizeof(double), cudaMemcpyDeviceToHost,
+                                 h->stream));
+    QH_CK(h, cudaStreamSynchronize(h->stream));
+    return QHFPE_OK;
+}
+
+qhfpe_status qhfpe_apply_dipole(qhfpe_t *h, int side, const int *replicas, int n)
+{
+    qhfpe_status r = check_handle(h);
+    if (r != QHFPE_OK) return r;
+    Prop &P = *h->main;
+    if (side < 1 || side > 3) return h->fail(QHFPE_EINVAL, "apply_dipole: side must be 1, 2 or 3");
+    const int *reps_dev = nullptr;
+    int count = P.g.n_rep;
+    if (replicas) {
+        for (int a = 0; a < n; ++a)
+            if (replicas[a] < 0 || replicas[a] >= P.g.n_rep) return h->fail(QHFPE_EINVAL, "apply_dipole: bad replica");
+        r = ensure_scratch(h, (size_t)n * sizeof(int) + 16);
+        if (r != QHFPE_OK) return r;
+        QH_CK(h, cudaMemcpyAsync(h->scratch, replicas, (size_t)n * sizeof(int), cudaMemcpyHostToDevice, h->stream));
+        reps_dev = (const int *)h->scratch;
+        count = n;
+    }
+    if (count > 0) {
+        r = apply_dipole_prop(h, P, side, reps_dev, count, 1.0);
+        if (r != QHFPE_OK) return r;
+    }
+    QH_CK(h, cudaStreamSynchronize(h->stream));
+    return QHFPE_OK;
+}
+
+qhfpe_status qhfpe_apply_rhs(qhfpe_t *h, int replica, int terms, double *out)
+{
+    qhfpe_status r = check_handle(h);
+    if (r != QHFPE_OK) return r;
+    Prop &P = *h->main;
+    if (!out || replica < 0 || replica >= P.g.n_rep) return h->fail(QHFPE_EINVAL, "apply_rhs: bad replica or NULL output");
+    cudaStream_t st = h->stream;
+    const Model &M = *P.m;
+    if (P.mixed) {
+        QH_CK(h, launch_potential<float>(P.g, M.t32(), (const float *)P.y, (float *)P.P, replica, 1, st));
+        QH_CK(h, (launch_stage<float, true>(P.g, M.elems, (const float *)P.y, (const float *)P.P, (const float *)P.y,
+                                            P.y0, (float *)P.vA, nullptr, 0.0, 0, terms, replica, 1, st)));
+    } else {
+        QH_CK(h, launch_potential<double>(P.g, M.t64(), (const double *)P.y, (double *)P.P, replica, 1, st));
+        QH_CK(h, (launch_stage<double, false>(P.g, M.elems, (const double *)P.y, (const double *)P.P,
+                                              (const double *)P.y, nullptr, (double *)P.vA, nullptr, 0.0, 0, terms,
+                                              replica, 1, st)));
+    }
+    const size_t n = (size_t)P.g.n_elem * P.g.S * P.g.S * P.g.blk;
+    r = ensure_scratch(h, n * 2 * sizeof(double));
+    if (r != QHFPE_OK) return r;
+    r = get_to_canonical(h, P, P.vA, nullptr, h->scratch, replica);
+    if (r != QHFPE_OK) return r;
+    QH_CK(h, cudaMemcpyAsync(out, h->scratch, n * 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
+    QH_CK(h, cudaStreamSynchronize(st));
+    return QHFPE_OK;
+}
+
+qhfpe_status qhfpe_trace(qhfpe_t *h, double *out)
+{
+    qhfpe_status r = check_handle(h);
+    if (r != QHFPE_OK) return r;
+    if (!out) return h->fail(QHFPE_EINVAL, "trace: NULL output");
+    Prop &P = *h->main;
+    r = ensure_trace(h, P, P.g.n_rep);
+    if (r != QHFPE_OK) return r;
+    set_sink_kernel<<<1, 1, 0, h->stream>>>(P.sink, P.trace_buf, 1, 0);
+    QH_CK(h, cudaGetLastError());
+    if (P.mixed) QH_CK(h, launch_trace<double>(P.g, P.y0, P.g.tier0_rep_stride, P.m->mu, P.sink, 0, h->stream));
+    else QH_CK(h, launch_trace<double>(P.g, (const double *)P.y, P.g.rep_stride, P.m->mu, P.sink, 0, h->stream));
+    QH_CK(h, cudaMemcpyAsync(out, P.trace_buf, (size_t)P.g.n_rep * 2 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    QH_CK(h, cudaStreamSynchronize(h->stream));
+    return QHFPE_OK;
+}
+
+qhfpe_status qhfpe_equilibrate(qhfpe_t *h, long n_steps, double *residual_out)
+{
+    qhfpe_status r = check_handle(h);
+    if (r != QHFPE_OK) return r;
+    if (n_steps < 0) return h->fail(QHFPE_EINVAL, "equilibrate: n_steps < 0");
+    const qhfpe_params &p = h->p;
+    const int nq = p.nq, np = p.np, S = p.n_states;
+    cudaStream_t st = h->stream;
+    if (!h->ground) {
+        std::vector<double> U00((size_t)nq * (np + 1));
+        for (int i = 0; i < nq; ++i)
+            for (int t = 0; t <= np; ++t) U00[(size_t)i * (np + 1) + t] = h->U[(size_t)i * (np + 1) + t];
+        const double zero = 0.0;
+        h->ground.reset(new Model());
+        r = build_model(h, *h->ground, 1, U00.data(), &zero);
+        if (r != QHFPE_OK) return r;
+    }
+    Model &G = *h->ground;
+    std::unique_ptr<Prop> GP;
+    r = make_prop(h, &G, 1, false, p.dt, GP);
+    if (r != QHFPE_OK) return r;
+    // classical Boltzmann start, unit trace
+    const size_t blk = (size_t)nq * np;
+    const size_t gn = (size_t)G.n_elem * blk;
+    std::vector<double> w0(2 * gn, 0.0);
+    double norm = 0.0;
+    const double dq = (p.q_max - p.q_min) / nq, dp = (p.p_max - p.p_min) / np;
+    for (int i = 0; i < nq; ++i)
+        for (int l = 0; l < np; ++l) {
+            const double pl = p.p_min + l * dp;
+            const double v = std::exp(-p.beta * (0.5 * pl * pl + h->U[(size_t)i * (np + 1) + np / 2]));
+            w0[2 * ((size_t)i * np + l)] = v;
+            norm += v;
+        }
+    norm *= dq * dp;
+    for (size_t c = 0; c < blk; ++c) w0[2 * c] /= norm;
+    const size_t full = (size_t)G.n_elem * S * S * blk;
+    r = ensure_scratch(h, std::max(gn, full) * 2 * sizeof(double) + 64);
+    if (r != QHFPE_OK) return r;
+    QH_CK(h, cudaMemcpyAsync(h->scratch, w0.data(), gn * 2 * sizeof(double), cudaMemcpyHostToDevice, st));
+    r = set_from_canonical(h, *GP, h->scratch, 0, 1);
+    if (r != QHFPE_OK) return r;
+    r = run_steps(h, *GP, n_steps, nullptr, 0);
+    if (r != QHFPE_OK) return r;
+    // residual ||L W|| / ||W||
+    QH_CK(h, launch_potential<double>(GP->g, G.t64(), (const double *)GP->y, (double *)GP->P, 0, 1, st));
+    QH_CK(h, (launch_stage<double, false>(GP->g, G.elems, (const double *)GP->y, (const double *)GP->P,
+                                          (const double *)GP->y, nullptr, (double *)GP->vA, nullptr, 0.0, 0,
+                                          QHFPE_TERM_ALL, 0, 1, st)));
+    QH_CK(h, launch_norm2((const double *)GP->vA, GP->g.rep_stride, h->scratch, st));
+    QH_CK(h, launch_norm2((const double *)GP->y, GP->g.rep_stride, h->scratch + 1, st));
+    double nn[2];
+    QH_CK(h, cudaMemcpyAsync(nn, h->scratch, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
+    QH_CK(h, cudaStreamSynchronize(st));
+    if (residual_out) *residual_out = std::sqrt(nn[0] / nn[1]);
+    if (!std::isfinite(nn[0]) || !std::isfinite(nn[1])) return h->fail(QHFPE_ENUMERIC, "equilibrate: state not finite");
+    // embed in the 00 block of every element
+    if (!h->eq) QH_CK(h, cudaMalloc((void **)&h->eq, full * 2 * sizeof(double)));
+    QH_CK(h, cudaMemsetAsync(h->eq, 0, full * 2 * sizeof(double), st));
+    r = get_to_canonical(h, *GP, GP->y, nullptr, h->scratch, 0);
+    if (r != QHFPE_OK) return r;
+    QH_CK(h, cudaMemcpy2DAsync(h->eq, (size_t)S * S * blk * 2 * sizeof(double), h->scratch, blk * 2 * sizeof(double),
+                               blk * 2 * sizeof(double), G.n_elem, cudaMemcpyDeviceToDevice, st));
+    h->have_eq = true;
+    r = set_from_canonical(h, *h->main, h->eq, 0, h->main->g.n_rep);
+    if (r != QHFPE_OK) return r;
+    QH_CK(h, cudaStreamSynchronize(st));
+    return QHFPE_OK;
+}
+
+qhfpe_status qhfpe_set_equilibrium(qhfpe_t *h, const double *src, int is_device)
+{
+    qhfpe_status r = check_handle(h);
+    if (r != QHFPE_OK) return r;
+    if (!src) return h->fail(QHFPE_EINVAL, "set_equilibrium: NULL source");
+    const Model &M = *h->model;
+    const size_t n = (size_t)M.n_elem * M.S * M.S * M.g.blk;
+    if (!is_device && !finite_all(src, 2 * n)) return h->fail(QHFPE_ENUMERIC, "set_equilibrium: NaN/Inf");
+    if (!h->eq) QH_CK(h, cudaMalloc((void **)&h->eq, n * 2 * sizeof(double)));
+    QH_CK(h, cudaMemcpyAsync(h->eq, src, n * 2 * sizeof(double), is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                             h->stream));
+    QH_CK(h, cudaStreamSynchronize(h->stream));
+    h->have_eq = true;
+    return QHFPE_OK;
+}
+
+qhfpe_status qhfpe_response(qhfpe_t *h, const qhfpe_schedule *s, double *R_out)
+{
+    qhfpe_status r = check_handle(h);
+    if (r != QHFPE_OK) return r;
+    if (!s || !R_out) return h->fail(QHFPE_EINVAL, "response: NULL schedule or output");
+    if (!h->have_eq) return h->fail(QHFPE_EINVAL, "response: no equilibrium state (call qhfpe_equilibrate or qhfpe_set_equilibrium)");
+    if (s->n_t3 < 0) return h->fail(QHFPE_EINVAL, "response: n_t3 < 0");
+    cudaStream_t st = h->stream;
+    const long nt = s->n_t3 + 1;
+    if (s->kind == QHFPE_LINEAR) {
+        Prop *B;
+        r = batch_prop(h, 1, &B);
+        if (r != QHFPE_OK) return r;
+        r = set_from_canonical(h, *B, h->eq, 0, 1);
+        if (r != QHFPE_OK) return r;
+        r = apply_dipole_prop(h, *B, QHFPE_COMMUTATOR, nullptr, 1, 1.0);
+        if (r != QHFPE_OK) return r;
+        r = ensure_trace(h, *B, nt);
+        if (r != QHFPE_OK) return r;
+        r = run_steps(h, *B, s->n_t3, B->trace_buf, nt);
+        if (r != QHFPE_OK) return r;
+        std::vector<double> tr(2 * nt);
+        QH_CK(h, cudaMemcpyAsync(tr.data(), B->trace_buf, nt * 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
+        QH_CK(h, cudaStreamSynchronize(st));
+        for (long c = 0; c < nt; ++c) {  // R1 = i * Tr
+            R_out[2 * c] = -tr[2 * c + 1];
+            R_out[2 * c + 1] = tr[2 * c];
+        }
+        return QHFPE_OK;
+    }
+    if (s->kind != QHFPE_THIRD_ORDER) return h->fail(QHFPE_EINVAL, "response: unknown kind");
+    if (s->n_t1 < 1 || s->t1_stride < 0 || s->n_t2 < 1 || !s->t2_steps)
+        return h->fail(QHFPE_EINVAL, "response: bad third-order schedule");
+    for (int b = 0; b < s->n_t2; ++b)
+        if (s->t2_steps[b] < 0 || (b > 0 && s->t2_steps[b] < s->t2_steps[b - 1]))
+            return h->fail(QHFPE_EINVAL, "response: t2_steps must be non-negative and ascending");
+    const int n_paths = s->split_pathways ? 2 : 1;
+    const int n1 = n_paths, n2 = n_paths * s->n_t1, n3 = n2 * s->n_t2;
+    Prop *P1, *P2, *P3;
+    if ((r = batch_prop(h, n1, &P1)) != QHFPE_OK) return r;
+    if ((r = batch_prop(h, n2, &P2)) != QHFPE_OK) return r;
+    if ((r = batch_prop(h, n3, &P3)) != QHFPE_OK) return r;
+    // Equal replica counts share one cached batch (only when n_t1 = 1 or n_t2 = 1); the snapshot
+    // copies then land on their own slots and are skipped.
+    // phase 1: first interaction
+    r = set_from_canonical(h, *P1, h->eq, 0, n1);
+    if (r != QHFPE_OK) return r;
+    if (s->split_pathways) {
+        int zero = 0, one = 1;
+        int *dev = nullptr;
+        r = ensure_scratch(h, 2 * sizeof(int) + 16);
+        if (r != QHFPE_OK) return r;
+        dev = (int *)h->scratch;
+        QH_CK(h, cudaMemcpyAsync(dev, &zero, sizeof(int), cudaMemcpyHostToDevice, st));
+        QH_CK(h, cudaMemcpyAsync(dev + 1, &one, sizeof(int), cudaMemcpyHostToDevice, st));
+        if ((r = apply_dipole_prop(h, *P1, QHFPE_LEFT, dev, 1, 1.0)) != QHFPE_OK) return r;
+        if ((r = apply_dipole_prop(h, *P1, QHFPE_RIGHT, dev + 1, 1, -1.0)) != QHFPE_OK) return r;
+        QH_CK(h, cudaStreamSynchronize(st));
+    } else {
+        if ((r = apply_dipole_prop(h, *P1, QHFPE_COMMUTATOR, nullptr, 1, 1.0)) != QHFPE_OK) return r;
+    }
+    // phase 2: t1 propagation with snapshots
+    for (int a = 0; a < s->n_t1; ++a) {
+        if (a > 0 && s->t1_stride > 0) {
+            if ((r = run_steps(h, *P1, s->t1_stride, nullptr, 0)) != QHFPE_OK) return r;
+        }
+        for (int pth = 0; pth < n_paths; ++pth)
+            if ((r = copy_replica(h, *P1, pth, *P2, pth * s->n_t1 + a)) != QHFPE_OK) return r;
+    }
+    if ((r = apply_dipole_prop(h, *P2, QHFPE_COMMUTATOR, nullptr, n2, 1.0)) != QHFPE_OK) return r;
+    // phase 3: t2 propagation with forks
+    int done = 0;
+    for (int b = 0; b < s->n_t2; ++b) {
+        const int t2 = s->t2_steps[b];
+        if (t2 > done) {
+            if ((r = run_steps(h, *P2, t2 - done, nullptr, 0)) != QHFPE_OK) return r;
+            done = t2;
+        }
+        for (int pth = 0; pth < n_paths; ++pth)
+            for (int a = 0; a < s->n_t1; ++a)
+                if ((r = copy_replica(h, *P2, pth * s->n_t1 + a, *P3, (pth * s->n_t2 + b) * s->n_t1 + a)) != QHFPE_OK)
+                    return r;
+    }
+    if ((r = apply_dipole_prop(h, *P3, QHFPE_COMMUTATOR, nullptr, n3, 1.0)) != QHFPE_OK) return r;
+    // phase 4: detection, every t3 job of the spectrum in one batch
+    if ((r = ensure_trace(h, *P3, (size_t)n3 * nt)) != QHFPE_OK) return r;
+    if ((r = run_steps(h, *P3, s->n_t3, P3->trace_buf, nt)) != QHFPE_OK) return r;
+    std::vector<double> tr((size_t)n3 * nt * 2);
+    QH_CK(h, cudaMemcpyAsync(tr.data(), P3->trace_buf, tr.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+    QH_CK(h, cudaStreamSynchronize(st));
+    for (size_t c = 0; c < (size_t)n3 * nt; ++c) {  // R3 = i^3 Tr = -i Tr
+        R_out[2 * c] = tr[2 * c + 1];
+        R_out[2 * c + 1] = -tr[2 * c];
+    }
+    return QHFPE_OK;
+}
+
+qhfpe_status qhfpe_spectrum_absorption(qhfpe_t *h, const double *R1, long n_t, double dt, const double *omega,
+                                       int n_omega, double *out)
+{
+    qhfpe_status r = check_handle(h);
+    if (r != QHFPE_OK) return r;
+    if (!R1 || !omega || !out || n_t < 1 || n_omega < 1) return h->fail(QHFPE_EINVAL, "spectrum_absorption: bad arguments");
+    const size_t bytes = (2 * n_t + 2 * n_omega) * sizeof(double);
+    if ((r = ensure_scratch(h, bytes)) != QHFPE_OK) return r;
+    double *dR = h->scratch, *dw = dR + 2 * n_t, *dout = dw + n_omega;
+    cudaStream_t st = h->stream;
+    QH_CK(h, cudaMemcpyAsync(dR, R1, 2 * n_t * sizeof(double), cudaMemcpyHostToDevice, st));
+    QH_CK(h, cudaMemcpyAsync(dw, omega, n_omega * sizeof(double), cudaMemcpyHostToDevice, st));
+    QH_CK(h, launch_absorption(dR, n_t, dt, dw, n_omega, dout, st));
+    QH_CK(h, cudaMemcpyAsync(out, dout, n_omega * sizeof(double), cudaMemcpyDeviceToHost, st));
+    QH_CK(h, cudaStreamSynchronize(st));
+    return QHFPE_OK;
+}
+
+qhfpe_status qhfpe_spectrum_2d(qhfpe_t *h, const double *R3, int n_t1, int n_t3, double dt1, double dt3,
+                               const double *omega1, int n_omega1, const double *omega3, int n_omega3, double *nr,
+                               double *re)
+{
+    qhfpe_status r = check_handle(h);
+    if (r != QHFPE_OK) return r;
+    if (!R3 || !omega1 || !omega3 || !nr || !re || n_t1 < 1 || n_t3 < 0 || n_omega1 < 1 || n_omega3 < 1)
+        return h->fail(QHFPE_EINVAL, "spectrum_2d: bad arguments");
+    const size_t nR = (size_t)n_t1 * (n_t3 + 1) * 2;
+    const size_t nG = (size_t)n_omega3 * n_t1 * 2;
+    const size_t nO = (size_t)n_omega1 * n_omega3;
+    const size_t bytes = (nR + nG + n_omega1 + n_omega3 + 2 * nO) * sizeof(double);
+    if ((r = ensure_scratch(h, bytes)) != QHFPE_OK) return r;
+    double *dR = h->scratch, *dG = dR + nR, *dw1 = dG + nG, *dw3 = dw1 + n_omega1, *dnr = dw3 + n_omega3, *dre = dnr + nO;
+    cudaStream_t st = h->stream;
+    QH_CK(h, cudaMemcpyAsync(dR, R3, nR * sizeof(double), cudaMemcpyHostToDevice, st));
+    QH_CK(h, cudaMemcpyAsync(dw1, omega1, n_omega1 * sizeof(double), cudaMemcpyHostToDevice, st));
+    QH_CK(h, cudaMemcpyAsync(dw3, omega3, n_omega3 * sizeof(double), cudaMemcpyHostToDevice, st));
+    QH_CK(h, launch_spectrum2d(dR, n_t1, n_t3, dt1, dt3, dw1, n_omega1, dw3, n_omega3, dnr, dre, dG, st));
+    QH_CK(h, cudaMemcpyAsync(nr, dnr, nO * sizeof(double), cudaMemcpyDeviceToHost, st));
+    QH_CK(h, cudaMemcpyAsync(re, dre, nO * sizeof(double), cudaMemcpyDeviceToHost, st));
+    QH_CK(h, cudaStreamSynchronize(st));
+    return QHFPE_OK;
+}
+
+qhfpe_status qhfpe_kernel_timing(qhfpe_t *h, int enable)
+{
+    qhfpe_status r = check_handle(h);
+    if (r != QHFPE_OK) return r;
+    h->timing.enabled = enable != 0;
+    return QHFPE_OK;
+}
+
+qhfpe_status qhfpe_kernel_timing_read(qhfpe_t *h, long *launches, double *total_ms, int n_kinds)
+{
+    qhfpe_status r = check_handle(h);
+    if (r != QHFPE_OK) return r;
+    QH_CK(h, cudaStreamSynchronize(h->stream));
+    Timing &T = h->timing;
+    for (auto &pe : T.pending) {
+        float ms = 0.f;
+        QH_CK(h, cudaEventElapsedTime(&ms, pe.second.first, pe.second.second));
+        T.launches[pe.first] += 1;
+        T.ms[pe.first] += ms;
+    }
+    T.pending.clear();
+    T.used = 0;
+    for (int k = 0; k < n_kinds && k < QH_KINDS; ++k) {
+        if (launches) launches[k] = T.launches[k];
+        if (total_ms) total_ms[k] = T.ms[k];
+        T.launches[k] = 0;
+        T.ms[k] = 0.0;
+    }
+    return QHFPE_OK;
+}
+
+}  // extern "C"
+

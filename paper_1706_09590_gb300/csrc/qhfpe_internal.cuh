@@ -1,0 +1,96 @@
+// Internal declarations of the QHFPE CUDA library (kernels + host orchestration).
+// Nothing here is part of the C ABI; see include/qhfpe.h for that.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stddef.h>
+
+#define QH_MAX_MODES 8
+#define QH_MAX_S 4
+
+// Per hierarchy element: the couplings of Eq. (heom) with the linear-coupling operators of Sec. II.
+//   tier-up   : + sum_k dW^(n+e_k)/dp                        (element up[k], or -1)
+//   tier-down : + sum_k n_k gamma_k (r_k p + c_k d/dp) W^(n-e_k)   (element dn[k], weights wr, wc)
+//   damping   : - (sum_k n_k gamma_k) W
+//   terminator: at the deepest tier with the Eq. (GMFP) closure, d/dp (r_0 p W) + c_0 d2W/dp2 replaces
+//               the missing tier-up term.
+struct ElemInfo {
+    int up[QH_MAX_MODES];
+    int dn[QH_MAX_MODES];
+    double wr[QH_MAX_MODES];
+    double wc[QH_MAX_MODES];
+    double ngam;
+    int n_up, n_dn;
+    int terminator;
+    int tier;
+};
+
+// Geometry and bath scalars shared by every kernel of one propagator.
+struct GridInfo {
+    int S, nq, np, log2np;
+    int n_elem, n_rep;
+    int periodic_q;
+    double q_min, p_min, dq, dp;
+    double cdelta;     // delta-term coefficient
+    double term_r0, term_c0;  // terminator coefficients (r_0, c_0)
+    size_t blk;        // nq*np (one re or im plane of one (j,k) block)
+    size_t elem_stride;    // S*S*2*blk reals per element
+    size_t rep_stride;     // n_elem*elem_stride reals per replica
+    size_t tier0_rep_stride;  // S*S*2*blk reals per replica in the FP64 tier-0 buffer
+};
+
+// Potential-kernel tables in FFT output (bit-reversed) order, pre-scaled by 1/np:
+//   D[j][k][i][pos]  = UL_jj(m) - UR_kk(m)          (coefficient of rho_jk)
+//   L[j][s][i][pos]  = UL_js(m)  (used for s != j)   R[s][k][i][pos] = UR_sk(m)  (used for s != k)
+// with m the r-grid mode sitting at FFT position pos.
+template <typename T>
+struct PotTables {
+    const T *D, *L, *R;
+    const T *tw;   // twiddles (cos, sin)(2 pi k / np), k < np/2, interleaved
+};
+
+// Device-side trace sink: trace kernel writes slot `counter` of every replica then the counter
+// advances; keeps captured graphs independent of the call's output length.
+struct TraceSink {
+    double *base;   // [n_rep][stride] complex
+    long stride;    // complex numbers per replica
+    long counter;
+};
+
+enum { QH_KIND_STAGE = 0, QH_KIND_POT = 1, QH_KIND_AUX = 2, QH_KINDS = 3 };
+
+// ---- launchers (qhfpe_kernels.cu) -----------------------------------------------------------------
+template <typename T>
+cudaError_t launch_potential(const GridInfo &g, const PotTables<T> &tab, const T *v, T *P, int rep0, int n_rep,
+                             cudaStream_t st);
+
+template <typename T, bool MIXED>
+cudaError_t launch_stage(const GridInfo &g, const ElemInfo *elems, const T *v_in, const T *P, const T *y,
+                         const double *y0, T *v_out, double *y0_out, double h, int mode, int terms,
+                         int rep0, int n_rep, cudaStream_t st);
+
+template <typename T>
+cudaError_t launch_trace(const GridInfo &g, const T *state, size_t rep_stride, const double *mu_dev,
+                         TraceSink *sink, int advance, cudaStream_t st);
+
+cudaError_t launch_advance(TraceSink *sink, cudaStream_t st);
+cudaError_t prepare_potential(size_t smem_bytes_fp64);
+
+template <typename T>
+cudaError_t launch_dipole(const GridInfo &g, T *state, double *y0, const int *reps, int n_reps,
+                          const double *mu_dev, int side, double scale, cudaStream_t st);
+
+template <typename T>
+cudaError_t launch_from_canonical(const GridInfo &g, const double *src, T *dst, double *y0_dst, int rep, int n_rep,
+                                  cudaStream_t st);
+template <typename T>
+cudaError_t launch_to_canonical(const GridInfo &g, const T *src, const double *y0_src, double *dst, int rep,
+                                cudaStream_t st);
+
+cudaError_t launch_norm2(const double *x, size_t n, double *out_dev, cudaStream_t st);
+cudaError_t launch_absorption(const double *R1, long n_t, double dt, const double *omega, int n_omega,
+                              double *out, cudaStream_t st);
+cudaError_t launch_spectrum2d(const double *R3, int n_t1, int n_t3, double dt1, double dt3, const double *omega1,
+                              int n1, const double *omega3, int n3, double *nr, double *re, double *scratch,
+                              cudaStream_t st);

@@ -1,0 +1,630 @@
+// SIMT kernels of the QHFPE library: right-hand side stages, FFT potential kernel, traces, dipoles,
+// layout conversion and spectra.  Templated on the state's real type (double for the FP64 form,
+// float for the mixed forms).
+//
+// State layout on the device ("internal"): [rep][elem][j][k][re|im][q][p] with p fastest, re and im in
+// separate planes of nq*np reals.  The mixed forms also keep the zeroth tier in FP64:
+// y0[rep][j][k][re|im][q][p].
+#include "qhfpe_internal.cuh"
+
+namespace {
+
+constexpr int STAGE_THREADS = 256;
+constexpr int POT_THREADS = 128;
+
+__device__ __forceinline__ int wrap(int x, int n) { return x < 0 ? x + n : (x >= n ? x - n : x); }
+
+// ---------------------------------------------------------------------------------------------------
+// Right-hand side of Eq. (heom) (linear coupling, Sec. II) at one cell, fused with the Horner update of
+// the degree-4 Taylor / RK4 step: v_out = base + h * L(v_in).  The potential term comes precomputed in P
+// (same layout as v_in).  mode 0: v_out = L(v_in) (diagnostics); 1: Horner stage; 2: final Horner
+// stage (mixed forms also write the FP64 zeroth tier).
+// ---------------------------------------------------------------------------------------------------
+template <typename T, bool MIXED>
+__global__ void __launch_bounds__(STAGE_THREADS)
+stage_kernel(GridInfo g, const ElemInfo *__restrict__ elems, const T *__restrict__ v_in, const T *__restrict__ P,
+             const T *y, const double *y0, T *v_out, double *y0_out, double h, int mode, int terms, int rep0,
+             int tiles_per_block)
+{
+    const int S2 = g.S * g.S;
+    const int bid = blockIdx.x / tiles_per_block;
+    const int tile = blockIdx.x - bid * tiles_per_block;
+    const int cell = tile * STAGE_THREADS + threadIdx.x;
+    if (cell >= (int)g.blk) return;
+    const int pair = bid % S2;
+    const int e = (bid / S2) % g.n_elem;
+    const int rep = rep0 + bid / (S2 * g.n_elem);
+    const int np = g.np, nq = g.nq;
+    const int l = cell & (np - 1);
+    const int i = cell >> g.log2np;
+    const size_t blk = g.blk;
+
+    const size_t rep_off = (size_t)rep * g.rep_stride;
+    const size_t pair_off = (size_t)pair * 2 * blk;
+    const T *V = v_in + rep_off + (size_t)e * g.elem_stride + pair_off;
+
+    const T p = (T)(g.p_min + l * g.dp);
+    T acc_r = 0, acc_i = 0;
+
+    // -p dW/dq, 5th-order upwind (Sec. III)
+    if (terms & 1) {
+        T sr = 0, si = 0;
+        auto ld = [&](int ii, T c) {
+            if (ii < 0 || ii >= nq) {
+                if (!g.periodic_q) return;
+                ii = ii < 0 ? ii + nq : ii - nq;
+            }
+            size_t o = (size_t)ii * np + l;
+            sr += c * V[o];
+            si += c * V[o + blk];
+        };
+        if (p < (T)0) {
+            ld(i + 3, (T)2); ld(i + 2, (T)-15); ld(i + 1, (T)60); ld(i, (T)-20); ld(i - 1, (T)-30); ld(i - 2, (T)3);
+        } else {
+            ld(i + 2, (T)-3); ld(i + 1, (T)30); ld(i, (T)20); ld(i - 1, (T)-60); ld(i - 2, (T)15); ld(i - 3, (T)-2);
+        }
+        const T f = -p / (T)(60.0 * g.dq);
+        acc_r += f * sr;
+        acc_i += f * si;
+    }
+    // -i [U, W], precomputed by the potential kernel
+    if (terms & 2) {
+        size_t o = rep_off + (size_t)e * g.elem_stride + pair_off + cell;
+        acc_r += P[o];
+        acc_i += P[o + blk];
+    }
+
+    const ElemInfo &E = elems[e];
+    const int lm2 = wrap(l - 2, np), lm1 = wrap(l - 1, np), lp1 = wrap(l + 1, np), lp2 = wrap(l + 2, np);
+    const size_t row = (size_t)i * np;
+    const T inv12dp = (T)(1.0 / (12.0 * g.dp));
+
+    // damping and delta-term, plus the terminator's c_0 d2/dp2
+    T cpp = 0;
+    if (terms & 4) {
+        const T c = V[row + l], ci = V[row + l + blk];
+        acc_r -= (T)E.ngam * c;
+        acc_i -= (T)E.ngam * ci;
+        cpp += (T)g.cdelta;
+    }
+    const bool term = (terms & 8) && E.terminator;
+    if (term) cpp += (T)g.term_c0;
+    if (cpp != (T)0) {
+        const T f = cpp * inv12dp / (T)g.dp;
+        const T *Vr = V + row, *Vi = V + row + blk;
+        acc_r += f * (-Vr[lm2] + (T)16 * Vr[lm1] - (T)30 * Vr[l] + (T)16 * Vr[lp1] - Vr[lp2]);
+        acc_i += f * (-Vi[lm2] + (T)16 * Vi[lm1] - (T)30 * Vi[l] + (T)16 * Vi[lp1] - Vi[lp2]);
+    }
+
+    // d/dp of G = sum_up W^(n+e_k) + sum_dn n_k gamma_k c_k W^(n-e_k) [+ r_0 p W^n at the terminator],
+    // plus p * sum_dn n_k gamma_k r_k W^(n-e_k)
+    T g_r[5] = {0, 0, 0, 0, 0}, g_i[5] = {0, 0, 0, 0, 0};
+    const int cols[5] = {lm2, lm1, l, lp1, lp2};
+    bool have_g = false;
+    const T *base_e0 = v_in + rep_off + pair_off;  // element 0 of this replica and pair
+    if (terms & 8) {
+        for (int a = 0; a < E.n_up; ++a) {
+            const T *U = base_e0 + (size_t)E.up[a] * g.elem_stride + row;
+            for (int t = 0; t < 5; ++t) {
+                if (t == 2) continue;
+                g_r[t] += U[cols[t]];
+                g_i[t] += U[cols[t] + blk];
+            }
+            have_g = true;
+        }
+        if (term) {
+            const T r0 = (T)g.term_r0;
+            for (int t = 0; t < 5; ++t) {
+                if (t == 2) continue;
+                const T pc = (T)(g.p_min + cols[t] * g.dp);
+                g_r[t] += r0 * pc * V[row + cols[t]];
+                g_i[t] += r0 * pc * V[row + cols[t] + blk];
+            }
+            have_g = true;
+        }
+    }
+    if (terms & 16) {
+        T pr = 0, pi = 0;
+        for (int a = 0; a < E.n_dn; ++a) {
+            const T *D = base_e0 + (size_t)E.dn[a] * g.elem_stride + row;
+            const T wc = (T)E.wc[a], wr = (T)E.wr[a];
+            for (int t = 0; t < 5; ++t) {
+                if (t == 2) continue;
+                g_r[t] += wc * D[cols[t]];
+                g_i[t] += wc * D[cols[t] + blk];
+            }
+            pr += wr * D[l];
+            pi += wr * D[l + blk];
+            have_g = true;
+        }
+        acc_r += p * pr;
+        acc_i += p * pi;
+    }
+    if (have_g) {
+        acc_r += inv12dp * (g_r[0] - (T)8 * g_r[1] + (T)8 * g_r[3] - g_r[4]);
+        acc_i += inv12dp * (g_i[0] - (T)8 * g_i[1] + (T)8 * g_i[3] - g_i[4]);
+    }
+
+    const size_t o = rep_off + (size_t)e * g.elem_stride + pair_off + cell;
+    if (mode == 0) {
+        v_out[o] = acc_r;
+        v_out[o + blk] = acc_i;
+        return;
+    }
+    if (MIXED && e == 0) {
+        const size_t o0 = (size_t)rep * g.tier0_rep_stride + pair_off + cell;
+        const double nr = y0[o0] + h * (double)acc_r;
+        const double ni = y0[o0 + blk] + h * (double)acc_i;
+        v_out[o] = (T)nr;
+        v_out[o + blk] = (T)ni;
+        if (mode == 2) {
+            y0_out[o0] = nr;
+            y0_out[o0 + blk] = ni;
+        }
+        return;
+    }
+    const T hh = (T)h;
+    const T br = y[o], bi = y[o + blk];
+    v_out[o] = br + hh * acc_r;
+    v_out[o + blk] = bi + hh * acc_i;
+}
+
+// ---------------------------------------------------------------------------------------------------
+// Potential kernel, Eq. (quantum-liouvillian): for one (replica, element, q row), all S*S blocks.
+// In r-space (the density matrix rho(q + r/2, q - r/2), Sec. II) the commutator is local:
+//   -i [ sum_s U_js(q + r/2) rho_sk - sum_s rho_js U_sk(q - r/2) ],
+// so: forward FFT along p of every block (sign +), the S x S mixing per mode, inverse FFT (sign -).
+// Radix-2 Gentleman-Sande forward leaves modes in bit-reversed order; the tables are stored in that
+// order and the Cooley-Tukey inverse takes bit-reversed input, so no permutation pass is needed.
+// ---------------------------------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ void fft_forward_dif(T *re, T *im, int log2N, const T *__restrict__ tw, int lane)
+{
+    const int N = 1 << log2N;
+    for (int s = log2N - 1; s >= 0; --s) {
+        const int h = 1 << s;
+        for (int b = lane; b < (N >> 1); b += 32) {
+            const int grp = b >> s, j = b & (h - 1);
+            const int i0 = (grp << (s + 1)) + j, i1 = i0 + h;
+            const T ar = re[i0], ai = im[i0], cr = re[i1], ci = im[i1];
+            re[i0] = ar + cr;
+            im[i0] = ai + ci;
+            const T dr = ar - cr, di = ai - ci;
+            const int t = j << (log2N - 1 - s);
+            const T wr = tw[2 * t], wi = tw[2 * t + 1];
+            re[i1] = dr * wr - di * wi;
+            im[i1] = dr * wi + di * wr;
+        }
+        __syncwarp();
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ void fft_inverse_dit(T *re, T *im, int log2N, const T *__restrict__ tw, int lane)
+{
+    const int N = 1 << log2N;
+    for (int s = 0; s < log2N; ++s) {
+        const int h = 1 << s;
+        for (int b = lane; b < (N >> 1); b += 32) {
+            const int grp = b >> s, j = b & (h - 1);
+            const int i0 = (grp << (s + 1)) + j, i1 = i0 + h;
+            const int t = j << (log2N - 1 - s);
+            const T wr = tw[2 * t], wi = -tw[2 * t + 1];
+            const T xr = re[i1] * wr - im[i1] * wi;
+            const T xi = re[i1] * wi + im[i1] * wr;
+            const T ar = re[i0], ai = im[i0];
+            re[i1] = ar - xr;
+            im[i1] = ai - xi;
+            re[i0] = ar + xr;
+            im[i0] = ai + xi;
+        }
+        __syncwarp();
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(POT_THREADS)
+pot_kernel(GridInfo g, PotTables<T> tab, const T *__restrict__ v, T *__restrict__ P, int rep0)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int S = g.S, S2 = S * S, N = g.np, nq = g.nq;
+    T *bin = reinterpret_cast<T *>(smem_raw);  // [S2][2][N]
+    T *bout = bin + (size_t)S2 * 2 * N;        // [S2][2][N]
+    const int row = blockIdx.x;
+    const int i = row % nq;
+    const int e = (row / nq) % g.n_elem;
+    const int rep = rep0 + row / (nq * g.n_elem);
+    const size_t blk = g.blk;
+    const size_t ebase = (size_t)rep * g.rep_stride + (size_t)e * g.elem_stride + (size_t)i * N;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
+
+    for (int idx = tid; idx < S2 * 2 * N; idx += blockDim.x) {
+        const int pr = idx / (2 * N), c = (idx / N) & 1, l = idx & (N - 1);
+        bin[idx] = v[ebase + (size_t)pr * 2 * blk + (size_t)c * blk + l];
+    }
+    __syncthreads();
+    for (int pr = warp; pr < S2; pr += nwarps) fft_forward_dif(bin + pr * 2 * N, bin + pr * 2 * N + N, g.log2np, tab.tw, lane);
+    __syncthreads();
+    for (int pos = tid; pos < N; pos += blockDim.x) {
+        for (int j = 0; j < S; ++j)
+            for (int k = 0; k < S; ++k) {
+                const size_t trow = (size_t)i * N + pos;
+                const T d = tab.D[((size_t)(j * S + k) * nq) * N + trow];
+                const T *rjk = bin + (j * S + k) * 2 * N;
+                T ar = d * rjk[pos], ai = d * rjk[N + pos];
+                for (int s = 0; s < S; ++s) {
+                    if (s != j) {
+                        const T u = tab.L[((size_t)(j * S + s) * nq) * N + trow];
+                        const T *r = bin + (s * S + k) * 2 * N;
+                        ar += u * r[pos];
+                        ai += u * r[N + pos];
+                    }
+                    if (s != k) {
+                        const T u = tab.R[((size_t)(s * S + k) * nq) * N + trow];
+                        const T *r = bin + (j * S + s) * 2 * N;
+                        ar -= u * r[pos];
+                        ai -= u * r[N + pos];
+                    }
+                }
+                // times -i
+                T *o = bout + (j * S + k) * 2 * N;
+                o[pos] = ai;
+                o[N + pos] = -ar;
+            }
+    }
+    __syncthreads();
+    for (int pr = warp; pr < S2; pr += nwarps) fft_inverse_dit(bout + pr * 2 * N, bout + pr * 2 * N + N, g.log2np, tab.tw, lane);
+    __syncthreads();
+    for (int idx = tid; idx < S2 * 2 * N; idx += blockDim.x) {
+        const int pr = idx / (2 * N), c = (idx / N) & 1, l = idx & (N - 1);
+        P[ebase + (size_t)pr * 2 * blk + (size_t)c * blk + l] = bout[idx];
+    }
+}
+
+// ---------------------------------------------------------------------------------------------------
+// Tr{mu W^(0)} = sum_jk mu_kj sum_il W^(0)_jk dq dp for every replica, FP64, fixed summation order
+// (deterministic): one block per replica.
+// ---------------------------------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(512)
+trace_kernel(GridInfo g, const T *__restrict__ state, size_t rep_stride, const double *__restrict__ mu,
+             TraceSink *sink)
+{
+    __shared__ double red[2][512];
+    const int rep = blockIdx.x;
+    const int S = g.S;
+    const size_t blk = g.blk;
+    const T *W = state + (size_t)rep * rep_stride;
+    double sr = 0.0, si = 0.0;
+    for (int j = 0; j < S; ++j)
+        for (int k = 0; k < S; ++k) {
+            const double m = mu[k * S + j];
+            if (m == 0.0) continue;
+            const T *b = W + (size_t)(j * S + k) * 2 * blk;
+            double ar = 0.0, ai = 0.0;
+            for (size_t c = threadIdx.x; c < blk; c += blockDim.x) {
+                ar += (double)b[c];
+                ai += (double)b[c + blk];
+            }
+            sr += m * ar;
+            si += m * ai;
+        }
+    red[0][threadIdx.x] = sr;
+    red[1][threadIdx.x] = si;
+    __syncthreads();
+    for (int w = blockDim.x >> 1; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) {
+            red[0][threadIdx.x] += red[0][threadIdx.x + w];
+            red[1][threadIdx.x] += red[1][threadIdx.x + w];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        const long slot = sink->counter;
+        double *out = sink->base + 2 * ((size_t)rep * sink->stride + slot);
+        out[0] = red[0][0] * g.dq * g.dp;
+        out[1] = red[1][0] * g.dq * g.dp;
+    }
+}
+
+__global__ void advance_kernel(TraceSink *sink) { sink->counter += 1; }
+
+// ---------------------------------------------------------------------------------------------------
+// Dipole super-operators (Sec. III, Condon): mu^-> W = mu W, mu^<- W = W mu, mu^x = mu^-> - mu^<-, on
+// every hierarchy element of the listed replicas, in place; `scale` multiplies the result.
+// ---------------------------------------------------------------------------------------------------
+template <typename T>
+__global__ void dipole_kernel(GridInfo g, T *state, double *y0, const int *__restrict__ reps, int n_reps,
+                              const double *__restrict__ mu, int side, double scale)
+{
+    const size_t blk = g.blk;
+    const size_t total = (size_t)n_reps * g.n_elem * blk;
+    const int S = g.S;
+    for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total; idx += (size_t)gridDim.x * blockDim.x) {
+        const size_t cell = idx % blk;
+        const int e = (int)((idx / blk) % g.n_elem);
+        const int ri = (int)(idx / (blk * g.n_elem));
+        const int rep = reps ? reps[ri] : ri;
+        const bool t0 = (y0 != nullptr) && e == 0;
+        T *W = state + (size_t)rep * g.rep_stride + (size_t)e * g.elem_stride + cell;
+        double *W0 = t0 ? y0 + (size_t)rep * g.tier0_rep_stride + cell : nullptr;
+        double xr[QH_MAX_S * QH_MAX_S], xi[QH_MAX_S * QH_MAX_S];
+        for (int a = 0; a < S * S; ++a) {
+            if (t0) {
+                xr[a] = W0[(size_t)a * 2 * blk];
+                xi[a] = W0[(size_t)a * 2 * blk + blk];
+            } else {
+                xr[a] = (double)W[(size_t)a * 2 * blk];
+                xi[a] = (double)W[(size_t)a * 2 * blk + blk];
+            }
+        }
+        for (int j = 0; j < S; ++j)
+            for (int k = 0; k < S; ++k) {
+                double lr = 0, li = 0, rr = 0, ri2 = 0;
+                for (int l = 0; l < S; ++l) {
+                    lr += mu[j * S + l] * xr[l * S + k];
+                    li += mu[j * S + l] * xi[l * S + k];
+                    rr += xr[j * S + l] * mu[l * S + k];
+                    ri2 += xi[j * S + l] * mu[l * S + k];
+                }
+                double o_r = side == 1 ? lr : (side == 2 ? rr : lr - rr);
+                double o_i = side == 1 ? li : (side == 2 ? ri2 : li - ri2);
+                o_r *= scale;
+                o_i *= scale;
+                const size_t a = (size_t)(j * S + k) * 2 * blk;
+                W[a] = (T)o_r;
+                W[a + blk] = (T)o_i;
+                if (t0) {
+                    W0[a] = o_r;
+                    W0[a + blk] = o_i;
+                }
+            }
+    }
+}
+
+// canonical complex128 [elem][j][k][q][p]  <->  internal planar layout of one replica
+template <typename T>
+__global__ void from_canonical_kernel(GridInfo g, const double *__restrict__ src, T *dst, double *y0, int rep0)
+{
+    const size_t blk = g.blk;
+    const size_t per = (size_t)g.n_elem * g.S * g.S * blk;
+    const int rep = rep0 + blockIdx.y;
+    for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < per; idx += (size_t)gridDim.x * blockDim.x) {
+        const size_t cell = idx % blk;
+        const size_t ep = idx / blk;  // e*S2 + pair
+        const double re = src[2 * idx], im = src[2 * idx + 1];
+        const size_t o = (size_t)rep * g.rep_stride + ep * 2 * blk + cell;
+        dst[o] = (T)re;
+        dst[o + blk] = (T)im;
+        if (y0 && ep < (size_t)(g.S * g.S)) {
+            const size_t o0 = (size_t)rep * g.tier0_rep_stride + ep * 2 * blk + cell;
+            y0[o0] = re;
+            y0[o0 + blk] = im;
+        }
+    }
+}
+
+template <typename T>
+__global__ void to_canonical_kernel(GridInfo g, const T *__restrict__ src, const double *__restrict__ y0,
+                                    double *dst, int rep)
+{
+    const size_t blk = g.blk;
+    const size_t per = (size_t)g.n_elem * g.S * g.S * blk;
+    for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < per; idx += (size_t)gridDim.x * blockDim.x) {
+        const size_t cell = idx % blk;
+        const size_t ep = idx / blk;
+        double re, im;
+        if (y0 && ep < (size_t)(g.S * g.S)) {
+            const size_t o0 = (size_t)rep * g.tier0_rep_stride + ep * 2 * blk + cell;
+            re = y0[o0];
+            im = y0[o0 + blk];
+        } else {
+            const size_t o = (size_t)rep * g.rep_stride + ep * 2 * blk + cell;
+            re = (double)src[o];
+            im = (double)src[o + blk];
+        }
+        dst[2 * idx] = re;
+        dst[2 * idx + 1] = im;
+    }
+}
+
+__global__ void __launch_bounds__(1024) norm2_kernel(const double *__restrict__ x, size_t n, double *out)
+{
+    __shared__ double red[1024];
+    double s = 0.0;
+    for (size_t i = threadIdx.x; i < n; i += blockDim.x) s += x[i] * x[i];
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = blockDim.x >> 1; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *out = red[0];
+}
+
+// Eq. (I1) by the trapezoid rule: out[w] = omega Im sum_c wgt_c e^{i omega t_c} R1[c]
+__global__ void absorption_kernel(const double *__restrict__ R1, long n_t, double dt, const double *__restrict__ omega,
+                                  int n_omega, double *out)
+{
+    const int w = blockIdx.x * blockDim.x + threadIdx.x;
+    if (w >= n_omega) return;
+    const double om = omega[w];
+    double acc = 0.0;
+    for (long c = 0; c < n_t; ++c) {
+        double s, co;
+        sincos(om * (c * dt), &s, &co);
+        const double wgt = (c == 0 || c == n_t - 1) ? 0.5 * dt : dt;
+        acc += wgt * (s * R1[2 * c] + co * R1[2 * c + 1]);
+    }
+    out[w] = om * acc;
+}
+
+// Eqs. (nonreph), (reph): first the t3 transform G[w3][a], then the t1 transforms of both signs.
+__global__ void spec2d_t3_kernel(const double *__restrict__ R3, int n_t1, int n_t3, double dt3,
+                                 const double *__restrict__ omega3, int n3, double *G)
+{
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= n3 * n_t1) return;
+    const int w = idx / n_t1, a = idx % n_t1;
+    const double om = omega3[w];
+    const int nt = n_t3 + 1;
+    double gr = 0.0, gi = 0.0;
+    for (int c = 0; c < nt; ++c) {
+        double s, co;
+        sincos(om * (c * dt3), &s, &co);
+        const double wgt = (c == 0 || c == nt - 1) ? 0.5 * dt3 : dt3;
+        const double rr = R3[2 * ((size_t)a * nt + c)], ri = R3[2 * ((size_t)a * nt + c) + 1];
+        gr += wgt * (co * rr - s * ri);
+        gi += wgt * (s * rr + co * ri);
+    }
+    G[2 * idx] = gr;
+    G[2 * idx + 1] = gi;
+}
+
+__global__ void spec2d_t1_kernel(const double *__restrict__ G, int n_t1, double dt1, const double *__restrict__ omega1,
+                                 int n1, int n3, double *nr, double *re)
+{
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= n3 * n1) return;
+    const int w3 = idx / n1, w1 = idx % n1;
+    const double om = omega1[w1];
+    double an = 0.0, ar = 0.0;
+    for (int a = 0; a < n_t1; ++a) {
+        double s, co;
+        sincos(om * (a * dt1), &s, &co);
+        const double wgt = (n_t1 == 1) ? 0.0 : ((a == 0 || a == n_t1 - 1) ? 0.5 * dt1 : dt1);
+        const double gr = G[2 * ((size_t)w3 * n_t1 + a)], gi = G[2 * ((size_t)w3 * n_t1 + a) + 1];
+        // Im[e^{+i om t} G] and Im[e^{-i om t} G]
+        an += wgt * (s * gr + co * gi);
+        ar += wgt * (-s * gr + co * gi);
+    }
+    nr[idx] = an;
+    re[idx] = ar;
+}
+
+inline int grid_for(size_t n, int threads, int cap = 152 * 32)
+{
+    size_t b = (n + threads - 1) / threads;
+    if (b > (size_t)cap) b = cap;
+    return (int)(b ? b : 1);
+}
+
+}  // namespace
+
+// ----------------------------------------- launchers ----------------------------------------------
+template <typename T>
+cudaError_t launch_potential(const GridInfo &g, const PotTables<T> &tab, const T *v, T *P, int rep0, int n_rep,
+                             cudaStream_t st)
+{
+    const size_t smem = (size_t)2 * g.S * g.S * 2 * g.np * sizeof(T);
+    const int blocks = n_rep * g.n_elem * g.nq;
+    if (blocks <= 0) return cudaSuccess;
+    pot_kernel<T><<<blocks, POT_THREADS, smem, st>>>(g, tab, v, P, rep0);
+    return cudaGetLastError();
+}
+
+template <typename T, bool MIXED>
+cudaError_t launch_stage(const GridInfo &g, const ElemInfo *elems, const T *v_in, const T *P, const T *y,
+                         const double *y0, T *v_out, double *y0_out, double h, int mode, int terms, int rep0,
+                         int n_rep, cudaStream_t st)
+{
+    const int tiles = (int)((g.blk + STAGE_THREADS - 1) / STAGE_THREADS);
+    const long blocks = (long)n_rep * g.n_elem * g.S * g.S * tiles;
+    if (blocks <= 0) return cudaSuccess;
+    stage_kernel<T, MIXED><<<(unsigned)blocks, STAGE_THREADS, 0, st>>>(g, elems, v_in, P, y, y0, v_out, y0_out, h, mode,
+                                                                       terms, rep0, tiles);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_trace(const GridInfo &g, const T *state, size_t rep_stride, const double *mu_dev,
+                         TraceSink *sink, int advance, cudaStream_t st)
+{
+    trace_kernel<T><<<g.n_rep, 512, 0, st>>>(g, state, rep_stride, mu_dev, sink);
+    cudaError_t err = cudaGetLastError();
+    if (err != cudaSuccess || !advance) return err;
+    advance_kernel<<<1, 1, 0, st>>>(sink);
+    return cudaGetLastError();
+}
+
+// Raises the dynamic shared-memory limit of the potential kernels; called at set-up, outside any
+// stream capture.
+cudaError_t prepare_potential(size_t smem_bytes_fp64)
+{
+    cudaError_t err = cudaFuncSetAttribute(pot_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)smem_bytes_fp64);
+    if (err != cudaSuccess) return err;
+    return cudaFuncSetAttribute(pot_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)(smem_bytes_fp64 / 2));
+}
+
+cudaError_t launch_advance(TraceSink *sink, cudaStream_t st)
+{
+    advance_kernel<<<1, 1, 0, st>>>(sink);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_dipole(const GridInfo &g, T *state, double *y0, const int *reps, int n_reps,
+                          const double *mu_dev, int side, double scale, cudaStream_t st)
+{
+    const size_t total = (size_t)n_reps * g.n_elem * g.blk;
+    dipole_kernel<T><<<grid_for(total, 256), 256, 0, st>>>(g, state, y0, reps, n_reps, mu_dev, side, scale);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_from_canonical(const GridInfo &g, const double *src, T *dst, double *y0_dst, int rep, int n_rep,
+                                  cudaStream_t st)
+{
+    const size_t per = (size_t)g.n_elem * g.S * g.S * g.blk;
+    dim3 grid(grid_for(per, 256, 2048), n_rep);
+    from_canonical_kernel<T><<<grid, 256, 0, st>>>(g, src, dst, y0_dst, rep);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_to_canonical(const GridInfo &g, const T *src, const double *y0_src, double *dst, int rep,
+                                cudaStream_t st)
+{
+    const size_t per = (size_t)g.n_elem * g.S * g.S * g.blk;
+    to_canonical_kernel<T><<<grid_for(per, 256, 2048), 256, 0, st>>>(g, src, y0_src, dst, rep);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_norm2(const double *x, size_t n, double *out_dev, cudaStream_t st)
+{
+    norm2_kernel<<<1, 1024, 0, st>>>(x, n, out_dev);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_absorption(const double *R1, long n_t, double dt, const double *omega, int n_omega,
+                              double *out, cudaStream_t st)
+{
+    absorption_kernel<<<(n_omega + 127) / 128, 128, 0, st>>>(R1, n_t, dt, omega, n_omega, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_spectrum2d(const double *R3, int n_t1, int n_t3, double dt1, double dt3, const double *omega1,
+                              int n1, const double *omega3, int n3, double *nr, double *re, double *scratch,
+                              cudaStream_t st)
+{
+    spec2d_t3_kernel<<<(n3 * n_t1 + 127) / 128, 128, 0, st>>>(R3, n_t1, n_t3, dt3, omega3, n3, scratch);
+    cudaError_t err = cudaGetLastError();
+    if (err != cudaSuccess) return err;
+    spec2d_t1_kernel<<<(n3 * n1 + 127) / 128, 128, 0, st>>>(scratch, n_t1, dt1, omega1, n1, n3, nr, re);
+    return cudaGetLastError();
+}
+
+// explicit instantiations
+template cudaError_t launch_potential<double>(const GridInfo &, const PotTables<double> &, const double *, double *, int, int, cudaStream_t);
+template cudaError_t launch_potential<float>(const GridInfo &, const PotTables<float> &, const float *, float *, int, int, cudaStream_t);
+template cudaError_t launch_stage<double, false>(const GridInfo &, const ElemInfo *, const double *, const double *, const double *, const double *, double *, double *, double, int, int, int, int, cudaStream_t);
+template cudaError_t launch_stage<float, true>(const GridInfo &, const ElemInfo *, const float *, const float *, const float *, const double *, float *, double *, double, int, int, int, int, cudaStream_t);
+template cudaError_t launch_trace<double>(const GridInfo &, const double *, size_t, const double *, TraceSink *, int, cudaStream_t);
+template cudaError_t launch_dipole<double>(const GridInfo &, double *, double *, const int *, int, const double *, int, double, cudaStream_t);
+template cudaError_t launch_dipole<float>(const GridInfo &, float *, double *, const int *, int, const double *, int, double, cudaStream_t);
+template cudaError_t launch_from_canonical<double>(const GridInfo &, const double *, double *, double *, int, int, cudaStream_t);
+template cudaError_t launch_from_canonical<float>(const GridInfo &, const double *, float *, double *, int, int, cudaStream_t);
+template cudaError_t launch_to_canonical<double>(const GridInfo &, const double *, const double *, double *, int, cudaStream_t);
+template cudaError_t launch_to_canonical<float>(const GridInfo &, const float *, const double *, double *, int, cudaStream_t);

@@ -1,0 +1,291 @@
+"""Thin Python binding of the C ABI in include/qhfpe.h (argument marshalling only).
+
+Every numerical step runs in libqhfpe.so; this module converts arguments (numpy / torch buffers,
+scalars) into the ABI's plain pointers and sizes and raises on error statuses.  There is no fallback:
+if the library is missing the import fails.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+LIB_PATH = _build.LIB
+
+FP64, MIXED, MIXED_BF16X3 = 0, 1, 2
+TRUNCATE, TERMINATOR, LEARNED = 0, 1, 2
+LEFT, RIGHT, COMMUTATOR = 1, 2, 3
+TERM_KINETIC, TERM_POTENTIAL, TERM_DAMPING, TERM_TIER_UP, TERM_TIER_DOWN, TERM_ALL = 1, 2, 4, 8, 16, 31
+LINEAR, THIRD_ORDER = 0, 1
+PRECISIONS = {"fp64": FP64, "mixed": MIXED, "bf16x3": MIXED_BF16X3}
+
+STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ENUMERIC", 5: "ETIMEOUT", 6: "EUNSUPPORTED",
+          7: "ESTATE"}
+
+EXPORTED = [
+    "qhfpe_create", "qhfpe_destroy", "qhfpe_last_error", "qhfpe_sizes", "qhfpe_hierarchy",
+    "qhfpe_bath_coefficients", "qhfpe_max_stable_dt", "qhfpe_set_state", "qhfpe_get_state", "qhfpe_fork",
+    "qhfpe_step", "qhfpe_apply_dipole", "qhfpe_apply_rhs", "qhfpe_trace", "qhfpe_equilibrate",
+    "qhfpe_set_equilibrium", "qhfpe_response", "qhfpe_spectrum_absorption", "qhfpe_spectrum_2d",
+    "qhfpe_kernel_timing", "qhfpe_kernel_timing_read",
+]
+
+
+class QhfpeError(RuntimeError):
+    def __init__(self, status, message):
+        super().__init__(f"{STATUS.get(status, status)}: {message}")
+        self.status = status
+
+
+class Params(ctypes.Structure):
+    _fields_ = [
+        ("n_states", ctypes.c_int), ("nq", ctypes.c_int), ("np", ctypes.c_int),
+        ("q_min", ctypes.c_double), ("q_max", ctypes.c_double), ("p_min", ctypes.c_double),
+        ("p_max", ctypes.c_double),
+        ("U_table", ctypes.POINTER(ctypes.c_double)), ("mu", ctypes.POINTER(ctypes.c_double)),
+        ("eta", ctypes.c_double), ("gamma", ctypes.c_double), ("beta", ctypes.c_double),
+        ("n_matsubara", ctypes.c_int), ("high_temperature", ctypes.c_int), ("use_cdelta", ctypes.c_int),
+        ("depth", ctypes.c_int), ("closure", ctypes.c_int), ("periodic_q", ctypes.c_int),
+        ("precision", ctypes.c_int), ("dt", ctypes.c_double), ("n_replicas", ctypes.c_int),
+    ]
+
+
+class Schedule(ctypes.Structure):
+    _fields_ = [
+        ("kind", ctypes.c_int), ("n_t1", ctypes.c_int), ("t1_stride", ctypes.c_int), ("n_t2", ctypes.c_int),
+        ("t2_steps", ctypes.POINTER(ctypes.c_int)), ("n_t3", ctypes.c_int), ("split_pathways", ctypes.c_int),
+    ]
+
+
+_lib = None
+
+
+def lib():
+    """Load libqhfpe.so (building it first if the sources are newer).  Raises if it cannot."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH) or _build._stale():
+        _build.build()
+    L = ctypes.CDLL(LIB_PATH)
+    vp, dp, ip, st = ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int), ctypes.c_int
+    L.qhfpe_create.argtypes = [ctypes.POINTER(Params), vp, ctypes.POINTER(vp)]
+    L.qhfpe_destroy.argtypes = [vp]
+    L.qhfpe_last_error.argtypes = [vp]
+    L.qhfpe_last_error.restype = ctypes.c_char_p
+    L.qhfpe_sizes.argtypes = [vp, ip, ip, ctypes.POINTER(ctypes.c_size_t)]
+    L.qhfpe_hierarchy.argtypes = [vp, ip]
+    L.qhfpe_bath_coefficients.argtypes = [vp, dp, dp, dp, dp]
+    L.qhfpe_max_stable_dt.argtypes = [vp, dp]
+    L.qhfpe_set_state.argtypes = [vp, ctypes.c_int, vp, ctypes.c_int]
+    L.qhfpe_get_state.argtypes = [vp, ctypes.c_int, vp, ctypes.c_int]
+    L.qhfpe_fork.argtypes = [vp, ctypes.c_int, ip, ctypes.c_int]
+    L.qhfpe_step.argtypes = [vp, ctypes.c_long, vp]
+    L.qhfpe_apply_dipole.argtypes = [vp, ctypes.c_int, ip, ctypes.c_int]
+    L.qhfpe_apply_rhs.argtypes = [vp, ctypes.c_int, ctypes.c_int, vp]
+    L.qhfpe_trace.argtypes = [vp, vp]
+    L.qhfpe_equilibrate.argtypes = [vp, ctypes.c_long, dp]
+    L.qhfpe_set_equilibrium.argtypes = [vp, vp, ctypes.c_int]
+    L.qhfpe_response.argtypes = [vp, ctypes.POINTER(Schedule), vp]
+    L.qhfpe_spectrum_absorption.argtypes = [vp, vp, ctypes.c_long, ctypes.c_double, vp, ctypes.c_int, vp]
+    L.qhfpe_spectrum_2d.argtypes = [vp, vp, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double, vp,
+                                    ctypes.c_int, vp, ctypes.c_int, vp, vp]
+    L.qhfpe_kernel_timing.argtypes = [vp, ctypes.c_int]
+    L.qhfpe_kernel_timing_read.argtypes = [vp, ctypes.POINTER(ctypes.c_long), dp, ctypes.c_int]
+    for name in EXPORTED:
+        if name != "qhfpe_last_error":
+            getattr(L, name).restype = st
+    _lib = L
+    return L
+
+
+def _ptr(a):
+    return ctypes.c_void_p(a.ctypes.data)
+
+
+def _c128(a):
+    return np.ascontiguousarray(a, dtype=np.complex128)
+
+
+def _dev_ptr(t):
+    """(pointer, is_device) for a numpy array or a torch tensor (CUDA tensors stay on the device)."""
+    if hasattr(t, "data_ptr") and hasattr(t, "is_cuda"):
+        if t.is_cuda:
+            assert t.is_contiguous()
+            return ctypes.c_void_p(t.data_ptr()), 1
+        t = t.numpy()
+    return _ptr(t), 0
+
+
+class Propagator:
+    """One handle of the library: a model on a grid with `n_replicas` independent propagations."""
+
+    def __init__(self, model, U_table, precision="fp64", n_replicas=1, stream=None, dt=None, closure=None):
+        L = lib()
+        self._L = L
+        S = model["S"]
+        self.T = np.ascontiguousarray(U_table, dtype=np.float64)
+        assert self.T.shape == (S, S, model["nq"], model["np"] + 1), self.T.shape
+        self.mu = np.ascontiguousarray(np.asarray(model["mu"], dtype=np.float64))
+        prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        dpp = ctypes.POINTER(ctypes.c_double)
+        self.params = Params(S, model["nq"], model["np"], model["q_min"], model["q_max"], model["p_min"],
+                             model["p_max"], self.T.ctypes.data_as(dpp), self.mu.ctypes.data_as(dpp),
+                             model["eta"], model["gamma"], model["beta"], model["n_matsubara"],
+                             model["high_temperature"], model["use_cdelta"], model["depth"],
+                             model["closure"] if closure is None else closure, model.get("periodic_q", 0),
+                             prec, model["dt"] if dt is None else dt, n_replicas)
+        self.model = model
+        self.n_replicas = n_replicas
+        self.dt = self.params.dt
+        self._stream_obj = stream
+        sptr = None
+        if stream is not None:
+            sptr = ctypes.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+        h = ctypes.c_void_p()
+        s = L.qhfpe_create(ctypes.byref(self.params), sptr, ctypes.byref(h))
+        if s != 0:
+            raise QhfpeError(s, L.qhfpe_last_error(None).decode())
+        self._h = h
+        ne, nm, se = ctypes.c_int(), ctypes.c_int(), ctypes.c_size_t()
+        L.qhfpe_sizes(h, ctypes.byref(ne), ctypes.byref(nm), ctypes.byref(se))
+        self.n_elem, self.n_modes, self.state_elems = ne.value, nm.value, se.value
+        self.shape = (self.n_elem, S, S, model["nq"], model["np"])
+
+    def _check(self, s):
+        if s != 0:
+            raise QhfpeError(s, self._L.qhfpe_last_error(self._h).decode())
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._L.qhfpe_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ---- introspection ---------------------------------------------------------------------------
+    def hierarchy(self):
+        out = np.zeros((self.n_elem, self.n_modes), dtype=np.int32)
+        self._check(self._L.qhfpe_hierarchy(self._h, out.ctypes.data_as(ctypes.POINTER(ctypes.c_int))))
+        return out
+
+    def bath_coefficients(self):
+        g, r, c, cd = (np.zeros(self.n_modes), np.zeros(self.n_modes), np.zeros(self.n_modes), np.zeros(1))
+        dpp = ctypes.POINTER(ctypes.c_double)
+        self._check(self._L.qhfpe_bath_coefficients(self._h, g.ctypes.data_as(dpp), r.ctypes.data_as(dpp),
+                                                     c.ctypes.data_as(dpp), cd.ctypes.data_as(dpp)))
+        return dict(gamma=g, r=r, c=c, cdelta=float(cd[0]))
+
+    def max_stable_dt(self):
+        v = ctypes.c_double()
+        self._check(self._L.qhfpe_max_stable_dt(self._h, ctypes.byref(v)))
+        return v.value
+
+    # ---- state -----------------------------------------------------------------------------------
+    def set_state(self, W, replica=-1):
+        if hasattr(W, "is_cuda"):
+            ptr, dev = _dev_ptr(W)
+            self._check(self._L.qhfpe_set_state(self._h, replica, ptr, dev))
+            return
+        W = _c128(W)
+        assert W.shape == self.shape, (W.shape, self.shape)
+        self._check(self._L.qhfpe_set_state(self._h, replica, _ptr(W), 0))
+
+    def get_state(self, replica=0, out=None):
+        if out is not None and hasattr(out, "is_cuda"):
+            ptr, dev = _dev_ptr(out)
+            self._check(self._L.qhfpe_get_state(self._h, replica, ptr, dev))
+            return out
+        out = np.empty(self.shape, dtype=np.complex128)
+        self._check(self._L.qhfpe_get_state(self._h, replica, _ptr(out), 0))
+        return out
+
+    def fork(self, src, dst):
+        d = np.ascontiguousarray(dst, dtype=np.int32)
+        self._check(self._L.qhfpe_fork(self._h, src, d.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), len(d)))
+
+    # ---- propagation -----------------------------------------------------------------------------
+    def step(self, n_steps, record_trace=False):
+        if record_trace:
+            tr = np.zeros((self.n_replicas, n_steps + 1), dtype=np.complex128)
+            self._check(self._L.qhfpe_step(self._h, n_steps, _ptr(tr)))
+            return tr
+        self._check(self._L.qhfpe_step(self._h, n_steps, None))
+        return None
+
+    def apply_dipole(self, side=COMMUTATOR, replicas=None):
+        if replicas is None:
+            self._check(self._L.qhfpe_apply_dipole(self._h, side, None, 0))
+        else:
+            r = np.ascontiguousarray(replicas, dtype=np.int32)
+            self._check(self._L.qhfpe_apply_dipole(self._h, side, r.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
+                                                   len(r)))
+
+    def apply_rhs(self, replica=0, terms=TERM_ALL):
+        out = np.empty(self.shape, dtype=np.complex128)
+        self._check(self._L.qhfpe_apply_rhs(self._h, replica, terms, _ptr(out)))
+        return out
+
+    def trace(self):
+        out = np.zeros(self.n_replicas, dtype=np.complex128)
+        self._check(self._L.qhfpe_trace(self._h, _ptr(out)))
+        return out
+
+    def equilibrate(self, n_steps):
+        res = ctypes.c_double()
+        self._check(self._L.qhfpe_equilibrate(self._h, n_steps, ctypes.byref(res)))
+        return res.value
+
+    def set_equilibrium(self, W):
+        W = _c128(W)
+        assert W.shape == self.shape
+        self._check(self._L.qhfpe_set_equilibrium(self._h, _ptr(W), 0))
+
+    # ---- response functions and spectra ----------------------------------------------------------
+    def linear_response(self, n_t3):
+        out = np.zeros(n_t3 + 1, dtype=np.complex128)
+        sch = Schedule(LINEAR, 0, 0, 0, None, n_t3, 0)
+        self._check(self._L.qhfpe_response(self._h, ctypes.byref(sch), _ptr(out)))
+        return out
+
+    def third_order_response(self, n_t1, t1_stride, t2_steps, n_t3, split_pathways=False):
+        t2 = np.ascontiguousarray(t2_steps, dtype=np.int32)
+        paths = 2 if split_pathways else 1
+        out = np.zeros((paths, len(t2), n_t1, n_t3 + 1), dtype=np.complex128)
+        sch = Schedule(THIRD_ORDER, n_t1, t1_stride, len(t2), t2.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
+                       n_t3, int(bool(split_pathways)))
+        self._check(self._L.qhfpe_response(self._h, ctypes.byref(sch), _ptr(out)))
+        return out if split_pathways else out[0]
+
+    def spectrum_absorption(self, R1, dt, omega):
+        R1 = _c128(R1)
+        om = np.ascontiguousarray(omega, dtype=np.float64)
+        out = np.zeros(len(om))
+        self._check(self._L.qhfpe_spectrum_absorption(self._h, _ptr(R1), len(R1), dt, _ptr(om), len(om), _ptr(out)))
+        return out
+
+    def spectrum_2d(self, R3, dt1, dt3, omega1, omega3):
+        R3 = _c128(R3)
+        w1 = np.ascontiguousarray(omega1, dtype=np.float64)
+        w3 = np.ascontiguousarray(omega3, dtype=np.float64)
+        nr = np.zeros((len(w3), len(w1)))
+        re = np.zeros((len(w3), len(w1)))
+        self._check(self._L.qhfpe_spectrum_2d(self._h, _ptr(R3), R3.shape[0], R3.shape[1] - 1, dt1, dt3, _ptr(w1),
+                                              len(w1), _ptr(w3), len(w3), _ptr(nr), _ptr(re)))
+        return nr, re, nr + re
+
+    # ---- measurement -----------------------------------------------------------------------------
+    def kernel_timing(self, enable):
+        self._check(self._L.qhfpe_kernel_timing(self._h, int(bool(enable))))
+
+    def kernel_timing_read(self):
+        n = (ctypes.c_long * 3)()
+        ms = (ctypes.c_double * 3)()
+        self._check(self._L.qhfpe_kernel_timing_read(self._h, n, ms, 3))
+        names = ("stage", "potential", "aux")
+        return {names[k]: (n[k], ms[k]) for k in range(3)}

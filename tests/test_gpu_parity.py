@@ -1,0 +1,234 @@
+"""Parity of the CUDA library (through the C ABI) with the FP64 CPU oracle, element by element.
+
+Tolerances: FP64 form 1e-10 relative L2 on states, traces, responses and spectra (the oracle uses
+classic RK4 and direct circulant sums, the library the Horner form and FFTs, so only rounding order
+differs); mixed forms 1e-4 on responses (the accuracy target for the reduced-precision forms) and
+bounds derived from FP32 rounding on single right-hand-side evaluations.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import qhfpe_inputs as qi
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1706_09590_gb300 as q
+    q.lib()
+
+
+def _P(model, precision="fp64", **kw):
+    from paper_1706_09590_gb300 import Propagator
+    return Propagator(model, qi.u_table(model), precision=precision, **kw)
+
+
+def rel(a, b):
+    return np.linalg.norm(np.ravel(a - b)) / max(np.linalg.norm(np.ravel(b)), 1e-300)
+
+
+def _models():
+    h = qi.harmonic_two_state()  # 32 x 32, depth 3, terminator
+    ph = qi.photoisomerization_two_state(nq=24, n_p=32, depth=3, n_matsubara=2)
+    ph_per = qi.photoisomerization_two_state(nq=13, n_p=16, depth=2, n_matsubara=1)
+    ph_per["periodic_q"] = 1
+    three = qi.three_state(nq=16, n_p=16, depth=2, n_matsubara=1)
+    single = qi.single_state(lambda q: 0.5 * q * q, nq=20, n_p=8, depth=0, closure=1)
+    big_np = qi.harmonic_two_state(nq=6, n_p=512, qr=(-8, 8), pr=(-40, 40), depth=1)
+    return {"harmonic": h, "photoiso": ph, "ragged_periodic": ph_per, "three_state": three, "single": single,
+            "np512": big_np}
+
+
+MODELS = _models()
+TERMS = [1, 2, 4, 8, 16, 31]
+
+
+@pytest.mark.parametrize("name", list(MODELS))
+def test_rhs_terms_fp64(name):
+    m = MODELS[name]
+    O = oracle.Oracle(m)
+    P = _P(m)
+    W = qi.random_state(m, seed=11)
+    P.set_state(W)
+    assert rel(P.get_state(0), W) == 0.0
+    for t in TERMS:
+        ref = O.rhs(W, t)
+        got = P.apply_rhs(0, t)
+        if np.linalg.norm(ref) == 0:
+            assert np.linalg.norm(got) == 0
+        else:
+            assert rel(got, ref) < 1e-12, (name, t, rel(got, ref))
+
+
+@pytest.mark.parametrize("name", ["harmonic", "photoiso", "three_state"])
+def test_rhs_mixed(name):
+    m = MODELS[name]
+    O = oracle.Oracle(m)
+    P = _P(m, "mixed")
+    W = qi.random_state(m, seed=12)
+    P.set_state(W)
+    got = P.get_state(0)
+    # tier 0 is held in FP64, the rest is rounded to FP32
+    assert rel(got[0], W[0]) == 0.0
+    assert rel(got, W) < 1e-7
+    for t in TERMS:
+        ref = O.rhs(P.get_state(0).astype(np.complex64).astype(np.complex128), t)
+        assert rel(P.apply_rhs(0, t), ref) < 2e-5, (name, t)
+
+
+@pytest.mark.parametrize("name", ["harmonic", "photoiso", "three_state", "ragged_periodic"])
+def test_steps_and_traces_fp64(name):
+    m = MODELS[name]
+    O = oracle.Oracle(m)
+    P = _P(m)
+    W = qi.random_state(m, seed=13, hermitian=True)
+    ref_W, ref_tr = O.step(W, 12)
+    P.set_state(W)
+    tr = P.step(12, record_trace=True)[0]
+    assert rel(P.get_state(0), ref_W) < 1e-11
+    assert rel(tr, ref_tr) < 1e-11
+    # chunked graph replays + remainder: 16 + 3 steps equal 19 single steps of the oracle
+    ref_W2, ref_tr2 = O.step(ref_W, 19)
+    tr2 = P.step(19, record_trace=True)[0]
+    assert rel(P.get_state(0), ref_W2) < 1e-11
+    assert rel(tr2, ref_tr2) < 1e-11
+
+
+def test_steps_mixed():
+    m = MODELS["harmonic"]
+    O = oracle.Oracle(m)
+    P = _P(m, "mixed")
+    W = qi.random_state(m, seed=14, hermitian=True)
+    ref_W, ref_tr = O.step(W, 40)
+    P.set_state(W)
+    tr = P.step(40, record_trace=True)[0]
+    assert rel(P.get_state(0)[0], ref_W[0]) < 1e-5
+    assert rel(tr, ref_tr) < 1e-5
+
+
+def test_replicas_independent_and_fork():
+    m = MODELS["photoiso"]
+    O = oracle.Oracle(m)
+    P = _P(m, n_replicas=3)
+    Ws = [qi.random_state(m, seed=20 + r) for r in range(3)]
+    for r, W in enumerate(Ws):
+        P.set_state(W, r)
+    tr = P.step(5, record_trace=True)
+    for r, W in enumerate(Ws):
+        ref_W, ref_tr = O.step(W, 5)
+        assert rel(P.get_state(r), ref_W) < 1e-11
+        assert rel(tr[r], ref_tr) < 1e-11
+    P.fork(1, [0, 2])
+    a = P.get_state(1)
+    assert rel(P.get_state(0), a) == 0 and rel(P.get_state(2), a) == 0
+    # zero steps: only the initial trace
+    tr0 = P.step(0, record_trace=True)
+    assert tr0.shape == (3, 1)
+    assert abs(tr0[1, 0] - O.trace(a)) < 1e-12 * max(1, abs(O.trace(a)))
+
+
+@pytest.mark.parametrize("side", [1, 2, 3])
+def test_dipole(side):
+    m = MODELS["three_state"]
+    O = oracle.Oracle(m)
+    P = _P(m, n_replicas=2)
+    W = qi.random_state(m, seed=30)
+    P.set_state(W, 0)
+    P.set_state(W, 1)
+    P.apply_dipole(side, replicas=[1])
+    assert rel(P.get_state(1), O.apply_dipole(W, side)) < 1e-15
+    assert rel(P.get_state(0), W) == 0
+    t = P.trace()
+    assert abs(t[1] - O.trace(O.apply_dipole(W, side))) < 1e-12 * max(1.0, abs(t[1]))
+
+
+def test_equilibrate_fp64():
+    m = MODELS["harmonic"]
+    O = oracle.Oracle(m)
+    P = _P(m)
+    ref, ref_res = O.equilibrate(300)
+    res = P.equilibrate(300)
+    assert rel(P.get_state(0), ref) < 1e-11
+    assert res == pytest.approx(ref_res, rel=1e-6)
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-10), ("mixed", 1e-4)])
+def test_linear_response(precision, tol):
+    m = MODELS["harmonic"]
+    O = oracle.Oracle(m)
+    Weq, _ = O.equilibrate(400)
+    ref = O.linear_response(Weq, 300)
+    P = _P(m, precision)
+    P.set_equilibrium(Weq)
+    got = P.linear_response(300)
+    assert rel(got, ref) < tol
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-10), ("mixed", 1e-4)])
+def test_third_order_response_split(precision, tol):
+    m = qi.harmonic_two_state(nq=16, n_p=16, depth=2)
+    O = oracle.Oracle(m)
+    Weq, _ = O.equilibrate(100)
+    args = (3, 4, [0, 3, 7], 10)
+    ket = O.third_order_response(Weq, *args, first=oracle.LEFT)
+    bra = O.third_order_response(Weq, *args, first=oracle.RIGHT)
+    P = _P(m, precision)
+    P.set_equilibrium(Weq)
+    got = P.third_order_response(*args, split_pathways=True)
+    assert rel(got[0], ket) < tol
+    assert rel(got[1], bra) < tol
+    full = P.third_order_response(*args, split_pathways=False)
+    assert rel(full, ket + bra) < tol
+    # transient absorption is the n_t1 = 1 schedule
+    tas = P.third_order_response(1, 0, [0, 5], 10)
+    ref_tas = O.third_order_response(Weq, 1, 0, [0, 5], 10)
+    assert rel(tas, ref_tas) < tol
+
+
+def test_spectra():
+    m = MODELS["harmonic"]
+    P = _P(m)
+    rng = np.random.default_rng(3)
+    R1 = rng.normal(size=301) + 1j * rng.normal(size=301)
+    om = np.linspace(-20, 20, 57)
+    assert rel(P.spectrum_absorption(R1, 0.01, om), oracle.absorption(R1, 0.01, om)) < 1e-12
+    R3 = rng.normal(size=(9, 41)) + 1j * rng.normal(size=(9, 41))
+    w1 = np.linspace(-15, 15, 31)
+    w3 = np.linspace(-12, 12, 25)
+    nr, re, corr = P.spectrum_2d(R3, 0.08, 0.01, w1, w3)
+    rnr, rre, rcorr = oracle.two_d(R3, 0.08, 0.01, w1, w3)
+    assert rel(nr, rnr) < 1e-12 and rel(re, rre) < 1e-12 and rel(corr, rcorr) < 1e-12
+
+
+def test_bath_and_hierarchy_match_oracle():
+    for name in ("photoiso", "three_state", "harmonic"):
+        m = MODELS[name]
+        O = oracle.Oracle(m)
+        P = _P(m)
+        assert (P.hierarchy() == O.hierarchy()).all()
+        a, b = P.bath_coefficients(), O.coefficients()
+        for k in ("gamma", "r", "c"):
+            assert np.allclose(a[k], b[k], rtol=1e-14, atol=0)
+        assert a["cdelta"] == pytest.approx(b["cdelta"], rel=1e-12, abs=1e-15)
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("mixed", 2e-5)])
+def test_full_size_rhs(precision, tol):
+    """The benchmark's workload (96 x 128 grid, depth 8, three modes, 165 elements, two states): one
+    full right-hand side in the benchmark's launch configuration against the oracle."""
+    m = qi.photoisomerization_two_state()
+    O = oracle.Oracle(m)
+    P = _P(m, precision)
+    W = qi.random_state(m, seed=40)
+    P.set_state(W)
+    Win = P.get_state(0)
+    if precision != "fp64":
+        Win[1:] = Win[1:].astype(np.complex64).astype(np.complex128)
+    ref = O.rhs(Win)
+    got = P.apply_rhs(0)
+    assert rel(got, ref) < tol
