@@ -173,7 +173,6 @@ def main():
     P = Propagator(m, T, precision=args.precision, stream=stream)
     cells = cells_of(m, P.n_elem)
     W0 = qi.random_state(m, seed=1706 + rank)
-    W0 *= 1e-3  # keep values O(1e-3) so that repeated benchmark steps stay finite
     P.set_state(W0)
 
     def barrier():
