@@ -195,6 +195,29 @@ qhfpe_status qhfpe_spectrum_2d(qhfpe_t *h, const double *R3, int n_t1, int n_t3,
 qhfpe_status qhfpe_kernel_timing(qhfpe_t *h, int enable);
 qhfpe_status qhfpe_kernel_timing_read(qhfpe_t *h, long *launches, double *total_ms, int n_kinds);
 
+/* ---- Potential term without allocation -----------------------------------------------------
+ * No counterpart in the paper: this entry point exists for callers that cannot allocate device
+ * memory -- code running while a stream is captured into a CUDA graph (cudaMalloc cannot be captured),
+ * code with a fixed device-memory budget owned by another allocator, or code that must not
+ * synchronise the device (which cudaMalloc/cudaFree may do).  It needs no handle.
+ *
+ * out_dev = -i [U, W] in Wigner space (the QHFPE_TERM_POTENTIAL part of qhfpe_apply_rhs, FP64) for
+ * n_elem hierarchy elements of one state.  W_dev, out_dev: device, canonical complex128 layout
+ * [n_elem][S][S][nq][np].  U_table_dev: device, [S][S][nq][np+1] as in qhfpe_params.  p_min, p_max:
+ * the p range.  stream: cudaStream_t (NULL: legacy default stream); the call only enqueues work.
+ *
+ * Scratch: a file-scope device array of QHFPE_STATIC_SCRATCH_BYTES (32 MiB) that every GPU which loads
+ * the library holds until the process exits.  Sizes with 7*S*S*nq*np + np doubles above that are
+ * rejected with QHFPE_EINVAL (message in qhfpe_last_error(NULL)); larger n_elem is processed in chunks.
+ * The first call on a device does a one-time set-up on that device (it looks up the array's device
+ * address and raises a kernel attribute), so make the first call before any stream capture.  Every
+ * call shares the one array: calls that overlap on the GPU race.  The call performs no cudaMalloc,
+ * cudaFree or other allocation. */
+#define QHFPE_STATIC_SCRATCH_BYTES (32u * 1024u * 1024u)
+qhfpe_status qhfpe_potential_term_static(int n_states, int nq, int np, double p_min, double p_max,
+                                         const double *U_table_dev, int n_elem, const double *W_dev,
+                                         double *out_dev, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -693,7 +693,7 @@ qhfpe_status qhfpe_destroy(qhfpe_t *h)
 
 const char *qhfpe_last_error(const qhfpe_t *h)
 {
-    if (!h) return g_create_error.c_str();  // a failed create has no handle
+    if (!h) return g_create_error.c_str();  // calls without a handle (failed create, static entry point)
     return h->err.c_str();
 }
 
@@ -1143,4 +1143,6 @@ qhfpe_status qhfpe_kernel_timing_read(qhfpe_t *h, long *launches, double *total_
 }
 
 }  // extern "C"
+
+void qh_set_free_error(const std::string &msg) { g_create_error = msg; }
 

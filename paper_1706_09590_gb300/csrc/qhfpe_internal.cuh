@@ -6,6 +6,8 @@
 #include <stdint.h>
 #include <stddef.h>
 
+#include <string>
+
 #define QH_MAX_MODES 8
 #define QH_MAX_S 4
 
@@ -76,6 +78,9 @@ cudaError_t launch_trace(const GridInfo &g, const T *state, size_t rep_stride, c
 
 cudaError_t launch_advance(TraceSink *sink, cudaStream_t st);
 cudaError_t prepare_potential(size_t smem_bytes_fp64);
+
+// Error text for calls without a handle (failed create, the static-scratch entry point).
+void qh_set_free_error(const std::string &msg);
 
 template <typename T>
 cudaError_t launch_dipole(const GridInfo &g, T *state, double *y0, const int *reps, int n_reps,

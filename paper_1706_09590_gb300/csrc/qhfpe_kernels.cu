@@ -7,6 +7,8 @@
 // y0[rep][j][k][re|im][q][p].
 #include "qhfpe_internal.cuh"
 
+#include <mutex>
+
 namespace {
 
 constexpr int STAGE_THREADS = 256;
@@ -549,13 +551,22 @@ cudaError_t launch_trace(const GridInfo &g, const T *state, size_t rep_stride, c
 
 // Raises the dynamic shared-memory limit of the potential kernels; called at set-up, outside any
 // stream capture.
+// The limit only ever rises (per device), so a later, smaller request cannot undo a larger one.
 cudaError_t prepare_potential(size_t smem_bytes_fp64)
 {
-    cudaError_t err = cudaFuncSetAttribute(pot_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           (int)smem_bytes_fp64);
+    static std::mutex mtx;
+    static size_t configured[64] = {0};
+    int dev = 0;
+    cudaError_t err = cudaGetDevice(&dev);
     if (err != cudaSuccess) return err;
-    return cudaFuncSetAttribute(pot_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)(smem_bytes_fp64 / 2));
+    std::lock_guard<std::mutex> lock(mtx);
+    if (dev >= 0 && dev < 64 && configured[dev] >= smem_bytes_fp64) return cudaSuccess;
+    err = cudaFuncSetAttribute(pot_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes_fp64);
+    if (err != cudaSuccess) return err;
+    err = cudaFuncSetAttribute(pot_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)(smem_bytes_fp64 / 2));
+    if (err == cudaSuccess && dev >= 0 && dev < 64) configured[dev] = smem_bytes_fp64;
+    return err;
 }
 
 cudaError_t launch_advance(TraceSink *sink, cudaStream_t st)

@@ -28,7 +28,7 @@ EXPORTED = [
     "qhfpe_bath_coefficients", "qhfpe_max_stable_dt", "qhfpe_set_state", "qhfpe_get_state", "qhfpe_fork",
     "qhfpe_step", "qhfpe_apply_dipole", "qhfpe_apply_rhs", "qhfpe_trace", "qhfpe_equilibrate",
     "qhfpe_set_equilibrium", "qhfpe_response", "qhfpe_spectrum_absorption", "qhfpe_spectrum_2d",
-    "qhfpe_kernel_timing", "qhfpe_kernel_timing_read",
+    "qhfpe_kernel_timing", "qhfpe_kernel_timing_read", "qhfpe_potential_term_static",
 ]
 
 
@@ -93,6 +93,8 @@ def lib():
                                     ctypes.c_int, vp, ctypes.c_int, vp, vp]
     L.qhfpe_kernel_timing.argtypes = [vp, ctypes.c_int]
     L.qhfpe_kernel_timing_read.argtypes = [vp, ctypes.POINTER(ctypes.c_long), dp, ctypes.c_int]
+    L.qhfpe_potential_term_static.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                              ctypes.c_double, vp, ctypes.c_int, vp, vp, vp]
     for name in EXPORTED:
         if name != "qhfpe_last_error":
             getattr(L, name).restype = st
@@ -116,6 +118,19 @@ def _dev_ptr(t):
             return ctypes.c_void_p(t.data_ptr()), 1
         t = t.numpy()
     return _ptr(t), 0
+
+
+def potential_term_static(U_table_dev, W_dev, out_dev, n_states, nq, np_, p_min, p_max, n_elem, stream=None):
+    """-i[U, W] for n_elem hierarchy elements, all arguments device buffers (torch CUDA tensors or raw
+    pointers), computed without any device allocation (static scratch; see include/qhfpe.h)."""
+    L = lib()
+    ptr = lambda t: ctypes.c_void_p(t.data_ptr() if hasattr(t, "data_ptr") else int(t))
+    sptr = None if stream is None else ctypes.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream")
+                                                       else int(stream))
+    s = L.qhfpe_potential_term_static(n_states, nq, np_, p_min, p_max, ptr(U_table_dev), n_elem, ptr(W_dev),
+                                      ptr(out_dev), sptr)
+    if s != 0:
+        raise QhfpeError(s, L.qhfpe_last_error(None).decode())
 
 
 class Propagator:
