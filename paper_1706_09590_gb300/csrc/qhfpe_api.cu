@@ -121,12 +121,19 @@ struct Model {
     {
         return {tab32, tab32 + tab_n, tab32 + 2 * tab_n, tab32 + 3 * tab_n};
     }
+    bool fused = false;         // fused stage kernel available for (np, S)
+    double *ftab64 = nullptr;   // its tables (digit-reversed order, np twiddles)
+    float *ftab32 = nullptr;
+    FusedTables<double> f64() const { return {ftab64, ftab64 + tab_n, ftab64 + 2 * tab_n, ftab64 + 3 * tab_n}; }
+    FusedTables<float> f32() const { return {ftab32, ftab32 + tab_n, ftab32 + 2 * tab_n, ftab32 + 3 * tab_n}; }
     ~Model()
     {
         if (elems) cudaFree(elems);
         if (mu) cudaFree(mu);
         if (tab64) cudaFree(tab64);
         if (tab32) cudaFree(tab32);
+        if (ftab64) cudaFree(ftab64);
+        if (ftab32) cudaFree(ftab32);
     }
 };
 
@@ -220,12 +227,14 @@ cudaError_t dalloc(T **p, size_t n)
     return cudaMalloc((void **)p, n * sizeof(T) + 16);
 }
 
-// Potential tables (Eq. (quantum-liouvillian) in r-space) for FFT output order, pre-scaled by 1/np.
-void build_tables(const Model &M, const double *U, std::vector<double> &out)
+// Potential tables (Eq. (quantum-liouvillian) in r-space) for an FFT's output order, pre-scaled by
+// 1/np.  freq(pos) gives the frequency index sitting at position pos; n_tw twiddles e^{2 pi i t/np}.
+template <typename F>
+void build_tables(const Model &M, const double *U, std::vector<double> &out, F freq, int n_tw)
 {
     const int S = M.S, nq = M.nq, N = M.np;
     const size_t n = (size_t)S * S * nq * N;
-    out.assign(3 * n + N, 0.0);
+    out.assign(3 * n + 2 * n_tw, 0.0);
     auto T = [&](int j, int k, int i, int t) { return U[(((size_t)j * S + k) * nq + i) * (N + 1) + t]; };
     auto UL = [&](int j, int s, int i, int m) {
         return m == -N / 2 ? 0.5 * (T(j, s, i, 0) + T(j, s, i, N)) : T(j, s, i, m + N / 2);
@@ -237,14 +246,14 @@ void build_tables(const Model &M, const double *U, std::vector<double> &out)
         for (int k = 0; k < S; ++k)
             for (int i = 0; i < nq; ++i)
                 for (int pos = 0; pos < N; ++pos) {
-                    const int kk = (int)bitrev((unsigned)pos, M.log2np);
+                    const int kk = freq(pos);
                     const int m = kk < N / 2 ? kk : kk - N;
                     const size_t o = (((size_t)j * S + k) * nq + i) * N + pos;
                     out[o] = (UL(j, j, i, m) - UR(k, k, i, m)) / N;
                     out[n + o] = UL(j, k, i, m) / N;
                     out[2 * n + o] = UR(j, k, i, m) / N;
                 }
-    for (int t = 0; t < N / 2; ++t) {
+    for (int t = 0; t < n_tw; ++t) {
         out[3 * n + 2 * t] = std::cos(2.0 * kPi * t / N);
         out[3 * n + 2 * t + 1] = std::sin(2.0 * kPi * t / N);
     }
@@ -315,8 +324,9 @@ qhfpe_status build_model(qhfpe *h, Model &M, int S, const double *U, const doubl
 
     M.mu_host.assign(mu, mu + S * S);
     std::vector<double> tab;
-    build_tables(M, U, tab);
+    build_tables(M, U, tab, [&](int pos) { return (int)bitrev((unsigned)pos, M.log2np); }, p.np / 2);
     M.tab_n = (size_t)S * S * p.nq * p.np;
+    M.fused = fused_supported(p.np, S);
 
     // Gershgorin-type bound of the spectral radius (for qhfpe_max_stable_dt)
     double pmax = std::max(std::fabs(p.p_min), std::fabs(p.p_max));
@@ -355,6 +365,17 @@ qhfpe_status build_model(qhfpe *h, Model &M, int S, const double *U, const doubl
     std::vector<float> tab32(tab.begin(), tab.end());
     QH_CK(h, dalloc(&M.tab32, tab32.size()));
     QH_CK(h, cudaMemcpyAsync(M.tab32, tab32.data(), sizeof(float) * tab32.size(), cudaMemcpyHostToDevice, st));
+    if (M.fused) {
+        std::vector<double> ft;
+        build_tables(M, U, ft, [&](int pos) { return fused_fft_frequency(p.np, pos); }, p.np);
+        QH_CK(h, dalloc(&M.ftab64, ft.size()));
+        QH_CK(h, cudaMemcpyAsync(M.ftab64, ft.data(), sizeof(double) * ft.size(), cudaMemcpyHostToDevice, st));
+        std::vector<float> ft32(ft.begin(), ft.end());
+        QH_CK(h, dalloc(&M.ftab32, ft32.size()));
+        QH_CK(h, cudaMemcpyAsync(M.ftab32, ft32.data(), sizeof(float) * ft32.size(), cudaMemcpyHostToDevice, st));
+        QH_CK(h, (prepare_fused<float, true>(p.np, S)));
+        QH_CK(h, (prepare_fused<double, false>(p.np, S)));
+    }
     QH_CK(h, cudaStreamSynchronize(st));
     return QHFPE_OK;
 }
@@ -436,6 +457,18 @@ qhfpe_status step_once(qhfpe *h, Prop &P, bool record)
     for (int k = 4; k >= 1; --k) {
         T *in = (k == 4) ? y : (k == 3 ? vA : (k == 2 ? vB : vA));
         T *out = (k == 1) ? y : (k == 4 ? vA : (k == 3 ? vB : vA));
+        if (M.fused) {
+            Bracket br(h, QH_KIND_STAGE);
+            if (MIXED)
+                QH_CK(h, (launch_fused<float, true>(P.g, M.elems, M.f32(), (const float *)in, (const float *)y, P.y0,
+                                                   (float *)out, k == 1 ? P.y0 : nullptr, P.dt / k, k == 1 ? 2 : 1,
+                                                   QHFPE_TERM_ALL, 0, P.g.n_rep, st)));
+            else
+                QH_CK(h, (launch_fused<double, false>(P.g, M.elems, M.f64(), (const double *)in, (const double *)y,
+                                                     nullptr, (double *)out, nullptr, P.dt / k, k == 1 ? 2 : 1,
+                                                     QHFPE_TERM_ALL, 0, P.g.n_rep, st)));
+            continue;
+        }
         {
             Bracket br(h, QH_KIND_POT);
             if (MIXED) QH_CK(h, launch_potential<float>(P.g, M.t32(), (const float *)in, (float *)Pt, 0, P.g.n_rep, st));
@@ -848,7 +881,14 @@ qhfpe_status qhfpe_apply_rhs(qhfpe_t *h, int replica, int terms, double *out)
     if (!out || replica < 0 || replica >= P.g.n_rep) return h->fail(QHFPE_EINVAL, "apply_rhs: bad replica or NULL output");
     cudaStream_t st = h->stream;
     const Model &M = *P.m;
-    if (P.mixed) {
+    if (M.fused) {
+        if (P.mixed)
+            QH_CK(h, (launch_fused<float, true>(P.g, M.elems, M.f32(), (const float *)P.y, (const float *)P.y, P.y0,
+                                               (float *)P.vA, nullptr, 0.0, 0, terms, replica, 1, st)));
+        else
+            QH_CK(h, (launch_fused<double, false>(P.g, M.elems, M.f64(), (const double *)P.y, (const double *)P.y,
+                                                 nullptr, (double *)P.vA, nullptr, 0.0, 0, terms, replica, 1, st)));
+    } else if (P.mixed) {
         QH_CK(h, launch_potential<float>(P.g, M.t32(), (const float *)P.y, (float *)P.P, replica, 1, st));
         QH_CK(h, (launch_stage<float, true>(P.g, M.elems, (const float *)P.y, (const float *)P.P, (const float *)P.y,
                                             P.y0, (float *)P.vA, nullptr, 0.0, 0, terms, replica, 1, st)));
@@ -930,10 +970,15 @@ qhfpe_status qhfpe_equilibrate(qhfpe_t *h, long n_steps, double *residual_out)
     r = run_steps(h, *GP, n_steps, nullptr, 0);
     if (r != QHFPE_OK) return r;
     // residual ||L W|| / ||W||
-    QH_CK(h, launch_potential<double>(GP->g, G.t64(), (const double *)GP->y, (double *)GP->P, 0, 1, st));
-    QH_CK(h, (launch_stage<double, false>(GP->g, G.elems, (const double *)GP->y, (const double *)GP->P,
-                                          (const double *)GP->y, nullptr, (double *)GP->vA, nullptr, 0.0, 0,
-                                          QHFPE_TERM_ALL, 0, 1, st)));
+    if (G.fused) {
+        QH_CK(h, (launch_fused<double, false>(GP->g, G.elems, G.f64(), (const double *)GP->y, (const double *)GP->y,
+                                              nullptr, (double *)GP->vA, nullptr, 0.0, 0, QHFPE_TERM_ALL, 0, 1, st)));
+    } else {
+        QH_CK(h, launch_potential<double>(GP->g, G.t64(), (const double *)GP->y, (double *)GP->P, 0, 1, st));
+        QH_CK(h, (launch_stage<double, false>(GP->g, G.elems, (const double *)GP->y, (const double *)GP->P,
+                                              (const double *)GP->y, nullptr, (double *)GP->vA, nullptr, 0.0, 0,
+                                              QHFPE_TERM_ALL, 0, 1, st)));
+    }
     QH_CK(h, launch_norm2((const double *)GP->vA, GP->g.rep_stride, h->scratch, st));
     QH_CK(h, launch_norm2((const double *)GP->y, GP->g.rep_stride, h->scratch + 1, st));
     double nn[2];

@@ -1,0 +1,538 @@
+// Fused right-hand-side stage: one launch evaluates the whole of Eq. (heom) (linear coupling, Sec. II)
+// for a tile of TQ q-rows of one (replica, hierarchy element) -- all S x S electronic blocks, all p --
+// and applies the Horner update of the RK4 step.
+//
+//   phase A  potential term, Eq. (quantum-liouvillian): the tile's p-rows are loaded into shared
+//            memory, transformed by a mixed-radix (8/4/2) in-place FFT (sign +, digit-reversed
+//            output), mixed per r-mode across the S x S blocks with the tables
+//            D = UL_jj - UR_kk, L = UL_js, R = UR_sk (pre-scaled by 1/np, stored in the same
+//            digit-reversed order), multiplied by -i, and transformed back (sign -, natural order).
+//   phase B  one warp per p-row: upwind q-stencil (rows i-3..i+3 through L1/L2), damping and
+//            delta-term, tier-up/-down couplings (neighbour elements' rows), terminator, the
+//            potential term from shared memory, and out = base + h * L.
+//
+// Grid order: the hierarchy element varies fastest, then the replica, then the q-tile, so the blocks
+// in flight cover all elements of a few q-tiles and the neighbour tiers and q-halos they re-read are
+// L2-resident.
+#include "qhfpe_internal.cuh"
+
+namespace {
+
+constexpr int FTHREADS = 256;
+
+template <typename T> struct V2;
+template <> struct V2<float> { using type = float2; };
+template <> struct V2<double> { using type = double2; };
+
+template <typename C> __device__ __forceinline__ C cadd(C a, C b) { return {a.x + b.x, a.y + b.y}; }
+template <typename C> __device__ __forceinline__ C csub(C a, C b) { return {a.x - b.x, a.y - b.y}; }
+template <typename C> __device__ __forceinline__ C cmul(C a, C b) { return {a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x}; }
+template <typename C> __device__ __forceinline__ C cconjmul(C a, C w) { return {a.x * w.x + a.y * w.y, a.y * w.x - a.x * w.y}; }
+// multiply by s*i, s = +1 or -1
+template <int SG, typename C> __device__ __forceinline__ C cmul_si(C a) { return SG > 0 ? C{-a.y, a.x} : C{a.y, -a.x}; }
+
+// In-register DFTs of length 2, 4, 8 with sign SG (y_u = sum_t x_t e^{SG 2 pi i t u / R}), natural order.
+template <int SG, typename C> __device__ __forceinline__ void dft2(C &a, C &b)
+{
+    C t = a;
+    a = cadd(t, b);
+    b = csub(t, b);
+}
+template <int SG, typename C> __device__ __forceinline__ void dft4(C &x0, C &x1, C &x2, C &x3)
+{
+    C t0 = cadd(x0, x2), t1 = csub(x0, x2), t2 = cadd(x1, x3), t3 = cmul_si<SG>(csub(x1, x3));
+    x0 = cadd(t0, t2);
+    x2 = csub(t0, t2);
+    x1 = cadd(t1, t3);
+    x3 = csub(t1, t3);
+}
+template <int SG, typename C> __device__ __forceinline__ void dft8(C *x)
+{
+    using R = decltype(x[0].x);
+    C e0 = x[0], e1 = x[2], e2 = x[4], e3 = x[6];
+    C o0 = x[1], o1 = x[3], o2 = x[5], o3 = x[7];
+    dft4<SG>(e0, e1, e2, e3);
+    dft4<SG>(o0, o1, o2, o3);
+    const R h = (R)0.70710678118654752440;
+    // w8^u, w8 = e^{SG 2 pi i / 8}
+    C w1o = {(o1.x - SG * o1.y) * h, (o1.y + SG * o1.x) * h};    // o1 * (1 + SG i)/sqrt2
+    C w2o = cmul_si<SG>(o2);                                       // o2 * SG i
+    C w3o = {(-o3.x - SG * o3.y) * h, (-o3.y + SG * o3.x) * h};  // o3 * (-1 + SG i)/sqrt2
+    x[0] = cadd(e0, o0);
+    x[4] = csub(e0, o0);
+    x[1] = cadd(e1, w1o);
+    x[5] = csub(e1, w1o);
+    x[2] = cadd(e2, w2o);
+    x[6] = csub(e2, w2o);
+    x[3] = cadd(e3, w3o);
+    x[7] = csub(e3, w3o);
+}
+template <int R, int SG, typename C> __device__ __forceinline__ void dft_small(C *x)
+{
+    if constexpr (R == 2) dft2<SG>(x[0], x[1]);
+    else if constexpr (R == 4) dft4<SG>(x[0], x[1], x[2], x[3]);
+    else dft8<SG>(x);
+}
+
+// Radix sequence (first pass = longest span) for each supported length.
+template <int NP> struct Radices;
+template <> struct Radices<32> { static constexpr int n = 2; static constexpr int r[3] = {8, 4, 1}; };
+template <> struct Radices<64> { static constexpr int n = 2; static constexpr int r[3] = {8, 8, 1}; };
+template <> struct Radices<128> { static constexpr int n = 3; static constexpr int r[3] = {8, 4, 4}; };
+template <> struct Radices<256> { static constexpr int n = 3; static constexpr int r[3] = {8, 8, 4}; };
+
+// One DIF pass (forward, sign +) or DIT pass (inverse, sign -) of radix R at sub-length M over
+// n_tr transforms of length NP stored contiguously in X.
+template <int NP, int R, int M, bool FWD, typename C>
+__device__ __forceinline__ void fft_pass(C *X, int n_tr, const C *__restrict__ tw)
+{
+    constexpr int S = M / R;
+    constexpr int PER = NP / R;
+    const int total = n_tr * PER;
+    for (int b = threadIdx.x; b < total; b += FTHREADS) {
+        const int tr = b / PER, jl = b - tr * PER;
+        const int g = jl / S, j = jl - g * S;
+        C *base = X + tr * NP + g * M + j;
+        C x[R];
+#pragma unroll
+        for (int t = 0; t < R; ++t) x[t] = base[t * S];
+        if (FWD) {
+            dft_small<R, +1>(x);
+#pragma unroll
+            for (int u = 1; u < R; ++u) x[u] = cmul(x[u], tw[(j * u) * (NP / M)]);
+        } else {
+#pragma unroll
+            for (int u = 1; u < R; ++u) x[u] = cconjmul(x[u], tw[(j * u) * (NP / M)]);
+            dft_small<R, -1>(x);
+        }
+#pragma unroll
+        for (int t = 0; t < R; ++t) base[t * S] = x[t];
+    }
+    __syncthreads();
+}
+
+template <int NP, bool FWD, typename C>
+__device__ __forceinline__ void fft_all(C *X, int n_tr, const C *tw)
+{
+    using RD = Radices<NP>;
+    constexpr int R0 = RD::r[0], R1 = RD::r[1], R2 = RD::r[2];
+    constexpr int M0 = NP, M1 = NP / R0, M2 = NP / (R0 * R1);
+    if (FWD) {
+        fft_pass<NP, R0, M0, true>(X, n_tr, tw);
+        fft_pass<NP, R1, M1, true>(X, n_tr, tw);
+        if constexpr (RD::n == 3) fft_pass<NP, R2, M2, true>(X, n_tr, tw);
+    } else {
+        if constexpr (RD::n == 3) fft_pass<NP, R2, M2, false>(X, n_tr, tw);
+        fft_pass<NP, R1, M1, false>(X, n_tr, tw);
+        fft_pass<NP, R0, M0, false>(X, n_tr, tw);
+    }
+}
+
+// VEC consecutive reals (16-byte vector accesses where the size allows; rows are 16-byte aligned)
+template <typename T, int VEC>
+__device__ __forceinline__ void ldv(const T *__restrict__ p, T *out)
+{
+    if constexpr (sizeof(T) * VEC % 16 == 0) {
+#pragma unroll
+        for (int c = 0; c < (int)(sizeof(T) * VEC / 16); ++c) {
+            const float4 q = reinterpret_cast<const float4 *>(p)[c];
+            reinterpret_cast<float4 *>(out)[c] = q;
+        }
+    } else if constexpr (sizeof(T) * VEC == 8) {
+        *reinterpret_cast<float2 *>(out) = *reinterpret_cast<const float2 *>(p);
+    } else {
+#pragma unroll
+        for (int v = 0; v < VEC; ++v) out[v] = p[v];
+    }
+}
+
+template <typename T, int VEC>
+__device__ __forceinline__ void stv(T *p, const T *in)
+{
+    if constexpr (sizeof(T) * VEC % 16 == 0) {
+#pragma unroll
+        for (int c = 0; c < (int)(sizeof(T) * VEC / 16); ++c)
+            reinterpret_cast<float4 *>(p)[c] = reinterpret_cast<const float4 *>(in)[c];
+    } else if constexpr (sizeof(T) * VEC == 8) {
+        *reinterpret_cast<float2 *>(p) = *reinterpret_cast<const float2 *>(in);
+    } else {
+#pragma unroll
+        for (int v = 0; v < VEC; ++v) p[v] = in[v];
+    }
+}
+
+template <typename T, int NP, int S, bool MIXED>
+__global__ void __launch_bounds__(FTHREADS)
+fused_stage_kernel(GridInfo g, const ElemInfo *__restrict__ elems, FusedTables<T> tab, const T *__restrict__ v_in,
+                   const T *y, const double *y0, T *v_out, double *y0_out, double h, int mode, int terms, int rep0,
+                   int n_rep, int tq)
+{
+    using C = typename V2<T>::type;
+    constexpr int S2 = S * S;
+    constexpr int VEC = NP / 32;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C *X = reinterpret_cast<C *>(smem_raw);          // [tq * S2][NP]
+    C *tw = X + (size_t)tq * S2 * NP;                // [NP]
+
+    const int nq = g.nq;
+    const int e = blockIdx.x % g.n_elem;
+    const int rep = rep0 + (blockIdx.x / g.n_elem) % n_rep;
+    const int tile = blockIdx.x / (g.n_elem * n_rep);
+    const int i0 = tile * tq;
+    const int rows = min(tq, nq - i0);
+    const size_t blk = g.blk;
+    const size_t ebase = (size_t)rep * g.rep_stride + (size_t)e * g.elem_stride;
+
+    for (int t = threadIdx.x; t < NP; t += FTHREADS) tw[t] = C{tab.tw[2 * t], tab.tw[2 * t + 1]};
+
+    // ---- phase A: potential term -------------------------------------------------------------
+    const bool want_pot = (terms & 2) != 0;
+    if (want_pot) {
+        for (int idx = threadIdx.x; idx < rows * S2 * NP; idx += FTHREADS) {
+            const int l = idx % NP, rp = idx / NP;
+            const int pr = rp % S2, r = rp / S2;
+            const T *src = v_in + ebase + (size_t)pr * 2 * blk + (size_t)(i0 + r) * NP + l;
+            X[(r * S2 + pr) * NP + l] = C{src[0], src[blk]};
+        }
+        __syncthreads();
+        fft_all<NP, true>(X, rows * S2, tw);
+        for (int idx = threadIdx.x; idx < rows * NP; idx += FTHREADS) {
+            const int pos = idx % NP, r = idx / NP;
+            const int i = i0 + r;
+            C rho[S2];
+#pragma unroll
+            for (int a = 0; a < S2; ++a) rho[a] = X[(r * S2 + a) * NP + pos];
+#pragma unroll
+            for (int j = 0; j < S; ++j)
+#pragma unroll
+                for (int k = 0; k < S; ++k) {
+                    const size_t trow = ((size_t)(j * S + k) * nq + i) * NP + pos;
+                    const T d = tab.D[trow];
+                    C acc = {d * rho[j * S + k].x, d * rho[j * S + k].y};
+#pragma unroll
+                    for (int s = 0; s < S; ++s) {
+                        if (s != j) {
+                            const T u = tab.L[((size_t)(j * S + s) * nq + i) * NP + pos];
+                            acc.x += u * rho[s * S + k].x;
+                            acc.y += u * rho[s * S + k].y;
+                        }
+                        if (s != k) {
+                            const T u = tab.R[((size_t)(s * S + k) * nq + i) * NP + pos];
+                            acc.x -= u * rho[j * S + s].x;
+                            acc.y -= u * rho[j * S + s].y;
+                        }
+                    }
+                    X[(r * S2 + j * S + k) * NP + pos] = C{acc.y, -acc.x};  // times -i
+                }
+        }
+        __syncthreads();
+        fft_all<NP, false>(X, rows * S2, tw);
+    }
+
+    // ---- phase B: one warp per p-row ------------------------------------------------------------
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const ElemInfo &E = elems[e];
+    const T inv12dp = (T)(1.0 / (12.0 * g.dp));
+    const T fkin = (T)(1.0 / (60.0 * g.dq));
+    const bool term = (terms & 8) && E.terminator;
+    const T cpp = ((terms & 4) ? (T)g.cdelta : (T)0) + (term ? (T)g.term_c0 : (T)0);
+    const int l0 = lane * VEC;
+    T pcol[VEC];
+#pragma unroll
+    for (int v = 0; v < VEC; ++v) pcol[v] = (T)(g.p_min + (l0 + v) * g.dp);
+
+    for (int rp = warp; rp < rows * S2; rp += FTHREADS / 32) {
+        const int pr = rp % S2, r = rp / S2;
+        const int i = i0 + r;
+        const size_t poff = ebase + (size_t)pr * 2 * blk;
+        const T *Vre = v_in + poff, *Vim = Vre + blk;
+        T ar[VEC], ai[VEC];
+#pragma unroll
+        for (int v = 0; v < VEC; ++v) ar[v] = ai[v] = (T)0;
+
+        // -p dW/dq, 5th-order upwind (Sec. III): coefficients for offsets -3..+3 by the sign of p
+        if (terms & 1) {
+            const T cneg[7] = {0, 3, -30, -20, 60, -15, 2};   // p < 0: offsets -3..+3
+            const T cpos[7] = {-2, 15, -60, 20, 30, -3, 0};   // p >= 0
+            T kr[VEC], ki[VEC];
+#pragma unroll
+            for (int v = 0; v < VEC; ++v) kr[v] = ki[v] = (T)0;
+#pragma unroll
+            for (int d = -3; d <= 3; ++d) {
+                int ii = i + d;
+                if (ii < 0 || ii >= nq) {
+                    if (!g.periodic_q) continue;
+                    ii = ii < 0 ? ii + nq : ii - nq;
+                }
+                T rr[VEC], ri[VEC];
+                ldv<T, VEC>(Vre + (size_t)ii * NP + l0, rr);
+                ldv<T, VEC>(Vim + (size_t)ii * NP + l0, ri);
+#pragma unroll
+                for (int v = 0; v < VEC; ++v) {
+                    const T c = pcol[v] < (T)0 ? cneg[d + 3] : cpos[d + 3];
+                    kr[v] += c * rr[v];
+                    ki[v] += c * ri[v];
+                }
+            }
+#pragma unroll
+            for (int v = 0; v < VEC; ++v) {
+                ar[v] -= pcol[v] * fkin * kr[v];
+                ai[v] -= pcol[v] * fkin * ki[v];
+            }
+        }
+        // own row (center) for damping / delta-term / terminator
+        T wr[VEC], wi[VEC];
+        ldv<T, VEC>(Vre + (size_t)i * NP + l0, wr);
+        ldv<T, VEC>(Vim + (size_t)i * NP + l0, wi);
+        if (terms & 4) {
+#pragma unroll
+            for (int v = 0; v < VEC; ++v) {
+                ar[v] -= (T)E.ngam * wr[v];
+                ai[v] -= (T)E.ngam * wi[v];
+            }
+        }
+        // G = sum_up W^(n+e_k) + sum_dn wc W^(n-e_k) [+ r_0 p W at the terminator]; d/dp of G below
+        T gr[VEC], gi[VEC];
+        bool have_g = false;
+#pragma unroll
+        for (int v = 0; v < VEC; ++v) gr[v] = gi[v] = (T)0;
+        const size_t rowoff = (size_t)rep * g.rep_stride + (size_t)pr * 2 * blk + (size_t)i * NP + l0;
+        if (terms & 8) {
+            for (int a = 0; a < E.n_up; ++a) {
+                const T *u = v_in + rowoff + (size_t)E.up[a] * g.elem_stride;
+                T xr[VEC], xi[VEC];
+                ldv<T, VEC>(u, xr);
+                ldv<T, VEC>(u + blk, xi);
+#pragma unroll
+                for (int v = 0; v < VEC; ++v) {
+                    gr[v] += xr[v];
+                    gi[v] += xi[v];
+                }
+                have_g = true;
+            }
+            if (term) {
+                const T r0 = (T)g.term_r0;
+#pragma unroll
+                for (int v = 0; v < VEC; ++v) {
+                    gr[v] += r0 * pcol[v] * wr[v];
+                    gi[v] += r0 * pcol[v] * wi[v];
+                }
+                have_g = true;
+            }
+        }
+        if (terms & 16) {
+            for (int a = 0; a < E.n_dn; ++a) {
+                const T *dd = v_in + rowoff + (size_t)E.dn[a] * g.elem_stride;
+                const T wc = (T)E.wc[a], wrr = (T)E.wr[a];
+                T xr[VEC], xi[VEC];
+                ldv<T, VEC>(dd, xr);
+                ldv<T, VEC>(dd + blk, xi);
+#pragma unroll
+                for (int v = 0; v < VEC; ++v) {
+                    gr[v] += wc * xr[v];
+                    gi[v] += wc * xi[v];
+                    ar[v] += wrr * pcol[v] * xr[v];
+                    ai[v] += wrr * pcol[v] * xi[v];
+                }
+                have_g = true;
+            }
+        }
+        // neighbours along p (periodic) through the warp: ext[k] = value at l0 - 2 + k
+        auto stencil = [&](const T *xr, const T *xi, T *er, T *ei) {
+#pragma unroll
+            for (int v = 0; v < VEC; ++v) {
+                er[v + 2] = xr[v];
+                ei[v + 2] = xi[v];
+            }
+            if constexpr (VEC >= 2) {
+                const int left = (lane + 31) & 31, right = (lane + 1) & 31;
+                er[0] = __shfl_sync(0xffffffffu, xr[VEC - 2], left);
+                er[1] = __shfl_sync(0xffffffffu, xr[VEC - 1], left);
+                ei[0] = __shfl_sync(0xffffffffu, xi[VEC - 2], left);
+                ei[1] = __shfl_sync(0xffffffffu, xi[VEC - 1], left);
+                er[VEC + 2] = __shfl_sync(0xffffffffu, xr[0], right);
+                er[VEC + 3] = __shfl_sync(0xffffffffu, xr[1], right);
+                ei[VEC + 2] = __shfl_sync(0xffffffffu, xi[0], right);
+                ei[VEC + 3] = __shfl_sync(0xffffffffu, xi[1], right);
+            } else {
+                er[0] = __shfl_sync(0xffffffffu, xr[0], (lane + 30) & 31);
+                er[1] = __shfl_sync(0xffffffffu, xr[0], (lane + 31) & 31);
+                er[3] = __shfl_sync(0xffffffffu, xr[0], (lane + 1) & 31);
+                er[4] = __shfl_sync(0xffffffffu, xr[0], (lane + 2) & 31);
+                ei[0] = __shfl_sync(0xffffffffu, xi[0], (lane + 30) & 31);
+                ei[1] = __shfl_sync(0xffffffffu, xi[0], (lane + 31) & 31);
+                ei[3] = __shfl_sync(0xffffffffu, xi[0], (lane + 1) & 31);
+                ei[4] = __shfl_sync(0xffffffffu, xi[0], (lane + 2) & 31);
+            }
+        };
+        if (have_g) {  // uniform across the warp (same element)
+            T er[VEC + 4], ei[VEC + 4];
+            stencil(gr, gi, er, ei);
+#pragma unroll
+            for (int v = 0; v < VEC; ++v) {
+                ar[v] += inv12dp * (er[v] - (T)8 * er[v + 1] + (T)8 * er[v + 3] - er[v + 4]);
+                ai[v] += inv12dp * (ei[v] - (T)8 * ei[v + 1] + (T)8 * ei[v + 3] - ei[v + 4]);
+            }
+        }
+        if (cpp != (T)0) {
+            T er[VEC + 4], ei[VEC + 4];
+            stencil(wr, wi, er, ei);
+            const T f = cpp * inv12dp / (T)g.dp;
+#pragma unroll
+            for (int v = 0; v < VEC; ++v) {
+                ar[v] += f * (-er[v] + (T)16 * er[v + 1] - (T)30 * er[v + 2] + (T)16 * er[v + 3] - er[v + 4]);
+                ai[v] += f * (-ei[v] + (T)16 * ei[v + 1] - (T)30 * ei[v + 2] + (T)16 * ei[v + 3] - ei[v + 4]);
+            }
+        }
+        if (want_pot) {
+            const C *pp = X + (r * S2 + pr) * NP + l0;
+#pragma unroll
+            for (int v = 0; v < VEC; ++v) {
+                ar[v] += pp[v].x;
+                ai[v] += pp[v].y;
+            }
+        }
+        // ---- update -------------------------------------------------------------------------------
+        const size_t o = poff + (size_t)i * NP + l0;
+        if (mode == 0) {
+            stv<T, VEC>(v_out + o, ar);
+            stv<T, VEC>(v_out + o + blk, ai);
+        } else if (MIXED && e == 0) {
+            const size_t o0 = (size_t)rep * g.tier0_rep_stride + (size_t)pr * 2 * blk + (size_t)i * NP + l0;
+#pragma unroll
+            for (int v = 0; v < VEC; ++v) {
+                const double nr = y0[o0 + v] + h * (double)ar[v];
+                const double ni = y0[o0 + v + blk] + h * (double)ai[v];
+                v_out[o + v] = (T)nr;
+                v_out[o + v + blk] = (T)ni;
+                if (mode == 2) {
+                    y0_out[o0 + v] = nr;
+                    y0_out[o0 + v + blk] = ni;
+                }
+            }
+        } else {
+            const T hh = (T)h;
+            T br[VEC], bi[VEC];
+            ldv<T, VEC>(y + o, br);
+            ldv<T, VEC>(y + o + blk, bi);
+#pragma unroll
+            for (int v = 0; v < VEC; ++v) {
+                br[v] += hh * ar[v];
+                bi[v] += hh * ai[v];
+            }
+            stv<T, VEC>(v_out + o, br);
+            stv<T, VEC>(v_out + o + blk, bi);
+        }
+    }
+}
+
+template <typename T, int NP, int S, bool MIXED>
+cudaError_t launch_fused_t(const GridInfo &g, const ElemInfo *elems, const FusedTables<T> &tab, const T *v_in,
+                           const T *y, const double *y0, T *v_out, double *y0_out, double h, int mode, int terms,
+                           int rep0, int n_rep, cudaStream_t st)
+{
+    const int tq = fused_rows_per_tile(NP, S, sizeof(T));
+    const size_t smem = ((size_t)tq * S * S * NP + NP) * 2 * sizeof(T);
+    const int tiles = (g.nq + tq - 1) / tq;
+    const long blocks = (long)tiles * n_rep * g.n_elem;
+    if (blocks <= 0) return cudaSuccess;
+    fused_stage_kernel<T, NP, S, MIXED><<<(unsigned)blocks, FTHREADS, smem, st>>>(
+        g, elems, tab, v_in, y, y0, v_out, y0_out, h, mode, terms, rep0, n_rep, tq);
+    return cudaGetLastError();
+}
+
+template <typename T, int NP, int S, bool MIXED>
+cudaError_t prepare_fused_t()
+{
+    const int tq = fused_rows_per_tile(NP, S, sizeof(T));
+    const size_t smem = ((size_t)tq * S * S * NP + NP) * 2 * sizeof(T);
+    return cudaFuncSetAttribute(fused_stage_kernel<T, NP, S, MIXED>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)smem);
+}
+
+}  // namespace
+
+int fused_rows_per_tile(int np, int S, int elem_bytes)
+{
+    // keep the shared-memory tile near 32 KB (FP32) so that several blocks fit per SM
+    const int budget = 32 * 1024 * (elem_bytes == 8 ? 2 : 1);
+    int tq = budget / (S * S * np * 2 * elem_bytes);
+    if (tq < 1) tq = 1;
+    if (tq > 16) tq = 16;
+    return tq;
+}
+
+bool fused_supported(int np, int S) { return (np == 32 || np == 64 || np == 128 || np == 256) && S >= 1 && S <= 3; }
+
+template <typename T, bool MIXED>
+cudaError_t launch_fused(const GridInfo &g, const ElemInfo *elems, const FusedTables<T> &tab, const T *v_in,
+                         const T *y, const double *y0, T *v_out, double *y0_out, double h, int mode, int terms,
+                         int rep0, int n_rep, cudaStream_t st)
+{
+#define QH_CALL(T_, NP_, S_, M_) launch_fused_t<T_, NP_, S_, M_>(g, elems, tab, v_in, y, y0, v_out, y0_out, h, mode, terms, rep0, n_rep, st)
+    switch (g.np * 8 + g.S) {
+    case 32 * 8 + 1: return QH_CALL(T, 32, 1, MIXED);
+    case 32 * 8 + 2: return QH_CALL(T, 32, 2, MIXED);
+    case 32 * 8 + 3: return QH_CALL(T, 32, 3, MIXED);
+    case 64 * 8 + 1: return QH_CALL(T, 64, 1, MIXED);
+    case 64 * 8 + 2: return QH_CALL(T, 64, 2, MIXED);
+    case 64 * 8 + 3: return QH_CALL(T, 64, 3, MIXED);
+    case 128 * 8 + 1: return QH_CALL(T, 128, 1, MIXED);
+    case 128 * 8 + 2: return QH_CALL(T, 128, 2, MIXED);
+    case 128 * 8 + 3: return QH_CALL(T, 128, 3, MIXED);
+    case 256 * 8 + 1: return QH_CALL(T, 256, 1, MIXED);
+    case 256 * 8 + 2: return QH_CALL(T, 256, 2, MIXED);
+    case 256 * 8 + 3: return QH_CALL(T, 256, 3, MIXED);
+    default: return cudaErrorInvalidValue;
+    }
+#undef QH_CALL
+}
+
+template <typename T, bool MIXED>
+cudaError_t prepare_fused(int np, int S)
+{
+    switch (np * 8 + S) {
+    case 32 * 8 + 1: return prepare_fused_t<T, 32, 1, MIXED>();
+    case 32 * 8 + 2: return prepare_fused_t<T, 32, 2, MIXED>();
+    case 32 * 8 + 3: return prepare_fused_t<T, 32, 3, MIXED>();
+    case 64 * 8 + 1: return prepare_fused_t<T, 64, 1, MIXED>();
+    case 64 * 8 + 2: return prepare_fused_t<T, 64, 2, MIXED>();
+    case 64 * 8 + 3: return prepare_fused_t<T, 64, 3, MIXED>();
+    case 128 * 8 + 1: return prepare_fused_t<T, 128, 1, MIXED>();
+    case 128 * 8 + 2: return prepare_fused_t<T, 128, 2, MIXED>();
+    case 128 * 8 + 3: return prepare_fused_t<T, 128, 3, MIXED>();
+    case 256 * 8 + 1: return prepare_fused_t<T, 256, 1, MIXED>();
+    case 256 * 8 + 2: return prepare_fused_t<T, 256, 2, MIXED>();
+    case 256 * 8 + 3: return prepare_fused_t<T, 256, 3, MIXED>();
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+// Position -> frequency index of the in-place mixed-radix DIF above: the pass with radix R_a at
+// sub-length M_a writes its output digit u_a at stride M_a / R_a, and that digit is the frequency's
+// a-th mixed-radix digit (weight R_0 ... R_{a-1}).
+int fused_fft_frequency(int np, int pos)
+{
+    int radix[3], n = 0;
+    switch (np) {
+    case 32: radix[0] = 8; radix[1] = 4; n = 2; break;
+    case 64: radix[0] = 8; radix[1] = 8; n = 2; break;
+    case 128: radix[0] = 8; radix[1] = 4; radix[2] = 4; n = 3; break;
+    case 256: radix[0] = 8; radix[1] = 8; radix[2] = 4; n = 3; break;
+    default: return -1;
+    }
+    int k = 0, weight = 1, span = np;
+    for (int a = 0; a < n; ++a) {
+        const int stride = span / radix[a];
+        const int u = (pos / stride) % radix[a];
+        k += u * weight;
+        weight *= radix[a];
+        span = stride;
+    }
+    return k;
+}
+
+template cudaError_t launch_fused<float, true>(const GridInfo &, const ElemInfo *, const FusedTables<float> &, const float *, const float *, const double *, float *, double *, double, int, int, int, int, cudaStream_t);
+template cudaError_t launch_fused<double, false>(const GridInfo &, const ElemInfo *, const FusedTables<double> &, const double *, const double *, const double *, double *, double *, double, int, int, int, int, cudaStream_t);
+template cudaError_t prepare_fused<float, true>(int, int);
+template cudaError_t prepare_fused<double, false>(int, int);

@@ -52,6 +52,14 @@ struct PotTables {
     const T *tw;   // twiddles (cos, sin)(2 pi k / np), k < np/2, interleaved
 };
 
+// Tables of the fused stage kernel: same D, L, R as PotTables but in the fused FFT's
+// digit-reversed order (fused_fft_frequency), and np twiddles e^{2 pi i t/np}, t < np.
+template <typename T>
+struct FusedTables {
+    const T *D, *L, *R;
+    const T *tw;
+};
+
 // Device-side trace sink: trace kernel writes slot `counter` of every replica then the counter
 // advances; keeps captured graphs independent of the call's output length.
 struct TraceSink {
@@ -78,6 +86,17 @@ cudaError_t launch_trace(const GridInfo &g, const T *state, size_t rep_stride, c
 
 cudaError_t launch_advance(TraceSink *sink, cudaStream_t st);
 cudaError_t prepare_potential(size_t smem_bytes_fp64);
+
+// ---- fused stage (qhfpe_fused.cu) -------------------------------------------------------------------
+bool fused_supported(int np, int S);
+int fused_rows_per_tile(int np, int S, int elem_bytes);
+int fused_fft_frequency(int np, int pos);
+template <typename T, bool MIXED>
+cudaError_t launch_fused(const GridInfo &g, const ElemInfo *elems, const FusedTables<T> &tab, const T *v_in,
+                         const T *y, const double *y0, T *v_out, double *y0_out, double h, int mode, int terms,
+                         int rep0, int n_rep, cudaStream_t st);
+template <typename T, bool MIXED>
+cudaError_t prepare_fused(int np, int S);
 
 // Error text for calls without a handle (failed create, the static-scratch entry point).
 void qh_set_free_error(const std::string &msg);

@@ -85,7 +85,7 @@ def _excited_anharmonic(q):
 
 
 def photoisomerization_two_state(nq=96, n_p=128, qr=(-10.0, 10.0), pr=(-16.0, 16.0), coupling=0.5,
-                                 eta=1.0, gamma=1.0, beta=1.0, n_matsubara=2, depth=8, dt=2.5e-3):
+                                 eta=1.0, gamma=1.0, beta=1.0, n_matsubara=2, depth=8, dt=1.6e-3):
     """Quartic double-well ground state (barrier 5, wells at +-4) and a displaced anharmonic excited
     well crossing it at q = 0; constant diabatic coupling; Drude bath with K Matsubara terms and the
     delta-term; surfaces continued linearly outside the q box."""
@@ -100,7 +100,7 @@ def photoisomerization_two_state(nq=96, n_p=128, qr=(-10.0, 10.0), pr=(-16.0, 16
 
 
 def three_state(nq=256, n_p=256, qr=(-10.0, 10.0), pr=(-16.0, 16.0), coupling=0.5, eta=1.0, gamma=2.0,
-                beta=0.5, n_matsubara=2, depth=10, dt=1.5e-3):
+                beta=0.5, n_matsubara=2, depth=10, dt=6.5e-4):
     """Ground double well plus two excited anharmonic wells (the second shifted by +1 in q and +2 in
     energy) with pairwise couplings forming an avoided crossing; mu_0j = mu_j0 = 1 for the excited
     states and 0 between them."""
