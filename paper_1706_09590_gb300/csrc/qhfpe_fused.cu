@@ -81,6 +81,10 @@ template <> struct Radices<64> { static constexpr int n = 2; static constexpr in
 template <> struct Radices<128> { static constexpr int n = 3; static constexpr int r[3] = {8, 4, 4}; };
 template <> struct Radices<256> { static constexpr int n = 3; static constexpr int r[3] = {8, 8, 4}; };
 
+// Shared-memory index with one padding slot per 16 complex values (breaks the power-of-two strides of
+// the FFT passes across banks).
+__device__ __forceinline__ int pad16(int i) { return i + (i >> 4); }
+
 // One DIF pass (forward, sign +) or DIT pass (inverse, sign -) of radix R at sub-length M over
 // n_tr transforms of length NP stored contiguously in X.
 template <int NP, int R, int M, bool FWD, typename C>
@@ -92,10 +96,10 @@ __device__ __forceinline__ void fft_pass(C *X, int n_tr, const C *__restrict__ t
     for (int b = threadIdx.x; b < total; b += FTHREADS) {
         const int tr = b / PER, jl = b - tr * PER;
         const int g = jl / S, j = jl - g * S;
-        C *base = X + tr * NP + g * M + j;
+        const int base = tr * NP + g * M + j;
         C x[R];
 #pragma unroll
-        for (int t = 0; t < R; ++t) x[t] = base[t * S];
+        for (int t = 0; t < R; ++t) x[t] = X[pad16(base + t * S)];
         if (FWD) {
             dft_small<R, +1>(x);
 #pragma unroll
@@ -106,7 +110,7 @@ __device__ __forceinline__ void fft_pass(C *X, int n_tr, const C *__restrict__ t
             dft_small<R, -1>(x);
         }
 #pragma unroll
-        for (int t = 0; t < R; ++t) base[t * S] = x[t];
+        for (int t = 0; t < R; ++t) X[pad16(base + t * S)] = x[t];
     }
     __syncthreads();
 }
@@ -162,7 +166,7 @@ __device__ __forceinline__ void stv(T *p, const T *in)
 }
 
 template <typename T, int NP, int S, bool MIXED>
-__global__ void __launch_bounds__(FTHREADS)
+__global__ void __launch_bounds__(FTHREADS, sizeof(T) == 4 ? 3 : 1)
 fused_stage_kernel(GridInfo g, const ElemInfo *__restrict__ elems, FusedTables<T> tab, const T *__restrict__ v_in,
                    const T *y, const double *y0, T *v_out, double *y0_out, double h, int mode, int terms, int rep0,
                    int n_rep, int tq)
@@ -171,8 +175,8 @@ fused_stage_kernel(GridInfo g, const ElemInfo *__restrict__ elems, FusedTables<T
     constexpr int S2 = S * S;
     constexpr int VEC = NP / 32;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    C *X = reinterpret_cast<C *>(smem_raw);          // [tq * S2][NP]
-    C *tw = X + (size_t)tq * S2 * NP;                // [NP]
+    C *X = reinterpret_cast<C *>(smem_raw);          // [tq * S2][NP], padded (pad16)
+    C *tw = X + pad16(tq * S2 * NP) + 1;             // [NP]
 
     const int nq = g.nq;
     const int e = blockIdx.x % g.n_elem;
@@ -192,7 +196,7 @@ fused_stage_kernel(GridInfo g, const ElemInfo *__restrict__ elems, FusedTables<T
             const int l = idx % NP, rp = idx / NP;
             const int pr = rp % S2, r = rp / S2;
             const T *src = v_in + ebase + (size_t)pr * 2 * blk + (size_t)(i0 + r) * NP + l;
-            X[(r * S2 + pr) * NP + l] = C{src[0], src[blk]};
+            X[pad16((r * S2 + pr) * NP + l)] = C{src[0], src[blk]};
         }
         __syncthreads();
         fft_all<NP, true>(X, rows * S2, tw);
@@ -201,7 +205,7 @@ fused_stage_kernel(GridInfo g, const ElemInfo *__restrict__ elems, FusedTables<T
             const int i = i0 + r;
             C rho[S2];
 #pragma unroll
-            for (int a = 0; a < S2; ++a) rho[a] = X[(r * S2 + a) * NP + pos];
+            for (int a = 0; a < S2; ++a) rho[a] = X[pad16((r * S2 + a) * NP + pos)];
 #pragma unroll
             for (int j = 0; j < S; ++j)
 #pragma unroll
@@ -222,7 +226,7 @@ fused_stage_kernel(GridInfo g, const ElemInfo *__restrict__ elems, FusedTables<T
                             acc.y -= u * rho[j * S + s].y;
                         }
                     }
-                    X[(r * S2 + j * S + k) * NP + pos] = C{acc.y, -acc.x};  // times -i
+                    X[pad16((r * S2 + j * S + k) * NP + pos)] = C{acc.y, -acc.x};  // times -i
                 }
         }
         __syncthreads();
@@ -240,6 +244,8 @@ fused_stage_kernel(GridInfo g, const ElemInfo *__restrict__ elems, FusedTables<T
     T pcol[VEC];
 #pragma unroll
     for (int v = 0; v < VEC; ++v) pcol[v] = (T)(g.p_min + (l0 + v) * g.dp);
+    const bool neg0 = pcol[0] < (T)0;
+    const bool uni_sign = neg0 == (pcol[VEC - 1] < (T)0);  // one upwind branch for the whole chunk
 
     for (int rp = warp; rp < rows * S2; rp += FTHREADS / 32) {
         const int pr = rp % S2, r = rp / S2;
@@ -267,11 +273,20 @@ fused_stage_kernel(GridInfo g, const ElemInfo *__restrict__ elems, FusedTables<T
                 T rr[VEC], ri[VEC];
                 ldv<T, VEC>(Vre + (size_t)ii * NP + l0, rr);
                 ldv<T, VEC>(Vim + (size_t)ii * NP + l0, ri);
+                if (uni_sign) {
+                    const T c = neg0 ? cneg[d + 3] : cpos[d + 3];
 #pragma unroll
-                for (int v = 0; v < VEC; ++v) {
-                    const T c = pcol[v] < (T)0 ? cneg[d + 3] : cpos[d + 3];
-                    kr[v] += c * rr[v];
-                    ki[v] += c * ri[v];
+                    for (int v = 0; v < VEC; ++v) {
+                        kr[v] += c * rr[v];
+                        ki[v] += c * ri[v];
+                    }
+                } else {
+#pragma unroll
+                    for (int v = 0; v < VEC; ++v) {
+                        const T c = pcol[v] < (T)0 ? cneg[d + 3] : cpos[d + 3];
+                        kr[v] += c * rr[v];
+                        ki[v] += c * ri[v];
+                    }
                 }
             }
 #pragma unroll
@@ -385,11 +400,12 @@ fused_stage_kernel(GridInfo g, const ElemInfo *__restrict__ elems, FusedTables<T
             }
         }
         if (want_pot) {
-            const C *pp = X + (r * S2 + pr) * NP + l0;
+            const int pb = (r * S2 + pr) * NP + l0;
 #pragma unroll
             for (int v = 0; v < VEC; ++v) {
-                ar[v] += pp[v].x;
-                ai[v] += pp[v].y;
+                const C pv = X[pad16(pb + v)];
+                ar[v] += pv.x;
+                ai[v] += pv.y;
             }
         }
         // ---- update -------------------------------------------------------------------------------
@@ -426,13 +442,19 @@ fused_stage_kernel(GridInfo g, const ElemInfo *__restrict__ elems, FusedTables<T
     }
 }
 
+size_t fused_smem_bytes(int tq, int np, int S, int elem_bytes)
+{
+    const int n = tq * S * S * np;
+    return ((size_t)(n + (n >> 4) + 1) + np) * 2 * elem_bytes;
+}
+
 template <typename T, int NP, int S, bool MIXED>
 cudaError_t launch_fused_t(const GridInfo &g, const ElemInfo *elems, const FusedTables<T> &tab, const T *v_in,
                            const T *y, const double *y0, T *v_out, double *y0_out, double h, int mode, int terms,
                            int rep0, int n_rep, cudaStream_t st)
 {
     const int tq = fused_rows_per_tile(NP, S, sizeof(T));
-    const size_t smem = ((size_t)tq * S * S * NP + NP) * 2 * sizeof(T);
+    const size_t smem = fused_smem_bytes(tq, NP, S, sizeof(T));
     const int tiles = (g.nq + tq - 1) / tq;
     const long blocks = (long)tiles * n_rep * g.n_elem;
     if (blocks <= 0) return cudaSuccess;
@@ -445,7 +467,7 @@ template <typename T, int NP, int S, bool MIXED>
 cudaError_t prepare_fused_t()
 {
     const int tq = fused_rows_per_tile(NP, S, sizeof(T));
-    const size_t smem = ((size_t)tq * S * S * NP + NP) * 2 * sizeof(T);
+    const size_t smem = fused_smem_bytes(tq, NP, S, sizeof(T));
     return cudaFuncSetAttribute(fused_stage_kernel<T, NP, S, MIXED>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)smem);
 }

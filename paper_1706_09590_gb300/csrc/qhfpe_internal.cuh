@@ -90,6 +90,7 @@ cudaError_t prepare_potential(size_t smem_bytes_fp64);
 // ---- fused stage (qhfpe_fused.cu) -------------------------------------------------------------------
 bool fused_supported(int np, int S);
 int fused_rows_per_tile(int np, int S, int elem_bytes);
+size_t fused_smem_bytes(int tq, int np, int S, int elem_bytes);
 int fused_fft_frequency(int np, int pos);
 template <typename T, bool MIXED>
 cudaError_t launch_fused(const GridInfo &g, const ElemInfo *elems, const FusedTables<T> &tab, const T *v_in,
