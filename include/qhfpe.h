@@ -127,7 +127,8 @@ qhfpe_status qhfpe_max_stable_dt(const qhfpe_t *h, double *dt_out);
 
 /* Copy a canonical-layout complex128 state into / out of replica `replica` (or every replica when
  * replica = -1 for set_state: the same state is broadcast).  is_device: the pointer is device memory.
- * In the mixed forms the state is rounded to FP32 except the zeroth tier, which stays FP64. */
+ * In the mixed forms the state is rounded to FP32 except the zeroth tier, which stays FP64.
+ * set_state checks the values on the device and returns QHFPE_ENUMERIC on NaN/Inf. */
 qhfpe_status qhfpe_set_state(qhfpe_t *h, int replica, const double *src, int is_device);
 qhfpe_status qhfpe_get_state(qhfpe_t *h, int replica, double *dst, int is_device);
 /* Copy replica src onto each of dst[0..n-1] (host int array). */

@@ -187,6 +187,7 @@ struct qhfpe {
     bool have_eq = false;
     double *scratch = nullptr;
     size_t scratch_cap = 0;
+    int *flag = nullptr;    // device flag for non-finite input checks
     Timing timing;
 
     ~qhfpe()
@@ -195,6 +196,7 @@ struct qhfpe {
         main.reset();
         if (eq) cudaFree(eq);
         if (scratch) cudaFree(scratch);
+        if (flag) cudaFree(flag);
         model.reset();
         ground.reset();
         if (own_stream && stream) cudaStreamDestroy(stream);
@@ -562,10 +564,12 @@ qhfpe_status ensure_scratch(qhfpe *h, size_t bytes)
     return QHFPE_OK;
 }
 
-qhfpe_status set_from_canonical(qhfpe *h, Prop &P, const double *src_dev, int rep, int n_rep)
+qhfpe_status set_from_canonical(qhfpe *h, Prop &P, const double *src_dev, int rep, int n_rep, int *nonfinite = nullptr)
 {
-    if (P.mixed) QH_CK(h, launch_from_canonical<float>(P.g, src_dev, (float *)P.y, P.y0, rep, n_rep, h->stream));
-    else QH_CK(h, launch_from_canonical<double>(P.g, src_dev, (double *)P.y, nullptr, rep, n_rep, h->stream));
+    if (P.mixed)
+        QH_CK(h, launch_from_canonical<float>(P.g, src_dev, (float *)P.y, P.y0, rep, n_rep, h->stream, nonfinite));
+    else
+        QH_CK(h, launch_from_canonical<double>(P.g, src_dev, (double *)P.y, nullptr, rep, n_rep, h->stream, nonfinite));
     return QHFPE_OK;
 }
 
@@ -777,16 +781,20 @@ qhfpe_status qhfpe_set_state(qhfpe_t *h, int replica, const double *src, int is_
     if (!src || replica < -1 || replica >= P.g.n_rep) return h->fail(QHFPE_EINVAL, "set_state: bad replica or NULL source");
     const size_t n = (size_t)P.g.n_elem * P.g.S * P.g.S * P.g.blk;
     const double *dsrc = src;
+    if (!h->flag) QH_CK(h, cudaMalloc((void **)&h->flag, sizeof(int)));
+    QH_CK(h, cudaMemsetAsync(h->flag, 0, sizeof(int), h->stream));
     if (!is_device) {
-        if (!finite_all(src, 2 * n)) return h->fail(QHFPE_ENUMERIC, "set_state: source holds NaN/Inf");
         r = ensure_scratch(h, n * 2 * sizeof(double));
         if (r != QHFPE_OK) return r;
         QH_CK(h, cudaMemcpyAsync(h->scratch, src, n * 2 * sizeof(double), cudaMemcpyHostToDevice, h->stream));
         dsrc = h->scratch;
     }
-    r = set_from_canonical(h, P, dsrc, replica < 0 ? 0 : replica, replica < 0 ? P.g.n_rep : 1);
+    r = set_from_canonical(h, P, dsrc, replica < 0 ? 0 : replica, replica < 0 ? P.g.n_rep : 1, h->flag);
     if (r != QHFPE_OK) return r;
+    int bad = 0;
+    QH_CK(h, cudaMemcpyAsync(&bad, h->flag, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
     QH_CK(h, cudaStreamSynchronize(h->stream));
+    if (bad) return h->fail(QHFPE_ENUMERIC, "set_state: source holds NaN/Inf (the replica now holds it too)");
     return QHFPE_OK;
 }
 

@@ -108,7 +108,7 @@ cudaError_t launch_dipole(const GridInfo &g, T *state, double *y0, const int *re
 
 template <typename T>
 cudaError_t launch_from_canonical(const GridInfo &g, const double *src, T *dst, double *y0_dst, int rep, int n_rep,
-                                  cudaStream_t st);
+                                  cudaStream_t st, int *nonfinite = nullptr);
 template <typename T>
 cudaError_t launch_to_canonical(const GridInfo &g, const T *src, const double *y0_src, double *dst, int rep,
                                 cudaStream_t st);

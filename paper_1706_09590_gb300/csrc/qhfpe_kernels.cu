@@ -386,7 +386,8 @@ __global__ void dipole_kernel(GridInfo g, T *state, double *y0, const int *__res
 
 // canonical complex128 [elem][j][k][q][p]  <->  internal planar layout of one replica
 template <typename T>
-__global__ void from_canonical_kernel(GridInfo g, const double *__restrict__ src, T *dst, double *y0, int rep0)
+__global__ void from_canonical_kernel(GridInfo g, const double *__restrict__ src, T *dst, double *y0, int rep0,
+                                      int *nonfinite)
 {
     const size_t blk = g.blk;
     const size_t per = (size_t)g.n_elem * g.S * g.S * blk;
@@ -395,6 +396,7 @@ __global__ void from_canonical_kernel(GridInfo g, const double *__restrict__ src
         const size_t cell = idx % blk;
         const size_t ep = idx / blk;  // e*S2 + pair
         const double re = src[2 * idx], im = src[2 * idx + 1];
+        if (nonfinite && !(isfinite(re) && isfinite(im))) *nonfinite = 1;
         const size_t o = (size_t)rep * g.rep_stride + ep * 2 * blk + cell;
         dst[o] = (T)re;
         dst[o + blk] = (T)im;
@@ -586,11 +588,11 @@ cudaError_t launch_dipole(const GridInfo &g, T *state, double *y0, const int *re
 
 template <typename T>
 cudaError_t launch_from_canonical(const GridInfo &g, const double *src, T *dst, double *y0_dst, int rep, int n_rep,
-                                  cudaStream_t st)
+                                  cudaStream_t st, int *nonfinite)
 {
     const size_t per = (size_t)g.n_elem * g.S * g.S * g.blk;
     dim3 grid(grid_for(per, 256, 2048), n_rep);
-    from_canonical_kernel<T><<<grid, 256, 0, st>>>(g, src, dst, y0_dst, rep);
+    from_canonical_kernel<T><<<grid, 256, 0, st>>>(g, src, dst, y0_dst, rep, nonfinite);
     return cudaGetLastError();
 }
 
@@ -635,7 +637,7 @@ template cudaError_t launch_stage<float, true>(const GridInfo &, const ElemInfo 
 template cudaError_t launch_trace<double>(const GridInfo &, const double *, size_t, const double *, TraceSink *, int, cudaStream_t);
 template cudaError_t launch_dipole<double>(const GridInfo &, double *, double *, const int *, int, const double *, int, double, cudaStream_t);
 template cudaError_t launch_dipole<float>(const GridInfo &, float *, double *, const int *, int, const double *, int, double, cudaStream_t);
-template cudaError_t launch_from_canonical<double>(const GridInfo &, const double *, double *, double *, int, int, cudaStream_t);
-template cudaError_t launch_from_canonical<float>(const GridInfo &, const double *, float *, double *, int, int, cudaStream_t);
+template cudaError_t launch_from_canonical<double>(const GridInfo &, const double *, double *, double *, int, int, cudaStream_t, int *);
+template cudaError_t launch_from_canonical<float>(const GridInfo &, const double *, float *, double *, int, int, cudaStream_t, int *);
 template cudaError_t launch_to_canonical<double>(const GridInfo &, const double *, const double *, double *, int, cudaStream_t);
 template cudaError_t launch_to_canonical<float>(const GridInfo &, const float *, const double *, double *, int, cudaStream_t);

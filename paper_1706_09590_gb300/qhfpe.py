@@ -212,9 +212,15 @@ class Propagator:
         self._check(self._L.qhfpe_set_state(self._h, replica, _ptr(W), 0))
 
     def get_state(self, replica=0, out=None):
+        """Canonical complex128 state of one replica.  out: optional destination (numpy array, e.g. a
+        view of pinned memory, or a contiguous CUDA tensor of matching size)."""
         if out is not None and hasattr(out, "is_cuda"):
             ptr, dev = _dev_ptr(out)
             self._check(self._L.qhfpe_get_state(self._h, replica, ptr, dev))
+            return out
+        if out is not None:
+            assert out.dtype == np.complex128 and out.flags.c_contiguous and out.size == int(np.prod(self.shape))
+            self._check(self._L.qhfpe_get_state(self._h, replica, _ptr(out), 0))
             return out
         out = np.empty(self.shape, dtype=np.complex128)
         self._check(self._L.qhfpe_get_state(self._h, replica, _ptr(out), 0))

@@ -232,3 +232,16 @@ def test_full_size_rhs(precision, tol):
     ref = O.rhs(Win)
     got = P.apply_rhs(0)
     assert rel(got, ref) < tol
+
+
+def test_set_state_rejects_non_finite():
+    from paper_1706_09590_gb300 import QhfpeError
+    m = MODELS["harmonic"]
+    P = _P(m)
+    W = qi.random_state(m, seed=50)
+    W[1, 0, 1, 3, 4] = np.nan
+    with pytest.raises(QhfpeError) as ei:
+        P.set_state(W)
+    assert ei.value.status == 4
+    P.set_state(qi.random_state(m, seed=51))  # the handle stays usable
+    P.step(1)
