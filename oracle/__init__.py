@@ -34,7 +34,7 @@ class _Params(ctypes.Structure):
         ("eta", ctypes.c_double), ("gamma", ctypes.c_double), ("beta", ctypes.c_double),
         ("n_matsubara", ctypes.c_int), ("high_temperature", ctypes.c_int), ("use_cdelta", ctypes.c_int),
         ("depth", ctypes.c_int), ("closure", ctypes.c_int), ("periodic_q", ctypes.c_int),
-        ("dt", ctypes.c_double),
+        ("dt", ctypes.c_double), ("closure_coef", ctypes.POINTER(ctypes.c_double)),
     ]
 
 
@@ -75,7 +75,9 @@ class Oracle:
     """One model (grid, surfaces, bath, hierarchy) on the CPU.  States are complex128 arrays of shape
     [n_elem][S][S][nq][np] (hierarchy element, ket state, bra state, q, p)."""
 
-    def __init__(self, model, U_table=None, periodic_q=None):
+    def __init__(self, model, U_table=None, periodic_q=None, closure_coef=None):
+        """closure_coef: [nq][np][10] coefficients of the learned closure (closure 2), e.g. from
+        oracle.closure.coefficients."""
         from qhfpe_inputs import u_table
         self.model = model
         self.T = np.ascontiguousarray(U_table if U_table is not None else u_table(model), dtype=np.float64)
@@ -86,7 +88,11 @@ class Oracle:
                           model["p_min"], model["p_max"], self.T.ctypes.data_as(dp), self.mu.ctypes.data_as(dp),
                           model["eta"], model["gamma"], model["beta"], model["n_matsubara"],
                           model["high_temperature"], model["use_cdelta"], model["depth"], model["closure"],
-                          int(per), model["dt"])
+                          int(per), model["dt"], None)
+        if closure_coef is not None:
+            self._coef = np.ascontiguousarray(closure_coef, dtype=np.float64)
+            assert self._coef.shape == (model["nq"], model["np"], 10)
+            self._p.closure_coef = self._coef.ctypes.data_as(dp)
         self._h = lib().oq_create(ctypes.byref(self._p))
         if not self._h:
             raise ValueError("oracle rejected the model parameters")

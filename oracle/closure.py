@@ -1,0 +1,142 @@
+"""Learned hierarchy closure, FP64 reference -- TEST INFRASTRUCTURE ONLY (part of the CPU oracle).
+
+The closure replaces the truncation W^(N+1) = 0 of Eq. (heom) at the deepest tier (one Drude mode,
+K = 0, so the hierarchy is a chain) by a local linear combination of the two tiers below:
+
+    W^(N+1)(q_i, p_l) ~ sum_{b=-2..2} c_b(x) W^N(q_i, p_{l+b}) + c_{5+b}(x) W^(N-1)(q_i, p_{l+b}),
+
+with the ten coefficients c(x) produced by a multilayer perceptron of x = (q/8, p/8, ln eta):
+three tanh hidden layers of width 256 and a linear output of width 10.  The combination is linear in
+the state, so the closed hierarchy keeps the linearity that the response functions of Eqs. (R1), (R3)
+presuppose (the Green's function G(t) is a linear map); the network only sets its coefficients.
+
+Training data are the deep hierarchy's own tiers: for every grid point x the samples
+(phi = the ten patch values of tiers N and N-1, y = tier N+1) from many states are compressed to
+    G_x = sum Re(conj(phi) phi^T)  (10 x 10),  h_x = sum Re(conj(phi) y),  yy_x = sum |y|^2,  n_x,
+so that the mean squared error over all samples is  sum_x (c^T G_x c - 2 c^T h_x + yy_x) / sum_x n_x.
+
+Flat weight layout (row-major): W1[256][3], b1[256], W2[256][256], b2[256], W3[256][256], b3[256],
+W4[10][256], b4[10].  Statistics layout per point: G upper triangle (55, row-major), h (10), yy, n.
+"""
+import numpy as np
+
+N_IN, N_HID, N_OUT = 3, 256, 10
+SHAPES = [(N_HID, N_IN), (N_HID,), (N_HID, N_HID), (N_HID,), (N_HID, N_HID), (N_HID,), (N_OUT, N_HID), (N_OUT,)]
+N_WEIGHTS = int(sum(np.prod(s) for s in SHAPES))
+N_STATS = 55 + 10 + 2
+TRIU = np.triu_indices(10)
+
+
+def unpack(w):
+    out, o = [], 0
+    for s in SHAPES:
+        n = int(np.prod(s))
+        out.append(np.asarray(w[o:o + n], dtype=np.float64).reshape(s))
+        o += n
+    return out
+
+
+def inputs(q, p, eta):
+    """Network input for grid points (q, p) at bath coupling eta: (q/8, p/8, ln eta)."""
+    q, p = np.broadcast_arrays(np.asarray(q, float), np.asarray(p, float))
+    return np.stack([q / 8.0, p / 8.0, np.full(q.shape, np.log(eta))], axis=-1)
+
+
+def init_weights(seed=1706):
+    """Glorot-uniform hidden layers; the output layer starts at zero (closure = truncation)."""
+    rng = np.random.default_rng(seed)
+    parts = []
+    for s in SHAPES:
+        if len(s) == 2 and s[0] != N_OUT:
+            lim = np.sqrt(6.0 / (s[0] + s[1]))
+            parts.append(rng.uniform(-lim, lim, s).ravel())
+        else:
+            parts.append(np.zeros(int(np.prod(s))))
+    return np.concatenate(parts)
+
+
+def forward(w, X):
+    W1, b1, W2, b2, W3, b3, W4, b4 = unpack(w)
+    h1 = np.tanh(X @ W1.T + b1)
+    h2 = np.tanh(h1 @ W2.T + b2)
+    h3 = np.tanh(h2 @ W3.T + b3)
+    c = h3 @ W4.T + b4
+    return c, (X, h1, h2, h3)
+
+
+def _full_G(stats):
+    G = np.zeros(stats.shape[:-1] + (10, 10))
+    G[..., TRIU[0], TRIU[1]] = stats[..., :55]
+    G = G + np.swapaxes(G, -1, -2) - np.eye(10) * G
+    return G
+
+
+def loss(w, X, stats):
+    c, _ = forward(w, X)
+    G = _full_G(stats)
+    h = stats[:, 55:65]
+    q = np.einsum("ni,nij,nj->n", c, G, c) - 2 * np.einsum("ni,ni->n", c, h) + stats[:, 65]
+    return q.sum() / stats[:, 66].sum()
+
+
+def loss_and_grad(w, X, stats):
+    """Mean squared closure error and its gradient with respect to the flat weights (plain backprop)."""
+    W1, b1, W2, b2, W3, b3, W4, b4 = unpack(w)
+    c, (X, h1, h2, h3) = forward(w, X)
+    G = _full_G(stats)
+    h = stats[:, 55:65]
+    ntot = stats[:, 66].sum()
+    q = np.einsum("ni,nij,nj->n", c, G, c) - 2 * np.einsum("ni,ni->n", c, h) + stats[:, 65]
+    L = q.sum() / ntot
+    dc = 2.0 * (np.einsum("nij,nj->ni", G, c) - h) / ntot
+    dW4 = dc.T @ h3
+    db4 = dc.sum(0)
+    dz3 = (dc @ W4) * (1 - h3 ** 2)
+    dW3 = dz3.T @ h2
+    db3 = dz3.sum(0)
+    dz2 = (dz3 @ W3) * (1 - h2 ** 2)
+    dW2 = dz2.T @ h1
+    db2 = dz2.sum(0)
+    dz1 = (dz2 @ W2) * (1 - h1 ** 2)
+    dW1 = dz1.T @ X
+    db1 = dz1.sum(0)
+    return L, np.concatenate([a.ravel() for a in (dW1, db1, dW2, db2, dW3, db3, dW4, db4)])
+
+
+def coefficients(w, model):
+    """[nq][np][10] closure coefficients on the model's grid at its eta."""
+    from qhfpe_inputs import axis
+    q = axis(model["nq"], model["q_min"], model["q_max"])
+    p = axis(model["np"], model["p_min"], model["p_max"])
+    Q, Pm = np.meshgrid(q, p, indexing="ij")
+    c, _ = forward(w, inputs(Q, Pm, model["eta"]))
+    return c
+
+
+def patch_samples(W, tier):
+    """Samples of the closure regression from a K = 0 hierarchy state W ([n_elem][S][S][nq][np],
+    element e = tier e): phi [nq][np][S*S][10] and y [nq][np][S*S] for the target tier `tier`."""
+    n_elem, S, _, nq, n_p = W.shape
+    A = W[tier - 1].reshape(S * S, nq, n_p)
+    B = W[tier - 2].reshape(S * S, nq, n_p) if tier >= 2 else np.zeros_like(A)
+    phi = np.zeros((nq, n_p, S * S, 10), complex)
+    for b in range(-2, 3):
+        phi[..., 2 + b] = np.moveaxis(np.roll(A, -b, axis=-1), 0, -1)
+        phi[..., 7 + b] = np.moveaxis(np.roll(B, -b, axis=-1), 0, -1)
+    y = np.moveaxis(W[tier].reshape(S * S, nq, n_p), 0, -1)
+    return phi, y
+
+
+def statistics(W, tier):
+    """Per-point statistics [nq*np][67] of one state (sum over the electronic pairs)."""
+    phi, y = patch_samples(W, tier)
+    nq, n_p = phi.shape[:2]
+    G = np.einsum("xysa,xysb->xyab", np.conj(phi), phi).real
+    h = np.einsum("xysa,xys->xya", np.conj(phi), y).real
+    yy = (np.abs(y) ** 2).sum(-1)
+    out = np.zeros((nq, n_p, N_STATS))
+    out[..., :55] = G[..., TRIU[0], TRIU[1]]
+    out[..., 55:65] = h
+    out[..., 65] = yy
+    out[..., 66] = phi.shape[2]
+    return out.reshape(nq * n_p, N_STATS)

@@ -61,6 +61,7 @@ typedef struct {
     int closure;           /* 0: truncate, 1: terminator of Eq. (GMFP) */
     int periodic_q;
     double dt;
+    const double *closure_coef; /* closure 2 (learned): [nq][np][10] coefficients, see oq_rhs */
 } oq_params;
 
 typedef struct {
@@ -75,6 +76,7 @@ typedef struct {
     double dq, dp, dr;
     double *qv, *pv;
     cplx *AL, *AR; /* circulant kernels [S][S][nq][np], index d = (l - l') mod np */
+    double *coef;  /* learned-closure coefficients [nq][np][10] (own copy) or NULL */
 } oq_ctx;
 
 /* ------------------------------------------------------------------------------------------------
@@ -186,14 +188,15 @@ void oq_destroy(oq_ctx *C)
 {
     if (!C) return;
     free(C->U); free(C->idx); free(C->up); free(C->dn);
-    free(C->qv); free(C->pv); free(C->AL); free(C->AR);
+    free(C->qv); free(C->pv); free(C->AL); free(C->AR); free(C->coef);
     free(C);
 }
 
 oq_ctx *oq_create(const oq_params *P)
 {
     if (P->S < 1 || P->S > 8 || P->nq < 1 || P->np < 2 || (P->np & 1) || P->depth < 0) return NULL;
-    if (P->closure == 1 && P->n_matsubara != 0) return NULL; /* terminator only given for K = 0 */
+    if ((P->closure == 1 || P->closure == 2) && P->n_matsubara != 0) return NULL; /* K = 0 closures only */
+    if (P->closure == 2 && !P->closure_coef) return NULL;
     oq_ctx *C = (oq_ctx *)calloc(1, sizeof(oq_ctx));
     C->P = *P;
     int S = P->S, nq = P->nq, np = P->np;
@@ -203,6 +206,11 @@ oq_ctx *oq_create(const oq_params *P)
     for (int a = 0; a < S * S; ++a) C->mu[a] = P->mu ? P->mu[a] : 0.0;
     C->P.U_table = C->U;
     C->P.mu = C->mu;
+    if (P->closure == 2) {
+        C->coef = (double *)malloc(sizeof(double) * (size_t)nq * np * 10);
+        memcpy(C->coef, P->closure_coef, sizeof(double) * (size_t)nq * np * 10);
+        C->P.closure_coef = C->coef;
+    }
 
     if (P->n_matsubara < 0 || P->n_matsubara > 30) { oq_destroy(C); return NULL; }
     C->n_modes = P->n_matsubara + 1;
@@ -314,6 +322,29 @@ static cplx dp_central(const oq_ctx *C, const cplx *row, int l, int times_p)
           + 8.0 * Xp(C, row, l + 1, times_p) - Xp(C, row, l + 2, times_p)) / (12.0 * C->dp);
 }
 
+/* Learned closure (K = 0 chain): the truncated element W^(N+1) at column l of row i is read as the
+ * local linear combination  sum_{b=-2..2} c_b(q_i, p_l) W^N(p_{l+b}) + c_{5+b}(q_i, p_l) W^(N-1)(p_{l+b})
+ * (p wrapped periodically; the W^(N-1) part is absent at N = 0). */
+static cplx closure_value(const oq_ctx *C, const cplx *rowN, const cplx *rowNm1, int i, int l)
+{
+    int np = C->P.np;
+    l = ((l % np) + np) % np;
+    const double *c = C->coef + ((size_t)i * np + l) * 10;
+    cplx v = 0.0;
+    for (int b = -2; b <= 2; ++b) {
+        int lb = ((l + b) % np + np) % np;
+        v += c[2 + b] * rowN[lb];
+        if (rowNm1) v += c[7 + b] * rowNm1[lb];
+    }
+    return v;
+}
+
+static cplx dp_closure(const oq_ctx *C, const cplx *rowN, const cplx *rowNm1, int i, int l)
+{
+    return (closure_value(C, rowN, rowNm1, i, l - 2) - 8.0 * closure_value(C, rowN, rowNm1, i, l - 1)
+          + 8.0 * closure_value(C, rowN, rowNm1, i, l + 1) - closure_value(C, rowN, rowNm1, i, l + 2)) / (12.0 * C->dp);
+}
+
 static cplx dpp_central(const oq_ctx *C, const cplx *row, int l)
 {
     return (-Xp(C, row, l - 2, 0) + 16.0 * Xp(C, row, l - 1, 0) - 30.0 * Xp(C, row, l, 0)
@@ -332,6 +363,7 @@ static cplx dpp_central(const oq_ctx *C, const cplx *row, int l)
  * At the deepest tier with the terminator closure (Eq. (GMFP), K = 0), the missing W^(N+1) in the
  * tier-up term is replaced by r_0 p W^N + c_0 dW^N/dp, i.e. the term becomes
  *   d/dp (r_0 p W^N) + c_0 d^2 W^N/dp^2.
+ * With the learned closure (K = 0) it is d/dp of closure_value (see there).
  * State layout: [n_elem][S][S][nq][np] complex.
  * ---------------------------------------------------------------------------------------------- */
 void oq_rhs(const oq_ctx *C, const cplx *W, cplx *dW, int terms)
@@ -381,6 +413,10 @@ void oq_rhs(const oq_ctx *C, const cplx *W, cplx *dW, int terms)
                                     acc += dp_central(C, urow, l, 0);
                                 } else if (P->closure == 1 && tier == P->depth) {
                                     acc += C->r[0] * dp_central(C, row, l, 1) + C->c[0] * dpp_central(C, row, l);
+                                } else if (P->closure == 2 && tier == P->depth) {
+                                    int dn = C->dn[e * M + a];
+                                    const cplx *rowm1 = dn >= 0 ? W + dn * elem + ((size_t)j * S + k) * blk + (size_t)i * np : NULL;
+                                    acc += dp_closure(C, row, rowm1, i, l);
                                 }
                             }
                         }
