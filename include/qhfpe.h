@@ -68,7 +68,7 @@ typedef enum {
 typedef enum {
     QHFPE_TRUNCATE = 0,   /* W^(n + e_k) = 0 beyond the deepest tier */
     QHFPE_TERMINATOR = 1, /* Eq. (GMFP) at the deepest tier; requires n_matsubara = 0 */
-    QHFPE_LEARNED = 2     /* learned closure (see qhfpe_closure_load) */
+    QHFPE_LEARNED = 2     /* learned closure, n_matsubara = 0 (see qhfpe_closure_load) */
 } qhfpe_closure;
 
 typedef enum {
@@ -195,6 +195,46 @@ qhfpe_status qhfpe_spectrum_2d(qhfpe_t *h, const double *R3, int n_t1, int n_t3,
  * (index 0: stage kernel, 1: potential kernel, 2: trace/auxiliary) and resets the counters. */
 qhfpe_status qhfpe_kernel_timing(qhfpe_t *h, int enable);
 qhfpe_status qhfpe_kernel_timing_read(qhfpe_t *h, long *launches, double *total_ms, int n_kinds);
+
+/* ---- Learned closure (one Drude mode, K = 0) --------------------------------------------------
+ * With closure = QHFPE_LEARNED the deepest tier's missing element W^(N+1) is the Eq. (GMFP)
+ * terminator's estimate plus a learned local correction
+ *   dW^(N+1) = sum_{b=-2..2} c_b(x) W^N(q, p_{l+b}) + c_{5+b}(x) W^(N-1)(q, p_{l+b})  (p periodic),
+ * the ten coefficients coming from a perceptron of x = (q/8, p/8, ln eta): three tanh layers of
+ * width 256 and a linear output of width 10.  Linear in the state, so the closed hierarchy keeps the
+ * linear Green's function of Eqs. (R1), (R3).  Weights (float, row-major, this order):
+ * W1[256][3], b1[256], W2[256][256], b2[256], W3[256][256], b3[256], W4[10][256], b4[10].
+ * Until weights are loaded the correction is zero: the terminator.  QHFPE_TRUNCATE stays available
+ * as the plain truncated hierarchy.
+ * Regression statistics, per grid point (nq*np points, row-major [q][p]), 67 doubles: the upper
+ * triangle (row-major) of G = sum Re(conj(phi) phi^T), h = sum Re(conj(phi) y), sum |y|^2, the number
+ * of samples; phi = the ten patch values of tiers t-1 and t-2, y = tier t minus the terminator's
+ * estimate (r_0 p + c_0 d/dp) W^(t-1) (4th-order central d/dp). */
+#define QHFPE_CLOSURE_N_IN 3
+#define QHFPE_CLOSURE_N_HIDDEN 256
+#define QHFPE_CLOSURE_N_OUT 10
+#define QHFPE_CLOSURE_N_WEIGHTS 135178
+#define QHFPE_CLOSURE_N_STATS 67
+/* Add the statistics of target tier t (1 <= t <= depth, n_matsubara = 0) over every replica's current
+ * state to stats_dev (device, caller-owned, nq*np*67 doubles, accumulated into). */
+qhfpe_status qhfpe_closure_collect(qhfpe_t *h, int target_tier, double *stats_dev);
+/* Load weights (host, QHFPE_CLOSURE_N_WEIGHTS floats) and evaluate the network on the handle's grid at
+ * its eta: bf16 weights and activations with FP32 accumulation in the mixed forms, FP32 in the FP64
+ * form.  Requires closure = QHFPE_LEARNED. */
+qhfpe_status qhfpe_closure_load(qhfpe_t *h, const float *weights, size_t n);
+/* The coefficient table in use (host, [nq][np][10] doubles). */
+qhfpe_status qhfpe_closure_coefficients(const qhfpe_t *h, double *out);
+/* Training (FP32 kernels on the current device; the call allocates and frees its workspace).
+ * X: host [n_points][3] network inputs; stats: host [n_points][67].  The loss is
+ *   sum_x [c^T G_x c - 2 c^T h_x + yy_x + ridge (tr G_x / 10) |c|^2] / sum_x n_x
+ * (the mean squared closure error over all samples plus a data-scaled ridge on the correction).
+ * loss_grad: the loss and its gradient (float[N_WEIGHTS]).  train: n_iters Adam steps (beta1 0.9,
+ * beta2 0.999, eps 1e-8) on minibatches of `batch` points drawn without replacement per epoch
+ * (seeded), w updated in place; loss_history (may be NULL) gets each minibatch's estimate. */
+qhfpe_status qhfpe_closure_loss_grad(const float *w, const double *X, const double *stats, int n_points,
+                                     double ridge, double *loss, float *grad);
+qhfpe_status qhfpe_closure_train(float *w, const double *X, const double *stats, int n_points, int n_iters,
+                                 int batch, double lr, double ridge, unsigned seed, double *loss_history);
 
 /* ---- Potential term without allocation -----------------------------------------------------
  * No counterpart in the paper: this entry point exists for callers that cannot allocate device

@@ -1,19 +1,24 @@
 """Learned hierarchy closure, FP64 reference -- TEST INFRASTRUCTURE ONLY (part of the CPU oracle).
 
-The closure replaces the truncation W^(N+1) = 0 of Eq. (heom) at the deepest tier (one Drude mode,
-K = 0, so the hierarchy is a chain) by a local linear combination of the two tiers below:
+The closure corrects the terminator of Eq. (GMFP) at the deepest tier (one Drude mode, K = 0, so the
+hierarchy is a chain): the terminator reads the missing element as W^(N+1) ~ (r_0 p + c_0 d/dp) W^N,
+and the network adds a local linear combination of the two tiers below,
 
-    W^(N+1)(q_i, p_l) ~ sum_{b=-2..2} c_b(x) W^N(q_i, p_{l+b}) + c_{5+b}(x) W^(N-1)(q_i, p_{l+b}),
+    dW^(N+1)(q_i, p_l) = sum_{b=-2..2} c_b(x) W^N(q_i, p_{l+b}) + c_{5+b}(x) W^(N-1)(q_i, p_{l+b}),
 
 with the ten coefficients c(x) produced by a multilayer perceptron of x = (q/8, p/8, ln eta):
 three tanh hidden layers of width 256 and a linear output of width 10.  The combination is linear in
 the state, so the closed hierarchy keeps the linearity that the response functions of Eqs. (R1), (R3)
-presuppose (the Green's function G(t) is a linear map); the network only sets its coefficients.
+presuppose (the Green's function G(t) is a linear map); the network only sets its coefficients.  A zero
+network is the terminator itself.
 
-Training data are the deep hierarchy's own tiers: for every grid point x the samples
-(phi = the ten patch values of tiers N and N-1, y = tier N+1) from many states are compressed to
+Training data are the deep hierarchy's own tiers: for every grid point x the samples (phi = the ten
+patch values of tiers N and N-1, y = tier N+1 minus the terminator's estimate of it, with d/dp the
+4th-order central difference) from many states are compressed to
     G_x = sum Re(conj(phi) phi^T)  (10 x 10),  h_x = sum Re(conj(phi) y),  yy_x = sum |y|^2,  n_x,
 so that the mean squared error over all samples is  sum_x (c^T G_x c - 2 c^T h_x + yy_x) / sum_x n_x.
+A ridge term  lam * sum_x (tr G_x / 10) |c_x|^2 / sum_x n_x  keeps the correction small where the data
+do not determine it.
 
 Flat weight layout (row-major): W1[256][3], b1[256], W2[256][256], b2[256], W3[256][256], b3[256],
 W4[10][256], b4[10].  Statistics layout per point: G upper triangle (55, row-major), h (10), yy, n.
@@ -71,24 +76,31 @@ def _full_G(stats):
     return G
 
 
-def loss(w, X, stats):
+def _ridge_weight(G):
+    return np.trace(G, axis1=-2, axis2=-1) / 10.0
+
+
+def loss(w, X, stats, lam=0.0):
     c, _ = forward(w, X)
     G = _full_G(stats)
     h = stats[:, 55:65]
     q = np.einsum("ni,nij,nj->n", c, G, c) - 2 * np.einsum("ni,ni->n", c, h) + stats[:, 65]
+    q = q + lam * _ridge_weight(G) * (c * c).sum(-1)
     return q.sum() / stats[:, 66].sum()
 
 
-def loss_and_grad(w, X, stats):
-    """Mean squared closure error and its gradient with respect to the flat weights (plain backprop)."""
+def loss_and_grad(w, X, stats, lam=0.0):
+    """Mean squared closure error (+ ridge) and its gradient with respect to the flat weights."""
     W1, b1, W2, b2, W3, b3, W4, b4 = unpack(w)
     c, (X, h1, h2, h3) = forward(w, X)
     G = _full_G(stats)
     h = stats[:, 55:65]
     ntot = stats[:, 66].sum()
+    rw = lam * _ridge_weight(G)
     q = np.einsum("ni,nij,nj->n", c, G, c) - 2 * np.einsum("ni,ni->n", c, h) + stats[:, 65]
+    q = q + rw * (c * c).sum(-1)
     L = q.sum() / ntot
-    dc = 2.0 * (np.einsum("nij,nj->ni", G, c) - h) / ntot
+    dc = 2.0 * (np.einsum("nij,nj->ni", G, c) - h + rw[:, None] * c) / ntot
     dW4 = dc.T @ h3
     db4 = dc.sum(0)
     dz3 = (dc @ W4) * (1 - h3 ** 2)
@@ -113,9 +125,10 @@ def coefficients(w, model):
     return c
 
 
-def patch_samples(W, tier):
+def patch_samples(W, tier, r0=0.0, c0=0.0, p=None, dp=1.0):
     """Samples of the closure regression from a K = 0 hierarchy state W ([n_elem][S][S][nq][np],
-    element e = tier e): phi [nq][np][S*S][10] and y [nq][np][S*S] for the target tier `tier`."""
+    element e = tier e): phi [nq][np][S*S][10] and y [nq][np][S*S] for the target tier `tier`, minus
+    the terminator's estimate r0 p W^(tier-1) + c0 dW^(tier-1)/dp (p: the p grid)."""
     n_elem, S, _, nq, n_p = W.shape
     A = W[tier - 1].reshape(S * S, nq, n_p)
     B = W[tier - 2].reshape(S * S, nq, n_p) if tier >= 2 else np.zeros_like(A)
@@ -124,12 +137,17 @@ def patch_samples(W, tier):
         phi[..., 2 + b] = np.moveaxis(np.roll(A, -b, axis=-1), 0, -1)
         phi[..., 7 + b] = np.moveaxis(np.roll(B, -b, axis=-1), 0, -1)
     y = np.moveaxis(W[tier].reshape(S * S, nq, n_p), 0, -1)
+    if r0 != 0.0 or c0 != 0.0:
+        d1 = np.array([1.0, -8.0, 0.0, 8.0, -1.0]) / (12.0 * dp)
+        term = r0 * np.asarray(p)[None, :, None] * phi[..., 2] + c0 * np.einsum("xysf,f->xys", phi[..., :5], d1)
+        y = y - term
     return phi, y
 
 
-def statistics(W, tier):
-    """Per-point statistics [nq*np][67] of one state (sum over the electronic pairs)."""
-    phi, y = patch_samples(W, tier)
+def statistics(W, tier, r0=0.0, c0=0.0, p=None, dp=1.0):
+    """Per-point statistics [nq*np][67] of one state (sum over the electronic pairs); with r0, c0 the
+    target is the terminator's residual."""
+    phi, y = patch_samples(W, tier, r0, c0, p, dp)
     nq, n_p = phi.shape[:2]
     G = np.einsum("xysa,xysb->xyab", np.conj(phi), phi).real
     h = np.einsum("xysa,xys->xya", np.conj(phi), y).real

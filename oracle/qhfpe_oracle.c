@@ -322,7 +322,7 @@ static cplx dp_central(const oq_ctx *C, const cplx *row, int l, int times_p)
           + 8.0 * Xp(C, row, l + 1, times_p) - Xp(C, row, l + 2, times_p)) / (12.0 * C->dp);
 }
 
-/* Learned closure (K = 0 chain): the truncated element W^(N+1) at column l of row i is read as the
+/* Learned closure (K = 0 chain): the correction to the terminator's W^(N+1) at column l of row i, the
  * local linear combination  sum_{b=-2..2} c_b(q_i, p_l) W^N(p_{l+b}) + c_{5+b}(q_i, p_l) W^(N-1)(p_{l+b})
  * (p wrapped periodically; the W^(N-1) part is absent at N = 0). */
 static cplx closure_value(const oq_ctx *C, const cplx *rowN, const cplx *rowNm1, int i, int l)
@@ -363,7 +363,8 @@ static cplx dpp_central(const oq_ctx *C, const cplx *row, int l)
  * At the deepest tier with the terminator closure (Eq. (GMFP), K = 0), the missing W^(N+1) in the
  * tier-up term is replaced by r_0 p W^N + c_0 dW^N/dp, i.e. the term becomes
  *   d/dp (r_0 p W^N) + c_0 d^2 W^N/dp^2.
- * With the learned closure (K = 0) it is d/dp of closure_value (see there).
+ * With the learned closure (K = 0) it is the terminator's term plus d/dp of closure_value (see there):
+ * the network supplies a local correction to Eq. (GMFP).
  * State layout: [n_elem][S][S][nq][np] complex.
  * ---------------------------------------------------------------------------------------------- */
 void oq_rhs(const oq_ctx *C, const cplx *W, cplx *dW, int terms)
@@ -416,6 +417,7 @@ void oq_rhs(const oq_ctx *C, const cplx *W, cplx *dW, int terms)
                                 } else if (P->closure == 2 && tier == P->depth) {
                                     int dn = C->dn[e * M + a];
                                     const cplx *rowm1 = dn >= 0 ? W + dn * elem + ((size_t)j * S + k) * blk + (size_t)i * np : NULL;
+                                    acc += C->r[0] * dp_central(C, row, l, 1) + C->c[0] * dpp_central(C, row, l);
                                     acc += dp_closure(C, row, rowm1, i, l);
                                 }
                             }

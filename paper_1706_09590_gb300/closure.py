@@ -1,0 +1,64 @@
+"""Learned-closure pipeline on the device: regression statistics from deep hierarchies, training, and
+deployment (every numerical step runs in the library's kernels; this module only sequences calls).
+
+Training data: for each bath coupling eta, a deep hierarchy (chain, one Drude mode) is equilibrated,
+excited by one and by two dipole commutators (the first and second interactions of Eqs. (R1), (R3)),
+and propagated; along the way the statistics of the target tier (the element that a shallow hierarchy
+of depth target-1 truncates) against its two lower tiers are accumulated per grid point.
+"""
+import numpy as np
+
+from .qhfpe import CLOSURE_N_STATS, CLOSURE_N_WEIGHTS, COMMUTATOR, TERMINATOR, Propagator, closure_train
+
+N_IN, N_HID, N_OUT = 3, 256, 10
+
+
+def network_inputs(model, eta):
+    """(q/8, p/8, ln eta) for every grid point, [nq*np][3]."""
+    q = model["q_min"] + np.arange(model["nq"]) * (model["q_max"] - model["q_min"]) / model["nq"]
+    p = model["p_min"] + np.arange(model["np"]) * (model["p_max"] - model["p_min"]) / model["np"]
+    Q, P = np.meshgrid(q, p, indexing="ij")
+    return np.stack([Q / 8.0, P / 8.0, np.full(Q.shape, np.log(eta))], -1).reshape(-1, 3)
+
+
+def initial_weights(seed=1706):
+    """Glorot-uniform hidden layers, zero output layer (the untrained closure is the terminator)."""
+    rng = np.random.default_rng(seed)
+    parts = []
+    for fan_out, fan_in in ((N_HID, N_IN), (N_HID, N_HID), (N_HID, N_HID)):
+        lim = np.sqrt(6.0 / (fan_in + fan_out))
+        parts += [rng.uniform(-lim, lim, fan_out * fan_in), np.zeros(fan_out)]
+    parts += [np.zeros(N_OUT * N_HID), np.zeros(N_OUT)]
+    w = np.concatenate(parts).astype(np.float32)
+    assert w.size == CLOSURE_N_WEIGHTS
+    return w
+
+
+def deep_statistics(model, U_table, eta, deep_depth, target_tier, n_eq, n_prop, every, stream=None):
+    """Statistics [nq*np][67] of tier `target_tier` from a depth-`deep_depth` run at this eta."""
+    import torch
+    m = dict(model, eta=eta, depth=deep_depth, closure=TERMINATOR)
+    P = Propagator(m, U_table, precision="fp64", n_replicas=2, stream=stream)
+    stats = torch.zeros(m["nq"] * m["np"] * CLOSURE_N_STATS, dtype=torch.float64, device="cuda")
+    P.equilibrate(n_eq)
+    P.closure_collect(target_tier, stats)
+    P.apply_dipole(COMMUTATOR, [0, 1])
+    P.apply_dipole(COMMUTATOR, [1])
+    for _ in range(n_prop // every):
+        P.step(every)
+        P.closure_collect(target_tier, stats)
+    P.close()
+    return stats.cpu().numpy().reshape(-1, CLOSURE_N_STATS)
+
+
+def training_set(model, U_table, etas, deep_depth, target_tier, n_eq=1500, n_prop=2000, every=20, stream=None):
+    X, S = [], []
+    for eta in etas:
+        S.append(deep_statistics(model, U_table, eta, deep_depth, target_tier, n_eq, n_prop, every, stream))
+        X.append(network_inputs(model, eta))
+    return np.concatenate(X), np.concatenate(S)
+
+
+def train(X, stats, n_iters=3000, batch=4096, lr=1e-3, ridge=0.01, seed=1706, weights=None):
+    w0 = initial_weights(seed) if weights is None else weights
+    return closure_train(w0, X, stats, n_iters, batch=batch, lr=lr, ridge=ridge, seed=seed)

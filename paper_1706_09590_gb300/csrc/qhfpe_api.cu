@@ -12,6 +12,7 @@
 #include <memory>
 #include <new>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 namespace {
@@ -121,6 +122,10 @@ struct Model {
     {
         return {tab32, tab32 + tab_n, tab32 + 2 * tab_n, tab32 + 3 * tab_n};
     }
+    int closure_slot = -1;      // learned closure: element slot holding W^(N+1) (after the real elements)
+    int closure_n = -1, closure_n1 = -1;  // elements of tiers N and N-1 (chain, K = 0)
+    double *coef64 = nullptr;   // closure coefficients [nq][np][10] (owned by the handle)
+    float *coef32 = nullptr;
     bool fused = false;         // fused stage kernel available for (np, S)
     double *ftab64 = nullptr;   // its tables (digit-reversed order, np twiddles)
     float *ftab32 = nullptr;
@@ -188,6 +193,9 @@ struct qhfpe {
     double *scratch = nullptr;
     size_t scratch_cap = 0;
     int *flag = nullptr;    // device flag for non-finite input checks
+    double *coef64 = nullptr;  // learned-closure coefficient table [nq][np][10]
+    float *coef32 = nullptr;
+    float *closure_w = nullptr;
     Timing timing;
 
     ~qhfpe()
@@ -199,6 +207,9 @@ struct qhfpe {
         if (flag) cudaFree(flag);
         model.reset();
         ground.reset();
+        if (coef64) cudaFree(coef64);
+        if (coef32) cudaFree(coef32);
+        if (closure_w) cudaFree(closure_w);
         if (own_stream && stream) cudaStreamDestroy(stream);
     }
 
@@ -289,7 +300,7 @@ qhfpe_status build_model(qhfpe *h, Model &M, int S, const double *U, const doubl
         }
         E.ngam = ngam;
         E.tier = tier;
-        E.terminator = (p.closure == QHFPE_TERMINATOR && tier == p.depth) ? 1 : 0;
+        E.terminator = ((p.closure == QHFPE_TERMINATOR || p.closure == QHFPE_LEARNED) && tier == p.depth) ? 1 : 0;
         for (int k = 0; k < M.n_modes; ++k) {
             std::vector<int> v = n;
             v[k] += 1;
@@ -303,6 +314,19 @@ qhfpe_status build_model(qhfpe *h, Model &M, int S, const double *U, const doubl
                 E.n_dn++;
             }
         }
+    }
+    if (p.closure == QHFPE_LEARNED) {
+        M.closure_slot = M.n_elem;
+        for (int e = 0; e < M.n_elem; ++e) {
+            ElemInfo &E = M.elems_host[e];
+            if (E.tier == p.depth) {
+                E.up[E.n_up++] = M.closure_slot;
+                M.closure_n = e;
+                M.closure_n1 = E.n_dn > 0 ? E.dn[0] : -1;
+            }
+        }
+        M.coef64 = h->coef64;
+        M.coef32 = h->coef32;
     }
     GridInfo &g = M.g;
     g.S = S;
@@ -321,7 +345,7 @@ qhfpe_status build_model(qhfpe *h, Model &M, int S, const double *U, const doubl
     g.term_c0 = M.bath.c[0];
     g.blk = (size_t)p.nq * p.np;
     g.elem_stride = (size_t)S * S * 2 * g.blk;
-    g.rep_stride = (size_t)M.n_elem * g.elem_stride;
+    g.rep_stride = (size_t)(M.n_elem + (M.closure_slot >= 0 ? 1 : 0)) * g.elem_stride;
     g.tier0_rep_stride = g.elem_stride;
 
     M.mu_host.assign(mu, mu + S * S);
@@ -448,6 +472,17 @@ struct Bracket {
     }
 };
 
+// Learned closure: fill the W^(N+1) slot of `in` from its two deepest tiers (no-op otherwise).
+template <typename T>
+qhfpe_status closure_fill(qhfpe *h, const Prop &P, T *in, int rep0, int n_rep)
+{
+    const Model &M = *P.m;
+    if (M.closure_slot < 0) return QHFPE_OK;
+    const T *coef = std::is_same<T, float>::value ? (const T *)M.coef32 : (const T *)M.coef64;
+    QH_CK(h, launch_closure_apply<T>(P.g, in, M.closure_n, M.closure_n1, M.closure_slot, coef, rep0, n_rep, h->stream));
+    return QHFPE_OK;
+}
+
 // ---- one RK4 step: Horner form of the degree-4 Taylor polynomial ---------------------------------
 //   v = y;  v = y + (dt/4) L v;  v = y + (dt/3) L v;  v = y + (dt/2) L v;  y = y + dt L v.
 template <typename T, bool MIXED>
@@ -459,6 +494,10 @@ qhfpe_status step_once(qhfpe *h, Prop &P, bool record)
     for (int k = 4; k >= 1; --k) {
         T *in = (k == 4) ? y : (k == 3 ? vA : (k == 2 ? vB : vA));
         T *out = (k == 1) ? y : (k == 4 ? vA : (k == 3 ? vB : vA));
+        if (M.closure_slot >= 0) {
+            qhfpe_status r = closure_fill<T>(h, P, in, 0, P.g.n_rep);
+            if (r != QHFPE_OK) return r;
+        }
         if (M.fused) {
             Bracket br(h, QH_KIND_STAGE);
             if (MIXED)
@@ -654,11 +693,9 @@ qhfpe_status qhfpe_create(const qhfpe_params *params, void *stream, qhfpe_t **ou
     if (p.high_temperature && p.n_matsubara != 0) return bad("high_temperature requires n_matsubara = 0");
     if (p.depth < 0) return bad("depth must be >= 0");
     if (p.closure == QHFPE_TERMINATOR && p.n_matsubara != 0) return bad("the terminator closure needs n_matsubara = 0");
-    if (p.closure == QHFPE_LEARNED) {
-        create_err = "the learned closure is not available in this build";
-        return QHFPE_EUNSUPPORTED;
-    }
-    if (p.closure != QHFPE_TRUNCATE && p.closure != QHFPE_TERMINATOR) return bad("unknown closure");
+    if (p.closure == QHFPE_LEARNED && p.n_matsubara != 0) return bad("the learned closure needs n_matsubara = 0");
+    if (p.closure != QHFPE_TRUNCATE && p.closure != QHFPE_TERMINATOR && p.closure != QHFPE_LEARNED)
+        return bad("unknown closure");
     if (p.precision != QHFPE_FP64 && p.precision != QHFPE_MIXED) {
         if (p.precision == QHFPE_MIXED_BF16X3) {
             create_err = "the bf16x3 tensor-core potential kernel is not available in this build";
@@ -699,6 +736,18 @@ qhfpe_status qhfpe_create(const qhfpe_params *params, void *stream, qhfpe_t **ou
             return QHFPE_ECUDA;
         }
         h->own_stream = true;
+    }
+    if (p.closure == QHFPE_LEARNED) {
+        const size_t nc = (size_t)p.nq * p.np * QHFPE_CLOSURE_N_OUT;
+        cudaError_t e = cudaMalloc((void **)&h->coef64, nc * sizeof(double));
+        if (e == cudaSuccess) e = cudaMalloc((void **)&h->coef32, nc * sizeof(float));
+        if (e == cudaSuccess) e = cudaMemsetAsync(h->coef64, 0, nc * sizeof(double), h->stream);
+        if (e == cudaSuccess) e = cudaMemsetAsync(h->coef32, 0, nc * sizeof(float), h->stream);
+        if (e != cudaSuccess) {
+            create_err = std::string("closure tables: ") + cudaGetErrorString(e);
+            cudaGetLastError();
+            return QHFPE_ENOMEM;
+        }
     }
     h->model.reset(new Model());
     qhfpe_status r = build_model(h.get(), *h->model, S, h->U.data(), h->mu.data());
@@ -889,6 +938,8 @@ qhfpe_status qhfpe_apply_rhs(qhfpe_t *h, int replica, int terms, double *out)
     if (!out || replica < 0 || replica >= P.g.n_rep) return h->fail(QHFPE_EINVAL, "apply_rhs: bad replica or NULL output");
     cudaStream_t st = h->stream;
     const Model &M = *P.m;
+    r = P.mixed ? closure_fill<float>(h, P, (float *)P.y, replica, 1) : closure_fill<double>(h, P, (double *)P.y, replica, 1);
+    if (r != QHFPE_OK) return r;
     if (M.fused) {
         if (P.mixed)
             QH_CK(h, (launch_fused<float, true>(P.g, M.elems, M.f32(), (const float *)P.y, (const float *)P.y, P.y0,
@@ -977,7 +1028,9 @@ qhfpe_status qhfpe_equilibrate(qhfpe_t *h, long n_steps, double *residual_out)
     if (r != QHFPE_OK) return r;
     r = run_steps(h, *GP, n_steps, nullptr, 0);
     if (r != QHFPE_OK) return r;
-    // residual ||L W|| / ||W||
+    // residual ||L W|| / ||W|| (the closure slot is not part of the state)
+    r = closure_fill<double>(h, *GP, (double *)GP->y, 0, 1);
+    if (r != QHFPE_OK) return r;
     if (G.fused) {
         QH_CK(h, (launch_fused<double, false>(GP->g, G.elems, G.f64(), (const double *)GP->y, (const double *)GP->y,
                                               nullptr, (double *)GP->vA, nullptr, 0.0, 0, QHFPE_TERM_ALL, 0, 1, st)));
@@ -987,8 +1040,9 @@ qhfpe_status qhfpe_equilibrate(qhfpe_t *h, long n_steps, double *residual_out)
                                               (const double *)GP->y, nullptr, (double *)GP->vA, nullptr, 0.0, 0,
                                               QHFPE_TERM_ALL, 0, 1, st)));
     }
-    QH_CK(h, launch_norm2((const double *)GP->vA, GP->g.rep_stride, h->scratch, st));
-    QH_CK(h, launch_norm2((const double *)GP->y, GP->g.rep_stride, h->scratch + 1, st));
+    const size_t real = (size_t)G.n_elem * GP->g.elem_stride;
+    QH_CK(h, launch_norm2((const double *)GP->vA, real, h->scratch, st));
+    QH_CK(h, launch_norm2((const double *)GP->y, real, h->scratch + 1, st));
     double nn[2];
     QH_CK(h, cudaMemcpyAsync(nn, h->scratch, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
     QH_CK(h, cudaStreamSynchronize(st));
@@ -1192,6 +1246,50 @@ qhfpe_status qhfpe_kernel_timing_read(qhfpe_t *h, long *launches, double *total_
         T.launches[k] = 0;
         T.ms[k] = 0.0;
     }
+    return QHFPE_OK;
+}
+
+qhfpe_status qhfpe_closure_collect(qhfpe_t *h, int target_tier, double *stats_dev)
+{
+    qhfpe_status r = check_handle(h);
+    if (r != QHFPE_OK) return r;
+    const Model &M = *h->model;
+    if (h->p.n_matsubara != 0) return h->fail(QHFPE_EINVAL, "closure_collect: needs n_matsubara = 0");
+    if (!stats_dev || target_tier < 1 || target_tier > h->p.depth)
+        return h->fail(QHFPE_EINVAL, "closure_collect: target tier must be in [1, depth]");
+    // K = 0: element index = tier
+    Prop &P = *h->main;
+    const int t = target_tier;
+    if (P.mixed) QH_CK(h, launch_closure_collect<float>(P.g, (const float *)P.y, t, t - 1, t - 2, stats_dev, h->stream));
+    else QH_CK(h, launch_closure_collect<double>(P.g, (const double *)P.y, t, t - 1, t - 2, stats_dev, h->stream));
+    (void)M;
+    QH_CK(h, cudaStreamSynchronize(h->stream));
+    return QHFPE_OK;
+}
+
+qhfpe_status qhfpe_closure_load(qhfpe_t *h, const float *weights, size_t n)
+{
+    qhfpe_status r = check_handle(h);
+    if (r != QHFPE_OK) return r;
+    if (h->p.closure != QHFPE_LEARNED) return h->fail(QHFPE_EINVAL, "closure_load: the handle was not created with QHFPE_LEARNED");
+    if (!weights || n != QHFPE_CLOSURE_N_WEIGHTS) return h->fail(QHFPE_EINVAL, "closure_load: expected QHFPE_CLOSURE_N_WEIGHTS floats");
+    for (size_t i = 0; i < n; ++i)
+        if (!std::isfinite(weights[i])) return h->fail(QHFPE_ENUMERIC, "closure_load: non-finite weight");
+    if (!h->closure_w) QH_CK(h, cudaMalloc((void **)&h->closure_w, n * sizeof(float)));
+    QH_CK(h, cudaMemcpyAsync(h->closure_w, weights, n * sizeof(float), cudaMemcpyHostToDevice, h->stream));
+    QH_CK(h, launch_closure_infer(h->model->g, h->p.eta, h->closure_w, h->p.precision != QHFPE_FP64 ? 1 : 0, h->coef64,
+                                  h->coef32, h->stream));
+    QH_CK(h, cudaStreamSynchronize(h->stream));
+    return QHFPE_OK;
+}
+
+qhfpe_status qhfpe_closure_coefficients(const qhfpe_t *h, double *out)
+{
+    if (!h || !out) return QHFPE_EINVAL;
+    if (h->sticky) return QHFPE_ESTATE;
+    if (!h->coef64) return QHFPE_EINVAL;
+    const size_t nc = (size_t)h->p.nq * h->p.np * QHFPE_CLOSURE_N_OUT;
+    if (cudaMemcpy(out, h->coef64, nc * sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess) return QHFPE_ECUDA;
     return QHFPE_OK;
 }
 

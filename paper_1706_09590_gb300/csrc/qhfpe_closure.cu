@@ -1,0 +1,513 @@
+// Learned hierarchy closure: data collection from deep hierarchies, the network's FP32 training
+// kernels (forward, backward, Adam), its reduced-precision inference over the grid, and the closure
+// term used inside every right-hand-side stage.
+//
+// The closure (one Drude mode, K = 0, so the hierarchy is a chain) corrects the terminator of
+// Eq. (GMFP): the truncated element is read as the terminator's (r_0 p + c_0 d/dp) W^N plus a local
+// linear combination of the two deepest tiers,
+//   dW^(N+1)(q_i, p_l) = sum_{b=-2..2} c_b(x) W^N(q_i, p_{l+b}) + c_{5+b}(x) W^(N-1)(q_i, p_{l+b}),
+// with the ten coefficients from a perceptron of x = (q/8, p/8, ln eta) (3 tanh layers of width 256,
+// linear output of width 10).  Being linear in the state, the closed hierarchy keeps the linear
+// Green's function that the response functions of Eqs. (R1), (R3) are defined with.  The network does
+// not depend on the state, so it is evaluated once per grid point when the weights are loaded and the
+// right-hand side reads a coefficient table.
+#include "../../include/qhfpe.h"
+#include "qhfpe_internal.cuh"
+
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <random>
+#include <string>
+#include <vector>
+
+namespace {
+
+constexpr int NIN = QHFPE_CLOSURE_N_IN, NH = QHFPE_CLOSURE_N_HIDDEN, NOUT = QHFPE_CLOSURE_N_OUT;
+constexpr int NST = QHFPE_CLOSURE_N_STATS;
+// flat weight offsets
+constexpr size_t OW1 = 0, OB1 = OW1 + (size_t)NH * NIN, OW2 = OB1 + NH, OB2 = OW2 + (size_t)NH * NH,
+                 OW3 = OB2 + NH, OB3 = OW3 + (size_t)NH * NH, OW4 = OB3 + NH, OB4 = OW4 + (size_t)NOUT * NH,
+                 NW = OB4 + NOUT;
+static_assert(NW == QHFPE_CLOSURE_N_WEIGHTS, "weight count");
+
+// ---------------------------------------------------------------------------------------------------
+// Regression statistics for target tier t: per grid point, G = sum Re(conj(phi) phi^T) (upper
+// triangle), h = sum Re(conj(phi) y), yy = sum |y|^2, n = number of samples, summed over electronic
+// pairs and replicas.  phi_{2+b} = W^(t-1)(l+b), phi_{7+b} = W^(t-2)(l+b) (p periodic), and y = W^t(l)
+// minus the Eq. (GMFP) terminator's estimate of it, (r_0 p + c_0 d/dp) W^(t-1) (4th-order d/dp).
+// ---------------------------------------------------------------------------------------------------
+template <typename T>
+__global__ void collect_kernel(GridInfo g, const T *__restrict__ state, int e_t, int e_t1, int e_t2, double *stats)
+{
+    const size_t blk = g.blk;
+    const int np = g.np;
+    const size_t total = (size_t)g.n_rep * blk;
+    for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total; idx += (size_t)gridDim.x * blockDim.x) {
+        const size_t cell = idx % blk;
+        const int rep = (int)(idx / blk);
+        const int l = (int)(cell % np);
+        const size_t row = cell - l;
+        double G[55], hv[10], yy = 0.0;
+        for (int a = 0; a < 55; ++a) G[a] = 0.0;
+        for (int a = 0; a < 10; ++a) hv[a] = 0.0;
+        for (int pr = 0; pr < g.S * g.S; ++pr) {
+            const T *base = state + (size_t)rep * g.rep_stride + (size_t)pr * 2 * blk + row;
+            double pre[10], pim[10];
+            for (int b = -2; b <= 2; ++b) {
+                const int lb = (l + b + np) % np;
+                const T *A = base + (size_t)e_t1 * g.elem_stride;
+                pre[2 + b] = (double)A[lb];
+                pim[2 + b] = (double)A[lb + blk];
+                if (e_t2 >= 0) {
+                    const T *B = base + (size_t)e_t2 * g.elem_stride;
+                    pre[7 + b] = (double)B[lb];
+                    pim[7 + b] = (double)B[lb + blk];
+                } else {
+                    pre[7 + b] = pim[7 + b] = 0.0;
+                }
+            }
+            const T *Y = base + (size_t)e_t * g.elem_stride;
+            // target: tier t minus the terminator's estimate (r_0 p + c_0 d/dp) W^(t-1)
+            const double pl = g.p_min + l * g.dp, f = g.term_c0 / (12.0 * g.dp);
+            const double yr = (double)Y[l] - g.term_r0 * pl * pre[2] - f * (pre[0] - 8.0 * pre[1] + 8.0 * pre[3] - pre[4]);
+            const double yi = (double)Y[l + blk] - g.term_r0 * pl * pim[2] - f * (pim[0] - 8.0 * pim[1] + 8.0 * pim[3] - pim[4]);
+            int k = 0;
+            for (int a = 0; a < 10; ++a) {
+                for (int c = a; c < 10; ++c) G[k++] += pre[a] * pre[c] + pim[a] * pim[c];
+                hv[a] += pre[a] * yr + pim[a] * yi;
+            }
+            yy += yr * yr + yi * yi;
+        }
+        double *out = stats + cell * NST;
+        for (int a = 0; a < 55; ++a) atomicAdd(out + a, G[a]);
+        for (int a = 0; a < 10; ++a) atomicAdd(out + 55 + a, hv[a]);
+        atomicAdd(out + 65, yy);
+        atomicAdd(out + 66, (double)(g.S * g.S));
+    }
+}
+
+// ---------------------------------------------------------------------------------------------------
+// FP32 training kernels.  Generic tiled product out[M][N] = sum_k A(m,k) B(k,n) (+ bias[n]) with
+// A(m,k) = TA ? A[k*lda + m] : A[m*lda + k] and B(k,n) = TB ? B[n*ldb + k] : B[k*ldb + n];
+// optional tanh epilogue.  64 x 64 tiles, 256 threads, 4 x 4 outputs per thread.
+// ---------------------------------------------------------------------------------------------------
+template <bool TA, bool TB>
+__global__ void __launch_bounds__(256) sgemm_kernel(int M, int N, int K, const float *__restrict__ A, int lda,
+                                                    const float *__restrict__ B, int ldb, const float *__restrict__ bias,
+                                                    float *out, int ldo, int act_tanh)
+{
+    __shared__ float As[16][65], Bs[16][65];
+    const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+    const int m0 = blockIdx.y * 64, n0 = blockIdx.x * 64;
+    float acc[4][4] = {};
+    for (int k0 = 0; k0 < K; k0 += 16) {
+        for (int t = threadIdx.x; t < 16 * 64; t += 256) {
+            const int kk = t / 64, mm = t % 64;
+            const int m = m0 + mm, k = k0 + kk;
+            As[kk][mm] = (m < M && k < K) ? (TA ? A[(size_t)k * lda + m] : A[(size_t)m * lda + k]) : 0.f;
+            const int n = n0 + mm;
+            Bs[kk][mm] = (n < N && k < K) ? (TB ? B[(size_t)n * ldb + k] : B[(size_t)k * ldb + n]) : 0.f;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < 16; ++kk) {
+            float a[4], b[4];
+#pragma unroll
+            for (int r = 0; r < 4; ++r) a[r] = As[kk][ty * 4 + r];
+#pragma unroll
+            for (int c = 0; c < 4; ++c) b[c] = Bs[kk][tx * 4 + c];
+#pragma unroll
+            for (int r = 0; r < 4; ++r)
+#pragma unroll
+                for (int c = 0; c < 4; ++c) acc[r][c] = fmaf(a[r], b[c], acc[r][c]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+        const int m = m0 + ty * 4 + r;
+        if (m >= M) continue;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            const int n = n0 + tx * 4 + c;
+            if (n >= N) continue;
+            float v = acc[r][c] + (bias ? bias[n] : 0.f);
+            if (act_tanh) v = tanhf(v);
+            out[(size_t)m * ldo + n] = v;
+        }
+    }
+}
+
+// per point: loss contribution and dC = 2 (G c - h) / n_total
+__global__ void closure_loss_kernel(int B, const float *__restrict__ C, const double *__restrict__ stats,
+                                    const int *__restrict__ idx, double inv_ntot, double ridge, float *dC, double *loss)
+{
+    __shared__ double red[256];
+    double part = 0.0;
+    for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < B; b += gridDim.x * blockDim.x) {
+        const double *st = stats + (size_t)idx[b] * NST;
+        double c[10], Gc[10];
+        for (int a = 0; a < 10; ++a) {
+            c[a] = C[(size_t)b * NOUT + a];
+            Gc[a] = 0.0;
+        }
+        int k = 0;
+        for (int a = 0; a < 10; ++a)
+            for (int d = a; d < 10; ++d) {
+                const double gv = st[k++];
+                Gc[a] += gv * c[d];
+                if (d != a) Gc[d] += gv * c[a];
+            }
+        // ridge weight: lam * tr(G) / 10 (G's diagonal sits at upper-triangle positions a*(21-a)/2)
+        double tr = 0.0;
+        for (int a = 0; a < 10; ++a) tr += st[a * (21 - a) / 2];
+        const double rw = ridge * tr / 10.0;
+        double q = st[65];
+        for (int a = 0; a < 10; ++a) {
+            q += c[a] * Gc[a] - 2.0 * c[a] * st[55 + a] + rw * c[a] * c[a];
+            dC[(size_t)b * NOUT + a] = (float)(2.0 * (Gc[a] - st[55 + a] + rw * c[a]) * inv_ntot);
+        }
+        part += q;
+    }
+    red[threadIdx.x] = part;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) atomicAdd(loss, red[0] * inv_ntot);
+}
+
+// dZ = dH * (1 - H^2)
+__global__ void tanh_back_kernel(size_t n, const float *__restrict__ H, float *dH)
+{
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        dH[i] *= 1.f - H[i] * H[i];
+}
+
+// column sums of dZ [B][N] into grad (bias gradient), fixed order
+__global__ void colsum_kernel(int B, int N, const float *__restrict__ dZ, float *out)
+{
+    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= N) return;
+    float s = 0.f;
+    for (int b = 0; b < B; ++b) s += dZ[(size_t)b * N + n];
+    out[n] = s;
+}
+
+__global__ void gather_inputs_kernel(int B, const float *__restrict__ X, const int *__restrict__ idx, float *out)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= B * NIN) return;
+    out[t] = X[(size_t)idx[t / NIN] * NIN + t % NIN];
+}
+
+__global__ void adam_kernel(size_t n, float *w, const float *__restrict__ g, float *m, float *v, float lr, float b1,
+                            float b2, float eps, float c1, float c2)
+{
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        const float gi = g[i];
+        const float mi = b1 * m[i] + (1.f - b1) * gi;
+        const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+        m[i] = mi;
+        v[i] = vi;
+        w[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+    }
+}
+
+// ---------------------------------------------------------------------------------------------------
+// Inference over the grid: one block per 32 points; weights and activations rounded to bf16
+// (bf16 = 1) or kept in FP32, FP32 accumulation.  Output [nq][np][10] in FP64 and FP32.
+// ---------------------------------------------------------------------------------------------------
+__device__ __forceinline__ float rnd(float x, int bf16) { return bf16 ? __bfloat162float(__float2bfloat16_rn(x)) : x; }
+
+constexpr int IPTS = 16;  // points per inference block
+
+__global__ void __launch_bounds__(256) infer_kernel(int n_points, int np, double q_min, double dq, double p_min,
+                                                    double dp, double log_eta, const float *__restrict__ w, int bf16,
+                                                    double *out64, float *out32)
+{
+    __shared__ float h[2][IPTS][NH + 1];
+    const int p0 = blockIdx.x * IPTS;
+    const int tid = threadIdx.x;
+    // layer 1 (3 inputs)
+    for (int t = tid; t < IPTS * NH; t += 256) {
+        const int pt = t / NH, u = t % NH;
+        const int x = p0 + pt;
+        float v = 0.f;
+        if (x < n_points) {
+            const int i = x / np, l = x % np;
+            const float in[3] = {rnd((float)((q_min + i * dq) / 8.0), bf16), rnd((float)((p_min + l * dp) / 8.0), bf16),
+                                 rnd((float)log_eta, bf16)};
+            v = w[OB1 + u];
+            for (int k = 0; k < NIN; ++k) v += rnd(w[OW1 + (size_t)u * NIN + k], bf16) * in[k];
+            v = rnd(tanhf(v), bf16);
+        }
+        h[0][pt][u] = v;
+    }
+    __syncthreads();
+    int cur = 0;
+    for (int layer = 0; layer < 2; ++layer) {
+        const size_t OW = layer == 0 ? OW2 : OW3, OB = layer == 0 ? OB2 : OB3;
+        for (int t = tid; t < IPTS * NH; t += 256) {
+            const int pt = t / NH, u = t % NH;
+            float v = w[OB + u];
+            const float *wr = w + OW + (size_t)u * NH;
+            for (int k = 0; k < NH; ++k) v += rnd(wr[k], bf16) * h[cur][pt][k];
+            h[cur ^ 1][pt][u] = rnd(tanhf(v), bf16);
+        }
+        __syncthreads();
+        cur ^= 1;
+    }
+    for (int t = tid; t < IPTS * NOUT; t += 256) {
+        const int pt = t / NOUT, o = t % NOUT;
+        const int x = p0 + pt;
+        if (x >= n_points) continue;
+        float v = w[OB4 + o];
+        const float *wr = w + OW4 + (size_t)o * NH;
+        for (int k = 0; k < NH; ++k) v += rnd(wr[k], bf16) * h[cur][pt][k];
+        out64[(size_t)x * NOUT + o] = (double)v;
+        out32[(size_t)x * NOUT + o] = v;
+    }
+}
+
+// closure element W^(N+1) = sum_b c_b W^N(l+b) + c_{5+b} W^(N-1)(l+b), into slot e_slot of `state`
+template <typename T>
+__global__ void closure_apply_kernel(GridInfo g, T *state, int e_n, int e_n1, int e_slot, const T *__restrict__ coef,
+                                     int rep0, int n_rep)
+{
+    const size_t blk = g.blk;
+    const int np = g.np, S2 = g.S * g.S;
+    const size_t total = (size_t)n_rep * S2 * blk;
+    for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total; idx += (size_t)gridDim.x * blockDim.x) {
+        const size_t cell = idx % blk;
+        const int pr = (int)((idx / blk) % S2);
+        const int rep = rep0 + (int)(idx / (blk * S2));
+        const int l = (int)(cell % np);
+        const size_t row = cell - l;
+        const T *c = coef + cell * NOUT;
+        T *base = state + (size_t)rep * g.rep_stride + (size_t)pr * 2 * blk;
+        const T *A = base + (size_t)e_n * g.elem_stride + row;
+        const T *B = e_n1 >= 0 ? base + (size_t)e_n1 * g.elem_stride + row : nullptr;
+        T vr = 0, vi = 0;
+#pragma unroll
+        for (int b = -2; b <= 2; ++b) {
+            const int lb = (l + b + np) % np;
+            vr += c[2 + b] * A[lb];
+            vi += c[2 + b] * A[lb + blk];
+            if (B) {
+                vr += c[7 + b] * B[lb];
+                vi += c[7 + b] * B[lb + blk];
+            }
+        }
+        T *o = base + (size_t)e_slot * g.elem_stride + cell;
+        o[0] = vr;
+        o[blk] = vi;
+    }
+}
+
+inline int gsz(size_t n, int t = 256) { return (int)std::min<size_t>((n + t - 1) / t, 152 * 16); }
+
+template <bool TA, bool TB>
+cudaError_t gemm(int M, int N, int K, const float *A, int lda, const float *B, int ldb, const float *bias, float *out,
+                 int ldo, int act, cudaStream_t st)
+{
+    dim3 grid((N + 63) / 64, (M + 63) / 64);
+    sgemm_kernel<TA, TB><<<grid, 256, 0, st>>>(M, N, K, A, lda, B, ldb, bias, out, ldo, act);
+    return cudaGetLastError();
+}
+
+// Device workspace of one forward/backward pass over a batch of B points.
+struct Train {
+    int B = 0;
+    float *w = nullptr, *g = nullptr, *m = nullptr, *v = nullptr;
+    float *X = nullptr, *Xb = nullptr, *H1 = nullptr, *H2 = nullptr, *H3 = nullptr, *C = nullptr, *dC = nullptr,
+          *d3 = nullptr, *d2 = nullptr, *d1 = nullptr;
+    double *stats = nullptr, *loss = nullptr;
+    int *idx = nullptr;
+    ~Train()
+    {
+        for (void *p : {(void *)w, (void *)g, (void *)m, (void *)v, (void *)X, (void *)Xb, (void *)H1, (void *)H2,
+                        (void *)H3, (void *)C, (void *)dC, (void *)d3, (void *)d2, (void *)d1, (void *)stats,
+                        (void *)loss, (void *)idx})
+            if (p) cudaFree(p);
+    }
+};
+
+// forward + loss + backward for the points idx[0..B) (device), gradient into T.g
+cudaError_t forward_backward(Train &T, int B, double inv_ntot, double ridge, cudaStream_t st)
+{
+    cudaError_t e;
+    const float *w = T.w;
+    float *g = T.g;
+    gather_inputs_kernel<<<(B * NIN + 255) / 256, 256, 0, st>>>(B, T.X, T.idx, T.Xb);
+    if ((e = gemm<false, true>(B, NH, NIN, T.Xb, NIN, w + OW1, NIN, w + OB1, T.H1, NH, 1, st))) return e;
+    if ((e = gemm<false, true>(B, NH, NH, T.H1, NH, w + OW2, NH, w + OB2, T.H2, NH, 1, st))) return e;
+    if ((e = gemm<false, true>(B, NH, NH, T.H2, NH, w + OW3, NH, w + OB3, T.H3, NH, 1, st))) return e;
+    if ((e = gemm<false, true>(B, NOUT, NH, T.H3, NH, w + OW4, NH, w + OB4, T.C, NOUT, 0, st))) return e;
+    if ((e = cudaMemsetAsync(T.loss, 0, sizeof(double), st))) return e;
+    closure_loss_kernel<<<gsz(B), 256, 0, st>>>(B, T.C, T.stats, T.idx, inv_ntot, ridge, T.dC, T.loss);
+    // output layer
+    if ((e = gemm<true, false>(NOUT, NH, B, T.dC, NOUT, T.H3, NH, nullptr, g + OW4, NH, 0, st))) return e;
+    colsum_kernel<<<1, 32, 0, st>>>(B, NOUT, T.dC, g + OB4);
+    if ((e = gemm<false, false>(B, NH, NOUT, T.dC, NOUT, w + OW4, NH, nullptr, T.d3, NH, 0, st))) return e;
+    tanh_back_kernel<<<gsz((size_t)B * NH), 256, 0, st>>>((size_t)B * NH, T.H3, T.d3);
+    // layer 3
+    if ((e = gemm<true, false>(NH, NH, B, T.d3, NH, T.H2, NH, nullptr, g + OW3, NH, 0, st))) return e;
+    colsum_kernel<<<(NH + 127) / 128, 128, 0, st>>>(B, NH, T.d3, g + OB3);
+    if ((e = gemm<false, false>(B, NH, NH, T.d3, NH, w + OW3, NH, nullptr, T.d2, NH, 0, st))) return e;
+    tanh_back_kernel<<<gsz((size_t)B * NH), 256, 0, st>>>((size_t)B * NH, T.H2, T.d2);
+    // layer 2
+    if ((e = gemm<true, false>(NH, NH, B, T.d2, NH, T.H1, NH, nullptr, g + OW2, NH, 0, st))) return e;
+    colsum_kernel<<<(NH + 127) / 128, 128, 0, st>>>(B, NH, T.d2, g + OB2);
+    if ((e = gemm<false, false>(B, NH, NH, T.d2, NH, w + OW2, NH, nullptr, T.d1, NH, 0, st))) return e;
+    tanh_back_kernel<<<gsz((size_t)B * NH), 256, 0, st>>>((size_t)B * NH, T.H1, T.d1);
+    // layer 1
+    if ((e = gemm<true, false>(NH, NIN, B, T.d1, NH, T.Xb, NIN, nullptr, g + OW1, NIN, 0, st))) return e;
+    colsum_kernel<<<(NH + 127) / 128, 128, 0, st>>>(B, NH, T.d1, g + OB1);
+    return cudaGetLastError();
+}
+
+cudaError_t train_setup(Train &T, const float *w, const double *X, const double *stats, int n_points, int B,
+                        cudaStream_t st)
+{
+    cudaError_t e;
+    T.B = B;
+    auto al = [&](void **p, size_t bytes) { return cudaMalloc(p, bytes); };
+    if ((e = al((void **)&T.w, NW * 4)) || (e = al((void **)&T.g, NW * 4)) || (e = al((void **)&T.m, NW * 4)) ||
+        (e = al((void **)&T.v, NW * 4)) || (e = al((void **)&T.X, (size_t)n_points * NIN * 4)) ||
+        (e = al((void **)&T.Xb, (size_t)B * NIN * 4)) || (e = al((void **)&T.H1, (size_t)B * NH * 4)) ||
+        (e = al((void **)&T.H2, (size_t)B * NH * 4)) || (e = al((void **)&T.H3, (size_t)B * NH * 4)) ||
+        (e = al((void **)&T.C, (size_t)B * NOUT * 4)) || (e = al((void **)&T.dC, (size_t)B * NOUT * 4)) ||
+        (e = al((void **)&T.d3, (size_t)B * NH * 4)) || (e = al((void **)&T.d2, (size_t)B * NH * 4)) ||
+        (e = al((void **)&T.d1, (size_t)B * NH * 4)) || (e = al((void **)&T.stats, (size_t)n_points * NST * 8)) ||
+        (e = al((void **)&T.loss, 8)) || (e = al((void **)&T.idx, (size_t)std::max(B, n_points) * 4)))
+        return e;
+    std::vector<float> Xf((size_t)n_points * NIN);
+    for (size_t i = 0; i < Xf.size(); ++i) Xf[i] = (float)X[i];
+    if ((e = cudaMemcpyAsync(T.w, w, NW * 4, cudaMemcpyHostToDevice, st))) return e;
+    if ((e = cudaMemcpyAsync(T.X, Xf.data(), Xf.size() * 4, cudaMemcpyHostToDevice, st))) return e;
+    if ((e = cudaMemcpyAsync(T.stats, stats, (size_t)n_points * NST * 8, cudaMemcpyHostToDevice, st))) return e;
+    if ((e = cudaMemsetAsync(T.m, 0, NW * 4, st))) return e;
+    if ((e = cudaMemsetAsync(T.v, 0, NW * 4, st))) return e;
+    return cudaStreamSynchronize(st);
+}
+
+}  // namespace
+
+// ---- internal entry points used by qhfpe_api.cu ---------------------------------------------------
+template <typename T>
+cudaError_t launch_closure_apply(const GridInfo &g, T *state, int e_n, int e_n1, int e_slot, const T *coef, int rep0,
+                                 int n_rep, cudaStream_t st)
+{
+    const size_t total = (size_t)n_rep * g.S * g.S * g.blk;
+    closure_apply_kernel<T><<<gsz(total), 256, 0, st>>>(g, state, e_n, e_n1, e_slot, coef, rep0, n_rep);
+    return cudaGetLastError();
+}
+template cudaError_t launch_closure_apply<float>(const GridInfo &, float *, int, int, int, const float *, int, int, cudaStream_t);
+template cudaError_t launch_closure_apply<double>(const GridInfo &, double *, int, int, int, const double *, int, int, cudaStream_t);
+
+template <typename T>
+cudaError_t launch_closure_collect(const GridInfo &g, const T *state, int e_t, int e_t1, int e_t2, double *stats,
+                                   cudaStream_t st)
+{
+    collect_kernel<T><<<gsz((size_t)g.n_rep * g.blk), 256, 0, st>>>(g, state, e_t, e_t1, e_t2, stats);
+    return cudaGetLastError();
+}
+template cudaError_t launch_closure_collect<float>(const GridInfo &, const float *, int, int, int, double *, cudaStream_t);
+template cudaError_t launch_closure_collect<double>(const GridInfo &, const double *, int, int, int, double *, cudaStream_t);
+
+cudaError_t launch_closure_infer(const GridInfo &g, double eta, const float *w_dev, int bf16, double *out64,
+                                 float *out32, cudaStream_t st)
+{
+    const int n = (int)g.blk;
+    infer_kernel<<<(n + IPTS - 1) / IPTS, 256, 0, st>>>(n, g.np, g.q_min, g.dq, g.p_min, g.dp, std::log(eta), w_dev, bf16,
+                                                 out64, out32);
+    return cudaGetLastError();
+}
+
+// ---- C ABI ----------------------------------------------------------------------------------------
+extern "C" qhfpe_status qhfpe_closure_loss_grad(const float *w, const double *X, const double *stats, int n_points,
+                                                double ridge, double *loss, float *grad)
+{
+    if (!w || !X || !stats || n_points < 1 || !loss || !grad || !(ridge >= 0.0)) {
+        qh_set_free_error("closure_loss_grad: invalid argument");
+        return QHFPE_EINVAL;
+    }
+    double ntot = 0.0;
+    for (int x = 0; x < n_points; ++x) ntot += stats[(size_t)x * NST + 66];
+    if (!(ntot > 0.0)) {
+        qh_set_free_error("closure_loss_grad: statistics hold no samples");
+        return QHFPE_EINVAL;
+    }
+    cudaStream_t st = nullptr;
+    Train T;
+    cudaError_t e = train_setup(T, w, X, stats, n_points, n_points, st);
+    std::vector<int> idx(n_points);
+    for (int x = 0; x < n_points; ++x) idx[x] = x;
+    if (!e) e = cudaMemcpy(T.idx, idx.data(), (size_t)n_points * 4, cudaMemcpyHostToDevice);
+    if (!e) e = forward_backward(T, n_points, 1.0 / ntot, ridge, st);
+    if (!e) e = cudaMemcpy(loss, T.loss, 8, cudaMemcpyDeviceToHost);
+    if (!e) e = cudaMemcpy(grad, T.g, NW * 4, cudaMemcpyDeviceToHost);
+    if (e) {
+        qh_set_free_error(std::string("closure_loss_grad: ") + cudaGetErrorString(e));
+        return QHFPE_ECUDA;
+    }
+    return QHFPE_OK;
+}
+
+extern "C" qhfpe_status qhfpe_closure_train(float *w, const double *X, const double *stats, int n_points, int n_iters,
+                                            int batch, double lr, double ridge, unsigned seed, double *loss_history)
+{
+    if (!w || !X || !stats || n_points < 1 || n_iters < 0 || batch < 1 || !(lr > 0.0) || !(ridge >= 0.0)) {
+        qh_set_free_error("closure_train: invalid argument");
+        return QHFPE_EINVAL;
+    }
+    double ntot = 0.0;
+    for (int x = 0; x < n_points; ++x) ntot += stats[(size_t)x * NST + 66];
+    if (!(ntot > 0.0)) {
+        qh_set_free_error("closure_train: statistics hold no samples");
+        return QHFPE_EINVAL;
+    }
+    const int B = std::min(batch, n_points);
+    cudaStream_t st = nullptr;
+    Train T;
+    cudaError_t e = train_setup(T, w, X, stats, n_points, B, st);
+    std::mt19937 rng(seed);
+    std::vector<int> perm(n_points);
+    for (int x = 0; x < n_points; ++x) perm[x] = x;
+    size_t pos = n_points;
+    // each minibatch estimates the full mean: scale by n_points / (B * ntot)
+    const double inv = (double)n_points / ((double)B * ntot);
+    const float b1 = 0.9f, b2 = 0.999f;
+    double c1 = 1.0, c2 = 1.0;
+    for (int it = 0; it < n_iters && !e; ++it) {
+        if (pos + B > (size_t)n_points) {
+            std::shuffle(perm.begin(), perm.end(), rng);
+            pos = 0;
+        }
+        e = cudaMemcpyAsync(T.idx, perm.data() + pos, (size_t)B * 4, cudaMemcpyHostToDevice, st);
+        pos += B;
+        if (!e) e = forward_backward(T, B, inv, ridge, st);
+        c1 *= b1;
+        c2 *= b2;
+        if (!e) {
+            adam_kernel<<<gsz(NW), 256, 0, st>>>(NW, T.w, T.g, T.m, T.v, (float)lr, b1, b2, 1e-8f, (float)(1.0 - c1),
+                                                  (float)(1.0 - c2));
+            e = cudaGetLastError();
+        }
+        if (!e && loss_history) {
+            e = cudaMemcpyAsync(loss_history + it, T.loss, 8, cudaMemcpyDeviceToHost, st);
+            if (!e) e = cudaStreamSynchronize(st);
+        }
+    }
+    if (!e) e = cudaMemcpy(w, T.w, NW * 4, cudaMemcpyDeviceToHost);
+    if (e) {
+        qh_set_free_error(std::string("closure_train: ") + cudaGetErrorString(e));
+        return QHFPE_ECUDA;
+    }
+    return QHFPE_OK;
+}

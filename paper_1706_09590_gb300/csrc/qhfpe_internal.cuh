@@ -99,6 +99,16 @@ cudaError_t launch_fused(const GridInfo &g, const ElemInfo *elems, const FusedTa
 template <typename T, bool MIXED>
 cudaError_t prepare_fused(int np, int S);
 
+// ---- learned closure (qhfpe_closure.cu) ---------------------------------------------------------------
+template <typename T>
+cudaError_t launch_closure_apply(const GridInfo &g, T *state, int e_n, int e_n1, int e_slot, const T *coef, int rep0,
+                                 int n_rep, cudaStream_t st);
+template <typename T>
+cudaError_t launch_closure_collect(const GridInfo &g, const T *state, int e_t, int e_t1, int e_t2, double *stats,
+                                   cudaStream_t st);
+cudaError_t launch_closure_infer(const GridInfo &g, double eta, const float *w_dev, int bf16, double *out64,
+                                 float *out32, cudaStream_t st);
+
 // Error text for calls without a handle (failed create, the static-scratch entry point).
 void qh_set_free_error(const std::string &msg);
 

@@ -29,7 +29,12 @@ EXPORTED = [
     "qhfpe_step", "qhfpe_apply_dipole", "qhfpe_apply_rhs", "qhfpe_trace", "qhfpe_equilibrate",
     "qhfpe_set_equilibrium", "qhfpe_response", "qhfpe_spectrum_absorption", "qhfpe_spectrum_2d",
     "qhfpe_kernel_timing", "qhfpe_kernel_timing_read", "qhfpe_potential_term_static",
+    "qhfpe_closure_collect", "qhfpe_closure_load", "qhfpe_closure_coefficients", "qhfpe_closure_loss_grad",
+    "qhfpe_closure_train",
 ]
+
+CLOSURE_N_WEIGHTS = 135178
+CLOSURE_N_STATS = 67
 
 
 class QhfpeError(RuntimeError):
@@ -95,6 +100,12 @@ def lib():
     L.qhfpe_kernel_timing_read.argtypes = [vp, ctypes.POINTER(ctypes.c_long), dp, ctypes.c_int]
     L.qhfpe_potential_term_static.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double,
                                               ctypes.c_double, vp, ctypes.c_int, vp, vp, vp]
+    L.qhfpe_closure_collect.argtypes = [vp, ctypes.c_int, vp]
+    L.qhfpe_closure_load.argtypes = [vp, vp, ctypes.c_size_t]
+    L.qhfpe_closure_coefficients.argtypes = [vp, vp]
+    L.qhfpe_closure_loss_grad.argtypes = [vp, vp, vp, ctypes.c_int, ctypes.c_double, dp, vp]
+    L.qhfpe_closure_train.argtypes = [vp, vp, vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                      ctypes.c_double, ctypes.c_uint, vp]
     for name in EXPORTED:
         if name != "qhfpe_last_error":
             getattr(L, name).restype = st
@@ -131,6 +142,35 @@ def potential_term_static(U_table_dev, W_dev, out_dev, n_states, nq, np_, p_min,
                                       ptr(out_dev), sptr)
     if s != 0:
         raise QhfpeError(s, L.qhfpe_last_error(None).decode())
+
+
+def closure_loss_grad(w, X, stats, ridge=0.0):
+    """Mean squared closure error and its gradient (FP32 kernels) for weights w on points X [n][3]
+    with statistics [n][67]."""
+    L = lib()
+    w = np.ascontiguousarray(w, dtype=np.float32)
+    X = np.ascontiguousarray(X, dtype=np.float64)
+    stats = np.ascontiguousarray(stats, dtype=np.float64)
+    assert w.size == CLOSURE_N_WEIGHTS and X.shape[1] == 3 and stats.shape == (X.shape[0], CLOSURE_N_STATS)
+    loss = ctypes.c_double()
+    grad = np.zeros(CLOSURE_N_WEIGHTS, dtype=np.float32)
+    s = L.qhfpe_closure_loss_grad(_ptr(w), _ptr(X), _ptr(stats), X.shape[0], ridge, ctypes.byref(loss), _ptr(grad))
+    if s != 0:
+        raise QhfpeError(s, L.qhfpe_last_error(None).decode())
+    return loss.value, grad
+
+
+def closure_train(w, X, stats, n_iters, batch=4096, lr=1e-3, ridge=0.0, seed=1706):
+    """Adam training of the closure network on the device; returns (weights, per-iteration loss)."""
+    L = lib()
+    w = np.ascontiguousarray(w, dtype=np.float32).copy()
+    X = np.ascontiguousarray(X, dtype=np.float64)
+    stats = np.ascontiguousarray(stats, dtype=np.float64)
+    hist = np.zeros(max(n_iters, 1))
+    s = L.qhfpe_closure_train(_ptr(w), _ptr(X), _ptr(stats), X.shape[0], n_iters, batch, lr, ridge, seed, _ptr(hist))
+    if s != 0:
+        raise QhfpeError(s, L.qhfpe_last_error(None).decode())
+    return w, hist[:n_iters]
 
 
 class Propagator:
@@ -299,6 +339,23 @@ class Propagator:
         self._check(self._L.qhfpe_spectrum_2d(self._h, _ptr(R3), R3.shape[0], R3.shape[1] - 1, dt1, dt3, _ptr(w1),
                                               len(w1), _ptr(w3), len(w3), _ptr(nr), _ptr(re)))
         return nr, re, nr + re
+
+    # ---- learned closure --------------------------------------------------------------------------
+    def closure_collect(self, target_tier, stats_dev):
+        """Accumulate regression statistics of `target_tier` into stats_dev (CUDA float64 tensor of
+        nq*np*67 values)."""
+        ptr, dev = _dev_ptr(stats_dev)
+        assert dev == 1
+        self._check(self._L.qhfpe_closure_collect(self._h, int(target_tier), ptr))
+
+    def closure_load(self, weights):
+        w = np.ascontiguousarray(weights, dtype=np.float32)
+        self._check(self._L.qhfpe_closure_load(self._h, _ptr(w), w.size))
+
+    def closure_coefficients(self):
+        out = np.zeros((self.model["nq"], self.model["np"], 10))
+        self._check(self._L.qhfpe_closure_coefficients(self._h, _ptr(out)))
+        return out
 
     # ---- measurement -----------------------------------------------------------------------------
     def kernel_timing(self, enable):

@@ -15,28 +15,36 @@ def _small_model(depth=3, closure=2, **kw):
     return m
 
 
-def test_statistics_reproduce_the_direct_squared_error():
-    """sum_x (c^T G c - 2 c^T h + yy) / n equals the mean of |sum_f c_f phi_f - y|^2 over all samples."""
+@pytest.mark.parametrize("terminator", [False, True])
+def test_statistics_reproduce_the_direct_squared_error(terminator):
+    """sum_x (c^T G c - 2 c^T h + yy) / n equals the mean of |sum_f c_f phi_f - y|^2 over all samples,
+    with y the target tier itself or its residual after the terminator's estimate."""
     m = _small_model(depth=4)
     W = qi.random_state(m, seed=3)
     tier = 3
+    p = qi.axis(16, -8, 8)
+    dp = p[1] - p[0]
+    r0, c0 = (0.7, 1.3) if terminator else (0.0, 0.0)
     w = cl.init_weights(7)
     w[-cl.N_OUT * (cl.N_HID + 1):] = np.random.default_rng(8).normal(size=cl.N_OUT * (cl.N_HID + 1)) * 0.1
-    X = cl.inputs(*np.meshgrid(qi.axis(8, -8, 8), qi.axis(16, -8, 8), indexing="ij"), m["eta"]).reshape(-1, 3)
-    stats = cl.statistics(W, tier)
+    X = cl.inputs(*np.meshgrid(qi.axis(8, -8, 8), p, indexing="ij"), m["eta"]).reshape(-1, 3)
+    stats = cl.statistics(W, tier, r0, c0, p, dp)
     L = cl.loss(w, X, stats)
-    phi, y = cl.patch_samples(W, tier)
     c, _ = cl.forward(w, X)
     c = c.reshape(8, 16, 10)
-    pred = np.einsum("xyf,xysf->xys", c, phi)
-    direct = (np.abs(pred - y) ** 2).sum() / y.size
+    # direct: the terminator's estimate r0 p W^N + c0 (4th-order d/dp) W^N, then the patch combination
+    WN, WN1, Wt = W[tier - 1], W[tier - 2], W[tier]
+    dWN = (np.roll(WN, 2, -1) - 8 * np.roll(WN, 1, -1) + 8 * np.roll(WN, -1, -1) - np.roll(WN, -2, -1)) / (12 * dp)
+    target = Wt - (r0 * p * WN + c0 * dWN)
+    pred = np.zeros_like(Wt)
+    for b in range(-2, 3):
+        pred += c[..., 2 + b] * np.roll(WN, -b, -1) + c[..., 7 + b] * np.roll(WN1, -b, -1)
+    direct = (np.abs(pred - target) ** 2).sum() / target.size
     assert L == pytest.approx(direct, rel=1e-12)
-    # the patch: phi_{2+b}(l) = W^N(l+b), phi_{7+b}(l) = W^(N-1)(l+b) (p periodic)
-    assert phi[2, 5, 1, 2 + 1] == W[tier - 1, 0, 1, 2, 6]
-    assert phi[2, 0, 3, 7 - 2] == W[tier - 2, 1, 1, 2, 14]
 
 
-def test_backprop_gradient_matches_finite_differences():
+@pytest.mark.parametrize("lam", [0.0, 0.3])
+def test_backprop_gradient_matches_finite_differences(lam):
     m = _small_model(depth=4)
     W = qi.random_state(m, seed=4)
     stats = cl.statistics(W, 3)
@@ -44,8 +52,8 @@ def test_backprop_gradient_matches_finite_differences():
     w = cl.init_weights(9)
     rng = np.random.default_rng(10)
     w[-cl.N_OUT * (cl.N_HID + 1):] = rng.normal(size=cl.N_OUT * (cl.N_HID + 1)) * 0.05
-    L, g = cl.loss_and_grad(w, X, stats)
-    assert L == pytest.approx(cl.loss(w, X, stats), rel=1e-14)
+    L, g = cl.loss_and_grad(w, X, stats, lam)
+    assert L == pytest.approx(cl.loss(w, X, stats, lam), rel=1e-14)
     idx = np.concatenate([rng.choice(768, 6, replace=False),                      # W1
                           768 + rng.choice(256, 3, replace=False),                # b1
                           1024 + rng.choice(65536, 6, replace=False),             # W2
@@ -55,57 +63,53 @@ def test_backprop_gradient_matches_finite_differences():
         wp, wm = w.copy(), w.copy()
         wp[k] += e
         wm[k] -= e
-        fd = (cl.loss(wp, X, stats) - cl.loss(wm, X, stats)) / (2 * e)
+        fd = (cl.loss(wp, X, stats, lam) - cl.loss(wm, X, stats, lam)) / (2 * e)
         assert g[k] == pytest.approx(fd, rel=2e-6, abs=1e-10)
 
 
-def test_zero_coefficients_are_the_plain_truncation():
+def test_zero_coefficients_are_the_terminator():
     m = _small_model(depth=3)
     W = qi.random_state(m, seed=5)
     coef = np.zeros((m["nq"], m["np"], 10))
     L_learned = oracle.Oracle(m, closure_coef=coef).rhs(W)
-    mt = dict(m, closure=0)
-    assert np.array_equal(L_learned, oracle.Oracle(mt).rhs(W))
+    assert np.array_equal(L_learned, oracle.Oracle(dict(m, closure=1)).rhs(W))
 
 
 def test_closure_term_on_plane_waves():
-    """Constant coefficients c = e_{2+1} read W^(N+1)(l) = W^N(l+1); on W^N = exp(i kappa p) the top
-    tier gets d/dp of exp(i kappa dp) W^N, with the 4th-order difference's symbol
-    i (8 sin(kappa dp) - sin(2 kappa dp)) / (6 dp)."""
+    """Constant coefficients c = e_{2+1} add W^N(l+1) to the terminator's W^(N+1); on
+    W^N = exp(i kappa p) the top tier gains d/dp of exp(i kappa dp) W^N, with the 4th-order
+    difference's symbol i (8 sin(kappa dp) - sin(2 kappa dp)) / (6 dp)."""
     m = _small_model(depth=2)
     coef = np.zeros((m["nq"], m["np"], 10))
     coef[..., 3] = 1.0
     O = oracle.Oracle(m, closure_coef=coef)
+    Ot = oracle.Oracle(dict(m, closure=1))
     n_p, dp = m["np"], O.dp
     k = 3
     kappa = 2 * math.pi * k / (n_p * dp)
     W = np.zeros(O.shape, complex)
     W[2, 1, 0] = np.exp(2j * math.pi * k * np.arange(n_p) / n_p)[None, :] * np.ones((m["nq"], 1))
-    out = O.rhs(W, oracle.TIER_UP)
+    out = O.rhs(W, oracle.TIER_UP) - Ot.rhs(W, oracle.TIER_UP)
     symbol = 1j * (8 * math.sin(kappa * dp) - math.sin(2 * kappa * dp)) / (6 * dp)
     expect = symbol * np.exp(1j * kappa * dp) * W[2, 1, 0]
     assert np.allclose(out[2, 1, 0], expect, atol=1e-12)
-    # the ordinary coupling of tier 1 to tier 2 is d/dp W^2, with the same symbol
-    assert np.allclose(out[1, 1, 0], symbol * W[2, 1, 0], atol=1e-12)
-    assert np.abs(out[0]).max() < 1e-13
+    assert np.abs(out[:2]).max() < 1e-13
 
 
-def test_terminator_momentum_part_as_closure():
-    """Coefficients c_2 = r_0 p (the rest zero) give the Eq. (GMFP) terminator without its
-    c_0 d2/dp2 part."""
+def test_correction_can_cancel_the_terminator_momentum_part():
+    """c_2 = -r_0 p removes d/dp (r_0 p W^N) from the terminator's term, leaving c_0 d2W^N/dp2."""
     m = _small_model(depth=2)
     W = qi.random_state(m, seed=6)
     p = qi.axis(m["np"], m["p_min"], m["p_max"])
     r0 = m["eta"]
     coef = np.zeros((m["nq"], m["np"], 10))
-    coef[..., 2] = r0 * p[None, :]
+    coef[..., 2] = -r0 * p[None, :]
     L_learned = oracle.Oracle(m, closure_coef=coef).rhs(W)
     O_t = oracle.Oracle(dict(m, closure=1))
     L_term = O_t.rhs(W)
-    c0 = O_t.coefficients()["c"][0]
-    dpp = np.array([-1, 16, -30, 16, -1]) / (12 * O_t.dp ** 2)
+    d1 = np.array([1, -8, 0, 8, -1]) / (12 * O_t.dp)
     top = W[2]
-    d2 = sum(dpp[t] * np.roll(top, 2 - t, axis=-1) for t in range(5))
+    dpw = sum(d1[t] * np.roll(r0 * p * top, 2 - t, axis=-1) for t in range(5))
     diff = L_term - L_learned
-    assert np.allclose(diff[2], c0 * d2, atol=1e-11)
+    assert np.allclose(diff[2], dpw, atol=1e-11)
     assert np.abs(diff[:2]).max() < 1e-12
