@@ -126,6 +126,8 @@ struct Model {
     int closure_n = -1, closure_n1 = -1;  // elements of tiers N and N-1 (chain, K = 0)
     double *coef64 = nullptr;   // closure coefficients [nq][np][10] (owned by the handle)
     float *coef32 = nullptr;
+    float *tcN = nullptr;       // tensor-core path: FP32 tables in natural mode order (D | L | R)
+    void *tcB = nullptr;        // tensor-core path: pre-swizzled bf16 hi/lo cosine and sine tiles
     bool fused = false;         // fused stage kernel available for (np, S)
     double *ftab64 = nullptr;   // its tables (digit-reversed order, np twiddles)
     float *ftab32 = nullptr;
@@ -139,6 +141,8 @@ struct Model {
         if (tab32) cudaFree(tab32);
         if (ftab64) cudaFree(ftab64);
         if (ftab32) cudaFree(ftab32);
+        if (tcN) cudaFree(tcN);
+        if (tcB) cudaFree(tcB);
     }
 };
 
@@ -160,6 +164,7 @@ struct Prop {
     Model *m = nullptr;
     GridInfo g{};
     bool mixed = false;
+    bool tc = false;        // potential term on the tensor cores (bf16 x3)
     double dt = 0.0;
     void *y = nullptr, *vA = nullptr, *vB = nullptr, *P = nullptr;
     double *y0 = nullptr;
@@ -193,6 +198,7 @@ struct qhfpe {
     double *scratch = nullptr;
     size_t scratch_cap = 0;
     int *flag = nullptr;    // device flag for non-finite input checks
+    int *tc_err = nullptr;  // device flag: a tensor-core kernel gave up waiting
     double *coef64 = nullptr;  // learned-closure coefficient table [nq][np][10]
     float *coef32 = nullptr;
     float *closure_w = nullptr;
@@ -205,6 +211,7 @@ struct qhfpe {
         if (eq) cudaFree(eq);
         if (scratch) cudaFree(scratch);
         if (flag) cudaFree(flag);
+        if (tc_err) cudaFree(tc_err);
         model.reset();
         ground.reset();
         if (coef64) cudaFree(coef64);
@@ -402,6 +409,18 @@ qhfpe_status build_model(qhfpe *h, Model &M, int S, const double *U, const doubl
         QH_CK(h, (prepare_fused<float, true>(p.np, S)));
         QH_CK(h, (prepare_fused<double, false>(p.np, S)));
     }
+    if (p.precision == QHFPE_MIXED_BF16X3 && tc_supported(p.np, S)) {
+        std::vector<double> nt;
+        build_tables(M, U, nt, [](int pos) { return pos; }, 0);
+        std::vector<float> nt32(nt.begin(), nt.begin() + 3 * M.tab_n);
+        QH_CK(h, dalloc(&M.tcN, nt32.size()));
+        QH_CK(h, cudaMemcpyAsync(M.tcN, nt32.data(), sizeof(float) * nt32.size(), cudaMemcpyHostToDevice, st));
+        std::vector<uint16_t> bm;
+        build_tc_matrices(p.np, bm);
+        QH_CK(h, cudaMalloc(&M.tcB, bm.size() * sizeof(uint16_t)));
+        QH_CK(h, cudaMemcpyAsync(M.tcB, bm.data(), bm.size() * sizeof(uint16_t), cudaMemcpyHostToDevice, st));
+        QH_CK(h, prepare_tc(p.np, S));
+    }
     QH_CK(h, cudaStreamSynchronize(st));
     return QHFPE_OK;
 }
@@ -414,6 +433,7 @@ qhfpe_status make_prop(qhfpe *h, Model *M, int n_rep, bool mixed, double dt, std
     P->g = M->g;
     P->g.n_rep = n_rep;
     P->mixed = mixed;
+    P->tc = mixed && M->tcB != nullptr;
     P->dt = dt;
     const size_t n = (size_t)n_rep * P->g.rep_stride;
     const size_t es = mixed ? sizeof(float) : sizeof(double);
@@ -498,6 +518,18 @@ qhfpe_status step_once(qhfpe *h, Prop &P, bool record)
             qhfpe_status r = closure_fill<T>(h, P, in, 0, P.g.n_rep);
             if (r != QHFPE_OK) return r;
         }
+        if (MIXED && P.tc) {
+            {
+                Bracket br(h, QH_KIND_POT);
+                QH_CK(h, launch_potential_tc(P.g, (const float *)in, (float *)Pt, M.tcB, M.tcN, M.tcN + M.tab_n,
+                                             M.tcN + 2 * M.tab_n, P.g.n_rep, h->tc_err, st));
+            }
+            Bracket br(h, QH_KIND_STAGE);
+            QH_CK(h, (launch_fused<float, true>(P.g, M.elems, M.f32(), (const float *)in, (const float *)y, P.y0,
+                                               (float *)out, k == 1 ? P.y0 : nullptr, P.dt / k, k == 1 ? 2 : 1,
+                                               QHFPE_TERM_ALL, 0, P.g.n_rep, st, (const float *)Pt)));
+            continue;
+        }
         if (M.fused) {
             Bracket br(h, QH_KIND_STAGE);
             if (MIXED)
@@ -577,6 +609,19 @@ qhfpe_status run_steps(qhfpe *h, Prop &P, long n_steps, double *trace_dev, long 
         }
         QH_CK(h, cudaGraphLaunch(ge, st));
         done += len;
+    }
+    return QHFPE_OK;
+}
+
+// After a synchronisation: did a tensor-core kernel give up waiting?
+qhfpe_status check_timeout(qhfpe *h)
+{
+    if (!h->tc_err) return QHFPE_OK;
+    int bad = 0;
+    QH_CK(h, cudaMemcpy(&bad, h->tc_err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (bad) {
+        h->sticky = true;
+        return h->fail(QHFPE_ETIMEOUT, "a tensor-core kernel gave up waiting for its MMAs");
     }
     return QHFPE_OK;
 }
@@ -696,12 +741,11 @@ qhfpe_status qhfpe_create(const qhfpe_params *params, void *stream, qhfpe_t **ou
     if (p.closure == QHFPE_LEARNED && p.n_matsubara != 0) return bad("the learned closure needs n_matsubara = 0");
     if (p.closure != QHFPE_TRUNCATE && p.closure != QHFPE_TERMINATOR && p.closure != QHFPE_LEARNED)
         return bad("unknown closure");
-    if (p.precision != QHFPE_FP64 && p.precision != QHFPE_MIXED) {
-        if (p.precision == QHFPE_MIXED_BF16X3) {
-            create_err = "the bf16x3 tensor-core potential kernel is not available in this build";
-            return QHFPE_EUNSUPPORTED;
-        }
+    if (p.precision != QHFPE_FP64 && p.precision != QHFPE_MIXED && p.precision != QHFPE_MIXED_BF16X3)
         return bad("unknown precision");
+    if (p.precision == QHFPE_MIXED_BF16X3 && !tc_supported(p.np, p.n_states)) {
+        create_err = "the bf16x3 tensor-core potential kernel covers np in {64, 128} and n_states <= 2";
+        return QHFPE_EUNSUPPORTED;
     }
     if (p.n_replicas < 1) return bad("n_replicas must be >= 1");
     if (!(p.beta > 0.0) || !(p.gamma > 0.0) || !(p.eta >= 0.0)) return bad("bath parameters out of range");
@@ -754,6 +798,14 @@ qhfpe_status qhfpe_create(const qhfpe_params *params, void *stream, qhfpe_t **ou
     if (r != QHFPE_OK) {
         create_err = h->err;
         return r;
+    }
+    if (h->model->tcB) {
+        cudaError_t e = cudaMalloc((void **)&h->tc_err, sizeof(int));
+        if (e == cudaSuccess) e = cudaMemsetAsync(h->tc_err, 0, sizeof(int), h->stream);
+        if (e != cudaSuccess) {
+            create_err = std::string("create: ") + cudaGetErrorString(e);
+            return QHFPE_ECUDA;
+        }
     }
     r = make_prop(h.get(), h->model.get(), p.n_replicas, p.precision != QHFPE_FP64, p.dt, h->main);
     if (r != QHFPE_OK) {
@@ -902,7 +954,7 @@ qhfpe_status qhfpe_step(qhfpe_t *h, long n_steps, double *trace_out)
         QH_CK(h, cudaMemcpyAsync(trace_out, tr, (size_t)P.g.n_rep * stride * 2 * sizeof(double), cudaMemcpyDeviceToHost,
                                  h->stream));
     QH_CK(h, cudaStreamSynchronize(h->stream));
-    return QHFPE_OK;
+    return check_timeout(h);
 }
 
 qhfpe_status qhfpe_apply_dipole(qhfpe_t *h, int side, const int *replicas, int n)
@@ -940,7 +992,12 @@ qhfpe_status qhfpe_apply_rhs(qhfpe_t *h, int replica, int terms, double *out)
     const Model &M = *P.m;
     r = P.mixed ? closure_fill<float>(h, P, (float *)P.y, replica, 1) : closure_fill<double>(h, P, (double *)P.y, replica, 1);
     if (r != QHFPE_OK) return r;
-    if (M.fused) {
+    if (P.tc) {
+        QH_CK(h, launch_potential_tc(P.g, (const float *)P.y, (float *)P.P, M.tcB, M.tcN, M.tcN + M.tab_n,
+                                     M.tcN + 2 * M.tab_n, P.g.n_rep, h->tc_err, st));
+        QH_CK(h, (launch_fused<float, true>(P.g, M.elems, M.f32(), (const float *)P.y, (const float *)P.y, P.y0,
+                                           (float *)P.vA, nullptr, 0.0, 0, terms, replica, 1, st, (const float *)P.P)));
+    } else if (M.fused) {
         if (P.mixed)
             QH_CK(h, (launch_fused<float, true>(P.g, M.elems, M.f32(), (const float *)P.y, (const float *)P.y, P.y0,
                                                (float *)P.vA, nullptr, 0.0, 0, terms, replica, 1, st)));
@@ -964,7 +1021,7 @@ qhfpe_status qhfpe_apply_rhs(qhfpe_t *h, int replica, int terms, double *out)
     if (r != QHFPE_OK) return r;
     QH_CK(h, cudaMemcpyAsync(out, h->scratch, n * 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
     QH_CK(h, cudaStreamSynchronize(st));
-    return QHFPE_OK;
+    return check_timeout(h);
 }
 
 qhfpe_status qhfpe_trace(qhfpe_t *h, double *out)
@@ -1102,6 +1159,7 @@ qhfpe_status qhfpe_response(qhfpe_t *h, const qhfpe_schedule *s, double *R_out)
         std::vector<double> tr(2 * nt);
         QH_CK(h, cudaMemcpyAsync(tr.data(), B->trace_buf, nt * 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
         QH_CK(h, cudaStreamSynchronize(st));
+        if ((r = check_timeout(h)) != QHFPE_OK) return r;
         for (long c = 0; c < nt; ++c) {  // R1 = i * Tr
             R_out[2 * c] = -tr[2 * c + 1];
             R_out[2 * c + 1] = tr[2 * c];
@@ -1168,6 +1226,7 @@ qhfpe_status qhfpe_response(qhfpe_t *h, const qhfpe_schedule *s, double *R_out)
     std::vector<double> tr((size_t)n3 * nt * 2);
     QH_CK(h, cudaMemcpyAsync(tr.data(), P3->trace_buf, tr.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
     QH_CK(h, cudaStreamSynchronize(st));
+    if ((r = check_timeout(h)) != QHFPE_OK) return r;
     for (size_t c = 0; c < (size_t)n3 * nt; ++c) {  // R3 = i^3 Tr = -i Tr
         R_out[2 * c] = tr[2 * c + 1];
         R_out[2 * c + 1] = -tr[2 * c];

@@ -169,7 +169,7 @@ template <typename T, int NP, int S, bool MIXED>
 __global__ void __launch_bounds__(FTHREADS, sizeof(T) == 4 ? 3 : 1)
 fused_stage_kernel(GridInfo g, const ElemInfo *__restrict__ elems, FusedTables<T> tab, const T *__restrict__ v_in,
                    const T *y, const double *y0, T *v_out, double *y0_out, double h, int mode, int terms, int rep0,
-                   int n_rep, int tq)
+                   int n_rep, int tq, const T *__restrict__ Pg)
 {
     using C = typename V2<T>::type;
     constexpr int S2 = S * S;
@@ -191,7 +191,7 @@ fused_stage_kernel(GridInfo g, const ElemInfo *__restrict__ elems, FusedTables<T
 
     // ---- phase A: potential term -------------------------------------------------------------
     const bool want_pot = (terms & 2) != 0;
-    if (want_pot) {
+    if (want_pot && !Pg) {
         for (int idx = threadIdx.x; idx < rows * S2 * NP; idx += FTHREADS) {
             const int l = idx % NP, rp = idx / NP;
             const int pr = rp % S2, r = rp / S2;
@@ -399,7 +399,16 @@ fused_stage_kernel(GridInfo g, const ElemInfo *__restrict__ elems, FusedTables<T
                 ai[v] += f * (-ei[v] + (T)16 * ei[v + 1] - (T)30 * ei[v + 2] + (T)16 * ei[v + 3] - ei[v + 4]);
             }
         }
-        if (want_pot) {
+        if (want_pot && Pg) {  // potential term computed by another kernel
+            T pr_[VEC], pi_[VEC];
+            ldv<T, VEC>(Pg + poff + (size_t)i * NP + l0, pr_);
+            ldv<T, VEC>(Pg + poff + blk + (size_t)i * NP + l0, pi_);
+#pragma unroll
+            for (int v = 0; v < VEC; ++v) {
+                ar[v] += pr_[v];
+                ai[v] += pi_[v];
+            }
+        } else if (want_pot) {
             const int pb = (r * S2 + pr) * NP + l0;
 #pragma unroll
             for (int v = 0; v < VEC; ++v) {
@@ -451,7 +460,7 @@ size_t fused_smem_bytes(int tq, int np, int S, int elem_bytes)
 template <typename T, int NP, int S, bool MIXED>
 cudaError_t launch_fused_t(const GridInfo &g, const ElemInfo *elems, const FusedTables<T> &tab, const T *v_in,
                            const T *y, const double *y0, T *v_out, double *y0_out, double h, int mode, int terms,
-                           int rep0, int n_rep, cudaStream_t st)
+                           int rep0, int n_rep, cudaStream_t st, const T *Pg)
 {
     const int tq = fused_rows_per_tile(NP, S, sizeof(T));
     const size_t smem = fused_smem_bytes(tq, NP, S, sizeof(T));
@@ -459,7 +468,7 @@ cudaError_t launch_fused_t(const GridInfo &g, const ElemInfo *elems, const Fused
     const long blocks = (long)tiles * n_rep * g.n_elem;
     if (blocks <= 0) return cudaSuccess;
     fused_stage_kernel<T, NP, S, MIXED><<<(unsigned)blocks, FTHREADS, smem, st>>>(
-        g, elems, tab, v_in, y, y0, v_out, y0_out, h, mode, terms, rep0, n_rep, tq);
+        g, elems, tab, v_in, y, y0, v_out, y0_out, h, mode, terms, rep0, n_rep, tq, Pg);
     return cudaGetLastError();
 }
 
@@ -489,9 +498,9 @@ bool fused_supported(int np, int S) { return (np == 32 || np == 64 || np == 128 
 template <typename T, bool MIXED>
 cudaError_t launch_fused(const GridInfo &g, const ElemInfo *elems, const FusedTables<T> &tab, const T *v_in,
                          const T *y, const double *y0, T *v_out, double *y0_out, double h, int mode, int terms,
-                         int rep0, int n_rep, cudaStream_t st)
+                         int rep0, int n_rep, cudaStream_t st, const T *Pg)
 {
-#define QH_CALL(T_, NP_, S_, M_) launch_fused_t<T_, NP_, S_, M_>(g, elems, tab, v_in, y, y0, v_out, y0_out, h, mode, terms, rep0, n_rep, st)
+#define QH_CALL(T_, NP_, S_, M_) launch_fused_t<T_, NP_, S_, M_>(g, elems, tab, v_in, y, y0, v_out, y0_out, h, mode, terms, rep0, n_rep, st, Pg)
     switch (g.np * 8 + g.S) {
     case 32 * 8 + 1: return QH_CALL(T, 32, 1, MIXED);
     case 32 * 8 + 2: return QH_CALL(T, 32, 2, MIXED);
@@ -554,7 +563,7 @@ int fused_fft_frequency(int np, int pos)
     return k;
 }
 
-template cudaError_t launch_fused<float, true>(const GridInfo &, const ElemInfo *, const FusedTables<float> &, const float *, const float *, const double *, float *, double *, double, int, int, int, int, cudaStream_t);
-template cudaError_t launch_fused<double, false>(const GridInfo &, const ElemInfo *, const FusedTables<double> &, const double *, const double *, const double *, double *, double *, double, int, int, int, int, cudaStream_t);
+template cudaError_t launch_fused<float, true>(const GridInfo &, const ElemInfo *, const FusedTables<float> &, const float *, const float *, const double *, float *, double *, double, int, int, int, int, cudaStream_t, const float *);
+template cudaError_t launch_fused<double, false>(const GridInfo &, const ElemInfo *, const FusedTables<double> &, const double *, const double *, const double *, double *, double *, double, int, int, int, int, cudaStream_t, const double *);
 template cudaError_t prepare_fused<float, true>(int, int);
 template cudaError_t prepare_fused<double, false>(int, int);

@@ -7,6 +7,7 @@
 #include <stddef.h>
 
 #include <string>
+#include <vector>
 
 #define QH_MAX_MODES 8
 #define QH_MAX_S 4
@@ -92,10 +93,19 @@ bool fused_supported(int np, int S);
 int fused_rows_per_tile(int np, int S, int elem_bytes);
 size_t fused_smem_bytes(int tq, int np, int S, int elem_bytes);
 int fused_fft_frequency(int np, int pos);
+// Pg: potential term computed elsewhere (same layout as v_in), or nullptr to compute it in the kernel
 template <typename T, bool MIXED>
 cudaError_t launch_fused(const GridInfo &g, const ElemInfo *elems, const FusedTables<T> &tab, const T *v_in,
                          const T *y, const double *y0, T *v_out, double *y0_out, double h, int mode, int terms,
-                         int rep0, int n_rep, cudaStream_t st);
+                         int rep0, int n_rep, cudaStream_t st, const T *Pg = nullptr);
+
+// ---- tensor-core potential term (qhfpe_tc.cu) ----------------------------------------------------------
+bool tc_supported(int np, int S);
+cudaError_t prepare_tc(int np, int S);
+// tD/tL/tR: FP32 potential tables in natural mode order [pair][i][m]; bmat: build_tc_matrices output
+cudaError_t launch_potential_tc(const GridInfo &g, const float *v, float *P, const void *bmat, const float *tD,
+                                const float *tL, const float *tR, int n_rep, int *err, cudaStream_t st);
+void build_tc_matrices(int np, std::vector<uint16_t> &out);
 template <typename T, bool MIXED>
 cudaError_t prepare_fused(int np, int S);
 

@@ -1,0 +1,425 @@
+// Potential term of Eq. (quantum-liouvillian) as a DFT-as-GEMM on the tcgen05 tensor cores.
+//
+// Every (replica, element, q row, electronic pair) row of the state is a length-np complex vector
+// along p.  The forward transform (sign +) of a tile of 128 rows is a real GEMM against the cosine and
+// sine matrices C[m][l] = cos(2 pi m l/np), S[m][l] = sin(2 pi m l/np):
+//     D_re = W_re C - W_im S,   D_im = W_re S + W_im C,
+// the S x S r-space mixing with the potential tables (pre-scaled by 1/np, times -i) is applied per row
+// in the epilogue (the pairs of one q row sit in neighbouring TMEM lanes), and the inverse transform
+// (sign -) is a second GEMM:
+//     P_re = Y_re C + Y_im S,   P_im = Y_im C - Y_re S.
+// Operands are bf16 split in two (x = hi + lo, hi = bf16(x), lo = bf16(x - hi)); each real product
+// takes three MMAs (hi*hi + hi*lo + lo*hi) accumulating in FP32 in tensor memory.  Operands are staged
+// in shared memory in the 128-byte-swizzled K-major layout the MMA descriptors expect; C and S (hi/lo)
+// are pre-swizzled on the host and copied in per 64-wide K slice.
+//
+// One CTA of 128 threads per 128-row tile: thread t owns row (TMEM lane) t in the epilogues; thread 0
+// issues the MMAs.  Waits on the MMA-completion barrier are bounded: on timeout the kernel records an
+// error, skips the rest of its work, and still frees its tensor memory.
+#include "qhfpe_internal.cuh"
+
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include <cmath>
+#include <vector>
+
+namespace {
+
+constexpr int TC_THREADS = 128;
+constexpr int TILE_M = 128;
+constexpr unsigned long long WAIT_LIMIT_NS = 2000000000ull;  // give up on an MMA barrier after 2 s
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ uint64_t sdesc_sw128(uint32_t saddr)
+{
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr >> 4) & 0x3FFFu);  // start address (16-byte units)
+    d |= (uint64_t)1u << 16;                  // leading byte offset (unused for swizzled K-major)
+    d |= (uint64_t)(1024u >> 4) << 32;        // stride byte offset: 8 rows x 128 B
+    d |= (uint64_t)1u << 46;                  // descriptor version
+    d |= (uint64_t)2u << 61;                  // 128-byte swizzle
+    return d;
+}
+
+// kind::f16 instruction descriptor: bf16 A and B, FP32 accumulator, both K-major, M x N.
+__device__ __forceinline__ uint32_t idesc_bf16(int M, int N, bool neg_a)
+{
+    return (1u << 4) | (1u << 7) | (1u << 10) | (neg_a ? (1u << 13) : 0u) | ((uint32_t)(N >> 3) << 17) |
+           ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc));
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t mbar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar)
+                 : "memory");
+}
+
+__device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+__device__ __forceinline__ void mbar_init(uint32_t addr, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(addr), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ unsigned long long globaltimer_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// bounded wait for the barrier phase `parity` (wall-clock limit); false on timeout
+__device__ __forceinline__ bool mbar_wait(uint32_t addr, uint32_t parity)
+{
+    const unsigned long long t0 = globaltimer_ns();
+    for (;;) {
+        uint32_t done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}\n"
+            : "=r"(done)
+            : "r"(addr), "r"(parity)
+            : "memory");
+        if (done) return true;
+        if (globaltimer_ns() - t0 > WAIT_LIMIT_NS) return false;
+    }
+}
+
+__device__ __forceinline__ void tmem_load32(uint32_t taddr, float *out)
+{
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int j = 0; j < 32; ++j) out[j] = __uint_as_float(r[j]);
+}
+
+// byte offset of element (row, k) (k < 64) in a 128-row x 64 bf16 K-major tile with 128-byte swizzle
+__device__ __forceinline__ uint32_t sw128_chunk(int row, int chunk)
+{
+    return (uint32_t)((row >> 3) * 1024 + (row & 7) * 128 + ((chunk ^ (row & 7)) << 4));
+}
+
+// split 8 floats into bf16 hi/lo and store them as one 16-byte chunk each
+__device__ __forceinline__ void split_store8(const float *x, char *hi_tile, char *lo_tile, uint32_t off)
+{
+    uint32_t h[4], l[4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        const __nv_bfloat16 h0 = __float2bfloat16_rn(x[2 * c]), h1 = __float2bfloat16_rn(x[2 * c + 1]);
+        const __nv_bfloat16 l0 = __float2bfloat16_rn(x[2 * c] - __bfloat162float(h0));
+        const __nv_bfloat16 l1 = __float2bfloat16_rn(x[2 * c + 1] - __bfloat162float(h1));
+        h[c] = (uint32_t)__bfloat16_as_ushort(h0) | ((uint32_t)__bfloat16_as_ushort(h1) << 16);
+        l[c] = (uint32_t)__bfloat16_as_ushort(l0) | ((uint32_t)__bfloat16_as_ushort(l1) << 16);
+    }
+    *reinterpret_cast<uint4 *>(hi_tile + off) = make_uint4(h[0], h[1], h[2], h[3]);
+    *reinterpret_cast<uint4 *>(lo_tile + off) = make_uint4(l[0], l[1], l[2], l[3]);
+}
+
+template <int NP, int S>
+__global__ void __launch_bounds__(TC_THREADS, 1)
+pot_tc_kernel(GridInfo g, const float *__restrict__ v, float *__restrict__ P, const uint4 *__restrict__ bmat,
+              const float *__restrict__ tD, const float *__restrict__ tL, const float *__restrict__ tR, long total_rows,
+              int *err)
+{
+    constexpr int KA = NP / 64;            // K slices of 64
+    constexpr int TILE = TILE_M * 64 * 2;  // bytes of one 128 x 64 bf16 tile (A side) = 16 KB
+    constexpr int BT = NP * 64 * 2;        // bytes of one np x 64 bf16 tile (B side)
+    constexpr int S2 = S * S;
+    // shared memory: [0, 4*KA*TILE): operand A region (forward: 4 tiles of the current slice; inverse:
+    // Y, all slices); then 4 B tiles of one slice; then barrier + TMEM address
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    // swizzled tiles need 1024-byte alignment in the shared window
+    unsigned char *smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
+    char *A = reinterpret_cast<char *>(smem);
+    char *Bs = A + 4 * KA * TILE;
+    uint64_t *mbar = reinterpret_cast<uint64_t *>(Bs + 4 * BT);
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(mbar + 1);
+
+    const int t = threadIdx.x, warp = t >> 5;
+    const long row = (long)blockIdx.x * TILE_M + t;
+    const bool valid = row < total_rows;
+    int pr = 0, i = 0;
+    size_t rbase = 0;
+    if (valid) {
+        long rest = row;
+        pr = (int)(rest % S2);
+        rest /= S2;
+        i = (int)(rest % g.nq);
+        rest /= g.nq;
+        const int e = (int)(rest % g.n_elem);
+        const int rep = (int)(rest / g.n_elem);
+        rbase = (size_t)rep * g.rep_stride + (size_t)e * g.elem_stride + (size_t)pr * 2 * g.blk + (size_t)i * NP;
+    }
+    const uint32_t mbar_a = smem_u32(mbar);
+    if (t == 0) {
+        mbar_init(mbar_a, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "r"((uint32_t)(2 * NP)));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    fence_before();
+    __syncthreads();
+    fence_after();
+    const uint32_t tmem = *tmem_slot;
+    const uint32_t d_re = tmem, d_im = tmem + NP;             // columns
+    const uint32_t lane_off = (uint32_t)(warp * 32) << 16;    // this warp's TMEM lanes
+    uint32_t phase = 0;
+    bool ok = true;
+
+    auto copy_b = [&](int slice) {
+        // four pre-swizzled np x 64 tiles (C_hi, C_lo, S_hi, S_lo) of this K slice
+        const uint4 *src = bmat + (size_t)slice * 4 * (BT / 16);
+        uint4 *dst = reinterpret_cast<uint4 *>(Bs);
+        for (int c = t; c < 4 * BT / 16; c += TC_THREADS) dst[c] = src[c];
+    };
+    auto issue = [&](const char *const *a_tiles, int slice_a, bool inverse, bool first) {
+        // products for one K slice: (dst, A tile, B tile, negate)
+        const uint32_t bC_hi = smem_u32(Bs), bC_lo = smem_u32(Bs + BT), bS_hi = smem_u32(Bs + 2 * BT),
+                       bS_lo = smem_u32(Bs + 3 * BT);
+        // a_tiles: re_hi, re_lo, im_hi, im_lo
+        const uint32_t ar_h = smem_u32(a_tiles[0]), ar_l = smem_u32(a_tiles[1]), ai_h = smem_u32(a_tiles[2]),
+                       ai_l = smem_u32(a_tiles[3]);
+        struct Prod { uint32_t d, a_h, a_l, b_h, b_l; bool neg; };
+        Prod prods[4];
+        if (!inverse) {
+            prods[0] = {d_re, ar_h, ar_l, bC_hi, bC_lo, false};  // + W_re C
+            prods[1] = {d_re, ai_h, ai_l, bS_hi, bS_lo, true};   // - W_im S
+            prods[2] = {d_im, ar_h, ar_l, bS_hi, bS_lo, false};  // + W_re S
+            prods[3] = {d_im, ai_h, ai_l, bC_hi, bC_lo, false};  // + W_im C
+        } else {
+            prods[0] = {d_re, ar_h, ar_l, bC_hi, bC_lo, false};  // + Y_re C
+            prods[1] = {d_re, ai_h, ai_l, bS_hi, bS_lo, false};  // + Y_im S
+            prods[2] = {d_im, ai_h, ai_l, bC_hi, bC_lo, false};  // + Y_im C
+            prods[3] = {d_im, ar_h, ar_l, bS_hi, bS_lo, true};   // - Y_re S
+        }
+        (void)slice_a;
+        for (int ks = 0; ks < 4; ++ks) {  // 4 x K = 16 inside the 64-wide slice: +32 bytes
+            const uint32_t ko = (uint32_t)ks * 32;
+            for (int q = 0; q < 4; ++q) {
+                const Prod &pp = prods[q];
+                const uint32_t id = idesc_bf16(TILE_M, NP, pp.neg);
+                const bool fresh = first && ks == 0 && (q == 0 || q == 2);
+                mma_bf16(pp.d, sdesc_sw128(pp.a_h + ko), sdesc_sw128(pp.b_h + ko), id, fresh ? 0u : 1u);
+                mma_bf16(pp.d, sdesc_sw128(pp.a_h + ko), sdesc_sw128(pp.b_l + ko), id, 1u);
+                mma_bf16(pp.d, sdesc_sw128(pp.a_l + ko), sdesc_sw128(pp.b_h + ko), id, 1u);
+            }
+        }
+        mma_commit(mbar_a);
+    };
+
+    // ---- forward transform -------------------------------------------------------------------
+    for (int s = 0; s < KA && ok; ++s) {
+        char *tiles[4] = {A, A + TILE, A + 2 * TILE, A + 3 * TILE};
+        float xr[8], xi[8];
+        for (int c = 0; c < 8; ++c) {
+            if (valid) {
+                const float4 *pr4 = reinterpret_cast<const float4 *>(v + rbase + s * 64 + c * 8);
+                const float4 *pi4 = reinterpret_cast<const float4 *>(v + rbase + g.blk + s * 64 + c * 8);
+                const float4 a0 = pr4[0], a1 = pr4[1], b0 = pi4[0], b1 = pi4[1];
+                xr[0] = a0.x; xr[1] = a0.y; xr[2] = a0.z; xr[3] = a0.w; xr[4] = a1.x; xr[5] = a1.y; xr[6] = a1.z; xr[7] = a1.w;
+                xi[0] = b0.x; xi[1] = b0.y; xi[2] = b0.z; xi[3] = b0.w; xi[4] = b1.x; xi[5] = b1.y; xi[6] = b1.z; xi[7] = b1.w;
+            } else {
+                for (int j = 0; j < 8; ++j) xr[j] = xi[j] = 0.f;
+            }
+            const uint32_t off = sw128_chunk(t, c);
+            split_store8(xr, tiles[0], tiles[1], off);
+            split_store8(xi, tiles[2], tiles[3], off);
+        }
+        copy_b(s);
+        fence_async_smem();
+        __syncthreads();
+        if (t == 0) {
+            fence_after();
+            issue(tiles, s, false, s == 0);
+        }
+        ok = __syncthreads_and(mbar_wait(mbar_a, phase));
+        phase ^= 1;
+        fence_after();
+    }
+
+    // ---- r-space mixing (epilogue of the forward GEMM), Y into the A region ---------------------
+    if (ok) {
+        const int jj = pr / S, kk = pr % S;
+        for (int c0 = 0; c0 < NP; c0 += 32) {
+            float dr[32], di[32];
+            tmem_load32(d_re + lane_off + c0, dr);
+            tmem_load32(d_im + lane_off + c0, di);
+            float yr[32], yi[32];
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+                const int m = c0 + j;
+                float ar, ai;
+                if (S == 1) {
+                    const float d = valid ? tD[(size_t)i * NP + m] : 0.f;
+                    ar = d * dr[j];
+                    ai = d * di[j];
+                } else {
+                    // pairs of this q row: lane ^ 2 holds (1-j, k), lane ^ 1 holds (j, 1-k)
+                    const float sr = __shfl_xor_sync(0xffffffffu, dr[j], 2), si = __shfl_xor_sync(0xffffffffu, di[j], 2);
+                    const float br = __shfl_xor_sync(0xffffffffu, dr[j], 1), bi = __shfl_xor_sync(0xffffffffu, di[j], 1);
+                    float d = 0.f, l = 0.f, r = 0.f;
+                    if (valid) {
+                        d = tD[((size_t)pr * g.nq + i) * NP + m];
+                        l = tL[((size_t)(jj * S + (1 - jj)) * g.nq + i) * NP + m];
+                        r = tR[((size_t)((1 - kk) * S + kk) * g.nq + i) * NP + m];
+                    }
+                    ar = d * dr[j] + l * sr - r * br;
+                    ai = d * di[j] + l * si - r * bi;
+                }
+                yr[j] = ai;   // times -i
+                yi[j] = -ar;
+            }
+            const int s = c0 / 64, cb = (c0 % 64) / 8;
+            char *y_re_h = A + (size_t)(4 * s + 0) * TILE, *y_re_l = A + (size_t)(4 * s + 1) * TILE;
+            char *y_im_h = A + (size_t)(4 * s + 2) * TILE, *y_im_l = A + (size_t)(4 * s + 3) * TILE;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const uint32_t off = sw128_chunk(t, cb + q);
+                split_store8(yr + 8 * q, y_re_h, y_re_l, off);
+                split_store8(yi + 8 * q, y_im_h, y_im_l, off);
+            }
+        }
+    }
+    fence_before();
+    __syncthreads();
+
+    // ---- inverse transform ---------------------------------------------------------------------
+    for (int s = 0; s < KA && ok; ++s) {
+        char *tiles[4] = {A + (size_t)(4 * s) * TILE, A + (size_t)(4 * s + 1) * TILE, A + (size_t)(4 * s + 2) * TILE,
+                          A + (size_t)(4 * s + 3) * TILE};
+        copy_b(s);
+        fence_async_smem();
+        __syncthreads();
+        if (t == 0) {
+            fence_after();
+            issue(tiles, s, true, s == 0);
+        }
+        ok = __syncthreads_and(mbar_wait(mbar_a, phase));  // also: B tiles are rewritten by the next slice
+        phase ^= 1;
+        fence_after();
+    }
+
+    // ---- epilogue: P rows to global ---------------------------------------------------------------
+    if (ok) {
+        for (int c0 = 0; c0 < NP; c0 += 32) {
+            float pr_[32], pi_[32];
+            tmem_load32(d_re + lane_off + c0, pr_);
+            tmem_load32(d_im + lane_off + c0, pi_);
+            if (valid) {
+                float4 *o_r = reinterpret_cast<float4 *>(P + rbase + c0);
+                float4 *o_i = reinterpret_cast<float4 *>(P + rbase + g.blk + c0);
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    o_r[q] = make_float4(pr_[4 * q], pr_[4 * q + 1], pr_[4 * q + 2], pr_[4 * q + 3]);
+                    o_i[q] = make_float4(pi_[4 * q], pi_[4 * q + 1], pi_[4 * q + 2], pi_[4 * q + 3]);
+                }
+            }
+        }
+    } else if (t == 0) {
+        atomicExch(err, 1);
+    }
+    fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)(2 * NP)));
+    }
+}
+
+template <int NP, int S>
+size_t tc_smem_bytes()
+{
+    return (size_t)4 * (NP / 64) * TILE_M * 64 * 2 + 4 * (size_t)NP * 64 * 2 + 64 + 1024;
+}
+
+template <int NP, int S>
+cudaError_t launch_tc_t(const GridInfo &g, const float *v, float *P, const void *bmat, const float *tD,
+                        const float *tL, const float *tR, int n_rep, int *err, cudaStream_t st)
+{
+    const long rows = (long)n_rep * g.n_elem * g.nq * S * S;
+    const int blocks = (int)((rows + TILE_M - 1) / TILE_M);
+    if (blocks <= 0) return cudaSuccess;
+    pot_tc_kernel<NP, S><<<blocks, TC_THREADS, tc_smem_bytes<NP, S>(), st>>>(
+        g, v, P, reinterpret_cast<const uint4 *>(bmat), tD, tL, tR, rows, err);
+    return cudaGetLastError();
+}
+
+template <int NP, int S>
+cudaError_t prepare_tc_t()
+{
+    return cudaFuncSetAttribute(pot_tc_kernel<NP, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)tc_smem_bytes<NP, S>());
+}
+
+}  // namespace
+
+bool tc_supported(int np, int S) { return (np == 64 || np == 128) && (S == 1 || S == 2); }
+
+cudaError_t prepare_tc(int np, int S)
+{
+    if (np == 64 && S == 1) return prepare_tc_t<64, 1>();
+    if (np == 64 && S == 2) return prepare_tc_t<64, 2>();
+    if (np == 128 && S == 1) return prepare_tc_t<128, 1>();
+    if (np == 128 && S == 2) return prepare_tc_t<128, 2>();
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_potential_tc(const GridInfo &g, const float *v, float *P, const void *bmat, const float *tD,
+                                const float *tL, const float *tR, int n_rep, int *err, cudaStream_t st)
+{
+    if (g.np == 64 && g.S == 1) return launch_tc_t<64, 1>(g, v, P, bmat, tD, tL, tR, n_rep, err, st);
+    if (g.np == 64 && g.S == 2) return launch_tc_t<64, 2>(g, v, P, bmat, tD, tL, tR, n_rep, err, st);
+    if (g.np == 128 && g.S == 1) return launch_tc_t<128, 1>(g, v, P, bmat, tD, tL, tR, n_rep, err, st);
+    if (g.np == 128 && g.S == 2) return launch_tc_t<128, 2>(g, v, P, bmat, tD, tL, tR, n_rep, err, st);
+    return cudaErrorInvalidValue;
+}
+
+// Host: C and S split into bf16 hi/lo, laid out per 64-wide K slice as four pre-swizzled np x 64
+// K-major tiles (C_hi, C_lo, S_hi, S_lo), each row m = output mode, K = l.
+void build_tc_matrices(int np, std::vector<uint16_t> &out)
+{
+    const int KA = np / 64;
+    const size_t tile = (size_t)np * 64;  // elements
+    out.assign((size_t)KA * 4 * tile, 0);
+    auto bf16_bits = [](float x) {
+        const __nv_bfloat16 b = __float2bfloat16_rn(x);
+        return __bfloat16_as_ushort(b);
+    };
+    auto bf16_val = [](float x) { return __bfloat162float(__float2bfloat16_rn(x)); };
+    const double two_pi = 6.283185307179586476925286766559;
+    for (int s = 0; s < KA; ++s)
+        for (int m = 0; m < np; ++m)
+            for (int k = 0; k < 64; ++k) {
+                const int l = s * 64 + k;
+                const long ml = ((long)m * l) % np;
+                const float c = (float)std::cos(two_pi * ml / np), sn = (float)std::sin(two_pi * ml / np);
+                const float vals[4] = {bf16_val(c), c - bf16_val(c), bf16_val(sn), sn - bf16_val(sn)};
+                // element (row m, k) of a 128-byte swizzled K-major tile
+                const int chunk = k / 8, within = k % 8;
+                const size_t byte = (size_t)(m >> 3) * 1024 + (m & 7) * 128 + ((chunk ^ (m & 7)) << 4) + within * 2;
+                for (int q = 0; q < 4; ++q) out[((size_t)s * 4 + q) * tile + byte / 2] = bf16_bits(vals[q]);
+            }
+}
