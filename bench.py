@@ -208,7 +208,7 @@ def main():
     ap.add_argument("--steps", type=int, default=40)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
-    ap.add_argument("--precision", default="mixed", choices=["fp64", "mixed"])
+    ap.add_argument("--precision", default="mixed", choices=["fp64", "mixed", "bf16x3"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-spectrum", action="store_true", help="skip the batched 2D-spectrum measurement")
     args = ap.parse_args()
@@ -291,25 +291,41 @@ def main():
     except (OSError, ValueError):
         pass
     hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    tc_peak = peaks.get("bf16_tflops_sustained", 1700.0)
     n_stage, ms_stage = kt["stage"]
     n_pot, ms_pot = kt["potential"]
-    esize = 4 if args.precision == "mixed" else 8
+    esize = 8 if args.precision == "fp64" else 4
     # algorithmic bytes of one right-hand-side stage: the 11 state passes of a Horner RK4 step
     # (complex values) spread over its 4 stages
     alg_bytes_stage = 11 * 2 * esize * cells / 4
-    dom_ms = ms_stage / max(n_stage, 1)
+    stage_ms = ms_stage / max(n_stage, 1)
     pot_ms = ms_pot / max(n_pot, 1)
-    roof = {"bound": "hbm", "kernel": "stage_kernel (stencil + bath + tier couplings + Horner update)",
-            "achieved": alg_bytes_stage / (dom_ms / 1e3) / 1e9, "peak": hbm_peak, "unit": "GB/s",
-            "frac": alg_bytes_stage / (dom_ms / 1e3) / 1e9 / hbm_peak, "traffic": None,
-            "peak_source": "MEASURED_PEAKS.json hbm_gbs (burst copy)" if peaks else "fallback 6800 GB/s",
-            "stage_ms_per_launch": dom_ms, "potential_ms_per_launch": pot_ms,
-            "share_stage": ms_stage / max(ms_stage + ms_pot + kt["aux"][1], 1e-9),
-            "share_potential": ms_pot / max(ms_stage + ms_pot + kt["aux"][1], 1e-9)}
+    total = max(ms_stage + ms_pot + kt["aux"][1], 1e-9)
+    stage_roof = {"bound": "hbm", "kernel": "fused_stage_kernel (FFT potential term, stencil, bath, tier couplings, "
+                  "Horner update)" if args.precision != "bf16x3" else
+                  "fused_stage_kernel (stencil, bath, tier couplings, Horner update; potential term read)",
+                  "achieved": alg_bytes_stage / (stage_ms / 1e3) / 1e9, "peak": hbm_peak, "unit": "GB/s",
+                  "frac": alg_bytes_stage / (stage_ms / 1e3) / 1e9 / hbm_peak, "traffic": None,
+                  "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if peaks else "fallback 6800 GB/s",
+                  "ms_per_launch": stage_ms, "share": ms_stage / total,
+                  "algorithmic_bytes_per_launch": alg_bytes_stage}
+    roof = stage_roof
+    if args.precision == "bf16x3" and n_pot:
+        # tensor flops issued per launch: forward and inverse DFT-GEMMs, 4 real products of
+        # [1 x np] x [np x np] per row, 3 bf16 products each
+        flops = 2 * 3 * 4 * 2 * m["np"] * m["np"] * (cells / m["np"])
+        tc_roof = {"bound": "tensor", "kernel": "pot_tc_kernel (tcgen05 split-bf16 DFT-GEMM potential term)",
+                   "achieved": flops / (pot_ms / 1e3) / 1e12, "peak": tc_peak, "unit": "TFLOP/s",
+                   "frac": flops / (pot_ms / 1e3) / 1e12 / tc_peak, "traffic": None,
+                   "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained (of measured)",
+                   "ms_per_launch": pot_ms, "share": ms_pot / total, "flops_per_launch": flops}
+        roof = dict(tc_roof) if ms_pot >= ms_stage else dict(stage_roof)
+        roof["other_kernel"] = stage_roof if ms_pot >= ms_stage else tc_roof
 
     line = {"metric": METRIC, "value": value, "unit": "cell-updates/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32" if args.precision == "mixed" else "f64", "data": "synthetic",
+            "vs_baseline": None, "dtype": {"mixed": "f32", "bf16x3": "f32+bf16x3", "fp64": "f64"}[args.precision],
+            "data": "synthetic",
             "config": {"workload": "photoiso_96x128_d8_K2 (2 states, depth 8, 3 modes, 165 elements, "
                                    f"{cells} cells per GPU)", "precision": args.precision,
                        "l2": f"working set {4 * cells * 2 * esize / 1e6:.0f} MB per step > 129 MB L2 (no flush)",

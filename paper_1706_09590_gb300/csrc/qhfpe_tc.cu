@@ -11,11 +11,14 @@
 // Operands are bf16 split in two (x = hi + lo, hi = bf16(x), lo = bf16(x - hi)); each real product
 // takes three MMAs (hi*hi + hi*lo + lo*hi) accumulating in FP32 in tensor memory.  Operands are staged
 // in shared memory in the 128-byte-swizzled K-major layout the MMA descriptors expect; C and S (hi/lo)
-// are pre-swizzled on the host and copied in per 64-wide K slice.
+// are pre-swizzled on the host.
 //
-// One CTA of 128 threads per 128-row tile: thread t owns row (TMEM lane) t in the epilogues; thread 0
-// issues the MMAs.  Waits on the MMA-completion barrier are bounded: on timeout the kernel records an
-// error, skips the rest of its work, and still frees its tensor memory.
+// Persistent CTAs (one per SM) of 256 threads loop over 128-row tiles; the cosine/sine operand tiles
+// stay in shared memory for the whole kernel.  Tensor memory holds the forward result D (2 np columns)
+// and the inverse accumulator P (2 np columns); the inverse runs slice by slice as the epilogue turns
+// each 64-mode slice of D into the bf16 operand Y.  Warps 4q..4q+3 share TMEM lane quadrant q and split
+// the columns.  Thread 0 issues the MMAs.  Waits on the MMA-completion barrier are bounded: on timeout
+// the kernel records an error, skips the rest of its work, and still frees its tensor memory.
 #include "qhfpe_internal.cuh"
 
 #include <cuda_bf16.h>
@@ -26,7 +29,7 @@
 
 namespace {
 
-constexpr int TC_THREADS = 128;
+constexpr int TC_THREADS = 256;
 constexpr int TILE_M = 128;
 constexpr unsigned long long WAIT_LIMIT_NS = 2000000000ull;  // give up on an MMA barrier after 2 s
 
@@ -145,31 +148,21 @@ pot_tc_kernel(GridInfo g, const float *__restrict__ v, float *__restrict__ P, co
     constexpr int TILE = TILE_M * 64 * 2;  // bytes of one 128 x 64 bf16 tile (A side) = 16 KB
     constexpr int BT = NP * 64 * 2;        // bytes of one np x 64 bf16 tile (B side)
     constexpr int S2 = S * S;
-    // shared memory: [0, 4*KA*TILE): operand A region (forward: 4 tiles of the current slice; inverse:
-    // Y, all slices); then 4 B tiles of one slice; then barrier + TMEM address
+    // shared memory: B resident for the whole kernel ([slice][C_hi, C_lo, S_hi, S_lo] tiles), then one
+    // slice of the A operand (forward: W re/im hi/lo; inverse: Y re/im hi/lo), then barrier + TMEM address
     extern __shared__ __align__(1024) unsigned char smem_raw[];
-    // swizzled tiles need 1024-byte alignment in the shared window
     unsigned char *smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
-    char *A = reinterpret_cast<char *>(smem);
-    char *Bs = A + 4 * KA * TILE;
-    uint64_t *mbar = reinterpret_cast<uint64_t *>(Bs + 4 * BT);
+    char *Bs = reinterpret_cast<char *>(smem);
+    char *A = Bs + (size_t)KA * 4 * BT;
+    uint64_t *mbar = reinterpret_cast<uint64_t *>(A + 4 * TILE);
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(mbar + 1);
 
-    const int t = threadIdx.x, warp = t >> 5;
-    const long row = (long)blockIdx.x * TILE_M + t;
-    const bool valid = row < total_rows;
-    int pr = 0, i = 0;
-    size_t rbase = 0;
-    if (valid) {
-        long rest = row;
-        pr = (int)(rest % S2);
-        rest /= S2;
-        i = (int)(rest % g.nq);
-        rest /= g.nq;
-        const int e = (int)(rest % g.n_elem);
-        const int rep = (int)(rest / g.n_elem);
-        rbase = (size_t)rep * g.rep_stride + (size_t)e * g.elem_stride + (size_t)pr * 2 * g.blk + (size_t)i * NP;
-    }
+    const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+    const int row_in_tile = t & (TILE_M - 1);   // A-load row of this thread
+    const int half = t >> 7;                    // which 32-wide half of a K slice this thread loads
+    const int quad = warp & 3;                  // TMEM lane quadrant of this warp
+    const int grp = warp >> 2;                  // column group of this warp in the epilogues
+    const int erow = quad * 32 + lane;          // epilogue row (TMEM lane) of this thread
     const uint32_t mbar_a = smem_u32(mbar);
     if (t == 0) {
         mbar_init(mbar_a, 1);
@@ -177,45 +170,44 @@ pot_tc_kernel(GridInfo g, const float *__restrict__ v, float *__restrict__ P, co
     }
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
-                     "r"((uint32_t)(2 * NP)));
+                     "r"((uint32_t)(4 * NP)));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
+    // the cosine / sine operand tiles, once per CTA
+    {
+        uint4 *dst = reinterpret_cast<uint4 *>(Bs);
+        for (int c = t; c < KA * 4 * BT / 16; c += TC_THREADS) dst[c] = bmat[c];
+    }
+    fence_async_smem();
     fence_before();
     __syncthreads();
     fence_after();
     const uint32_t tmem = *tmem_slot;
-    const uint32_t d_re = tmem, d_im = tmem + NP;             // columns
-    const uint32_t lane_off = (uint32_t)(warp * 32) << 16;    // this warp's TMEM lanes
+    const uint32_t d_re = tmem, d_im = tmem + NP, p_re = tmem + 2 * NP, p_im = tmem + 3 * NP;
+    const uint32_t lane_off = (uint32_t)(quad * 32) << 16;
     uint32_t phase = 0;
     bool ok = true;
+    const uint32_t a_tiles[4] = {smem_u32(A), smem_u32(A + TILE), smem_u32(A + 2 * TILE), smem_u32(A + 3 * TILE)};
 
-    auto copy_b = [&](int slice) {
-        // four pre-swizzled np x 64 tiles (C_hi, C_lo, S_hi, S_lo) of this K slice
-        const uint4 *src = bmat + (size_t)slice * 4 * (BT / 16);
-        uint4 *dst = reinterpret_cast<uint4 *>(Bs);
-        for (int c = t; c < 4 * BT / 16; c += TC_THREADS) dst[c] = src[c];
-    };
-    auto issue = [&](const char *const *a_tiles, int slice_a, bool inverse, bool first) {
-        // products for one K slice: (dst, A tile, B tile, negate)
-        const uint32_t bC_hi = smem_u32(Bs), bC_lo = smem_u32(Bs + BT), bS_hi = smem_u32(Bs + 2 * BT),
-                       bS_lo = smem_u32(Bs + 3 * BT);
-        // a_tiles: re_hi, re_lo, im_hi, im_lo
-        const uint32_t ar_h = smem_u32(a_tiles[0]), ar_l = smem_u32(a_tiles[1]), ai_h = smem_u32(a_tiles[2]),
-                       ai_l = smem_u32(a_tiles[3]);
+    // one K slice of one transform: 4 real products x 3 bf16 products x 4 k-steps
+    auto issue = [&](int slice, bool inverse, bool first) {
+        const uint32_t b0 = smem_u32(Bs + (size_t)slice * 4 * BT);
+        const uint32_t bC_hi = b0, bC_lo = b0 + BT, bS_hi = b0 + 2 * BT, bS_lo = b0 + 3 * BT;
+        const uint32_t ar_h = a_tiles[0], ar_l = a_tiles[1], ai_h = a_tiles[2], ai_l = a_tiles[3];
+        const uint32_t o_re = inverse ? p_re : d_re, o_im = inverse ? p_im : d_im;
         struct Prod { uint32_t d, a_h, a_l, b_h, b_l; bool neg; };
         Prod prods[4];
         if (!inverse) {
-            prods[0] = {d_re, ar_h, ar_l, bC_hi, bC_lo, false};  // + W_re C
-            prods[1] = {d_re, ai_h, ai_l, bS_hi, bS_lo, true};   // - W_im S
-            prods[2] = {d_im, ar_h, ar_l, bS_hi, bS_lo, false};  // + W_re S
-            prods[3] = {d_im, ai_h, ai_l, bC_hi, bC_lo, false};  // + W_im C
+            prods[0] = {o_re, ar_h, ar_l, bC_hi, bC_lo, false};  // + W_re C
+            prods[1] = {o_re, ai_h, ai_l, bS_hi, bS_lo, true};   // - W_im S
+            prods[2] = {o_im, ar_h, ar_l, bS_hi, bS_lo, false};  // + W_re S
+            prods[3] = {o_im, ai_h, ai_l, bC_hi, bC_lo, false};  // + W_im C
         } else {
-            prods[0] = {d_re, ar_h, ar_l, bC_hi, bC_lo, false};  // + Y_re C
-            prods[1] = {d_re, ai_h, ai_l, bS_hi, bS_lo, false};  // + Y_im S
-            prods[2] = {d_im, ai_h, ai_l, bC_hi, bC_lo, false};  // + Y_im C
-            prods[3] = {d_im, ar_h, ar_l, bS_hi, bS_lo, true};   // - Y_re S
+            prods[0] = {o_re, ar_h, ar_l, bC_hi, bC_lo, false};  // + Y_re C
+            prods[1] = {o_re, ai_h, ai_l, bS_hi, bS_lo, false};  // + Y_im S
+            prods[2] = {o_im, ai_h, ai_l, bC_hi, bC_lo, false};  // + Y_im C
+            prods[3] = {o_im, ar_h, ar_l, bS_hi, bS_lo, true};   // - Y_re S
         }
-        (void)slice_a;
         for (int ks = 0; ks < 4; ++ks) {  // 4 x K = 16 inside the 64-wide slice: +32 bytes
             const uint32_t ko = (uint32_t)ks * 32;
             for (int q = 0; q < 4; ++q) {
@@ -229,130 +221,165 @@ pot_tc_kernel(GridInfo g, const float *__restrict__ v, float *__restrict__ P, co
         }
         mma_commit(mbar_a);
     };
-
-    // ---- forward transform -------------------------------------------------------------------
-    for (int s = 0; s < KA && ok; ++s) {
-        char *tiles[4] = {A, A + TILE, A + 2 * TILE, A + 3 * TILE};
-        float xr[8], xi[8];
-        for (int c = 0; c < 8; ++c) {
-            if (valid) {
-                const float4 *pr4 = reinterpret_cast<const float4 *>(v + rbase + s * 64 + c * 8);
-                const float4 *pi4 = reinterpret_cast<const float4 *>(v + rbase + g.blk + s * 64 + c * 8);
-                const float4 a0 = pr4[0], a1 = pr4[1], b0 = pi4[0], b1 = pi4[1];
-                xr[0] = a0.x; xr[1] = a0.y; xr[2] = a0.z; xr[3] = a0.w; xr[4] = a1.x; xr[5] = a1.y; xr[6] = a1.z; xr[7] = a1.w;
-                xi[0] = b0.x; xi[1] = b0.y; xi[2] = b0.z; xi[3] = b0.w; xi[4] = b1.x; xi[5] = b1.y; xi[6] = b1.z; xi[7] = b1.w;
-            } else {
-                for (int j = 0; j < 8; ++j) xr[j] = xi[j] = 0.f;
-            }
-            const uint32_t off = sw128_chunk(t, c);
-            split_store8(xr, tiles[0], tiles[1], off);
-            split_store8(xi, tiles[2], tiles[3], off);
-        }
-        copy_b(s);
+    auto run_and_wait = [&](int slice, bool inverse, bool first) {
         fence_async_smem();
         __syncthreads();
         if (t == 0) {
             fence_after();
-            issue(tiles, s, false, s == 0);
+            issue(slice, inverse, first);
         }
         ok = __syncthreads_and(mbar_wait(mbar_a, phase));
         phase ^= 1;
         fence_after();
-    }
+    };
 
-    // ---- r-space mixing (epilogue of the forward GEMM), Y into the A region ---------------------
-    if (ok) {
-        const int jj = pr / S, kk = pr % S;
-        for (int c0 = 0; c0 < NP; c0 += 32) {
-            float dr[32], di[32];
-            tmem_load32(d_re + lane_off + c0, dr);
-            tmem_load32(d_im + lane_off + c0, di);
-            float yr[32], yi[32];
-#pragma unroll
-            for (int j = 0; j < 32; ++j) {
-                const int m = c0 + j;
-                float ar, ai;
-                if (S == 1) {
-                    const float d = valid ? tD[(size_t)i * NP + m] : 0.f;
-                    ar = d * dr[j];
-                    ai = d * di[j];
-                } else {
-                    // pairs of this q row: lane ^ 2 holds (1-j, k), lane ^ 1 holds (j, 1-k)
-                    const float sr = __shfl_xor_sync(0xffffffffu, dr[j], 2), si = __shfl_xor_sync(0xffffffffu, di[j], 2);
-                    const float br = __shfl_xor_sync(0xffffffffu, dr[j], 1), bi = __shfl_xor_sync(0xffffffffu, di[j], 1);
-                    float d = 0.f, l = 0.f, r = 0.f;
+    const long n_tiles = (total_rows + TILE_M - 1) / TILE_M;
+    for (long tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x) {
+        // ---- forward transform: W rows -> D ------------------------------------------------------
+        {
+            const long row = tile * TILE_M + row_in_tile;
+            size_t rb = 0;
+            const bool valid = row < total_rows;
+            if (valid) {
+                long rest = row;
+                const int pr = (int)(rest % S2);
+                rest /= S2;
+                const int i = (int)(rest % g.nq);
+                rest /= g.nq;
+                const int e = (int)(rest % g.n_elem);
+                const int rep = (int)(rest / g.n_elem);
+                rb = (size_t)rep * g.rep_stride + (size_t)e * g.elem_stride + (size_t)pr * 2 * g.blk + (size_t)i * NP;
+            }
+            for (int s = 0; s < KA && ok; ++s) {
+                for (int cc = 0; cc < 4; ++cc) {
+                    const int c = half * 4 + cc;  // 16-byte chunk (8 elements) of the 64-wide slice
+                    float xr[8], xi[8];
                     if (valid) {
-                        d = tD[((size_t)pr * g.nq + i) * NP + m];
-                        l = tL[((size_t)(jj * S + (1 - jj)) * g.nq + i) * NP + m];
-                        r = tR[((size_t)((1 - kk) * S + kk) * g.nq + i) * NP + m];
-                    }
-                    ar = d * dr[j] + l * sr - r * br;
-                    ai = d * di[j] + l * si - r * bi;
-                }
-                yr[j] = ai;   // times -i
-                yi[j] = -ar;
-            }
-            const int s = c0 / 64, cb = (c0 % 64) / 8;
-            char *y_re_h = A + (size_t)(4 * s + 0) * TILE, *y_re_l = A + (size_t)(4 * s + 1) * TILE;
-            char *y_im_h = A + (size_t)(4 * s + 2) * TILE, *y_im_l = A + (size_t)(4 * s + 3) * TILE;
+                        const float4 *pr4 = reinterpret_cast<const float4 *>(v + rb + s * 64 + c * 8);
+                        const float4 *pi4 = reinterpret_cast<const float4 *>(v + rb + g.blk + s * 64 + c * 8);
+                        const float4 a0 = pr4[0], a1 = pr4[1], b0 = pi4[0], b1 = pi4[1];
+                        xr[0] = a0.x; xr[1] = a0.y; xr[2] = a0.z; xr[3] = a0.w;
+                        xr[4] = a1.x; xr[5] = a1.y; xr[6] = a1.z; xr[7] = a1.w;
+                        xi[0] = b0.x; xi[1] = b0.y; xi[2] = b0.z; xi[3] = b0.w;
+                        xi[4] = b1.x; xi[5] = b1.y; xi[6] = b1.z; xi[7] = b1.w;
+                    } else {
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const uint32_t off = sw128_chunk(t, cb + q);
-                split_store8(yr + 8 * q, y_re_h, y_re_l, off);
-                split_store8(yi + 8 * q, y_im_h, y_im_l, off);
+                        for (int j = 0; j < 8; ++j) xr[j] = xi[j] = 0.f;
+                    }
+                    const uint32_t off = sw128_chunk(row_in_tile, c);
+                    split_store8(xr, A, A + TILE, off);
+                    split_store8(xi, A + 2 * TILE, A + 3 * TILE, off);
+                }
+                run_and_wait(s, false, s == 0);
             }
         }
-    }
-    fence_before();
-    __syncthreads();
-
-    // ---- inverse transform ---------------------------------------------------------------------
-    for (int s = 0; s < KA && ok; ++s) {
-        char *tiles[4] = {A + (size_t)(4 * s) * TILE, A + (size_t)(4 * s + 1) * TILE, A + (size_t)(4 * s + 2) * TILE,
-                          A + (size_t)(4 * s + 3) * TILE};
-        copy_b(s);
-        fence_async_smem();
-        __syncthreads();
-        if (t == 0) {
-            fence_after();
-            issue(tiles, s, true, s == 0);
+        // ---- r-space mixing per slice of modes, then that slice of the inverse transform ------------
+        {
+            const long row = tile * TILE_M + erow;
+            const bool valid = row < total_rows;
+            int pr = 0, i = 0;
+            if (valid) {
+                long rest = row;
+                pr = (int)(rest % S2);
+                rest /= S2;
+                i = (int)(rest % g.nq);
+            }
+            const int jj = pr / S, kk = pr % S;
+            for (int s = 0; s < KA && ok; ++s) {
+                const int c0 = s * 64 + grp * 32;  // 32 modes of this warp
+                // this row's 32 table entries, as 16-byte vectors
+                float td[32], tl[32], tr[32];
+                {
+                    const float4 *pd = reinterpret_cast<const float4 *>(tD + ((size_t)pr * g.nq + i) * NP + c0);
+                    const float4 *pl = reinterpret_cast<const float4 *>(
+                        tL + ((size_t)(jj * S + (S > 1 ? 1 - jj : 0)) * g.nq + i) * NP + c0);
+                    const float4 *pq = reinterpret_cast<const float4 *>(
+                        tR + ((size_t)((S > 1 ? 1 - kk : 0) * S + kk) * g.nq + i) * NP + c0);
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) {
+                        const float4 a = valid ? pd[q] : make_float4(0.f, 0.f, 0.f, 0.f);
+                        td[4 * q] = a.x; td[4 * q + 1] = a.y; td[4 * q + 2] = a.z; td[4 * q + 3] = a.w;
+                        if (S > 1) {
+                            const float4 b = valid ? pl[q] : make_float4(0.f, 0.f, 0.f, 0.f);
+                            const float4 c = valid ? pq[q] : make_float4(0.f, 0.f, 0.f, 0.f);
+                            tl[4 * q] = b.x; tl[4 * q + 1] = b.y; tl[4 * q + 2] = b.z; tl[4 * q + 3] = b.w;
+                            tr[4 * q] = c.x; tr[4 * q + 1] = c.y; tr[4 * q + 2] = c.z; tr[4 * q + 3] = c.w;
+                        }
+                    }
+                }
+                float dr[32], di[32];
+                tmem_load32(d_re + lane_off + c0, dr);
+                tmem_load32(d_im + lane_off + c0, di);
+                float yr[32], yi[32];
+#pragma unroll
+                for (int j = 0; j < 32; ++j) {
+                    float ar, ai;
+                    if (S == 1) {
+                        ar = td[j] * dr[j];
+                        ai = td[j] * di[j];
+                    } else {
+                        // pairs of this q row: lane ^ 2 holds (1-j, k), lane ^ 1 holds (j, 1-k)
+                        const float sr = __shfl_xor_sync(0xffffffffu, dr[j], 2), si = __shfl_xor_sync(0xffffffffu, di[j], 2);
+                        const float br = __shfl_xor_sync(0xffffffffu, dr[j], 1), bi = __shfl_xor_sync(0xffffffffu, di[j], 1);
+                        ar = td[j] * dr[j] + tl[j] * sr - tr[j] * br;
+                        ai = td[j] * di[j] + tl[j] * si - tr[j] * bi;
+                    }
+                    yr[j] = ai;  // times -i
+                    yi[j] = -ar;
+                }
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const uint32_t off = sw128_chunk(erow, grp * 4 + q);
+                    split_store8(yr + 8 * q, A, A + TILE, off);
+                    split_store8(yi + 8 * q, A + 2 * TILE, A + 3 * TILE, off);
+                }
+                fence_before();
+                run_and_wait(s, true, s == 0);
+            }
+            // ---- P rows to global -------------------------------------------------------------------
+            if (ok) {
+                size_t rb = 0;
+                if (valid) {
+                    long rest = row / S2 / g.nq;
+                    const int e = (int)(rest % g.n_elem);
+                    const int rep = (int)(rest / g.n_elem);
+                    rb = (size_t)rep * g.rep_stride + (size_t)e * g.elem_stride + (size_t)pr * 2 * g.blk +
+                         (size_t)i * NP;
+                }
+                for (int c0 = grp * (NP / 2); c0 < (grp + 1) * (NP / 2); c0 += 32) {
+                    float pr_[32], pi_[32];
+                    tmem_load32(p_re + lane_off + c0, pr_);
+                    tmem_load32(p_im + lane_off + c0, pi_);
+                    if (valid) {
+                        float4 *o_r = reinterpret_cast<float4 *>(P + rb + c0);
+                        float4 *o_i = reinterpret_cast<float4 *>(P + rb + g.blk + c0);
+#pragma unroll
+                        for (int q = 0; q < 8; ++q) {
+                            o_r[q] = make_float4(pr_[4 * q], pr_[4 * q + 1], pr_[4 * q + 2], pr_[4 * q + 3]);
+                            o_i[q] = make_float4(pi_[4 * q], pi_[4 * q + 1], pi_[4 * q + 2], pi_[4 * q + 3]);
+                        }
+                    }
+                }
+            }
         }
-        ok = __syncthreads_and(mbar_wait(mbar_a, phase));  // also: B tiles are rewritten by the next slice
-        phase ^= 1;
+        // tensor memory of this tile fully read before the next tile's MMAs overwrite it
+        fence_before();
+        __syncthreads();
         fence_after();
     }
-
-    // ---- epilogue: P rows to global ---------------------------------------------------------------
-    if (ok) {
-        for (int c0 = 0; c0 < NP; c0 += 32) {
-            float pr_[32], pi_[32];
-            tmem_load32(d_re + lane_off + c0, pr_);
-            tmem_load32(d_im + lane_off + c0, pi_);
-            if (valid) {
-                float4 *o_r = reinterpret_cast<float4 *>(P + rbase + c0);
-                float4 *o_i = reinterpret_cast<float4 *>(P + rbase + g.blk + c0);
-#pragma unroll
-                for (int q = 0; q < 8; ++q) {
-                    o_r[q] = make_float4(pr_[4 * q], pr_[4 * q + 1], pr_[4 * q + 2], pr_[4 * q + 3]);
-                    o_i[q] = make_float4(pi_[4 * q], pi_[4 * q + 1], pi_[4 * q + 2], pi_[4 * q + 3]);
-                }
-            }
-        }
-    } else if (t == 0) {
-        atomicExch(err, 1);
-    }
+    if (!ok && t == 0) atomicExch(err, 1);
     fence_before();
     __syncthreads();
     if (warp == 0) {
         fence_after();
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)(2 * NP)));
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)(4 * NP)));
     }
 }
 
 template <int NP, int S>
 size_t tc_smem_bytes()
 {
-    return (size_t)4 * (NP / 64) * TILE_M * 64 * 2 + 4 * (size_t)NP * 64 * 2 + 64 + 1024;
+    return (size_t)(NP / 64) * 4 * NP * 64 * 2 + 4 * (size_t)TILE_M * 64 * 2 + 64 + 1024;
 }
 
 template <int NP, int S>
@@ -360,8 +387,16 @@ cudaError_t launch_tc_t(const GridInfo &g, const float *v, float *P, const void 
                         const float *tL, const float *tR, int n_rep, int *err, cudaStream_t st)
 {
     const long rows = (long)n_rep * g.n_elem * g.nq * S * S;
-    const int blocks = (int)((rows + TILE_M - 1) / TILE_M);
-    if (blocks <= 0) return cudaSuccess;
+    const long tiles = (rows + TILE_M - 1) / TILE_M;
+    if (tiles <= 0) return cudaSuccess;
+    static int n_sm = 0;
+    if (!n_sm) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+        if (n_sm <= 0) n_sm = 148;
+    }
+    const int blocks = (int)(tiles < n_sm ? tiles : n_sm);  // persistent: one CTA per SM
     pot_tc_kernel<NP, S><<<blocks, TC_THREADS, tc_smem_bytes<NP, S>(), st>>>(
         g, v, P, reinterpret_cast<const uint4 *>(bmat), tD, tL, tR, rows, err);
     return cudaGetLastError();
