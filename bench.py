@@ -329,6 +329,7 @@ def main():
             "config": {"workload": "photoiso_96x128_d8_K2 (2 states, depth 8, 3 modes, 165 elements, "
                                    f"{cells} cells per GPU)", "precision": args.precision,
                        "l2": f"working set {4 * cells * 2 * esize / 1e6:.0f} MB per step > 129 MB L2 (no flush)",
+                       "tile_rows_autotuned": P.tile_rows(),
                        "parallelism": f"replicas x{world}"},
             "e2e": {"value": e2e, "unit": "cell-updates/s", "h2d_bytes_per_step": state_bytes,
                     "d2h_bytes_per_step": state_bytes + 16 * 2},

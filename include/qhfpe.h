@@ -194,6 +194,10 @@ qhfpe_status qhfpe_spectrum_2d(qhfpe_t *h, const double *R3, int n_t1, int n_t3,
  * handle's stream.  read returns the launch count and total device milliseconds per kernel kind
  * (index 0: stage kernel, 1: potential kernel, 2: trace/auxiliary) and resets the counters. */
 qhfpe_status qhfpe_kernel_timing(qhfpe_t *h, int enable);
+/* Tile of the fused right-hand-side kernel (q rows per block) picked by the autotuner for the
+ * handle's replicas: timed with CUDA events on the first propagation (0 before it, or when the
+ * shape has no fused kernel). */
+qhfpe_status qhfpe_tile_rows(const qhfpe_t *h, int *rows);
 qhfpe_status qhfpe_kernel_timing_read(qhfpe_t *h, long *launches, double *total_ms, int n_kinds);
 
 /* ---- Learned closure (one Drude mode, K = 0) --------------------------------------------------

@@ -165,6 +165,7 @@ struct Prop {
     GridInfo g{};
     bool mixed = false;
     bool tc = false;        // potential term on the tensor cores (bf16 x3)
+    int tq = 0;             // fused stage kernel: q rows per block (autotuned on first use; 0 = not yet)
     double dt = 0.0;
     void *y = nullptr, *vA = nullptr, *vB = nullptr, *P = nullptr;
     double *y0 = nullptr;
@@ -527,7 +528,7 @@ qhfpe_status step_once(qhfpe *h, Prop &P, bool record)
             Bracket br(h, QH_KIND_STAGE);
             QH_CK(h, (launch_fused<float, true>(P.g, M.elems, M.f32(), (const float *)in, (const float *)y, P.y0,
                                                (float *)out, k == 1 ? P.y0 : nullptr, P.dt / k, k == 1 ? 2 : 1,
-                                               QHFPE_TERM_ALL, 0, P.g.n_rep, st, (const float *)Pt)));
+                                               QHFPE_TERM_ALL, 0, P.g.n_rep, st, (const float *)Pt, P.tq)));
             continue;
         }
         if (M.fused) {
@@ -535,11 +536,11 @@ qhfpe_status step_once(qhfpe *h, Prop &P, bool record)
             if (MIXED)
                 QH_CK(h, (launch_fused<float, true>(P.g, M.elems, M.f32(), (const float *)in, (const float *)y, P.y0,
                                                    (float *)out, k == 1 ? P.y0 : nullptr, P.dt / k, k == 1 ? 2 : 1,
-                                                   QHFPE_TERM_ALL, 0, P.g.n_rep, st)));
+                                                   QHFPE_TERM_ALL, 0, P.g.n_rep, st, nullptr, P.tq)));
             else
                 QH_CK(h, (launch_fused<double, false>(P.g, M.elems, M.f64(), (const double *)in, (const double *)y,
                                                      nullptr, (double *)out, nullptr, P.dt / k, k == 1 ? 2 : 1,
-                                                     QHFPE_TERM_ALL, 0, P.g.n_rep, st)));
+                                                     QHFPE_TERM_ALL, 0, P.g.n_rep, st, nullptr, P.tq)));
             continue;
         }
         {
@@ -566,6 +567,51 @@ qhfpe_status step_dispatch(qhfpe *h, Prop &P, bool record)
     return P.mixed ? step_once<float, true>(h, P, record) : step_once<double, false>(h, P, record);
 }
 
+// Autotuner of the fused stage kernel's tile (q rows per block): each candidate evaluates the full
+// right-hand side of every replica (into a stage buffer, which holds no data between steps) a few
+// times, timed with CUDA events on the handle's stream; the fastest is kept for this propagator.
+// Results do not depend on the tile (every cell is computed by the same arithmetic).
+qhfpe_status autotune(qhfpe *h, Prop &P)
+{
+    const Model &M = *P.m;
+    if (P.tq || !M.fused) return QHFPE_OK;
+    cudaStream_t st = h->stream;
+    const int esize = P.mixed ? 4 : 8;
+    const int tmax = std::min(fused_max_rows(P.g.np, P.g.S, esize), P.g.nq);
+    cudaEvent_t a, b;
+    QH_CK(h, cudaEventCreate(&a));
+    QH_CK(h, cudaEventCreate(&b));
+    float best = 1e30f;
+    int best_tq = 1;
+    for (int tq = 1; tq <= tmax; tq *= 2) {
+        float ms = 0.f;
+        for (int rep = 0; rep < 4; ++rep) {
+            if (rep == 1) QH_CK(h, cudaEventRecord(a, st));
+            cudaError_t e;
+            if (P.mixed)
+                e = launch_fused<float, true>(P.g, M.elems, M.f32(), (const float *)P.y, (const float *)P.y, P.y0,
+                                              (float *)P.vB, nullptr, 0.0, 0, QHFPE_TERM_ALL, 0, P.g.n_rep, st,
+                                              P.tc ? (const float *)P.P : nullptr, tq);
+            else
+                e = launch_fused<double, false>(P.g, M.elems, M.f64(), (const double *)P.y, (const double *)P.y,
+                                                nullptr, (double *)P.vB, nullptr, 0.0, 0, QHFPE_TERM_ALL, 0, P.g.n_rep,
+                                                st, nullptr, tq);
+            QH_CK(h, e);
+        }
+        QH_CK(h, cudaEventRecord(b, st));
+        QH_CK(h, cudaEventSynchronize(b));
+        QH_CK(h, cudaEventElapsedTime(&ms, a, b));
+        if (ms < best) {
+            best = ms;
+            best_tq = tq;
+        }
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    P.tq = best_tq;
+    return QHFPE_OK;
+}
+
 __global__ void set_sink_kernel(TraceSink *s, double *base, long stride, long counter)
 {
     s->base = base;
@@ -576,6 +622,10 @@ __global__ void set_sink_kernel(TraceSink *s, double *base, long stride, long co
 qhfpe_status run_steps(qhfpe *h, Prop &P, long n_steps, double *trace_dev, long stride)
 {
     cudaStream_t st = h->stream;
+    if (!P.tq && P.m->fused && n_steps > 0) {
+        qhfpe_status r = autotune(h, P);
+        if (r != QHFPE_OK) return r;
+    }
     const bool record = trace_dev != nullptr;
     if (record) {
         set_sink_kernel<<<1, 1, 0, st>>>(P.sink, trace_dev, stride, 0);
@@ -1274,6 +1324,13 @@ qhfpe_status qhfpe_spectrum_2d(qhfpe_t *h, const double *R3, int n_t1, int n_t3,
     QH_CK(h, cudaMemcpyAsync(nr, dnr, nO * sizeof(double), cudaMemcpyDeviceToHost, st));
     QH_CK(h, cudaMemcpyAsync(re, dre, nO * sizeof(double), cudaMemcpyDeviceToHost, st));
     QH_CK(h, cudaStreamSynchronize(st));
+    return QHFPE_OK;
+}
+
+qhfpe_status qhfpe_tile_rows(const qhfpe_t *h, int *rows)
+{
+    if (!h || !rows) return QHFPE_EINVAL;
+    *rows = h->main->tq;
     return QHFPE_OK;
 }
 

@@ -451,18 +451,13 @@ fused_stage_kernel(GridInfo g, const ElemInfo *__restrict__ elems, FusedTables<T
     }
 }
 
-size_t fused_smem_bytes(int tq, int np, int S, int elem_bytes)
-{
-    const int n = tq * S * S * np;
-    return ((size_t)(n + (n >> 4) + 1) + np) * 2 * elem_bytes;
-}
-
 template <typename T, int NP, int S, bool MIXED>
 cudaError_t launch_fused_t(const GridInfo &g, const ElemInfo *elems, const FusedTables<T> &tab, const T *v_in,
                            const T *y, const double *y0, T *v_out, double *y0_out, double h, int mode, int terms,
-                           int rep0, int n_rep, cudaStream_t st, const T *Pg)
+                           int rep0, int n_rep, cudaStream_t st, const T *Pg, int tq_req)
 {
-    const int tq = fused_rows_per_tile(NP, S, sizeof(T));
+    int tq = tq_req > 0 ? tq_req : fused_rows_per_tile(NP, S, sizeof(T));
+    if (tq > g.nq) tq = g.nq;
     const size_t smem = fused_smem_bytes(tq, NP, S, sizeof(T));
     const int tiles = (g.nq + tq - 1) / tq;
     const long blocks = (long)tiles * n_rep * g.n_elem;
@@ -475,7 +470,7 @@ cudaError_t launch_fused_t(const GridInfo &g, const ElemInfo *elems, const Fused
 template <typename T, int NP, int S, bool MIXED>
 cudaError_t prepare_fused_t()
 {
-    const int tq = fused_rows_per_tile(NP, S, sizeof(T));
+    const int tq = fused_max_rows(NP, S, sizeof(T));
     const size_t smem = fused_smem_bytes(tq, NP, S, sizeof(T));
     return cudaFuncSetAttribute(fused_stage_kernel<T, NP, S, MIXED>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)smem);
@@ -493,14 +488,28 @@ int fused_rows_per_tile(int np, int S, int elem_bytes)
     return tq;
 }
 
+size_t fused_smem_bytes(int tq, int np, int S, int elem_bytes)
+{
+    const int n = tq * S * S * np;
+    return ((size_t)(n + (n >> 4) + 1) + np) * 2 * elem_bytes;
+}
+
+// Largest tile (q rows) the autotuner may pick: at most 16 rows and at most 96 KB of shared memory.
+int fused_max_rows(int np, int S, int elem_bytes)
+{
+    int tq = 16;
+    while (tq > 1 && fused_smem_bytes(tq, np, S, elem_bytes) > 96 * 1024) tq /= 2;
+    return tq;
+}
+
 bool fused_supported(int np, int S) { return (np == 32 || np == 64 || np == 128 || np == 256) && S >= 1 && S <= 3; }
 
 template <typename T, bool MIXED>
 cudaError_t launch_fused(const GridInfo &g, const ElemInfo *elems, const FusedTables<T> &tab, const T *v_in,
                          const T *y, const double *y0, T *v_out, double *y0_out, double h, int mode, int terms,
-                         int rep0, int n_rep, cudaStream_t st, const T *Pg)
+                         int rep0, int n_rep, cudaStream_t st, const T *Pg, int tq)
 {
-#define QH_CALL(T_, NP_, S_, M_) launch_fused_t<T_, NP_, S_, M_>(g, elems, tab, v_in, y, y0, v_out, y0_out, h, mode, terms, rep0, n_rep, st, Pg)
+#define QH_CALL(T_, NP_, S_, M_) launch_fused_t<T_, NP_, S_, M_>(g, elems, tab, v_in, y, y0, v_out, y0_out, h, mode, terms, rep0, n_rep, st, Pg, tq)
     switch (g.np * 8 + g.S) {
     case 32 * 8 + 1: return QH_CALL(T, 32, 1, MIXED);
     case 32 * 8 + 2: return QH_CALL(T, 32, 2, MIXED);
@@ -563,7 +572,7 @@ int fused_fft_frequency(int np, int pos)
     return k;
 }
 
-template cudaError_t launch_fused<float, true>(const GridInfo &, const ElemInfo *, const FusedTables<float> &, const float *, const float *, const double *, float *, double *, double, int, int, int, int, cudaStream_t, const float *);
-template cudaError_t launch_fused<double, false>(const GridInfo &, const ElemInfo *, const FusedTables<double> &, const double *, const double *, const double *, double *, double *, double, int, int, int, int, cudaStream_t, const double *);
+template cudaError_t launch_fused<float, true>(const GridInfo &, const ElemInfo *, const FusedTables<float> &, const float *, const float *, const double *, float *, double *, double, int, int, int, int, cudaStream_t, const float *, int);
+template cudaError_t launch_fused<double, false>(const GridInfo &, const ElemInfo *, const FusedTables<double> &, const double *, const double *, const double *, double *, double *, double, int, int, int, int, cudaStream_t, const double *, int);
 template cudaError_t prepare_fused<float, true>(int, int);
 template cudaError_t prepare_fused<double, false>(int, int);

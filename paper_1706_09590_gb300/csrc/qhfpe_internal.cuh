@@ -93,11 +93,13 @@ bool fused_supported(int np, int S);
 int fused_rows_per_tile(int np, int S, int elem_bytes);
 size_t fused_smem_bytes(int tq, int np, int S, int elem_bytes);
 int fused_fft_frequency(int np, int pos);
-// Pg: potential term computed elsewhere (same layout as v_in), or nullptr to compute it in the kernel
+// Pg: potential term computed elsewhere (same layout as v_in), or nullptr to compute it in the kernel.
+// tq: q rows per block (0: the default heuristic), at most fused_max_rows.
 template <typename T, bool MIXED>
 cudaError_t launch_fused(const GridInfo &g, const ElemInfo *elems, const FusedTables<T> &tab, const T *v_in,
                          const T *y, const double *y0, T *v_out, double *y0_out, double h, int mode, int terms,
-                         int rep0, int n_rep, cudaStream_t st, const T *Pg = nullptr);
+                         int rep0, int n_rep, cudaStream_t st, const T *Pg = nullptr, int tq = 0);
+int fused_max_rows(int np, int S, int elem_bytes);
 
 // ---- tensor-core potential term (qhfpe_tc.cu) ----------------------------------------------------------
 bool tc_supported(int np, int S);
