@@ -194,6 +194,11 @@ qhfpe_status qhfpe_spectrum_2d(qhfpe_t *h, const double *R3, int n_t1, int n_t3,
  * handle's stream.  read returns the launch count and total device milliseconds per kernel kind
  * (index 0: stage kernel, 1: potential kernel, 2: trace/auxiliary) and resets the counters. */
 qhfpe_status qhfpe_kernel_timing(qhfpe_t *h, int enable);
+/* Failure-detection self-test: a one-thread kernel waits on a device flag with the library's bounded
+ * wait (%globaltimer limit of limit_ms milliseconds, 1..10000).  release = 1 sets the flag first
+ * (returns QHFPE_OK); release = 0 leaves it unset, so the wait gives up and the call returns
+ * QHFPE_ETIMEOUT while the handle and the CUDA context stay usable. */
+qhfpe_status qhfpe_wait_selftest(qhfpe_t *h, int release, int limit_ms);
 /* Tile of the fused right-hand-side kernel (q rows per block) picked by the autotuner for the
  * handle's replicas: timed with CUDA events on the first propagation (0 before it, or when the
  * shape has no fused kernel). */

@@ -1327,6 +1327,25 @@ qhfpe_status qhfpe_spectrum_2d(qhfpe_t *h, const double *R3, int n_t1, int n_t3,
     return QHFPE_OK;
 }
 
+qhfpe_status qhfpe_wait_selftest(qhfpe_t *h, int release, int limit_ms)
+{
+    qhfpe_status r = check_handle(h);
+    if (r != QHFPE_OK) return r;
+    if (limit_ms < 1 || limit_ms > 10000) return h->fail(QHFPE_EINVAL, "wait_selftest: limit_ms must be in [1, 10000]");
+    int *buf = nullptr;
+    QH_CK(h, cudaMalloc((void **)&buf, 2 * sizeof(int)));
+    int init[2] = {release ? 1 : 0, 0};
+    cudaError_t e = cudaMemcpyAsync(buf, init, sizeof(init), cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess) e = launch_wait_flag(buf, (unsigned long long)limit_ms * 1000000ull, buf + 1, h->stream);
+    int status = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&status, buf + 1, sizeof(int), cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    cudaFree(buf);
+    QH_CK(h, e);
+    if (status == 2) return h->fail(QHFPE_ETIMEOUT, "wait_selftest: the device wait gave up (flag never set)");
+    return status == 1 ? QHFPE_OK : h->fail(QHFPE_ECUDA, "wait_selftest: no status written");
+}
+
 qhfpe_status qhfpe_tile_rows(const qhfpe_t *h, int *rows)
 {
     if (!h || !rows) return QHFPE_EINVAL;

@@ -136,6 +136,7 @@ cudaError_t launch_to_canonical(const GridInfo &g, const T *src, const double *y
                                 cudaStream_t st);
 
 cudaError_t launch_norm2(const double *x, size_t n, double *out_dev, cudaStream_t st);
+cudaError_t launch_wait_flag(const int *flag, unsigned long long limit_ns, int *status, cudaStream_t st);
 cudaError_t launch_absorption(const double *R1, long n_t, double dt, const double *omega, int n_omega,
                               double *out, cudaStream_t st);
 cudaError_t launch_spectrum2d(const double *R3, int n_t1, int n_t3, double dt1, double dt3, const double *omega1,

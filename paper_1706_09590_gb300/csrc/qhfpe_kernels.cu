@@ -506,6 +506,26 @@ __global__ void spec2d_t1_kernel(const double *__restrict__ G, int n_t1, double 
     re[idx] = ar;
 }
 
+// Bounded wait on a device flag (the pattern every device-side wait of the library follows): spin until
+// *flag != 0 or `limit_ns` of %globaltimer have passed; status 1 = the flag arrived, 2 = gave up.
+__global__ void wait_flag_kernel(const volatile int *flag, unsigned long long limit_ns, int *status)
+{
+    unsigned long long t0, t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
+    for (;;) {
+        if (*flag != 0) {
+            *status = 1;
+            return;
+        }
+        asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+        if (t - t0 > limit_ns) {
+            *status = 2;
+            return;
+        }
+        __nanosleep(1000);
+    }
+}
+
 inline int grid_for(size_t n, int threads, int cap = 152 * 32)
 {
     size_t b = (n + threads - 1) / threads;
@@ -602,6 +622,12 @@ cudaError_t launch_to_canonical(const GridInfo &g, const T *src, const double *y
 {
     const size_t per = (size_t)g.n_elem * g.S * g.S * g.blk;
     to_canonical_kernel<T><<<grid_for(per, 256, 2048), 256, 0, st>>>(g, src, y0_src, dst, rep);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_wait_flag(const int *flag, unsigned long long limit_ns, int *status, cudaStream_t st)
+{
+    wait_flag_kernel<<<1, 1, 0, st>>>(flag, limit_ns, status);
     return cudaGetLastError();
 }
 

@@ -30,7 +30,7 @@ EXPORTED = [
     "qhfpe_set_equilibrium", "qhfpe_response", "qhfpe_spectrum_absorption", "qhfpe_spectrum_2d",
     "qhfpe_kernel_timing", "qhfpe_kernel_timing_read", "qhfpe_potential_term_static",
     "qhfpe_closure_collect", "qhfpe_closure_load", "qhfpe_closure_coefficients", "qhfpe_closure_loss_grad",
-    "qhfpe_closure_train", "qhfpe_tile_rows",
+    "qhfpe_closure_train", "qhfpe_tile_rows", "qhfpe_wait_selftest",
 ]
 
 CLOSURE_N_WEIGHTS = 135178
@@ -101,6 +101,7 @@ def lib():
     L.qhfpe_potential_term_static.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double,
                                               ctypes.c_double, vp, ctypes.c_int, vp, vp, vp]
     L.qhfpe_tile_rows.argtypes = [vp, ip]
+    L.qhfpe_wait_selftest.argtypes = [vp, ctypes.c_int, ctypes.c_int]
     L.qhfpe_closure_collect.argtypes = [vp, ctypes.c_int, vp]
     L.qhfpe_closure_load.argtypes = [vp, vp, ctypes.c_size_t]
     L.qhfpe_closure_coefficients.argtypes = [vp, vp]
@@ -359,6 +360,10 @@ class Propagator:
         return out
 
     # ---- measurement -----------------------------------------------------------------------------
+    def wait_selftest(self, release, limit_ms=200):
+        """Status of the bounded device wait self-test (0 = OK, 5 = ETIMEOUT)."""
+        return self._L.qhfpe_wait_selftest(self._h, int(release), int(limit_ms))
+
     def tile_rows(self):
         v = ctypes.c_int()
         self._check(self._L.qhfpe_tile_rows(self._h, ctypes.byref(v)))

@@ -245,3 +245,36 @@ def test_set_state_rejects_non_finite():
     assert ei.value.status == 4
     P.set_state(qi.random_state(m, seed=51))  # the handle stays usable
     P.step(1)
+
+
+def test_device_wait_gives_up_and_context_survives():
+    """A device wait on a flag that nothing sets returns ETIMEOUT after its limit; the handle and the
+    context keep working afterwards."""
+    m = MODELS["harmonic"]
+    P = _P(m)
+    assert P.wait_selftest(release=1, limit_ms=200) == 0
+    assert P.wait_selftest(release=0, limit_ms=200) == 5
+    W = qi.random_state(m, seed=80)
+    P.set_state(W)
+    P.step(3)
+    O = oracle.Oracle(m)
+    assert rel(P.get_state(0), O.step(W, 3)[0]) < 1e-11
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_resume_is_bitwise_identical(precision):
+    """Checkpoint/resume: 7 + 9 steps through get_state/set_state on a second handle equal 16 steps."""
+    m = MODELS["photoiso"]
+    W = qi.random_state(m, seed=81)
+    A = _P(m, precision)
+    A.set_state(W)
+    trA = A.step(16, record_trace=True)[0]
+    B = _P(m, precision)
+    B.set_state(W)
+    trB1 = B.step(7, record_trace=True)[0]
+    ck = B.get_state(0)
+    C = _P(m, precision)
+    C.set_state(ck)
+    trC = C.step(9, record_trace=True)[0]
+    assert np.array_equal(A.get_state(0), C.get_state(0))
+    assert np.array_equal(trA[:8], trB1) and np.array_equal(trA[7:], trC)
