@@ -102,11 +102,15 @@ __device__ __forceinline__ void fft_pass(C *X, int n_tr, const C *__restrict__ t
         for (int t = 0; t < R; ++t) x[t] = X[pad16(base + t * S)];
         if (FWD) {
             dft_small<R, +1>(x);
+            if constexpr (S > 1) {  // the last pass (sub-length R) has only unit twiddles
 #pragma unroll
-            for (int u = 1; u < R; ++u) x[u] = cmul(x[u], tw[(j * u) * (NP / M)]);
+                for (int u = 1; u < R; ++u) x[u] = cmul(x[u], tw[(j * u) * (NP / M)]);
+            }
         } else {
+            if constexpr (S > 1) {
 #pragma unroll
-            for (int u = 1; u < R; ++u) x[u] = cconjmul(x[u], tw[(j * u) * (NP / M)]);
+                for (int u = 1; u < R; ++u) x[u] = cconjmul(x[u], tw[(j * u) * (NP / M)]);
+            }
             dft_small<R, -1>(x);
         }
 #pragma unroll
@@ -192,41 +196,62 @@ fused_stage_kernel(GridInfo g, const ElemInfo *__restrict__ elems, FusedTables<T
     // ---- phase A: potential term -------------------------------------------------------------
     const bool want_pot = (terms & 2) != 0;
     if (want_pot && !Pg) {
-        for (int idx = threadIdx.x; idx < rows * S2 * NP; idx += FTHREADS) {
-            const int l = idx % NP, rp = idx / NP;
+        constexpr int LV = 4;  // p values per load
+        for (int idx = threadIdx.x; idx < rows * S2 * (NP / LV); idx += FTHREADS) {
+            const int l = (idx % (NP / LV)) * LV, rp = idx / (NP / LV);
             const int pr = rp % S2, r = rp / S2;
             const T *src = v_in + ebase + (size_t)pr * 2 * blk + (size_t)(i0 + r) * NP + l;
-            X[pad16((r * S2 + pr) * NP + l)] = C{src[0], src[blk]};
+            T re[LV], im[LV];
+            ldv<T, LV>(src, re);
+            ldv<T, LV>(src + blk, im);
+            const int base = (r * S2 + pr) * NP + l;
+#pragma unroll
+            for (int v = 0; v < LV; ++v) X[pad16(base + v)] = C{re[v], im[v]};
         }
         __syncthreads();
         fft_all<NP, true>(X, rows * S2, tw);
-        for (int idx = threadIdx.x; idx < rows * NP; idx += FTHREADS) {
-            const int pos = idx % NP, r = idx / NP;
+        constexpr int MV = S >= 3 ? 1 : (S == 2 ? 2 : 4);  // modes per thread (vector table loads)
+        for (int idx = threadIdx.x; idx < rows * (NP / MV); idx += FTHREADS) {
+            const int pos0 = (idx % (NP / MV)) * MV, r = idx / (NP / MV);
             const int i = i0 + r;
-            C rho[S2];
+            C rho[S2][MV];
 #pragma unroll
-            for (int a = 0; a < S2; ++a) rho[a] = X[pad16((r * S2 + a) * NP + pos)];
+            for (int a = 0; a < S2; ++a)
+#pragma unroll
+                for (int v = 0; v < MV; ++v) rho[a][v] = X[pad16((r * S2 + a) * NP + pos0 + v)];
 #pragma unroll
             for (int j = 0; j < S; ++j)
 #pragma unroll
                 for (int k = 0; k < S; ++k) {
-                    const size_t trow = ((size_t)(j * S + k) * nq + i) * NP + pos;
-                    const T d = tab.D[trow];
-                    C acc = {d * rho[j * S + k].x, d * rho[j * S + k].y};
+                    T d[MV];
+                    ldv<T, MV>(tab.D + ((size_t)(j * S + k) * nq + i) * NP + pos0, d);
+                    C acc[MV];
+#pragma unroll
+                    for (int v = 0; v < MV; ++v) acc[v] = C{d[v] * rho[j * S + k][v].x, d[v] * rho[j * S + k][v].y};
 #pragma unroll
                     for (int s = 0; s < S; ++s) {
                         if (s != j) {
-                            const T u = tab.L[((size_t)(j * S + s) * nq + i) * NP + pos];
-                            acc.x += u * rho[s * S + k].x;
-                            acc.y += u * rho[s * S + k].y;
+                            T u[MV];
+                            ldv<T, MV>(tab.L + ((size_t)(j * S + s) * nq + i) * NP + pos0, u);
+#pragma unroll
+                            for (int v = 0; v < MV; ++v) {
+                                acc[v].x += u[v] * rho[s * S + k][v].x;
+                                acc[v].y += u[v] * rho[s * S + k][v].y;
+                            }
                         }
                         if (s != k) {
-                            const T u = tab.R[((size_t)(s * S + k) * nq + i) * NP + pos];
-                            acc.x -= u * rho[j * S + s].x;
-                            acc.y -= u * rho[j * S + s].y;
+                            T u[MV];
+                            ldv<T, MV>(tab.R + ((size_t)(s * S + k) * nq + i) * NP + pos0, u);
+#pragma unroll
+                            for (int v = 0; v < MV; ++v) {
+                                acc[v].x -= u[v] * rho[j * S + s][v].x;
+                                acc[v].y -= u[v] * rho[j * S + s][v].y;
+                            }
                         }
                     }
-                    X[pad16((r * S2 + j * S + k) * NP + pos)] = C{acc.y, -acc.x};  // times -i
+#pragma unroll
+                    for (int v = 0; v < MV; ++v)
+                        X[pad16((r * S2 + j * S + k) * NP + pos0 + v)] = C{acc[v].y, -acc[v].x};  // times -i
                 }
         }
         __syncthreads();
