@@ -1046,14 +1046,16 @@ qhfpe_status qhfpe_apply_rhs(qhfpe_t *h, int replica, int terms, double *out)
         QH_CK(h, launch_potential_tc(P.g, (const float *)P.y, (float *)P.P, M.tcB, M.tcN, M.tcN + M.tab_n,
                                      M.tcN + 2 * M.tab_n, P.g.n_rep, h->tc_err, st));
         QH_CK(h, (launch_fused<float, true>(P.g, M.elems, M.f32(), (const float *)P.y, (const float *)P.y, P.y0,
-                                           (float *)P.vA, nullptr, 0.0, 0, terms, replica, 1, st, (const float *)P.P)));
+                                           (float *)P.vA, nullptr, 0.0, 0, terms, replica, 1, st, (const float *)P.P,
+                                           P.tq)));
     } else if (M.fused) {
         if (P.mixed)
             QH_CK(h, (launch_fused<float, true>(P.g, M.elems, M.f32(), (const float *)P.y, (const float *)P.y, P.y0,
-                                               (float *)P.vA, nullptr, 0.0, 0, terms, replica, 1, st)));
+                                               (float *)P.vA, nullptr, 0.0, 0, terms, replica, 1, st, nullptr, P.tq)));
         else
             QH_CK(h, (launch_fused<double, false>(P.g, M.elems, M.f64(), (const double *)P.y, (const double *)P.y,
-                                                 nullptr, (double *)P.vA, nullptr, 0.0, 0, terms, replica, 1, st)));
+                                                 nullptr, (double *)P.vA, nullptr, 0.0, 0, terms, replica, 1, st,
+                                                 nullptr, P.tq)));
     } else if (P.mixed) {
         QH_CK(h, launch_potential<float>(P.g, M.t32(), (const float *)P.y, (float *)P.P, replica, 1, st));
         QH_CK(h, (launch_stage<float, true>(P.g, M.elems, (const float *)P.y, (const float *)P.P, (const float *)P.y,

@@ -482,6 +482,8 @@ cudaError_t launch_fused_t(const GridInfo &g, const ElemInfo *elems, const Fused
                            int rep0, int n_rep, cudaStream_t st, const T *Pg, int tq_req)
 {
     int tq = tq_req > 0 ? tq_req : fused_rows_per_tile(NP, S, sizeof(T));
+    const int tmax = fused_max_rows(NP, S, sizeof(T));  // the shared-memory limit set at preparation
+    if (tq > tmax) tq = tmax;
     if (tq > g.nq) tq = g.nq;
     const size_t smem = fused_smem_bytes(tq, NP, S, sizeof(T));
     const int tiles = (g.nq + tq - 1) / tq;
