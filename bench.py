@@ -309,6 +309,16 @@ def main():
                   "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if peaks else "fallback 6800 GB/s",
                   "ms_per_launch": stage_ms, "share": ms_stage / total,
                   "algorithmic_bytes_per_launch": alg_bytes_stage}
+    # DRAM bytes per launch from the committed ncu capture, valid only for the kernel source it was
+    # taken from
+    try:
+        import hashlib
+        tr = json.load(open(os.path.join(ROOT, "profiles", "ncu_traffic_fused_stage_photoiso_96x128_d8.json")))
+        src = open(os.path.join(ROOT, tr["source"]), "rb").read()
+        if hashlib.sha256(src).hexdigest() == tr["source_sha256"] and args.precision == "mixed":
+            stage_roof["traffic"] = tr["dram_bytes_per_launch"]
+    except (OSError, ValueError, KeyError):
+        pass
     roof = stage_roof
     if args.precision == "bf16x3" and n_pot:
         # tensor flops issued per launch: forward and inverse DFT-GEMMs, 4 real products of
