@@ -170,6 +170,7 @@ struct Prop {
     void *y = nullptr, *vA = nullptr, *vB = nullptr, *P = nullptr;
     double *y0 = nullptr;
     TraceSink *sink = nullptr;
+    double *partial = nullptr;  // trace reduction partials [n_rep][QH_TRACE_MAX_CHUNKS][2]
     double *trace_buf = nullptr;
     size_t trace_cap = 0;
     cudaGraphExec_t graphs[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};  // [chunk][trace]
@@ -179,7 +180,7 @@ struct Prop {
         for (auto &a : graphs)
             for (auto &x : a)
                 if (x) cudaGraphExecDestroy(x);
-        for (void *b : {y, vA, vB, P, (void *)y0, (void *)sink, (void *)trace_buf})
+        for (void *b : {y, vA, vB, P, (void *)y0, (void *)sink, (void *)partial, (void *)trace_buf})
             if (b) cudaFree(b);
     }
 };
@@ -454,6 +455,7 @@ qhfpe_status make_prop(qhfpe *h, Model *M, int n_rep, bool mixed, double dt, std
         }
         QH_CK(h, cudaMemsetAsync(P->y0, 0, (size_t)n_rep * P->g.tier0_rep_stride * sizeof(double), h->stream));
     }
+    QH_CK(h, cudaMalloc((void **)&P->partial, (size_t)n_rep * QH_TRACE_MAX_CHUNKS * 2 * sizeof(double)));
     QH_CK(h, cudaMalloc((void **)&P->sink, sizeof(TraceSink)));
     QH_CK(h, cudaMemsetAsync(P->sink, 0, sizeof(TraceSink), h->stream));
     out = std::move(P);
@@ -556,8 +558,8 @@ qhfpe_status step_once(qhfpe *h, Prop &P, bool record)
     }
     if (record) {
         Bracket br(h, QH_KIND_AUX);
-        if (MIXED) QH_CK(h, launch_trace<double>(P.g, P.y0, P.g.tier0_rep_stride, M.mu, P.sink, 1, st));
-        else QH_CK(h, launch_trace<double>(P.g, (const double *)P.y, P.g.rep_stride, M.mu, P.sink, 1, st));
+        if (MIXED) QH_CK(h, launch_trace<double>(P.g, P.y0, P.g.tier0_rep_stride, M.mu, P.sink, 1, P.partial, st));
+        else QH_CK(h, launch_trace<double>(P.g, (const double *)P.y, P.g.rep_stride, M.mu, P.sink, 1, P.partial, st));
     }
     return QHFPE_OK;
 }
@@ -630,8 +632,8 @@ qhfpe_status run_steps(qhfpe *h, Prop &P, long n_steps, double *trace_dev, long 
     if (record) {
         set_sink_kernel<<<1, 1, 0, st>>>(P.sink, trace_dev, stride, 0);
         QH_CK(h, cudaGetLastError());
-        if (P.mixed) QH_CK(h, launch_trace<double>(P.g, P.y0, P.g.tier0_rep_stride, P.m->mu, P.sink, 1, st));
-        else QH_CK(h, launch_trace<double>(P.g, (const double *)P.y, P.g.rep_stride, P.m->mu, P.sink, 1, st));
+        if (P.mixed) QH_CK(h, launch_trace<double>(P.g, P.y0, P.g.tier0_rep_stride, P.m->mu, P.sink, 1, P.partial, st));
+        else QH_CK(h, launch_trace<double>(P.g, (const double *)P.y, P.g.rep_stride, P.m->mu, P.sink, 1, P.partial, st));
     }
     if (h->timing.enabled) {
         for (long s = 0; s < n_steps; ++s) {
@@ -1086,8 +1088,8 @@ qhfpe_status qhfpe_trace(qhfpe_t *h, double *out)
     if (r != QHFPE_OK) return r;
     set_sink_kernel<<<1, 1, 0, h->stream>>>(P.sink, P.trace_buf, 1, 0);
     QH_CK(h, cudaGetLastError());
-    if (P.mixed) QH_CK(h, launch_trace<double>(P.g, P.y0, P.g.tier0_rep_stride, P.m->mu, P.sink, 0, h->stream));
-    else QH_CK(h, launch_trace<double>(P.g, (const double *)P.y, P.g.rep_stride, P.m->mu, P.sink, 0, h->stream));
+    if (P.mixed) QH_CK(h, launch_trace<double>(P.g, P.y0, P.g.tier0_rep_stride, P.m->mu, P.sink, 0, P.partial, h->stream));
+    else QH_CK(h, launch_trace<double>(P.g, (const double *)P.y, P.g.rep_stride, P.m->mu, P.sink, 0, P.partial, h->stream));
     QH_CK(h, cudaMemcpyAsync(out, P.trace_buf, (size_t)P.g.n_rep * 2 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
     QH_CK(h, cudaStreamSynchronize(h->stream));
     return QHFPE_OK;

@@ -81,9 +81,11 @@ cudaError_t launch_stage(const GridInfo &g, const ElemInfo *elems, const T *v_in
                          const double *y0, T *v_out, double *y0_out, double h, int mode, int terms,
                          int rep0, int n_rep, cudaStream_t st);
 
+// partial: device scratch of 2 * n_rep * QH_TRACE_MAX_CHUNKS doubles
+#define QH_TRACE_MAX_CHUNKS 64
 template <typename T>
 cudaError_t launch_trace(const GridInfo &g, const T *state, size_t rep_stride, const double *mu_dev,
-                         TraceSink *sink, int advance, cudaStream_t st);
+                         TraceSink *sink, int advance, double *partial, cudaStream_t st);
 
 cudaError_t launch_advance(TraceSink *sink, cudaStream_t st);
 cudaError_t prepare_potential(size_t smem_bytes_fp64);

@@ -284,18 +284,21 @@ pot_kernel(GridInfo g, PotTables<T> tab, const T *__restrict__ v, T *__restrict_
 }
 
 // ---------------------------------------------------------------------------------------------------
-// Tr{mu W^(0)} = sum_jk mu_kj sum_il W^(0)_jk dq dp for every replica, FP64, fixed summation order
-// (deterministic): one block per replica.
+// Tr{mu W^(0)} = sum_jk mu_kj sum_il W^(0)_jk dq dp for every replica, FP64, in a fixed summation
+// order (deterministic): pass 1 sums fixed chunks of cells per (replica, chunk) block into partials,
+// pass 2 adds each replica's partials in chunk order, writes the sink slot and advances the counter.
 // ---------------------------------------------------------------------------------------------------
 template <typename T>
-__global__ void __launch_bounds__(512)
-trace_kernel(GridInfo g, const T *__restrict__ state, size_t rep_stride, const double *__restrict__ mu,
-             TraceSink *sink)
+__global__ void __launch_bounds__(256)
+trace_partial_kernel(GridInfo g, const T *__restrict__ state, size_t rep_stride, const double *__restrict__ mu,
+                     double *partial, int n_chunks)
 {
-    __shared__ double red[2][512];
-    const int rep = blockIdx.x;
+    __shared__ double red[2][256];
+    const int chunk = blockIdx.x, rep = blockIdx.y;
     const int S = g.S;
     const size_t blk = g.blk;
+    const size_t len = (blk + n_chunks - 1) / n_chunks;
+    const size_t c0 = (size_t)chunk * len, c1 = c0 + len < blk ? c0 + len : blk;
     const T *W = state + (size_t)rep * rep_stride;
     double sr = 0.0, si = 0.0;
     for (int j = 0; j < S; ++j)
@@ -304,7 +307,7 @@ trace_kernel(GridInfo g, const T *__restrict__ state, size_t rep_stride, const d
             if (m == 0.0) continue;
             const T *b = W + (size_t)(j * S + k) * 2 * blk;
             double ar = 0.0, ai = 0.0;
-            for (size_t c = threadIdx.x; c < blk; c += blockDim.x) {
+            for (size_t c = c0 + threadIdx.x; c < c1; c += blockDim.x) {
                 ar += (double)b[c];
                 ai += (double)b[c + blk];
             }
@@ -322,11 +325,27 @@ trace_kernel(GridInfo g, const T *__restrict__ state, size_t rep_stride, const d
         __syncthreads();
     }
     if (threadIdx.x == 0) {
-        const long slot = sink->counter;
-        double *out = sink->base + 2 * ((size_t)rep * sink->stride + slot);
-        out[0] = red[0][0] * g.dq * g.dp;
-        out[1] = red[1][0] * g.dq * g.dp;
+        partial[2 * ((size_t)rep * n_chunks + chunk)] = red[0][0];
+        partial[2 * ((size_t)rep * n_chunks + chunk) + 1] = red[1][0];
     }
+}
+
+__global__ void trace_finish_kernel(GridInfo g, const double *__restrict__ partial, int n_chunks, TraceSink *sink,
+                                    int advance)
+{
+    const long slot = sink->counter;
+    for (int rep = threadIdx.x; rep < g.n_rep; rep += blockDim.x) {
+        double sr = 0.0, si = 0.0;
+        for (int c = 0; c < n_chunks; ++c) {
+            sr += partial[2 * ((size_t)rep * n_chunks + c)];
+            si += partial[2 * ((size_t)rep * n_chunks + c) + 1];
+        }
+        double *out = sink->base + 2 * ((size_t)rep * sink->stride + slot);
+        out[0] = sr * g.dq * g.dp;
+        out[1] = si * g.dq * g.dp;
+    }
+    __syncthreads();
+    if (advance && threadIdx.x == 0) sink->counter = slot + 1;
 }
 
 __global__ void advance_kernel(TraceSink *sink) { sink->counter += 1; }
@@ -560,14 +579,23 @@ cudaError_t launch_stage(const GridInfo &g, const ElemInfo *elems, const T *v_in
     return cudaGetLastError();
 }
 
+int trace_chunks(int n_rep, size_t blk)
+{
+    int c = (int)((304 + n_rep - 1) / n_rep);  // about two blocks per SM in total
+    if (c > QH_TRACE_MAX_CHUNKS) c = QH_TRACE_MAX_CHUNKS;
+    if ((size_t)c > blk) c = (int)blk;
+    return c < 1 ? 1 : c;
+}
+
 template <typename T>
 cudaError_t launch_trace(const GridInfo &g, const T *state, size_t rep_stride, const double *mu_dev,
-                         TraceSink *sink, int advance, cudaStream_t st)
+                         TraceSink *sink, int advance, double *partial, cudaStream_t st)
 {
-    trace_kernel<T><<<g.n_rep, 512, 0, st>>>(g, state, rep_stride, mu_dev, sink);
+    const int nc = trace_chunks(g.n_rep, g.blk);
+    trace_partial_kernel<T><<<dim3(nc, g.n_rep), 256, 0, st>>>(g, state, rep_stride, mu_dev, partial, nc);
     cudaError_t err = cudaGetLastError();
-    if (err != cudaSuccess || !advance) return err;
-    advance_kernel<<<1, 1, 0, st>>>(sink);
+    if (err != cudaSuccess) return err;
+    trace_finish_kernel<<<1, 512, 0, st>>>(g, partial, nc, sink, advance);
     return cudaGetLastError();
 }
 
@@ -660,7 +688,7 @@ template cudaError_t launch_potential<double>(const GridInfo &, const PotTables<
 template cudaError_t launch_potential<float>(const GridInfo &, const PotTables<float> &, const float *, float *, int, int, cudaStream_t);
 template cudaError_t launch_stage<double, false>(const GridInfo &, const ElemInfo *, const double *, const double *, const double *, const double *, double *, double *, double, int, int, int, int, cudaStream_t);
 template cudaError_t launch_stage<float, true>(const GridInfo &, const ElemInfo *, const float *, const float *, const float *, const double *, float *, double *, double, int, int, int, int, cudaStream_t);
-template cudaError_t launch_trace<double>(const GridInfo &, const double *, size_t, const double *, TraceSink *, int, cudaStream_t);
+template cudaError_t launch_trace<double>(const GridInfo &, const double *, size_t, const double *, TraceSink *, int, double *, cudaStream_t);
 template cudaError_t launch_dipole<double>(const GridInfo &, double *, double *, const int *, int, const double *, int, double, cudaStream_t);
 template cudaError_t launch_dipole<float>(const GridInfo &, float *, double *, const int *, int, const double *, int, double, cudaStream_t);
 template cudaError_t launch_from_canonical<double>(const GridInfo &, const double *, double *, double *, int, int, cudaStream_t, int *);
