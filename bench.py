@@ -33,6 +33,21 @@ def _env_int(k, d):
         return d
 
 
+def max_over_ranks(value, dist=None, device="cpu"):
+    """The largest of `value` over all ranks (the job's time is its slowest rank's)."""
+    if dist is None or not dist.is_initialized() or dist.get_world_size() == 1:
+        return float(value)
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(units_per_rank, steps, world, max_ms):
+    """Whole-job units per second: every rank processes its own replicas (no shared work)."""
+    return units_per_rank * steps * world / (max_ms / 1e3)
+
+
 def workload():
     import qhfpe_inputs as qi
     m = qi.photoisomerization_two_state()
@@ -262,12 +277,9 @@ def main():
     ms = ev0.elapsed_time(ev1)
     kt = P.kernel_timing_read()
     P.kernel_timing(False)
-    if dist is not None:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, dist, device="cuda")
     assert np.all(np.isfinite(tr)), "non-finite trace"
-    value = cells * args.steps * world / (ms / 1e3)
+    value = job_throughput(cells, args.steps, world, ms)
 
     # ---- end to end through the C ABI with host buffers --------------------------------------------
     # every step: the state from pinned host memory, one RK4 step with its trace, the state back
@@ -284,8 +296,8 @@ def main():
         P.step(1, record_trace=True)
         P.get_state(0, out=w_out)
     torch.cuda.synchronize()
-    e2e_s = time.perf_counter() - t0
-    e2e = cells * n_e2e * world / e2e_s
+    e2e_s = max_over_ranks(time.perf_counter() - t0, dist, device="cuda")
+    e2e = job_throughput(cells, n_e2e, world, 1e3 * e2e_s)
 
     # ---- roofline of the dominant kernel ------------------------------------------------------------
     import json as _j
