@@ -52,6 +52,8 @@ def lib():
         L.oq_get_hierarchy.argtypes = [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int)]
         L.oq_get_coefficients.argtypes = [ctypes.c_void_p, dp, dp, dp, dp]
         L.oq_rhs.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]
+        L.oq_rhs_rows.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p,
+                                  ctypes.c_int]
         L.oq_step.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_long, ctypes.c_void_p]
         L.oq_trace.argtypes = [ctypes.c_void_p, ctypes.c_void_p, dp]
         L.oq_apply_dipole.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]
@@ -130,6 +132,15 @@ class Oracle:
         W = self._check(W)
         out = np.empty_like(W)
         lib().oq_rhs(self._h, _ptr(W), _ptr(out), int(terms))
+        return out
+
+    def rhs_rows(self, W, rows, terms=ALL):
+        """The right-hand side at selected rows only: rows = [(element, j, k, q index), ...] -> [n][np]."""
+        W = self._check(W)
+        R = np.ascontiguousarray(rows, dtype=np.int32).reshape(-1, 4)
+        out = np.empty((len(R), self.shape[-1]), dtype=np.complex128)
+        if lib().oq_rhs_rows(self._h, _ptr(W), _ptr(R), len(R), _ptr(out), int(terms)) != 0:
+            raise ValueError("row index out of range")
         return out
 
     def step(self, W, n_steps):

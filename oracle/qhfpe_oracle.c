@@ -367,73 +367,98 @@ static cplx dpp_central(const oq_ctx *C, const cplx *row, int l)
  * the network supplies a local correction to Eq. (GMFP).
  * State layout: [n_elem][S][S][nq][np] complex.
  * ---------------------------------------------------------------------------------------------- */
-void oq_rhs(const oq_ctx *C, const cplx *W, cplx *dW, int terms)
+/* One row of the right-hand side above: element e, pair (j, k), q index i, all p; out[np]. */
+static void rhs_row(const oq_ctx *C, const cplx *W, int e, int j, int k, int i, cplx *out, int terms)
 {
     const oq_params *P = &C->P;
     int S = P->S, nq = P->nq, np = P->np, M = C->n_modes;
+    size_t blk = (size_t)nq * np;
+    size_t elem = (size_t)S * S * blk;
+    const int *n = C->idx + (size_t)e * M;
+    int tier = 0;
+    double ngam = 0.0;
+    for (int a = 0; a < M; ++a) { tier += n[a]; ngam += n[a] * C->gam[a]; }
+    const cplx *Wjk = W + e * elem + ((size_t)j * S + k) * blk;
+    const cplx *row = Wjk + (size_t)i * np;
+    for (int l = 0; l < np; ++l) {
+        cplx acc = 0.0;
+        if (terms & OQ_KINETIC) acc += -C->pv[l] * dq_upwind(C, Wjk, i, l);
+        if (terms & OQ_POTENTIAL) {
+            cplx pot = 0.0;
+            for (int s = 0; s < S; ++s) {
+                const cplx *Wsk = W + e * elem + ((size_t)s * S + k) * blk + (size_t)i * np;
+                const cplx *Wjs = W + e * elem + ((size_t)j * S + s) * blk + (size_t)i * np;
+                const cplx *aL = C->AL + (((size_t)j * S + s) * nq + i) * np;
+                const cplx *aR = C->AR + (((size_t)s * S + k) * nq + i) * np;
+                for (int lp = 0; lp < np; ++lp) {
+                    int d = ((l - lp) % np + np) % np;
+                    pot += aL[d] * Wsk[lp] - aR[d] * Wjs[lp];
+                }
+            }
+            acc += -I * pot;
+        }
+        if (terms & OQ_DAMPING) {
+            acc += -ngam * row[l];
+            if (C->cdelta != 0.0) acc += C->cdelta * dpp_central(C, row, l);
+        }
+        if (terms & OQ_TIER_UP) {
+            for (int a = 0; a < M; ++a) {
+                int u = C->up[e * M + a];
+                if (u >= 0) {
+                    const cplx *urow = W + u * elem + ((size_t)j * S + k) * blk + (size_t)i * np;
+                    acc += dp_central(C, urow, l, 0);
+                } else if (P->closure == 1 && tier == P->depth) {
+                    acc += C->r[0] * dp_central(C, row, l, 1) + C->c[0] * dpp_central(C, row, l);
+                } else if (P->closure == 2 && tier == P->depth) {
+                    int dn = C->dn[e * M + a];
+                    const cplx *rowm1 = dn >= 0 ? W + dn * elem + ((size_t)j * S + k) * blk + (size_t)i * np : NULL;
+                    acc += C->r[0] * dp_central(C, row, l, 1) + C->c[0] * dpp_central(C, row, l);
+                    acc += dp_closure(C, row, rowm1, i, l);
+                }
+            }
+        }
+        if (terms & OQ_TIER_DOWN) {
+            for (int a = 0; a < M; ++a) {
+                int dn = C->dn[e * M + a];
+                if (dn < 0) continue;
+                const cplx *drow = W + dn * elem + ((size_t)j * S + k) * blk + (size_t)i * np;
+                double w = n[a] * C->gam[a];
+                acc += w * (C->r[a] * C->pv[l] * drow[l] + C->c[a] * dp_central(C, drow, l, 0));
+            }
+        }
+        out[l] = acc;
+    }
+}
+
+void oq_rhs(const oq_ctx *C, const cplx *W, cplx *dW, int terms)
+{
+    int S = C->P.S, nq = C->P.nq, np = C->P.np;
     size_t blk = (size_t)nq * np;
     size_t elem = (size_t)S * S * blk;
 #pragma omp parallel for collapse(4) schedule(static)
     for (int e = 0; e < C->n_elem; ++e)
         for (int j = 0; j < S; ++j)
             for (int k = 0; k < S; ++k)
-                for (int i = 0; i < nq; ++i) {
-                    const int *n = C->idx + (size_t)e * M;
-                    int tier = 0;
-                    double ngam = 0.0;
-                    for (int a = 0; a < M; ++a) { tier += n[a]; ngam += n[a] * C->gam[a]; }
-                    const cplx *Wjk = W + e * elem + ((size_t)j * S + k) * blk;
-                    const cplx *row = Wjk + (size_t)i * np;
-                    cplx *out = dW + e * elem + ((size_t)j * S + k) * blk + (size_t)i * np;
-                    for (int l = 0; l < np; ++l) {
-                        cplx acc = 0.0;
-                        if (terms & OQ_KINETIC) acc += -C->pv[l] * dq_upwind(C, Wjk, i, l);
-                        if (terms & OQ_POTENTIAL) {
-                            cplx pot = 0.0;
-                            for (int s = 0; s < S; ++s) {
-                                const cplx *Wsk = W + e * elem + ((size_t)s * S + k) * blk + (size_t)i * np;
-                                const cplx *Wjs = W + e * elem + ((size_t)j * S + s) * blk + (size_t)i * np;
-                                const cplx *aL = C->AL + (((size_t)j * S + s) * nq + i) * np;
-                                const cplx *aR = C->AR + (((size_t)s * S + k) * nq + i) * np;
-                                for (int lp = 0; lp < np; ++lp) {
-                                    int d = ((l - lp) % np + np) % np;
-                                    pot += aL[d] * Wsk[lp] - aR[d] * Wjs[lp];
-                                }
-                            }
-                            acc += -I * pot;
-                        }
-                        if (terms & OQ_DAMPING) {
-                            acc += -ngam * row[l];
-                            if (C->cdelta != 0.0) acc += C->cdelta * dpp_central(C, row, l);
-                        }
-                        if (terms & OQ_TIER_UP) {
-                            for (int a = 0; a < M; ++a) {
-                                int u = C->up[e * M + a];
-                                if (u >= 0) {
-                                    const cplx *urow = W + u * elem + ((size_t)j * S + k) * blk + (size_t)i * np;
-                                    acc += dp_central(C, urow, l, 0);
-                                } else if (P->closure == 1 && tier == P->depth) {
-                                    acc += C->r[0] * dp_central(C, row, l, 1) + C->c[0] * dpp_central(C, row, l);
-                                } else if (P->closure == 2 && tier == P->depth) {
-                                    int dn = C->dn[e * M + a];
-                                    const cplx *rowm1 = dn >= 0 ? W + dn * elem + ((size_t)j * S + k) * blk + (size_t)i * np : NULL;
-                                    acc += C->r[0] * dp_central(C, row, l, 1) + C->c[0] * dpp_central(C, row, l);
-                                    acc += dp_closure(C, row, rowm1, i, l);
-                                }
-                            }
-                        }
-                        if (terms & OQ_TIER_DOWN) {
-                            for (int a = 0; a < M; ++a) {
-                                int dn = C->dn[e * M + a];
-                                if (dn < 0) continue;
-                                const cplx *drow = W + dn * elem + ((size_t)j * S + k) * blk + (size_t)i * np;
-                                double w = n[a] * C->gam[a];
-                                acc += w * (C->r[a] * C->pv[l] * drow[l] + C->c[a] * dp_central(C, drow, l, 0));
-                            }
-                        }
-                        out[l] = acc;
-                    }
-                }
+                for (int i = 0; i < nq; ++i)
+                    rhs_row(C, W, e, j, k, i, dW + e * elem + ((size_t)j * S + k) * blk + (size_t)i * np, terms);
+}
+
+/* The same right-hand side at n_rows selected rows only (rows[4 r .. 4 r + 3] = e, j, k, i); out is
+ * [n_rows][np].  For checking a full-size state at sampled rows without the whole evaluation. */
+int oq_rhs_rows(const oq_ctx *C, const cplx *W, const int *rows, int n_rows, cplx *out, int terms)
+{
+    int S = C->P.S, nq = C->P.nq, np = C->P.np;
+    for (int r = 0; r < n_rows; ++r) {
+        const int *x = rows + 4 * r;
+        if (x[0] < 0 || x[0] >= C->n_elem || x[1] < 0 || x[1] >= S || x[2] < 0 || x[2] >= S || x[3] < 0 || x[3] >= nq)
+            return -1;
+    }
+#pragma omp parallel for schedule(dynamic)
+    for (int r = 0; r < n_rows; ++r) {
+        const int *x = rows + 4 * r;
+        rhs_row(C, W, x[0], x[1], x[2], x[3], out + (size_t)r * np, terms);
+    }
+    return 0;
 }
 
 /* ------------------------------------------------------------------------------------------------

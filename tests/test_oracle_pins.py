@@ -530,3 +530,20 @@ def test_morse_reading_reproduces_printed_resonances():
     nu1 = (U00(q1) - U11(q1)) * scale
     assert nu0 == pytest.approx(vals["nu0"], rel=1e-3)
     assert nu1 == pytest.approx(vals["nu1"], rel=1e-3)
+
+
+def test_rhs_rows_equal_the_full_rhs():
+    """The sampled-rows entry (used at full problem sizes) returns exactly the rows of the full RHS."""
+    for m in (qi.three_state(nq=12, n_p=16, depth=2, n_matsubara=1), qi.harmonic_two_state(nq=16, n_p=16, depth=3)):
+        O = oracle.Oracle(m)
+        W = qi.random_state(m, seed=77)
+        full = O.rhs(W)
+        S, nq = m["S"], m["nq"]
+        rng = np.random.default_rng(5)
+        rows = [(int(rng.integers(full.shape[0])), int(rng.integers(S)), int(rng.integers(S)), int(i))
+                for i in (0, 1, nq - 1, nq // 2, 3)]
+        got = O.rhs_rows(W, rows)
+        for r, (e, j, k, i) in enumerate(rows):
+            assert np.array_equal(got[r], full[e, j, k, i])
+    with pytest.raises(ValueError):
+        O.rhs_rows(W, [(0, 0, 0, nq)])
