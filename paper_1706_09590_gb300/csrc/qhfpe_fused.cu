@@ -3,7 +3,7 @@
 // and applies the Horner update of the RK4 step.
 //
 //   phase A  potential term, Eq. (quantum-liouvillian): the tile's p-rows are loaded into shared
-//            memory, transformed by a mixed-radix (8/4/2) in-place FFT (sign +, digit-reversed
+//            memory, transformed by a two-pass in-place FFT (radix NP/16, then 16; sign +, digit-reversed
 //            output), mixed per r-mode across the S x S blocks with the tables
 //            D = UL_jj - UR_kk, L = UL_js, R = UR_sk (pre-scaled by 1/np, stored in the same
 //            digit-reversed order), multiplied by -i, and transformed back (sign -, natural order).
@@ -67,19 +67,53 @@ template <int SG, typename C> __device__ __forceinline__ void dft8(C *x)
     x[3] = cadd(e3, w3o);
     x[7] = csub(e3, w3o);
 }
+// Length 16 as 4 x 4 (index n = 4 n1 + n2, frequency k = k1 + 4 k2): length-4 DFTs over n1, the
+// twiddles w16^(n2 k1), length-4 DFTs over n2.
+template <int SG, typename C> __device__ __forceinline__ void dft16(C *x)
+{
+    using R = decltype(x[0].x);
+    const R c1 = (R)0.92387953251128675613;  // cos(pi/8)
+    const R s1 = (R)0.38268343236508977173;  // sin(pi/8)
+    const R h = (R)0.70710678118654752440;   // cos(pi/4)
+#pragma unroll
+    for (int n2 = 0; n2 < 4; ++n2) dft4<SG>(x[n2], x[4 + n2], x[8 + n2], x[12 + n2]);  // y[n2][k1] at x[4 k1 + n2]
+    // w16^m = cos(2 pi m / 16) + SG i sin(2 pi m / 16) for m = n2 k1 in {1, 2, 3, 4, 6, 9}
+    auto rot = [](C a, R c, R s) { return C{a.x * c - a.y * s, a.x * s + a.y * c}; };
+    x[5] = rot(x[5], c1, SG * s1);    // n2 = 1, k1 = 1
+    x[9] = rot(x[9], h, SG * h);      // n2 = 1, k1 = 2
+    x[13] = rot(x[13], s1, SG * c1);  // n2 = 1, k1 = 3
+    x[6] = rot(x[6], h, SG * h);      // n2 = 2, k1 = 1
+    x[10] = cmul_si<SG>(x[10]);       // n2 = 2, k1 = 2
+    x[14] = rot(x[14], -h, SG * h);   // n2 = 2, k1 = 3
+    x[7] = rot(x[7], s1, SG * c1);    // n2 = 3, k1 = 1
+    x[11] = rot(x[11], -h, SG * h);   // n2 = 3, k1 = 2
+    x[15] = rot(x[15], -c1, -SG * s1); // n2 = 3, k1 = 3
+#pragma unroll
+    for (int k1 = 0; k1 < 4; ++k1) dft4<SG>(x[4 * k1], x[4 * k1 + 1], x[4 * k1 + 2], x[4 * k1 + 3]);  // -> X[k1 + 4 k2] at x[4 k1 + k2]
+    C t[16];
+#pragma unroll
+    for (int k1 = 0; k1 < 4; ++k1)
+#pragma unroll
+        for (int k2 = 0; k2 < 4; ++k2) t[k1 + 4 * k2] = x[4 * k1 + k2];
+#pragma unroll
+    for (int k = 0; k < 16; ++k) x[k] = t[k];
+}
 template <int R, int SG, typename C> __device__ __forceinline__ void dft_small(C *x)
 {
     if constexpr (R == 2) dft2<SG>(x[0], x[1]);
     else if constexpr (R == 4) dft4<SG>(x[0], x[1], x[2], x[3]);
-    else dft8<SG>(x);
+    else if constexpr (R == 8) dft8<SG>(x);
+    else dft16<SG>(x);
 }
 
-// Radix sequence (first pass = longest span) for each supported length.
+// Radix sequence (first pass = longest span): a first pass of span NP with stride 16 and a last pass
+// of radix 16.  With the padding below, the 16 threads of a half-warp then touch 16 distinct bank
+// pairs in both passes.
 template <int NP> struct Radices;
-template <> struct Radices<32> { static constexpr int n = 2; static constexpr int r[3] = {8, 4, 1}; };
-template <> struct Radices<64> { static constexpr int n = 2; static constexpr int r[3] = {8, 8, 1}; };
-template <> struct Radices<128> { static constexpr int n = 3; static constexpr int r[3] = {8, 4, 4}; };
-template <> struct Radices<256> { static constexpr int n = 3; static constexpr int r[3] = {8, 8, 4}; };
+template <> struct Radices<32> { static constexpr int n = 2; static constexpr int r[2] = {2, 16}; };
+template <> struct Radices<64> { static constexpr int n = 2; static constexpr int r[2] = {4, 16}; };
+template <> struct Radices<128> { static constexpr int n = 2; static constexpr int r[2] = {8, 16}; };
+template <> struct Radices<256> { static constexpr int n = 2; static constexpr int r[2] = {16, 16}; };
 
 // Shared-memory index with one padding slot per 16 complex values (breaks the power-of-two strides of
 // the FFT passes across banks).
@@ -123,16 +157,14 @@ template <int NP, bool FWD, typename C>
 __device__ __forceinline__ void fft_all(C *X, int n_tr, const C *tw)
 {
     using RD = Radices<NP>;
-    constexpr int R0 = RD::r[0], R1 = RD::r[1], R2 = RD::r[2];
-    constexpr int M0 = NP, M1 = NP / R0, M2 = NP / (R0 * R1);
+    constexpr int R0 = RD::r[0], R1 = RD::r[1];
+    static_assert(R0 * R1 == NP, "radices");
     if (FWD) {
-        fft_pass<NP, R0, M0, true>(X, n_tr, tw);
-        fft_pass<NP, R1, M1, true>(X, n_tr, tw);
-        if constexpr (RD::n == 3) fft_pass<NP, R2, M2, true>(X, n_tr, tw);
+        fft_pass<NP, R0, NP, true>(X, n_tr, tw);
+        fft_pass<NP, R1, R1, true>(X, n_tr, tw);
     } else {
-        if constexpr (RD::n == 3) fft_pass<NP, R2, M2, false>(X, n_tr, tw);
-        fft_pass<NP, R1, M1, false>(X, n_tr, tw);
-        fft_pass<NP, R0, M0, false>(X, n_tr, tw);
+        fft_pass<NP, R1, R1, false>(X, n_tr, tw);
+        fft_pass<NP, R0, NP, false>(X, n_tr, tw);
     }
 }
 
@@ -259,53 +291,117 @@ fused_stage_kernel(GridInfo g, const ElemInfo *__restrict__ elems, FusedTables<T
     }
 
     // ---- phase B: one warp per p-row ------------------------------------------------------------
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    // Neighbour tiers of this element as one list (tier-up entries first): element offset relative to
+    // this element, weight into G (1 up, n_k gamma_k c_k down) and weight of p W (n_k gamma_k r_k down).
+    __shared__ long long nb_off[2 * QH_MAX_MODES];
+    __shared__ T nb_wg[2 * QH_MAX_MODES], nb_wa[2 * QH_MAX_MODES];
     const ElemInfo &E = elems[e];
+    const int n_up = (terms & 8) ? E.n_up : 0;
+    const int n_nb = n_up + ((terms & 16) ? E.n_dn : 0);
+    if (threadIdx.x < n_nb) {
+        const int a = threadIdx.x;
+        const bool up = a < n_up;
+        const int el = up ? E.up[a] : E.dn[a - n_up];
+        nb_off[a] = (long long)(el - e) * (long long)g.elem_stride;
+        nb_wg[a] = up ? (T)1 : (T)E.wc[a - n_up];
+        nb_wa[a] = up ? (T)0 : (T)E.wr[a - n_up];
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const T inv12dp = (T)(1.0 / (12.0 * g.dp));
     const T fkin = (T)(1.0 / (60.0 * g.dq));
     const bool term = (terms & 8) && E.terminator;
     const T cpp = ((terms & 4) ? (T)g.cdelta : (T)0) + (term ? (T)g.term_c0 : (T)0);
+    const T ngam = (terms & 4) ? (T)E.ngam : (T)0;
     const int l0 = lane * VEC;
     T pcol[VEC];
 #pragma unroll
     for (int v = 0; v < VEC; ++v) pcol[v] = (T)(g.p_min + (l0 + v) * g.dp);
     const bool neg0 = pcol[0] < (T)0;
-    const bool uni_sign = neg0 == (pcol[VEC - 1] < (T)0);  // one upwind branch for the whole chunk
+    // the 5th-order upwind stencil of Sec. III uses rows -2..+3 for p < 0 and -3..+2 for p >= 0; when
+    // every lane's p values share one sign, each lane loads its six rows (offset by its sign)
+    const bool uni_warp = __all_sync(0xffffffffu, neg0 == (pcol[VEC - 1] < (T)0));
+    const int sh = neg0 ? 1 : 0;  // first row offset = sh - 3
 
     for (int rp = warp; rp < rows * S2; rp += FTHREADS / 32) {
         const int pr = rp % S2, r = rp / S2;
         const int i = i0 + r;
         const size_t poff = ebase + (size_t)pr * 2 * blk;
         const T *Vre = v_in + poff, *Vim = Vre + blk;
-        T ar[VEC], ai[VEC];
+        const size_t o = poff + (size_t)i * NP + l0;
+        T ar[VEC], ai[VEC], wr[VEC], wi[VEC];
 #pragma unroll
         for (int v = 0; v < VEC; ++v) ar[v] = ai[v] = (T)0;
 
-        // -p dW/dq, 5th-order upwind (Sec. III): coefficients for offsets -3..+3 by the sign of p
-        if (terms & 1) {
-            const T cneg[7] = {0, 3, -30, -20, 60, -15, 2};   // p < 0: offsets -3..+3
-            const T cpos[7] = {-2, 15, -60, 20, 30, -3, 0};   // p >= 0
+        if (uni_warp) {
+            // the six stencil rows in two batches of three (loads of a batch issued before use); the
+            // centre row is among them
+            const T cneg[6] = {3, -30, -20, 60, -15, 2};  // p < 0: offsets -2..+3
+            const T cpos[6] = {-2, 15, -60, 20, 30, -3};  // p >= 0: offsets -3..+2
+            const int tc = neg0 ? 2 : 3;                  // centre row
             T kr[VEC], ki[VEC];
 #pragma unroll
             for (int v = 0; v < VEC; ++v) kr[v] = ki[v] = (T)0;
 #pragma unroll
-            for (int d = -3; d <= 3; ++d) {
-                int ii = i + d;
-                if (ii < 0 || ii >= nq) {
-                    if (!g.periodic_q) continue;
-                    ii = ii < 0 ? ii + nq : ii - nq;
+            for (int t0 = 0; t0 < 6; t0 += 3) {
+                T sr[3][VEC], si[3][VEC];
+#pragma unroll
+                for (int b = 0; b < 3; ++b) {
+                    int ii = i + t0 + b - 3 + sh;
+                    bool ok = ii >= 0 && ii < nq;
+                    if (!ok && g.periodic_q) {
+                        ii = ii < 0 ? ii + nq : ii - nq;
+                        ok = true;
+                    }
+                    if (ok) {
+                        ldv<T, VEC>(Vre + (size_t)ii * NP + l0, sr[b]);
+                        ldv<T, VEC>(Vim + (size_t)ii * NP + l0, si[b]);
+                    } else {
+#pragma unroll
+                        for (int v = 0; v < VEC; ++v) sr[b][v] = si[b][v] = (T)0;
+                    }
                 }
-                T rr[VEC], ri[VEC];
-                ldv<T, VEC>(Vre + (size_t)ii * NP + l0, rr);
-                ldv<T, VEC>(Vim + (size_t)ii * NP + l0, ri);
-                if (uni_sign) {
-                    const T c = neg0 ? cneg[d + 3] : cpos[d + 3];
+#pragma unroll
+                for (int b = 0; b < 3; ++b) {
+                    const T c = neg0 ? cneg[t0 + b] : cpos[t0 + b];
 #pragma unroll
                     for (int v = 0; v < VEC; ++v) {
-                        kr[v] += c * rr[v];
-                        ki[v] += c * ri[v];
+                        kr[v] += c * sr[b][v];
+                        ki[v] += c * si[b][v];
                     }
-                } else {
+                    if (t0 + b == tc) {
+#pragma unroll
+                        for (int v = 0; v < VEC; ++v) {
+                            wr[v] = sr[b][v];
+                            wi[v] = si[b][v];
+                        }
+                    }
+                }
+            }
+            if (terms & 1) {
+#pragma unroll
+                for (int v = 0; v < VEC; ++v) {
+                    ar[v] -= pcol[v] * fkin * kr[v];
+                    ai[v] -= pcol[v] * fkin * ki[v];
+                }
+            }
+        } else {
+            if (terms & 1) {
+                const T cneg[7] = {0, 3, -30, -20, 60, -15, 2};
+                const T cpos[7] = {-2, 15, -60, 20, 30, -3, 0};
+                T kr[VEC], ki[VEC];
+#pragma unroll
+                for (int v = 0; v < VEC; ++v) kr[v] = ki[v] = (T)0;
+#pragma unroll
+                for (int d = -3; d <= 3; ++d) {
+                    int ii = i + d;
+                    if (ii < 0 || ii >= nq) {
+                        if (!g.periodic_q) continue;
+                        ii = ii < 0 ? ii + nq : ii - nq;
+                    }
+                    T rr[VEC], ri[VEC];
+                    ldv<T, VEC>(Vre + (size_t)ii * NP + l0, rr);
+                    ldv<T, VEC>(Vim + (size_t)ii * NP + l0, ri);
 #pragma unroll
                     for (int v = 0; v < VEC; ++v) {
                         const T c = pcol[v] < (T)0 ? cneg[d + 3] : cpos[d + 3];
@@ -313,68 +409,45 @@ fused_stage_kernel(GridInfo g, const ElemInfo *__restrict__ elems, FusedTables<T
                         ki[v] += c * ri[v];
                     }
                 }
-            }
 #pragma unroll
-            for (int v = 0; v < VEC; ++v) {
-                ar[v] -= pcol[v] * fkin * kr[v];
-                ai[v] -= pcol[v] * fkin * ki[v];
+                for (int v = 0; v < VEC; ++v) {
+                    ar[v] -= pcol[v] * fkin * kr[v];
+                    ai[v] -= pcol[v] * fkin * ki[v];
+                }
             }
+            ldv<T, VEC>(Vre + (size_t)i * NP + l0, wr);
+            ldv<T, VEC>(Vim + (size_t)i * NP + l0, wi);
         }
-        // own row (center) for damping / delta-term / terminator
-        T wr[VEC], wi[VEC];
-        ldv<T, VEC>(Vre + (size_t)i * NP + l0, wr);
-        ldv<T, VEC>(Vim + (size_t)i * NP + l0, wi);
-        if (terms & 4) {
 #pragma unroll
-            for (int v = 0; v < VEC; ++v) {
-                ar[v] -= (T)E.ngam * wr[v];
-                ai[v] -= (T)E.ngam * wi[v];
-            }
+        for (int v = 0; v < VEC; ++v) {
+            ar[v] -= ngam * wr[v];
+            ai[v] -= ngam * wi[v];
         }
         // G = sum_up W^(n+e_k) + sum_dn wc W^(n-e_k) [+ r_0 p W at the terminator]; d/dp of G below
         T gr[VEC], gi[VEC];
-        bool have_g = false;
 #pragma unroll
         for (int v = 0; v < VEC; ++v) gr[v] = gi[v] = (T)0;
-        const size_t rowoff = (size_t)rep * g.rep_stride + (size_t)pr * 2 * blk + (size_t)i * NP + l0;
-        if (terms & 8) {
-            for (int a = 0; a < E.n_up; ++a) {
-                const T *u = v_in + rowoff + (size_t)E.up[a] * g.elem_stride;
-                T xr[VEC], xi[VEC];
-                ldv<T, VEC>(u, xr);
-                ldv<T, VEC>(u + blk, xi);
+        for (int a = 0; a < n_nb; ++a) {
+            const T *u = v_in + (long long)o + nb_off[a];
+            T xr[VEC], xi[VEC];
+            ldv<T, VEC>(u, xr);
+            ldv<T, VEC>(u + blk, xi);
+            const T wg = nb_wg[a], wa = nb_wa[a];
 #pragma unroll
-                for (int v = 0; v < VEC; ++v) {
-                    gr[v] += xr[v];
-                    gi[v] += xi[v];
-                }
-                have_g = true;
-            }
-            if (term) {
-                const T r0 = (T)g.term_r0;
-#pragma unroll
-                for (int v = 0; v < VEC; ++v) {
-                    gr[v] += r0 * pcol[v] * wr[v];
-                    gi[v] += r0 * pcol[v] * wi[v];
-                }
-                have_g = true;
+            for (int v = 0; v < VEC; ++v) {
+                gr[v] += wg * xr[v];
+                gi[v] += wg * xi[v];
+                ar[v] += wa * pcol[v] * xr[v];
+                ai[v] += wa * pcol[v] * xi[v];
             }
         }
-        if (terms & 16) {
-            for (int a = 0; a < E.n_dn; ++a) {
-                const T *dd = v_in + rowoff + (size_t)E.dn[a] * g.elem_stride;
-                const T wc = (T)E.wc[a], wrr = (T)E.wr[a];
-                T xr[VEC], xi[VEC];
-                ldv<T, VEC>(dd, xr);
-                ldv<T, VEC>(dd + blk, xi);
+        const bool have_g = n_nb > 0 || term;
+        if (term) {
+            const T r0 = (T)g.term_r0;
 #pragma unroll
-                for (int v = 0; v < VEC; ++v) {
-                    gr[v] += wc * xr[v];
-                    gi[v] += wc * xi[v];
-                    ar[v] += wrr * pcol[v] * xr[v];
-                    ai[v] += wrr * pcol[v] * xi[v];
-                }
-                have_g = true;
+            for (int v = 0; v < VEC; ++v) {
+                gr[v] += r0 * pcol[v] * wr[v];
+                gi[v] += r0 * pcol[v] * wi[v];
             }
         }
         // neighbours along p (periodic) through the warp: ext[k] = value at l0 - 2 + k
@@ -405,7 +478,7 @@ fused_stage_kernel(GridInfo g, const ElemInfo *__restrict__ elems, FusedTables<T
                 ei[4] = __shfl_sync(0xffffffffu, xi[0], (lane + 2) & 31);
             }
         };
-        if (have_g) {  // uniform across the warp (same element)
+        if (have_g) {  // uniform across the block (same element)
             T er[VEC + 4], ei[VEC + 4];
             stencil(gr, gi, er, ei);
 #pragma unroll
@@ -443,7 +516,6 @@ fused_stage_kernel(GridInfo g, const ElemInfo *__restrict__ elems, FusedTables<T
             }
         }
         // ---- update -------------------------------------------------------------------------------
-        const size_t o = poff + (size_t)i * NP + l0;
         if (mode == 0) {
             stv<T, VEC>(v_out + o, ar);
             stv<T, VEC>(v_out + o + blk, ai);
@@ -580,14 +652,15 @@ cudaError_t prepare_fused(int np, int S)
 // a-th mixed-radix digit (weight R_0 ... R_{a-1}).
 int fused_fft_frequency(int np, int pos)
 {
-    int radix[3], n = 0;
+    int radix[2], n = 2;
     switch (np) {
-    case 32: radix[0] = 8; radix[1] = 4; n = 2; break;
-    case 64: radix[0] = 8; radix[1] = 8; n = 2; break;
-    case 128: radix[0] = 8; radix[1] = 4; radix[2] = 4; n = 3; break;
-    case 256: radix[0] = 8; radix[1] = 8; radix[2] = 4; n = 3; break;
+    case 32: radix[0] = 2; break;
+    case 64: radix[0] = 4; break;
+    case 128: radix[0] = 8; break;
+    case 256: radix[0] = 16; break;
     default: return -1;
     }
+    radix[1] = 16;
     int k = 0, weight = 1, span = np;
     for (int a = 0; a < n; ++a) {
         const int stride = span / radix[a];
