@@ -7,6 +7,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <memory>
@@ -580,6 +581,15 @@ qhfpe_status autotune(qhfpe *h, Prop &P)
     cudaStream_t st = h->stream;
     const int esize = P.mixed ? 4 : 8;
     const int tmax = std::min(fused_max_rows(P.g.np, P.g.S, esize), P.g.nq);
+    // QHFPE_TILE_ROWS pins the tile (a power of two up to the limit) instead of timing the candidates,
+    // e.g. to profile the launch configuration that a timed run chose
+    if (const char *env = std::getenv("QHFPE_TILE_ROWS")) {
+        const int t = std::atoi(env);
+        if (t >= 1 && t <= tmax && (t & (t - 1)) == 0) {
+            P.tq = t;
+            return QHFPE_OK;
+        }
+    }
     cudaEvent_t a, b;
     QH_CK(h, cudaEventCreate(&a));
     QH_CK(h, cudaEventCreate(&b));

@@ -126,14 +126,18 @@ __device__ __forceinline__ void fft_pass(C *X, int n_tr, const C *__restrict__ t
 {
     constexpr int S = M / R;
     constexpr int PER = NP / R;
+    // padded stride between the R inputs of a butterfly: exact when S is a multiple of 16, or when
+    // S = 1 and every butterfly starts on a multiple of 16 (M a multiple of 16, R <= 16)
+    static_assert(S % 16 == 0 || (S == 1 && M % 16 == 0 && R <= 16), "padding");
+    constexpr int PS = S + S / 16;
     const int total = n_tr * PER;
     for (int b = threadIdx.x; b < total; b += FTHREADS) {
         const int tr = b / PER, jl = b - tr * PER;
         const int g = jl / S, j = jl - g * S;
-        const int base = tr * NP + g * M + j;
+        const int p0 = pad16(tr * NP + g * M + j);
         C x[R];
 #pragma unroll
-        for (int t = 0; t < R; ++t) x[t] = X[pad16(base + t * S)];
+        for (int t = 0; t < R; ++t) x[t] = X[p0 + t * PS];
         if (FWD) {
             dft_small<R, +1>(x);
             if constexpr (S > 1) {  // the last pass (sub-length R) has only unit twiddles
@@ -148,7 +152,7 @@ __device__ __forceinline__ void fft_pass(C *X, int n_tr, const C *__restrict__ t
             dft_small<R, -1>(x);
         }
 #pragma unroll
-        for (int t = 0; t < R; ++t) X[pad16(base + t * S)] = x[t];
+        for (int t = 0; t < R; ++t) X[p0 + t * PS] = x[t];
     }
     __syncthreads();
 }
@@ -168,18 +172,28 @@ __device__ __forceinline__ void fft_all(C *X, int n_tr, const C *tw)
     }
 }
 
-// VEC consecutive reals (16-byte vector accesses where the size allows; rows are 16-byte aligned)
+// VEC consecutive reals through 16-byte vector accesses where the size allows (rows are 16-byte
+// aligned); the vector is unpacked member by member so that the destination stays in registers.
+template <typename T> struct Vec16;
+template <> struct Vec16<float> { using type = float4; };
+template <> struct Vec16<double> { using type = double2; };
+
+__device__ __forceinline__ void unpack(const float4 &q, float *o) { o[0] = q.x; o[1] = q.y; o[2] = q.z; o[3] = q.w; }
+__device__ __forceinline__ void unpack(const double2 &q, double *o) { o[0] = q.x; o[1] = q.y; }
+__device__ __forceinline__ float4 pack(const float *i) { return make_float4(i[0], i[1], i[2], i[3]); }
+__device__ __forceinline__ double2 pack(const double *i) { return make_double2(i[0], i[1]); }
+
 template <typename T, int VEC>
 __device__ __forceinline__ void ldv(const T *__restrict__ p, T *out)
 {
-    if constexpr (sizeof(T) * VEC % 16 == 0) {
+    constexpr int N = 16 / (int)sizeof(T);
+    if constexpr (VEC % N == 0) {
 #pragma unroll
-        for (int c = 0; c < (int)(sizeof(T) * VEC / 16); ++c) {
-            const float4 q = reinterpret_cast<const float4 *>(p)[c];
-            reinterpret_cast<float4 *>(out)[c] = q;
-        }
-    } else if constexpr (sizeof(T) * VEC == 8) {
-        *reinterpret_cast<float2 *>(out) = *reinterpret_cast<const float2 *>(p);
+        for (int c = 0; c < VEC / N; ++c) unpack(reinterpret_cast<const typename Vec16<T>::type *>(p)[c], out + c * N);
+    } else if constexpr (sizeof(T) == 4 && VEC == 2) {
+        const float2 q = *reinterpret_cast<const float2 *>(p);
+        out[0] = q.x;
+        out[1] = q.y;
     } else {
 #pragma unroll
         for (int v = 0; v < VEC; ++v) out[v] = p[v];
@@ -189,12 +203,12 @@ __device__ __forceinline__ void ldv(const T *__restrict__ p, T *out)
 template <typename T, int VEC>
 __device__ __forceinline__ void stv(T *p, const T *in)
 {
-    if constexpr (sizeof(T) * VEC % 16 == 0) {
+    constexpr int N = 16 / (int)sizeof(T);
+    if constexpr (VEC % N == 0) {
 #pragma unroll
-        for (int c = 0; c < (int)(sizeof(T) * VEC / 16); ++c)
-            reinterpret_cast<float4 *>(p)[c] = reinterpret_cast<const float4 *>(in)[c];
-    } else if constexpr (sizeof(T) * VEC == 8) {
-        *reinterpret_cast<float2 *>(p) = *reinterpret_cast<const float2 *>(in);
+        for (int c = 0; c < VEC / N; ++c) reinterpret_cast<typename Vec16<T>::type *>(p)[c] = pack(in + c * N);
+    } else if constexpr (sizeof(T) == 4 && VEC == 2) {
+        *reinterpret_cast<float2 *>(p) = make_float2(in[0], in[1]);
     } else {
 #pragma unroll
         for (int v = 0; v < VEC; ++v) p[v] = in[v];
