@@ -333,16 +333,26 @@ trace_partial_kernel(GridInfo g, const T *__restrict__ state, size_t rep_stride,
 __global__ void trace_finish_kernel(GridInfo g, const double *__restrict__ partial, int n_chunks, TraceSink *sink,
                                     int advance)
 {
+    // one warp per replica: lanes sum strided chunk partials, then a fixed butterfly over the lanes
+    // (the same order on every call, so the result is reproducible bit for bit)
     const long slot = sink->counter;
-    for (int rep = threadIdx.x; rep < g.n_rep; rep += blockDim.x) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, n_warps = blockDim.x >> 5;
+    for (int rep = warp; rep < g.n_rep; rep += n_warps) {
         double sr = 0.0, si = 0.0;
-        for (int c = 0; c < n_chunks; ++c) {
+        for (int c = lane; c < n_chunks; c += 32) {
             sr += partial[2 * ((size_t)rep * n_chunks + c)];
             si += partial[2 * ((size_t)rep * n_chunks + c) + 1];
         }
-        double *out = sink->base + 2 * ((size_t)rep * sink->stride + slot);
-        out[0] = sr * g.dq * g.dp;
-        out[1] = si * g.dq * g.dp;
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            sr += __shfl_xor_sync(0xffffffffu, sr, off);
+            si += __shfl_xor_sync(0xffffffffu, si, off);
+        }
+        if (lane == 0) {
+            double *out = sink->base + 2 * ((size_t)rep * sink->stride + slot);
+            out[0] = sr * g.dq * g.dp;
+            out[1] = si * g.dq * g.dp;
+        }
     }
     __syncthreads();
     if (advance && threadIdx.x == 0) sink->counter = slot + 1;
