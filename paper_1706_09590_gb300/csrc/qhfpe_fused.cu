@@ -31,6 +31,85 @@ template <typename C> __device__ __forceinline__ C cconjmul(C a, C w) { return {
 // multiply by s*i, s = +1 or -1
 template <int SG, typename C> __device__ __forceinline__ C cmul_si(C a) { return SG > 0 ? C{-a.y, a.x} : C{a.y, -a.x}; }
 
+// a + SG i b and a - SG i b
+template <int SG, typename C> __device__ __forceinline__ C cadd_si(C a, C b) { return {a.x - SG * b.y, a.y + SG * b.x}; }
+template <int SG, typename C> __device__ __forceinline__ C csub_si(C a, C b) { return {a.x + SG * b.y, a.y - SG * b.x}; }
+
+// ---- packed FP32x2 arithmetic (sm_100 and later) ---------------------------------------------------
+// An FP32 complex value occupies a register pair, so one packed instruction adds or subtracts both of
+// its parts; the lanes' runs of consecutive p values pair up the same way.  Each component is rounded
+// exactly as the scalar instruction would round it.  The FP64 form keeps scalar arithmetic.
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b)
+{
+    float2 r;
+    asm("{\n\t.reg .b64 pa, pb, pd;\n\tmov.b64 pa, {%2, %3};\n\tmov.b64 pb, {%4, %5};\n\t"
+        "sub.rn.f32x2 pd, pa, pb;\n\tmov.b64 {%0, %1}, pd;\n\t}"
+        : "=f"(r.x), "=f"(r.y)
+        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return r;
+}
+
+// y += a x (a broadcast), y += u x (elementwise), y += x over N values
+template <int N> __device__ __forceinline__ void v_axpy(float *y, float a, const float *x)
+{
+    if constexpr (N % 2 == 0) {
+        const float2 a2 = make_float2(a, a);
+#pragma unroll
+        for (int v = 0; v < N; v += 2) {
+            const float2 r = __ffma2_rn(a2, make_float2(x[v], x[v + 1]), make_float2(y[v], y[v + 1]));
+            y[v] = r.x;
+            y[v + 1] = r.y;
+        }
+    } else {
+#pragma unroll
+        for (int v = 0; v < N; ++v) y[v] = fmaf(a, x[v], y[v]);
+    }
+}
+template <int N> __device__ __forceinline__ void v_axpy(double *y, double a, const double *x)
+{
+#pragma unroll
+    for (int v = 0; v < N; ++v) y[v] = fma(a, x[v], y[v]);
+}
+template <int N> __device__ __forceinline__ void v_fma(float *y, const float *u, const float *x)
+{
+    if constexpr (N % 2 == 0) {
+#pragma unroll
+        for (int v = 0; v < N; v += 2) {
+            const float2 r = __ffma2_rn(make_float2(u[v], u[v + 1]), make_float2(x[v], x[v + 1]), make_float2(y[v], y[v + 1]));
+            y[v] = r.x;
+            y[v + 1] = r.y;
+        }
+    } else {
+#pragma unroll
+        for (int v = 0; v < N; ++v) y[v] = fmaf(u[v], x[v], y[v]);
+    }
+}
+template <int N> __device__ __forceinline__ void v_fma(double *y, const double *u, const double *x)
+{
+#pragma unroll
+    for (int v = 0; v < N; ++v) y[v] = fma(u[v], x[v], y[v]);
+}
+template <int N> __device__ __forceinline__ void v_add(float *y, const float *x)
+{
+    if constexpr (N % 2 == 0) {
+#pragma unroll
+        for (int v = 0; v < N; v += 2) {
+            const float2 r = __fadd2_rn(make_float2(x[v], x[v + 1]), make_float2(y[v], y[v + 1]));
+            y[v] = r.x;
+            y[v + 1] = r.y;
+        }
+    } else {
+#pragma unroll
+        for (int v = 0; v < N; ++v) y[v] += x[v];
+    }
+}
+template <int N> __device__ __forceinline__ void v_add(double *y, const double *x)
+{
+#pragma unroll
+    for (int v = 0; v < N; ++v) y[v] += x[v];
+}
+
 // In-register DFTs of length 2, 4, 8 with sign SG (y_u = sum_t x_t e^{SG 2 pi i t u / R}), natural order.
 template <int SG, typename C> __device__ __forceinline__ void dft2(C &a, C &b)
 {
@@ -40,11 +119,11 @@ template <int SG, typename C> __device__ __forceinline__ void dft2(C &a, C &b)
 }
 template <int SG, typename C> __device__ __forceinline__ void dft4(C &x0, C &x1, C &x2, C &x3)
 {
-    C t0 = cadd(x0, x2), t1 = csub(x0, x2), t2 = cadd(x1, x3), t3 = cmul_si<SG>(csub(x1, x3));
+    const C t0 = cadd(x0, x2), t1 = csub(x0, x2), t2 = cadd(x1, x3), d = csub(x1, x3);
     x0 = cadd(t0, t2);
     x2 = csub(t0, t2);
-    x1 = cadd(t1, t3);
-    x3 = csub(t1, t3);
+    x1 = cadd_si<SG>(t1, d);
+    x3 = csub_si<SG>(t1, d);
 }
 template <int SG, typename C> __device__ __forceinline__ void dft8(C *x)
 {
@@ -56,14 +135,13 @@ template <int SG, typename C> __device__ __forceinline__ void dft8(C *x)
     const R h = (R)0.70710678118654752440;
     // w8^u, w8 = e^{SG 2 pi i / 8}
     C w1o = {(o1.x - SG * o1.y) * h, (o1.y + SG * o1.x) * h};    // o1 * (1 + SG i)/sqrt2
-    C w2o = cmul_si<SG>(o2);                                       // o2 * SG i
     C w3o = {(-o3.x - SG * o3.y) * h, (-o3.y + SG * o3.x) * h};  // o3 * (-1 + SG i)/sqrt2
     x[0] = cadd(e0, o0);
     x[4] = csub(e0, o0);
     x[1] = cadd(e1, w1o);
     x[5] = csub(e1, w1o);
-    x[2] = cadd(e2, w2o);
-    x[6] = csub(e2, w2o);
+    x[2] = cadd_si<SG>(e2, o2);  // e2 +- o2 * SG i
+    x[6] = csub_si<SG>(e2, o2);
     x[3] = cadd(e3, w3o);
     x[7] = csub(e3, w3o);
 }
@@ -125,34 +203,42 @@ template <int NP, int R, int M, bool FWD, typename C>
 __device__ __forceinline__ void fft_pass(C *X, int n_tr, const C *__restrict__ tw)
 {
     constexpr int S = M / R;
-    constexpr int PER = NP / R;
+    constexpr int PER = NP / R;  // butterflies per transform
     // padded stride between the R inputs of a butterfly: exact when S is a multiple of 16, or when
     // S = 1 and every butterfly starts on a multiple of 16 (M a multiple of 16, R <= 16)
     static_assert(S % 16 == 0 || (S == 1 && M % 16 == 0 && R <= 16), "padding");
+    // a thread keeps the same butterfly position (and twiddles) in every transform it visits
+    static_assert(FTHREADS % PER == 0, "butterfly positions");
     constexpr int PS = S + S / 16;
-    const int total = n_tr * PER;
-    for (int b = threadIdx.x; b < total; b += FTHREADS) {
-        const int tr = b / PER, jl = b - tr * PER;
-        const int g = jl / S, j = jl - g * S;
-        const int p0 = pad16(tr * NP + g * M + j);
+    constexpr int PNP = NP + NP / 16;  // padded length of one transform
+    const int jl = threadIdx.x % PER;
+    const int grp = jl / S, j = jl - grp * S;
+    const int off = pad16(grp * M + j);
+    C w[R];
+    if constexpr (S > 1) {  // the last pass (sub-length R) has only unit twiddles
+#pragma unroll
+        for (int u = 1; u < R; ++u) w[u] = tw[(j * u) * (NP / M)];
+    }
+    for (int tr = threadIdx.x / PER; tr < n_tr; tr += FTHREADS / PER) {
+        C *xb = X + tr * PNP + off;
         C x[R];
 #pragma unroll
-        for (int t = 0; t < R; ++t) x[t] = X[p0 + t * PS];
+        for (int t = 0; t < R; ++t) x[t] = xb[t * PS];
         if (FWD) {
             dft_small<R, +1>(x);
-            if constexpr (S > 1) {  // the last pass (sub-length R) has only unit twiddles
+            if constexpr (S > 1) {
 #pragma unroll
-                for (int u = 1; u < R; ++u) x[u] = cmul(x[u], tw[(j * u) * (NP / M)]);
+                for (int u = 1; u < R; ++u) x[u] = cmul(x[u], w[u]);
             }
         } else {
             if constexpr (S > 1) {
 #pragma unroll
-                for (int u = 1; u < R; ++u) x[u] = cconjmul(x[u], tw[(j * u) * (NP / M)]);
+                for (int u = 1; u < R; ++u) x[u] = cconjmul(x[u], w[u]);
             }
             dft_small<R, -1>(x);
         }
 #pragma unroll
-        for (int t = 0; t < R; ++t) X[p0 + t * PS] = x[t];
+        for (int t = 0; t < R; ++t) xb[t * PS] = x[t];
     }
     __syncthreads();
 }
@@ -215,9 +301,14 @@ __device__ __forceinline__ void stv(T *p, const T *in)
     }
 }
 
+template <typename T>
+struct StageScalars {
+    T inv12dp, fkin, fdelta, fterm, r0, h;
+};
 template <typename T, int NP, int S, bool MIXED>
-__global__ void __launch_bounds__(FTHREADS, sizeof(T) == 4 ? 3 : 1)
-fused_stage_kernel(GridInfo g, const ElemInfo *__restrict__ elems, FusedTables<T> tab, const T *__restrict__ v_in,
+// FP32: three blocks per SM (80 registers); two for NP = 256, whose wider rows need more registers.
+__global__ void __launch_bounds__(FTHREADS, sizeof(T) == 4 ? (NP >= 256 ? 2 : 3) : 1)
+fused_stage_kernel(GridInfo g, const ElemInfo *__restrict__ elems, FusedTables<T> tab, StageScalars<T> sc, const T *__restrict__ v_in,
                    const T *y, const double *y0, T *v_out, double *y0_out, double h, int mode, int terms, int rep0,
                    int n_rep, int tq, const T *__restrict__ Pg)
 {
@@ -237,14 +328,49 @@ fused_stage_kernel(GridInfo g, const ElemInfo *__restrict__ elems, FusedTables<T
     const size_t blk = g.blk;
     const size_t ebase = (size_t)rep * g.rep_stride + (size_t)e * g.elem_stride;
 
-    for (int t = threadIdx.x; t < NP; t += FTHREADS) tw[t] = C{tab.tw[2 * t], tab.tw[2 * t + 1]};
+    __shared__ long long nb_off[2 * QH_MAX_MODES];
+    __shared__ T nb_wg[2 * QH_MAX_MODES], nb_wa[2 * QH_MAX_MODES];
+    __shared__ int s_cnt[4];
+    __shared__ T s_ngam;
+    __shared__ __align__(16) T pgrid[NP];
+    if (threadIdx.x == 0) {
+        const ElemInfo &E = elems[e];
+        int n = 0;
+        const int n_up = (terms & 8) ? E.n_up : 0;
+        for (int a = 0; a < n_up; ++a, ++n) {
+            nb_off[n] = (long long)(E.up[a] - e) * (long long)g.elem_stride;
+            nb_wg[n] = (T)1;
+            nb_wa[n] = (T)0;
+        }
+        const int n_dn = (terms & 16) ? E.n_dn : 0;
+        for (int pass = 0; pass < 2; ++pass) {
+            for (int a = 0; a < n_dn; ++a) {
+                if ((E.wr[a] != 0.0) != (pass == 1)) continue;
+                nb_off[n] = (long long)(E.dn[a] - e) * (long long)g.elem_stride;
+                nb_wg[n] = (T)E.wc[a];
+                nb_wa[n] = (T)E.wr[a];
+                ++n;
+            }
+            if (pass == 0) s_cnt[1] = n;
+        }
+        s_cnt[0] = n_up;
+        s_cnt[2] = n;
+        s_cnt[3] = (terms & 8) && E.terminator;
+        s_ngam = (terms & 4) ? (T)E.ngam : (T)0;
+    }
+    for (int t = threadIdx.x; t < NP; t += FTHREADS) {
+        tw[t] = C{tab.tw[2 * t], tab.tw[2 * t + 1]};
+        pgrid[t] = (T)(g.p_min + t * g.dp);
+    }
 
     // ---- phase A: potential term -------------------------------------------------------------
     const bool want_pot = (terms & 2) != 0;
     if (want_pot && !Pg) {
         constexpr int LV = 4;  // p values per load
-        for (int idx = threadIdx.x; idx < rows * S2 * (NP / LV); idx += FTHREADS) {
-            const int l = (idx % (NP / LV)) * LV, rp = idx / (NP / LV);
+        constexpr int PL = NP / LV;
+        static_assert(FTHREADS % PL == 0, "load positions");
+        const int l = (threadIdx.x % PL) * LV;
+        for (int rp = threadIdx.x / PL; rp < rows * S2; rp += FTHREADS / PL) {
             const int pr = rp % S2, r = rp / S2;
             const T *src = v_in + ebase + (size_t)pr * 2 * blk + (size_t)(i0 + r) * NP + l;
             T re[LV], im[LV];
@@ -257,8 +383,9 @@ fused_stage_kernel(GridInfo g, const ElemInfo *__restrict__ elems, FusedTables<T
         __syncthreads();
         fft_all<NP, true>(X, rows * S2, tw);
         constexpr int MV = S >= 3 ? 1 : (S == 2 ? 2 : 4);  // modes per thread (vector table loads)
-        for (int idx = threadIdx.x; idx < rows * (NP / MV); idx += FTHREADS) {
-            const int pos0 = (idx % (NP / MV)) * MV, r = idx / (NP / MV);
+        static_assert(FTHREADS % (NP / MV) == 0, "mixing positions");
+        const int pos0 = (threadIdx.x % (NP / MV)) * MV;
+        for (int r = threadIdx.x / (NP / MV); r < rows; r += FTHREADS / (NP / MV)) {
             const int i = i0 + r;
             C rho[S2][MV];
 #pragma unroll
@@ -305,37 +432,24 @@ fused_stage_kernel(GridInfo g, const ElemInfo *__restrict__ elems, FusedTables<T
     }
 
     // ---- phase B: one warp per p-row ------------------------------------------------------------
-    // Neighbour tiers of this element as one list (tier-up entries first): element offset relative to
-    // this element, weight into G (1 up, n_k gamma_k c_k down) and weight of p W (n_k gamma_k r_k down).
-    __shared__ long long nb_off[2 * QH_MAX_MODES];
-    __shared__ T nb_wg[2 * QH_MAX_MODES], nb_wa[2 * QH_MAX_MODES];
-    const ElemInfo &E = elems[e];
-    const int n_up = (terms & 8) ? E.n_up : 0;
-    const int n_nb = n_up + ((terms & 16) ? E.n_dn : 0);
-    if (threadIdx.x < n_nb) {
-        const int a = threadIdx.x;
-        const bool up = a < n_up;
-        const int el = up ? E.up[a] : E.dn[a - n_up];
-        nb_off[a] = (long long)(el - e) * (long long)g.elem_stride;
-        nb_wg[a] = up ? (T)1 : (T)E.wc[a - n_up];
-        nb_wa[a] = up ? (T)0 : (T)E.wr[a - n_up];
-    }
     __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const T inv12dp = (T)(1.0 / (12.0 * g.dp));
-    const T fkin = (T)(1.0 / (60.0 * g.dq));
-    const bool term = (terms & 8) && E.terminator;
-    const T cpp = ((terms & 4) ? (T)g.cdelta : (T)0) + (term ? (T)g.term_c0 : (T)0);
-    const T ngam = (terms & 4) ? (T)E.ngam : (T)0;
+    const int n_up = s_cnt[0], n_d0 = s_cnt[1], n_nb = s_cnt[2];
+    const bool term = s_cnt[3] != 0;
+    const T ngam = s_ngam;
+    const T inv12dp = sc.inv12dp;
+    const T fkin = sc.fkin;
+    const T fpp = ((terms & 4) ? sc.fdelta : (T)0) + (term ? sc.fterm : (T)0);
     const int l0 = lane * VEC;
     T pcol[VEC];
-#pragma unroll
-    for (int v = 0; v < VEC; ++v) pcol[v] = (T)(g.p_min + (l0 + v) * g.dp);
+    ldv<T, VEC>(pgrid + l0, pcol);
     const bool neg0 = pcol[0] < (T)0;
-    // the 5th-order upwind stencil of Sec. III uses rows -2..+3 for p < 0 and -3..+2 for p >= 0; when
-    // every lane's p values share one sign, each lane loads its six rows (offset by its sign)
     const bool uni_warp = __all_sync(0xffffffffu, neg0 == (pcol[VEC - 1] < (T)0));
-    const int sh = neg0 ? 1 : 0;  // first row offset = sh - 3
+    const int sh = neg0 ? 1 : 0;
+    const bool interior = i0 >= 3 && i0 + rows + 3 <= nq;  // no q-stencil row outside the grid
+    T pk[VEC];  // -p / (60 dq)
+#pragma unroll
+    for (int v = 0; v < VEC; ++v) pk[v] = -(pcol[v] * fkin);
 
     for (int rp = warp; rp < rows * S2; rp += FTHREADS / 32) {
         const int pr = rp % S2, r = rp / S2;
@@ -356,11 +470,19 @@ fused_stage_kernel(GridInfo g, const ElemInfo *__restrict__ elems, FusedTables<T
             T kr[VEC], ki[VEC];
 #pragma unroll
             for (int v = 0; v < VEC; ++v) kr[v] = ki[v] = (T)0;
+            // interior tiles: the six rows lie inside the grid, at fixed offsets from row i - 3 + sh
+            const T *rre = interior ? Vre + (size_t)(i - 3 + sh) * NP + l0 : Vre;
+            const T *rim = rre + blk;
 #pragma unroll
             for (int t0 = 0; t0 < 6; t0 += 3) {
                 T sr[3][VEC], si[3][VEC];
 #pragma unroll
                 for (int b = 0; b < 3; ++b) {
+                    if (interior) {
+                        ldv<T, VEC>(rre + (t0 + b) * NP, sr[b]);
+                        ldv<T, VEC>(rim + (t0 + b) * NP, si[b]);
+                        continue;
+                    }
                     int ii = i + t0 + b - 3 + sh;
                     bool ok = ii >= 0 && ii < nq;
                     if (!ok && g.periodic_q) {
@@ -378,11 +500,8 @@ fused_stage_kernel(GridInfo g, const ElemInfo *__restrict__ elems, FusedTables<T
 #pragma unroll
                 for (int b = 0; b < 3; ++b) {
                     const T c = neg0 ? cneg[t0 + b] : cpos[t0 + b];
-#pragma unroll
-                    for (int v = 0; v < VEC; ++v) {
-                        kr[v] += c * sr[b][v];
-                        ki[v] += c * si[b][v];
-                    }
+                    v_axpy<VEC>(kr, c, sr[b]);
+                    v_axpy<VEC>(ki, c, si[b]);
                     if (t0 + b == tc) {
 #pragma unroll
                         for (int v = 0; v < VEC; ++v) {
@@ -393,11 +512,8 @@ fused_stage_kernel(GridInfo g, const ElemInfo *__restrict__ elems, FusedTables<T
                 }
             }
             if (terms & 1) {
-#pragma unroll
-                for (int v = 0; v < VEC; ++v) {
-                    ar[v] -= pcol[v] * fkin * kr[v];
-                    ai[v] -= pcol[v] * fkin * ki[v];
-                }
+                v_fma<VEC>(ar, pk, kr);
+                v_fma<VEC>(ai, pk, ki);
             }
         } else {
             if (terms & 1) {
@@ -423,46 +539,57 @@ fused_stage_kernel(GridInfo g, const ElemInfo *__restrict__ elems, FusedTables<T
                         ki[v] += c * ri[v];
                     }
                 }
-#pragma unroll
-                for (int v = 0; v < VEC; ++v) {
-                    ar[v] -= pcol[v] * fkin * kr[v];
-                    ai[v] -= pcol[v] * fkin * ki[v];
-                }
+                v_fma<VEC>(ar, pk, kr);
+                v_fma<VEC>(ai, pk, ki);
             }
             ldv<T, VEC>(Vre + (size_t)i * NP + l0, wr);
             ldv<T, VEC>(Vim + (size_t)i * NP + l0, wi);
         }
-#pragma unroll
-        for (int v = 0; v < VEC; ++v) {
-            ar[v] -= ngam * wr[v];
-            ai[v] -= ngam * wi[v];
-        }
+        v_axpy<VEC>(ar, -ngam, wr);
+        v_axpy<VEC>(ai, -ngam, wi);
         // G = sum_up W^(n+e_k) + sum_dn wc W^(n-e_k) [+ r_0 p W at the terminator]; d/dp of G below
-        T gr[VEC], gi[VEC];
+        T gr[VEC], gi[VEC], hr[VEC], hi[VEC];
 #pragma unroll
-        for (int v = 0; v < VEC; ++v) gr[v] = gi[v] = (T)0;
-        for (int a = 0; a < n_nb; ++a) {
+        for (int v = 0; v < VEC; ++v) gr[v] = gi[v] = hr[v] = hi[v] = (T)0;
+        for (int a = 0; a < n_up; ++a) {
             const T *u = v_in + (long long)o + nb_off[a];
             T xr[VEC], xi[VEC];
             ldv<T, VEC>(u, xr);
             ldv<T, VEC>(u + blk, xi);
-            const T wg = nb_wg[a], wa = nb_wa[a];
-#pragma unroll
-            for (int v = 0; v < VEC; ++v) {
-                gr[v] += wg * xr[v];
-                gi[v] += wg * xi[v];
-                ar[v] += wa * pcol[v] * xr[v];
-                ai[v] += wa * pcol[v] * xi[v];
+            v_add<VEC>(gr, xr);
+            v_add<VEC>(gi, xi);
+        }
+        for (int a = n_up; a < n_d0; ++a) {
+            const T *u = v_in + (long long)o + nb_off[a];
+            T xr[VEC], xi[VEC];
+            ldv<T, VEC>(u, xr);
+            ldv<T, VEC>(u + blk, xi);
+            const T wg = nb_wg[a];
+            v_axpy<VEC>(gr, wg, xr);
+            v_axpy<VEC>(gi, wg, xi);
+        }
+        if (n_d0 < n_nb) {
+            for (int a = n_d0; a < n_nb; ++a) {
+                const T *u = v_in + (long long)o + nb_off[a];
+                T xr[VEC], xi[VEC];
+                ldv<T, VEC>(u, xr);
+                ldv<T, VEC>(u + blk, xi);
+                const T wg = nb_wg[a], wa = nb_wa[a];
+                v_axpy<VEC>(gr, wg, xr);
+                v_axpy<VEC>(gi, wg, xi);
+                v_axpy<VEC>(hr, wa, xr);
+                v_axpy<VEC>(hi, wa, xi);
             }
+            v_fma<VEC>(ar, pcol, hr);
+            v_fma<VEC>(ai, pcol, hi);
         }
         const bool have_g = n_nb > 0 || term;
         if (term) {
-            const T r0 = (T)g.term_r0;
+            T r0p[VEC];
 #pragma unroll
-            for (int v = 0; v < VEC; ++v) {
-                gr[v] += r0 * pcol[v] * wr[v];
-                gi[v] += r0 * pcol[v] * wi[v];
-            }
+            for (int v = 0; v < VEC; ++v) r0p[v] = sc.r0 * pcol[v];
+            v_fma<VEC>(gr, r0p, wr);
+            v_fma<VEC>(gi, r0p, wi);
         }
         // neighbours along p (periodic) through the warp: ext[k] = value at l0 - 2 + k
         auto stencil = [&](const T *xr, const T *xi, T *er, T *ei) {
@@ -501,10 +628,10 @@ fused_stage_kernel(GridInfo g, const ElemInfo *__restrict__ elems, FusedTables<T
                 ai[v] += inv12dp * (ei[v] - (T)8 * ei[v + 1] + (T)8 * ei[v + 3] - ei[v + 4]);
             }
         }
-        if (cpp != (T)0) {
+        if (fpp != (T)0) {
             T er[VEC + 4], ei[VEC + 4];
             stencil(wr, wi, er, ei);
-            const T f = cpp * inv12dp / (T)g.dp;
+            const T f = fpp;
 #pragma unroll
             for (int v = 0; v < VEC; ++v) {
                 ar[v] += f * (-er[v] + (T)16 * er[v + 1] - (T)30 * er[v + 2] + (T)16 * er[v + 3] - er[v + 4]);
@@ -547,15 +674,12 @@ fused_stage_kernel(GridInfo g, const ElemInfo *__restrict__ elems, FusedTables<T
                 }
             }
         } else {
-            const T hh = (T)h;
+            const T hh = sc.h;
             T br[VEC], bi[VEC];
             ldv<T, VEC>(y + o, br);
             ldv<T, VEC>(y + o + blk, bi);
-#pragma unroll
-            for (int v = 0; v < VEC; ++v) {
-                br[v] += hh * ar[v];
-                bi[v] += hh * ai[v];
-            }
+            v_axpy<VEC>(br, hh, ar);
+            v_axpy<VEC>(bi, hh, ai);
             stv<T, VEC>(v_out + o, br);
             stv<T, VEC>(v_out + o + blk, bi);
         }
@@ -575,8 +699,15 @@ cudaError_t launch_fused_t(const GridInfo &g, const ElemInfo *elems, const Fused
     const int tiles = (g.nq + tq - 1) / tq;
     const long blocks = (long)tiles * n_rep * g.n_elem;
     if (blocks <= 0) return cudaSuccess;
+    StageScalars<T> sc;
+    sc.inv12dp = (T)(1.0 / (12.0 * g.dp));
+    sc.fkin = (T)(1.0 / (60.0 * g.dq));
+    sc.fdelta = (T)(g.cdelta / (12.0 * g.dp * g.dp));
+    sc.fterm = (T)(g.term_c0 / (12.0 * g.dp * g.dp));
+    sc.r0 = (T)g.term_r0;
+    sc.h = (T)h;
     fused_stage_kernel<T, NP, S, MIXED><<<(unsigned)blocks, FTHREADS, smem, st>>>(
-        g, elems, tab, v_in, y, y0, v_out, y0_out, h, mode, terms, rep0, n_rep, tq, Pg);
+        g, elems, tab, sc, v_in, y, y0, v_out, y0_out, h, mode, terms, rep0, n_rep, tq, Pg);
     return cudaGetLastError();
 }
 

@@ -40,8 +40,11 @@ def _models():
     three = qi.three_state(nq=16, n_p=16, depth=2, n_matsubara=1)
     single = qi.single_state(lambda q: 0.5 * q * q, nq=20, n_p=8, depth=0, closure=1)
     big_np = qi.harmonic_two_state(nq=6, n_p=512, qr=(-8, 8), pr=(-40, 40), depth=1)
+    # p = 0 falls inside one lane's run of p values (l = 31 with two values per lane): the fused
+    # kernel's generic seven-row q-stencil path
+    asym_p = qi.photoisomerization_two_state(nq=20, n_p=64, pr=(-7.75, 8.25), depth=2, n_matsubara=1)
     return {"harmonic": h, "photoiso": ph, "ragged_periodic": ph_per, "three_state": three, "single": single,
-            "np512": big_np}
+            "np512": big_np, "asym_p": asym_p}
 
 
 MODELS = _models()
@@ -65,7 +68,7 @@ def test_rhs_terms_fp64(name):
             assert rel(got, ref) < 1e-12, (name, t, rel(got, ref))
 
 
-@pytest.mark.parametrize("name", ["harmonic", "photoiso", "three_state"])
+@pytest.mark.parametrize("name", ["harmonic", "photoiso", "three_state", "asym_p"])
 def test_rhs_mixed(name):
     m = MODELS[name]
     O = oracle.Oracle(m)
@@ -97,6 +100,30 @@ def test_steps_and_traces_fp64(name):
     tr2 = P.step(19, record_trace=True)[0]
     assert rel(P.get_state(0), ref_W2) < 1e-11
     assert rel(tr2, ref_tr2) < 1e-11
+
+
+TILE_MODELS = {
+    "photoiso_s2": qi.photoisomerization_two_state(nq=27, n_p=128, depth=2, n_matsubara=2),
+    "three_s3": qi.three_state(nq=21, n_p=32, depth=2, n_matsubara=1),
+    "single_s1": qi.single_state(lambda q: 0.5 * q * q + 0.05 * q ** 4, nq=37, n_p=64, depth=3, closure=1),
+    "asym_p": MODELS["asym_p"],
+}
+
+
+@pytest.mark.parametrize("tile", [1, 2, 4, 8, 16])
+@pytest.mark.parametrize("name", list(TILE_MODELS))
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("mixed", 2e-5)])
+def test_rhs_every_tile(name, tile, precision, tol, monkeypatch):
+    """The fused stage kernel at each tile height (q rows per block; ragged last tiles, one or several
+    runs of rows per warp) against the oracle's right-hand side."""
+    m = TILE_MODELS[name]
+    monkeypatch.setenv("QHFPE_TILE_ROWS", str(tile))
+    P = _P(m, precision)
+    P.set_state(qi.random_state(m, seed=31, hermitian=True))
+    P.step(1)
+    W = P.get_state(0)
+    ref = oracle.Oracle(m).rhs(W if precision == "fp64" else W.astype(np.complex64).astype(np.complex128), 31)
+    assert rel(P.apply_rhs(0, 31), ref) < tol, (name, tile, precision)
 
 
 def test_steps_mixed():
