@@ -16,9 +16,14 @@
 // Persistent CTAs (one per SM) of 256 threads loop over 128-row tiles; the cosine/sine operand tiles
 // stay in shared memory for the whole kernel.  Tensor memory holds the forward result D (2 np columns)
 // and the inverse accumulator P (2 np columns); the inverse runs slice by slice as the epilogue turns
-// each 64-mode slice of D into the bf16 operand Y.  Warps 4q..4q+3 share TMEM lane quadrant q and split
-// the columns.  Thread 0 issues the MMAs.  Waits on the MMA-completion barrier are bounded: on timeout
-// the kernel records an error, skips the rest of its work, and still frees its tensor memory.
+// each 64-mode slice of D into the bf16 operand Y.  The A operand is streamed in sub-slices (one re/im
+// plane of one 64-wide K slice: hi and lo tiles, 32 KB) through two buffers, so that the threads load,
+// split and store (or mix) the next sub-slice while the tensor core multiplies the current one; each
+// sub-slice's MMAs end with a commit to that buffer's barrier, which the threads wait for before they
+// refill the buffer.  Warps 4q..4q+3 share TMEM lane quadrant q and split the columns.  Thread 0
+// issues the MMAs.  Waits on the MMA-completion barriers are bounded: on timeout the kernel records an
+// error, skips the rest of its work, waits (bounded) for MMAs still in flight, and frees its tensor
+// memory.
 #include "qhfpe_internal.cuh"
 
 #include <cuda_bf16.h>
@@ -148,14 +153,15 @@ pot_tc_kernel(GridInfo g, const float *__restrict__ v, float *__restrict__ P, co
     constexpr int TILE = TILE_M * 64 * 2;  // bytes of one 128 x 64 bf16 tile (A side) = 16 KB
     constexpr int BT = NP * 64 * 2;        // bytes of one np x 64 bf16 tile (B side)
     constexpr int S2 = S * S;
-    // shared memory: B resident for the whole kernel ([slice][C_hi, C_lo, S_hi, S_lo] tiles), then one
-    // slice of the A operand (forward: W re/im hi/lo; inverse: Y re/im hi/lo), then barrier + TMEM address
+    // shared memory: B resident for the whole kernel ([slice][C_hi, C_lo, S_hi, S_lo] tiles); two A
+    // buffers, each one sub-slice (the hi and lo tiles of one re/im plane of one K slice); one
+    // MMA-completion barrier per A buffer; the TMEM address
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char *smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
     char *Bs = reinterpret_cast<char *>(smem);
     char *A = Bs + (size_t)KA * 4 * BT;
     uint64_t *mbar = reinterpret_cast<uint64_t *>(A + 4 * TILE);
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(mbar + 1);
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(mbar + 2);
 
     const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
     const int row_in_tile = t & (TILE_M - 1);   // A-load row of this thread
@@ -163,9 +169,10 @@ pot_tc_kernel(GridInfo g, const float *__restrict__ v, float *__restrict__ P, co
     const int quad = warp & 3;                  // TMEM lane quadrant of this warp
     const int grp = warp >> 2;                  // column group of this warp in the epilogues
     const int erow = quad * 32 + lane;          // epilogue row (TMEM lane) of this thread
-    const uint32_t mbar_a = smem_u32(mbar);
+    const uint32_t mbar0 = smem_u32(mbar), mbar1 = smem_u32(mbar + 1);
     if (t == 0) {
-        mbar_init(mbar_a, 1);
+        mbar_init(mbar0, 1);
+        mbar_init(mbar1, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 0) {
@@ -185,57 +192,64 @@ pot_tc_kernel(GridInfo g, const float *__restrict__ v, float *__restrict__ P, co
     const uint32_t tmem = *tmem_slot;
     const uint32_t d_re = tmem, d_im = tmem + NP, p_re = tmem + 2 * NP, p_im = tmem + 3 * NP;
     const uint32_t lane_off = (uint32_t)(quad * 32) << 16;
-    uint32_t phase = 0;
     bool ok = true;
-    const uint32_t a_tiles[4] = {smem_u32(A), smem_u32(A + TILE), smem_u32(A + 2 * TILE), smem_u32(A + 3 * TILE)};
 
-    // one K slice of one transform: 4 real products x 3 bf16 products x 4 k-steps
-    auto issue = [&](int slice, bool inverse, bool first) {
-        const uint32_t b0 = smem_u32(Bs + (size_t)slice * 4 * BT);
-        const uint32_t bC_hi = b0, bC_lo = b0 + BT, bS_hi = b0 + 2 * BT, bS_lo = b0 + 3 * BT;
-        const uint32_t ar_h = a_tiles[0], ar_l = a_tiles[1], ai_h = a_tiles[2], ai_l = a_tiles[3];
-        const uint32_t o_re = inverse ? p_re : d_re, o_im = inverse ? p_im : d_im;
-        struct Prod { uint32_t d, a_h, a_l, b_h, b_l; bool neg; };
-        Prod prods[4];
-        if (!inverse) {
-            prods[0] = {o_re, ar_h, ar_l, bC_hi, bC_lo, false};  // + W_re C
-            prods[1] = {o_re, ai_h, ai_l, bS_hi, bS_lo, true};   // - W_im S
-            prods[2] = {o_im, ar_h, ar_l, bS_hi, bS_lo, false};  // + W_re S
-            prods[3] = {o_im, ai_h, ai_l, bC_hi, bC_lo, false};  // + W_im C
-        } else {
-            prods[0] = {o_re, ar_h, ar_l, bC_hi, bC_lo, false};  // + Y_re C
-            prods[1] = {o_re, ai_h, ai_l, bS_hi, bS_lo, false};  // + Y_im S
-            prods[2] = {o_im, ai_h, ai_l, bC_hi, bC_lo, false};  // + Y_im C
-            prods[3] = {o_im, ar_h, ar_l, bS_hi, bS_lo, true};   // - Y_re S
+    // Buffer b may be overwritten once the MMAs of its last sub-slice have completed: every use ends
+    // with one commit to barrier b, and every reuse first waits for that phase (at most one pending).
+    // (per-buffer state in scalars, bit b of `pending` and of `phases`, so that nothing is indexed at
+    // run time and nothing lands in local memory)
+    uint32_t phases = 0u, pending = 0u;
+    auto free_buf = [&](int b) {
+        if (pending & (1u << b)) {
+            if (ok) ok = mbar_wait(b ? mbar1 : mbar0, (phases >> b) & 1u);
+            phases ^= 1u << b;
+            pending &= ~(1u << b);
         }
+    };
+
+    // One sub-slice: 2 real products x 3 bf16 products x 4 k-steps, then a commit to barrier b.
+    //   forward  re: D_re += W_re C,   D_im += W_re S        im: D_re -= W_im S,  D_im += W_im C
+    //   inverse  re: P_re += Y_re C,   P_im -= Y_re S        im: P_re += Y_im S,  P_im += Y_im C
+    auto issue_sub = [&](int slice, bool inverse, int plane, int b, bool first) {
+        const uint32_t b0 = smem_u32(Bs + (size_t)slice * 4 * BT);  // C_hi, C_lo, S_hi, S_lo at 0, 1, 2, 3 BT
+        const uint32_t a_h = smem_u32(A + (size_t)b * 2 * TILE), a_l = a_h + TILE;
+        // product 0 accumulates into the real part, product 1 into the imaginary part; the first uses
+        // C (forward re, inverse re) or S, the second the other matrix
+        const uint32_t acc0 = inverse ? p_re : d_re, acc1 = inverse ? p_im : d_im;
+        const uint32_t m0 = plane == 0 ? b0 : b0 + 2 * BT, m1 = plane == 0 ? b0 + 2 * BT : b0;
+        const bool neg0 = !inverse && plane == 1, neg1 = inverse && plane == 0;
+        const uint32_t id0 = idesc_bf16(TILE_M, NP, neg0), id1 = idesc_bf16(TILE_M, NP, neg1);
+#pragma unroll
         for (int ks = 0; ks < 4; ++ks) {  // 4 x K = 16 inside the 64-wide slice: +32 bytes
             const uint32_t ko = (uint32_t)ks * 32;
-            for (int q = 0; q < 4; ++q) {
-                const Prod &pp = prods[q];
-                const uint32_t id = idesc_bf16(TILE_M, NP, pp.neg);
-                const bool fresh = first && ks == 0 && (q == 0 || q == 2);
-                mma_bf16(pp.d, sdesc_sw128(pp.a_h + ko), sdesc_sw128(pp.b_h + ko), id, fresh ? 0u : 1u);
-                mma_bf16(pp.d, sdesc_sw128(pp.a_h + ko), sdesc_sw128(pp.b_l + ko), id, 1u);
-                mma_bf16(pp.d, sdesc_sw128(pp.a_l + ko), sdesc_sw128(pp.b_h + ko), id, 1u);
-            }
+            const uint32_t acc = (first && ks == 0) ? 0u : 1u;
+            mma_bf16(acc0, sdesc_sw128(a_h + ko), sdesc_sw128(m0 + ko), id0, acc);
+            mma_bf16(acc0, sdesc_sw128(a_h + ko), sdesc_sw128(m0 + BT + ko), id0, 1u);
+            mma_bf16(acc0, sdesc_sw128(a_l + ko), sdesc_sw128(m0 + ko), id0, 1u);
+            mma_bf16(acc1, sdesc_sw128(a_h + ko), sdesc_sw128(m1 + ko), id1, acc);
+            mma_bf16(acc1, sdesc_sw128(a_h + ko), sdesc_sw128(m1 + BT + ko), id1, 1u);
+            mma_bf16(acc1, sdesc_sw128(a_l + ko), sdesc_sw128(m1 + ko), id1, 1u);
         }
-        mma_commit(mbar_a);
+        mma_commit(b ? mbar1 : mbar0);
     };
-    auto run_and_wait = [&](int slice, bool inverse, bool first) {
+    int sub = 0;  // sub-slices issued so far; sub-slice n uses buffer n & 1
+    // hand the sub-slice just written to buffer (sub & 1) to the tensor core
+    auto submit = [&](int slice, bool inverse, int plane, bool first) {
+        const int b = sub & 1;
         fence_async_smem();
-        __syncthreads();
-        if (t == 0) {
+        fence_before();
+        ok = __syncthreads_and(ok);
+        if (ok && t == 0) {
             fence_after();
-            issue(slice, inverse, first);
+            issue_sub(slice, inverse, plane, b, first);
         }
-        ok = __syncthreads_and(mbar_wait(mbar_a, phase));
-        phase ^= 1;
-        fence_after();
+        if (ok) pending |= 1u << b;  // (ok is uniform here: nothing was issued otherwise)
+        ++sub;
     };
 
     const long n_tiles = (total_rows + TILE_M - 1) / TILE_M;
     for (long tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x) {
-        // ---- forward transform: W rows -> D ------------------------------------------------------
+        // ---- forward transform: W rows -> D, sub-slices (slice, plane) ----------------------------
         {
             const long row = tile * TILE_M + row_in_tile;
             size_t rb = 0;
@@ -250,27 +264,35 @@ pot_tc_kernel(GridInfo g, const float *__restrict__ v, float *__restrict__ P, co
                 const int rep = (int)(rest / g.n_elem);
                 rb = (size_t)rep * g.rep_stride + (size_t)e * g.elem_stride + (size_t)pr * 2 * g.blk + (size_t)i * NP;
             }
-            for (int s = 0; s < KA && ok; ++s) {
-                for (int cc = 0; cc < 4; ++cc) {
-                    const int c = half * 4 + cc;  // 16-byte chunk (8 elements) of the 64-wide slice
-                    float xr[8], xi[8];
-                    if (valid) {
-                        const float4 *pr4 = reinterpret_cast<const float4 *>(v + rb + s * 64 + c * 8);
-                        const float4 *pi4 = reinterpret_cast<const float4 *>(v + rb + g.blk + s * 64 + c * 8);
-                        const float4 a0 = pr4[0], a1 = pr4[1], b0 = pi4[0], b1 = pi4[1];
-                        xr[0] = a0.x; xr[1] = a0.y; xr[2] = a0.z; xr[3] = a0.w;
-                        xr[4] = a1.x; xr[5] = a1.y; xr[6] = a1.z; xr[7] = a1.w;
-                        xi[0] = b0.x; xi[1] = b0.y; xi[2] = b0.z; xi[3] = b0.w;
-                        xi[4] = b1.x; xi[5] = b1.y; xi[6] = b1.z; xi[7] = b1.w;
-                    } else {
+            // this thread's 32 values (one plane of its row, its half of the K slice)
+            auto load = [&](int j, float *x) {
+                if (valid) {
+                    const float4 *p4 = reinterpret_cast<const float4 *>(v + rb + (size_t)(j & 1) * g.blk +
+                                                                        (j >> 1) * 64 + half * 32);
 #pragma unroll
-                        for (int j = 0; j < 8; ++j) xr[j] = xi[j] = 0.f;
+                    for (int q = 0; q < 8; ++q) {
+                        const float4 a = p4[q];
+                        x[4 * q] = a.x;
+                        x[4 * q + 1] = a.y;
+                        x[4 * q + 2] = a.z;
+                        x[4 * q + 3] = a.w;
                     }
-                    const uint32_t off = sw128_chunk(row_in_tile, c);
-                    split_store8(xr, A, A + TILE, off);
-                    split_store8(xi, A + 2 * TILE, A + 3 * TILE, off);
+                } else {
+#pragma unroll
+                    for (int q = 0; q < 32; ++q) x[q] = 0.f;
                 }
-                run_and_wait(s, false, s == 0);
+            };
+            float x[32];
+            load(0, x);
+            for (int j = 0; j < 2 * KA; ++j) {
+                const int b = sub & 1;
+                free_buf(b);
+                char *hi = A + (size_t)b * 2 * TILE;
+#pragma unroll
+                for (int cc = 0; cc < 4; ++cc) split_store8(x + 8 * cc, hi, hi + TILE, sw128_chunk(row_in_tile, half * 4 + cc));
+                submit(j >> 1, false, j & 1, j == 0);
+                if (!ok) break;
+                if (j + 1 < 2 * KA) load(j + 1, x);  // in flight while the tensor core works
             }
         }
         // ---- r-space mixing per slice of modes, then that slice of the inverse transform ------------
@@ -285,6 +307,9 @@ pot_tc_kernel(GridInfo g, const float *__restrict__ v, float *__restrict__ P, co
                 i = (int)(rest % g.nq);
             }
             const int jj = pr / S, kk = pr % S;
+            free_buf((sub - 1) & 1);  // the last forward commit: every forward MMA has completed
+            ok = __syncthreads_and(ok);
+            fence_after();
             for (int s = 0; s < KA && ok; ++s) {
                 const int c0 = s * 64 + grp * 32;  // 32 modes of this warp
                 // this row's 32 table entries, as 16-byte vectors
@@ -310,7 +335,7 @@ pot_tc_kernel(GridInfo g, const float *__restrict__ v, float *__restrict__ P, co
                 float dr[32], di[32];
                 tmem_load32(d_re + lane_off + c0, dr);
                 tmem_load32(d_im + lane_off + c0, di);
-                float yr[32], yi[32];
+                float y2[2][32];  // Y re, im of this row's 32 modes
 #pragma unroll
                 for (int j = 0; j < 32; ++j) {
                     float ar, ai;
@@ -324,18 +349,24 @@ pot_tc_kernel(GridInfo g, const float *__restrict__ v, float *__restrict__ P, co
                         ar = td[j] * dr[j] + tl[j] * sr - tr[j] * br;
                         ai = td[j] * di[j] + tl[j] * si - tr[j] * bi;
                     }
-                    yr[j] = ai;  // times -i
-                    yi[j] = -ar;
+                    y2[0][j] = ai;  // times -i
+                    y2[1][j] = -ar;
                 }
 #pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    const uint32_t off = sw128_chunk(erow, grp * 4 + q);
-                    split_store8(yr + 8 * q, A, A + TILE, off);
-                    split_store8(yi + 8 * q, A + 2 * TILE, A + 3 * TILE, off);
+                for (int plane = 0; plane < 2; ++plane) {
+                    const int b = sub & 1;
+                    free_buf(b);
+                    char *hi = A + (size_t)b * 2 * TILE;
+#pragma unroll
+                    for (int q = 0; q < 4; ++q)
+                        split_store8(y2[plane] + 8 * q, hi, hi + TILE, sw128_chunk(erow, grp * 4 + q));
+                    submit(s, true, plane, s == 0 && plane == 0);
+                    if (!ok) break;
                 }
-                fence_before();
-                run_and_wait(s, true, s == 0);
             }
+            free_buf((sub - 1) & 1);  // the last inverse commit: P is complete
+            ok = __syncthreads_and(ok);
+            fence_after();
             // ---- P rows to global -------------------------------------------------------------------
             if (ok) {
                 size_t rb = 0;
@@ -368,6 +399,9 @@ pot_tc_kernel(GridInfo g, const float *__restrict__ v, float *__restrict__ P, co
         fence_after();
     }
     if (!ok && t == 0) atomicExch(err, 1);
+    // MMAs possibly still in flight after a give-up: wait for them (bounded) before freeing TMEM
+    if (pending & 1u) mbar_wait(mbar0, phases & 1u);
+    if (pending & 2u) mbar_wait(mbar1, (phases >> 1) & 1u);
     fence_before();
     __syncthreads();
     if (warp == 0) {
@@ -379,7 +413,7 @@ pot_tc_kernel(GridInfo g, const float *__restrict__ v, float *__restrict__ P, co
 template <int NP, int S>
 size_t tc_smem_bytes()
 {
-    return (size_t)(NP / 64) * 4 * NP * 64 * 2 + 4 * (size_t)TILE_M * 64 * 2 + 64 + 1024;
+    return (size_t)(NP / 64) * 4 * NP * 64 * 2 + 4 * (size_t)TILE_M * 64 * 2 + 64 + 1024;  // B, 2 A buffers, barriers
 }
 
 template <int NP, int S>
