@@ -314,7 +314,12 @@ fused_stage_kernel(GridInfo g, const ElemInfo *__restrict__ elems, FusedTables<T
 {
     using C = typename V2<T>::type;
     constexpr int S2 = S * S;
-    constexpr int VEC = NP / 32;
+    // phase B: a lane holds VEC consecutive p values of one row, a row spans LPR lanes, and a warp
+    // covers RPW rows (several for NP < 128, so that short rows still fill a warp with 16-byte loads)
+    constexpr int VEC = NP >= 128 ? NP / 32 : 4;
+    constexpr int LPR = NP / VEC;
+    constexpr int RPW = 32 / LPR;
+    static_assert(LPR * VEC == NP && RPW * LPR == 32, "lane layout");
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C *X = reinterpret_cast<C *>(smem_raw);          // [tq * S2][NP], padded (pad16)
     C *tw = X + pad16(tq * S2 * NP) + 1;             // [NP]
@@ -440,7 +445,8 @@ fused_stage_kernel(GridInfo g, const ElemInfo *__restrict__ elems, FusedTables<T
     const T inv12dp = sc.inv12dp;
     const T fkin = sc.fkin;
     const T fpp = ((terms & 4) ? sc.fdelta : (T)0) + (term ? sc.fterm : (T)0);
-    const int l0 = lane * VEC;
+    const int lr = lane / LPR;            // this lane's row among the warp's RPW rows
+    const int l0 = (lane % LPR) * VEC;    // its first p index
     T pcol[VEC];
     ldv<T, VEC>(pgrid + l0, pcol);
     const bool neg0 = pcol[0] < (T)0;
@@ -451,8 +457,21 @@ fused_stage_kernel(GridInfo g, const ElemInfo *__restrict__ elems, FusedTables<T
 #pragma unroll
     for (int v = 0; v < VEC; ++v) pk[v] = -(pcol[v] * fkin);
 
-    for (int rp = warp; rp < rows * S2; rp += FTHREADS / 32) {
-        const int pr = rp % S2, r = rp / S2;
+    // work unit: RPW consecutive rows of one pair; lanes past the tile's last row compute a copy of it
+    // (their shuffles are needed) and store nothing
+    const int n_units = RPW == 1 ? rows * S2 : ((rows + RPW - 1) / RPW) * S2;
+    for (int rp = warp; rp < n_units; rp += FTHREADS / 32) {
+        int pr, r;
+        bool act = true;
+        if constexpr (RPW == 1) {
+            pr = rp % S2;
+            r = rp / S2;
+        } else {
+            pr = rp % S2;
+            const int r_lane = (rp / S2) * RPW + lr;
+            act = r_lane < rows;
+            r = act ? r_lane : rows - 1;
+        }
         const int i = i0 + r;
         const size_t poff = ebase + (size_t)pr * 2 * blk;
         const T *Vre = v_in + poff, *Vim = Vre + blk;
@@ -598,26 +617,25 @@ fused_stage_kernel(GridInfo g, const ElemInfo *__restrict__ elems, FusedTables<T
                 er[v + 2] = xr[v];
                 ei[v + 2] = xi[v];
             }
-            if constexpr (VEC >= 2) {
-                const int left = (lane + 31) & 31, right = (lane + 1) & 31;
-                er[0] = __shfl_sync(0xffffffffu, xr[VEC - 2], left);
-                er[1] = __shfl_sync(0xffffffffu, xr[VEC - 1], left);
-                ei[0] = __shfl_sync(0xffffffffu, xi[VEC - 2], left);
-                ei[1] = __shfl_sync(0xffffffffu, xi[VEC - 1], left);
-                er[VEC + 2] = __shfl_sync(0xffffffffu, xr[0], right);
-                er[VEC + 3] = __shfl_sync(0xffffffffu, xr[1], right);
-                ei[VEC + 2] = __shfl_sync(0xffffffffu, xi[0], right);
-                ei[VEC + 3] = __shfl_sync(0xffffffffu, xi[1], right);
+            // lanes of one row form a shuffle segment of width LPR; source lanes are relative to it
+            static_assert(VEC >= 2, "two p values per lane");
+            int left, right;
+            if constexpr (LPR == 32) {
+                left = (lane + 31) & 31;
+                right = (lane + 1) & 31;
             } else {
-                er[0] = __shfl_sync(0xffffffffu, xr[0], (lane + 30) & 31);
-                er[1] = __shfl_sync(0xffffffffu, xr[0], (lane + 31) & 31);
-                er[3] = __shfl_sync(0xffffffffu, xr[0], (lane + 1) & 31);
-                er[4] = __shfl_sync(0xffffffffu, xr[0], (lane + 2) & 31);
-                ei[0] = __shfl_sync(0xffffffffu, xi[0], (lane + 30) & 31);
-                ei[1] = __shfl_sync(0xffffffffu, xi[0], (lane + 31) & 31);
-                ei[3] = __shfl_sync(0xffffffffu, xi[0], (lane + 1) & 31);
-                ei[4] = __shfl_sync(0xffffffffu, xi[0], (lane + 2) & 31);
+                const int li = lane % LPR;
+                left = (li + LPR - 1) & (LPR - 1);
+                right = (li + 1) & (LPR - 1);
             }
+            er[0] = __shfl_sync(0xffffffffu, xr[VEC - 2], left, LPR);
+            er[1] = __shfl_sync(0xffffffffu, xr[VEC - 1], left, LPR);
+            ei[0] = __shfl_sync(0xffffffffu, xi[VEC - 2], left, LPR);
+            ei[1] = __shfl_sync(0xffffffffu, xi[VEC - 1], left, LPR);
+            er[VEC + 2] = __shfl_sync(0xffffffffu, xr[0], right, LPR);
+            er[VEC + 3] = __shfl_sync(0xffffffffu, xr[1], right, LPR);
+            ei[VEC + 2] = __shfl_sync(0xffffffffu, xi[0], right, LPR);
+            ei[VEC + 3] = __shfl_sync(0xffffffffu, xi[1], right, LPR);
         };
         if (have_g) {  // uniform across the block (same element)
             T er[VEC + 4], ei[VEC + 4];
@@ -657,7 +675,8 @@ fused_stage_kernel(GridInfo g, const ElemInfo *__restrict__ elems, FusedTables<T
             }
         }
         // ---- update -------------------------------------------------------------------------------
-        if (mode == 0) {
+        if (!act) {
+        } else if (mode == 0) {
             stv<T, VEC>(v_out + o, ar);
             stv<T, VEC>(v_out + o + blk, ai);
         } else if (MIXED && e == 0) {

@@ -244,10 +244,11 @@ def test_bath_and_hierarchy_match_oracle():
         assert a["cdelta"] == pytest.approx(b["cdelta"], rel=1e-12, abs=1e-15)
 
 
-@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("mixed", 2e-5)])
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("mixed", 2e-5), ("bf16x3", 2e-4)])
 def test_full_size_rhs(precision, tol):
     """The benchmark's workload (96 x 128 grid, depth 8, three modes, 165 elements, two states): one
-    full right-hand side in the benchmark's launch configuration against the oracle."""
+    full right-hand side in the benchmark's launch configuration against the oracle (for the tensor-core
+    form: 495 row tiles, several per persistent CTA)."""
     m = qi.photoisomerization_two_state()
     O = oracle.Oracle(m)
     P = _P(m, precision)
