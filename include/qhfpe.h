@@ -150,6 +150,18 @@ qhfpe_status qhfpe_apply_rhs(qhfpe_t *h, int replica, int terms, double *out);
 /* Tr{mu W^(0)} of every replica now: host complex128 [n_replicas]. */
 qhfpe_status qhfpe_trace(qhfpe_t *h, double *out);
 
+/* Adiabatic-basis wavepacket marginals, Sec. III ("Wavepacket dynamics"): for replica `replica`,
+ *   out[a][b][i] = sum_jk V_ja(q_i) V_kb(q_i) dp sum_l W^(0)_jk(q_i, p_l),
+ * the coordinate marginal of the zeroth-tier Wigner distribution (the reduced density matrix on its
+ * diagonal q = q') in the adiabatic basis.  V(q_i) holds the eigenvectors of the real symmetric
+ * diabatic matrix U_jk(q_i) (the U_table column of zero offset, t = np/2), ordered by ascending
+ * eigenvalue (a = 0 is the lowest adiabatic surface); each is signed so that its first component of
+ * largest magnitude (within 1e-9) is positive.  Because the rotation is local in q it is exact for the
+ * coordinate marginal.  out: host complex128 [S][S][nq] (re, im interleaved).  FP64 sums in a fixed
+ * order on the device; the mixed forms use their FP64 zeroth tier.  Errors: QHFPE_EINVAL for a bad
+ * replica or NULL output. */
+qhfpe_status qhfpe_adiabatic_marginals(qhfpe_t *h, int replica, double *out);
+
 /* Equilibrium of Sec. III: the ground surface U_00 alone with the full hierarchy, started from the
  * classical Boltzmann distribution exp(-beta (p^2/2 + U_00(q))) normalised to unit trace, propagated
  * n_steps RK4 steps (FP64 always).  The result (ground block of every hierarchy element, all other

@@ -98,6 +98,60 @@ struct DevBuf {
     ~DevBuf() { if (p) cudaFree(p); }
 };
 
+
+// Eigenvectors of a real symmetric S x S matrix (S <= QH_MAX_S) by cyclic Jacobi rotations, ordered by
+// ascending eigenvalue; each vector is signed so that its first component of largest magnitude (within
+// 1e-9) is positive.  v[j * S + a] = component j of eigenvector a.
+void sym_eigvec(int S, const double *A, double *v)
+{
+    double a[QH_MAX_S][QH_MAX_S], e[QH_MAX_S][QH_MAX_S];
+    for (int r = 0; r < S; ++r)
+        for (int c = 0; c < S; ++c) {
+            a[r][c] = 0.5 * (A[r * S + c] + A[c * S + r]);
+            e[r][c] = r == c ? 1.0 : 0.0;
+        }
+    for (int sweep = 0; sweep < 64; ++sweep) {
+        double off = 0.0;
+        for (int p = 0; p < S; ++p)
+            for (int q = p + 1; q < S; ++q) off += a[p][q] * a[p][q];
+        if (off == 0.0) break;
+        for (int p = 0; p < S; ++p)
+            for (int q = p + 1; q < S; ++q) {
+                if (a[p][q] == 0.0) continue;
+                // rotation that zeroes a[p][q]: t = tan(phi) of the smaller root
+                const double th = (a[q][q] - a[p][p]) / (2.0 * a[p][q]);
+                const double t = (th >= 0.0 ? 1.0 : -1.0) / (std::fabs(th) + std::sqrt(th * th + 1.0));
+                const double c = 1.0 / std::sqrt(t * t + 1.0), sn = t * c;
+                for (int k = 0; k < S; ++k) {
+                    const double kp = a[k][p], kq = a[k][q];
+                    a[k][p] = c * kp - sn * kq;
+                    a[k][q] = sn * kp + c * kq;
+                }
+                for (int k = 0; k < S; ++k) {
+                    const double pk = a[p][k], qk = a[q][k];
+                    a[p][k] = c * pk - sn * qk;
+                    a[q][k] = sn * pk + c * qk;
+                }
+                for (int k = 0; k < S; ++k) {
+                    const double kp = e[k][p], kq = e[k][q];
+                    e[k][p] = c * kp - sn * kq;
+                    e[k][q] = sn * kp + c * kq;
+                }
+            }
+    }
+    int order[QH_MAX_S];
+    for (int k = 0; k < S; ++k) order[k] = k;
+    std::sort(order, order + S, [&](int x, int y) { return a[x][x] < a[y][y]; });
+    for (int col = 0; col < S; ++col) {
+        const int src = order[col];
+        double mx = 0.0;
+        for (int r = 0; r < S; ++r) mx = std::max(mx, std::fabs(e[r][src]));
+        int lead = 0;
+        while (std::fabs(e[lead][src]) < mx - 1e-9) ++lead;
+        const double sg = e[lead][src] < 0.0 ? -1.0 : 1.0;
+        for (int r = 0; r < S; ++r) v[r * S + col] = sg * e[r][src];
+    }
+}
 }  // namespace
 
 // A model: grid, bath and hierarchy data and the potential tables for one set of surfaces.
@@ -114,6 +168,8 @@ struct Model {
     float *tab32 = nullptr;    // same in FP32
     size_t tab_n = 0;          // entries of one of D, L, R
     double max_rate = 0.0;     // Gershgorin estimate of the generator's spectral radius
+    std::vector<double> adia_host;  // adiabatic eigenvectors of U(q_i): [nq][S][S], v[j][a]
+    double *adia = nullptr;
 
     PotTables<double> t64() const
     {
@@ -144,6 +200,7 @@ struct Model {
         if (ftab32) cudaFree(ftab32);
         if (tcN) cudaFree(tcN);
         if (tcB) cudaFree(tcB);
+        if (adia) cudaFree(adia);
     }
 };
 
@@ -396,6 +453,17 @@ qhfpe_status build_model(qhfpe *h, Model &M, int S, const double *U, const doubl
     QH_CK(h, cudaMemcpyAsync(M.elems, M.elems_host.data(), sizeof(ElemInfo) * M.n_elem, cudaMemcpyHostToDevice, st));
     QH_CK(h, dalloc(&M.mu, S * S));
     QH_CK(h, cudaMemcpyAsync(M.mu, M.mu_host.data(), sizeof(double) * S * S, cudaMemcpyHostToDevice, st));
+    // adiabatic basis at each grid point: eigenvectors of the diabatic matrix U_jk(q_i), the table
+    // column of zero offset
+    M.adia_host.assign((size_t)p.nq * S * S, 0.0);
+    for (int i = 0; i < p.nq; ++i) {
+        double A[QH_MAX_S * QH_MAX_S];
+        for (int j = 0; j < S; ++j)
+            for (int k = 0; k < S; ++k) A[j * S + k] = U[(((size_t)j * S + k) * p.nq + i) * (p.np + 1) + p.np / 2];
+        sym_eigvec(S, A, M.adia_host.data() + (size_t)i * S * S);
+    }
+    QH_CK(h, dalloc(&M.adia, M.adia_host.size()));
+    QH_CK(h, cudaMemcpyAsync(M.adia, M.adia_host.data(), sizeof(double) * M.adia_host.size(), cudaMemcpyHostToDevice, st));
     QH_CK(h, dalloc(&M.tab64, tab.size()));
     QH_CK(h, cudaMemcpyAsync(M.tab64, tab.data(), sizeof(double) * tab.size(), cudaMemcpyHostToDevice, st));
     std::vector<float> tab32(tab.begin(), tab.end());
@@ -1101,6 +1169,24 @@ qhfpe_status qhfpe_trace(qhfpe_t *h, double *out)
     if (P.mixed) QH_CK(h, launch_trace<double>(P.g, P.y0, P.g.tier0_rep_stride, P.m->mu, P.sink, 0, P.partial, h->stream));
     else QH_CK(h, launch_trace<double>(P.g, (const double *)P.y, P.g.rep_stride, P.m->mu, P.sink, 0, P.partial, h->stream));
     QH_CK(h, cudaMemcpyAsync(out, P.trace_buf, (size_t)P.g.n_rep * 2 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    QH_CK(h, cudaStreamSynchronize(h->stream));
+    return QHFPE_OK;
+}
+
+qhfpe_status qhfpe_adiabatic_marginals(qhfpe_t *h, int replica, double *out)
+{
+    qhfpe_status r = check_handle(h);
+    if (r != QHFPE_OK) return r;
+    Prop &P = *h->main;
+    if (!out || replica < 0 || replica >= P.g.n_rep)
+        return h->fail(QHFPE_EINVAL, "adiabatic_marginals: bad replica or NULL output");
+    const size_t n = 2 * (size_t)P.g.S * P.g.S * P.g.nq;
+    r = ensure_scratch(h, n * sizeof(double));
+    if (r != QHFPE_OK) return r;
+    const double *tier0 = P.mixed ? P.y0 + (size_t)replica * P.g.tier0_rep_stride
+                                  : (const double *)P.y + (size_t)replica * P.g.rep_stride;
+    QH_CK(h, launch_marginals(P.g, tier0, P.m->adia, (double *)h->scratch, h->stream));
+    QH_CK(h, cudaMemcpyAsync(out, h->scratch, n * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
     QH_CK(h, cudaStreamSynchronize(h->stream));
     return QHFPE_OK;
 }

@@ -137,6 +137,9 @@ template <typename T>
 cudaError_t launch_to_canonical(const GridInfo &g, const T *src, const double *y0_src, double *dst, int rep,
                                 cudaStream_t st);
 
+// Adiabatic-basis coordinate marginals of one replica's zeroth tier (FP64, layout [S][S][re|im][q][p]);
+// V: [nq][S][S] eigenvector components; out: [S][S][nq] complex.
+cudaError_t launch_marginals(const GridInfo &g, const double *tier0, const double *V, double *out, cudaStream_t st);
 cudaError_t launch_norm2(const double *x, size_t n, double *out_dev, cudaStream_t st);
 cudaError_t launch_wait_flag(const int *flag, unsigned long long limit_ns, int *status, cudaStream_t st);
 cudaError_t launch_absorption(const double *R1, long n_t, double dt, const double *omega, int n_omega,

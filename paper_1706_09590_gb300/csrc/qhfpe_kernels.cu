@@ -693,6 +693,56 @@ cudaError_t launch_spectrum2d(const double *R3, int n_t1, int n_t3, double dt1, 
     return cudaGetLastError();
 }
 
+// Adiabatic-basis coordinate marginals of the zeroth tier (Sec. III, "Wavepacket dynamics"): one block
+// per q row.  Warp w sums the p row of pairs jk = w, w + warps, ... in a fixed order (lanes over p,
+// then a butterfly), so the result is reproducible; then S*S threads rotate the S x S marginal with
+// the row's eigenvector matrix V[i][j][a].
+__global__ void marginal_kernel(GridInfo g, const double *__restrict__ state, const double *__restrict__ V,
+                                double *__restrict__ out)
+{
+    __shared__ double rho[2 * QH_MAX_S * QH_MAX_S];
+    const int i = blockIdx.x, S = g.S, np = g.np;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, n_warps = blockDim.x >> 5;
+    for (int jk = warp; jk < S * S; jk += n_warps) {
+        const double *re = state + (size_t)(2 * jk) * g.blk + (size_t)i * np;
+        const double *im = re + g.blk;
+        double sr = 0.0, si = 0.0;
+        for (int l = lane; l < np; l += 32) {
+            sr += re[l];
+            si += im[l];
+        }
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            sr += __shfl_xor_sync(0xffffffffu, sr, off);
+            si += __shfl_xor_sync(0xffffffffu, si, off);
+        }
+        if (lane == 0) {
+            rho[2 * jk] = sr * g.dp;
+            rho[2 * jk + 1] = si * g.dp;
+        }
+    }
+    __syncthreads();
+    if ((int)threadIdx.x < S * S) {
+        const int a = threadIdx.x / S, b = threadIdx.x % S;
+        const double *v = V + (size_t)i * S * S;  // v[j * S + a]: component j of adiabatic state a
+        double pr = 0.0, pi = 0.0;
+        for (int j = 0; j < S; ++j)
+            for (int k = 0; k < S; ++k) {
+                const double w = v[j * S + a] * v[k * S + b];
+                pr += w * rho[2 * (j * S + k)];
+                pi += w * rho[2 * (j * S + k) + 1];
+            }
+        out[2 * ((size_t)(a * S + b) * g.nq + i)] = pr;
+        out[2 * ((size_t)(a * S + b) * g.nq + i) + 1] = pi;
+    }
+}
+
+cudaError_t launch_marginals(const GridInfo &g, const double *tier0, const double *V, double *out, cudaStream_t st)
+{
+    marginal_kernel<<<g.nq, 128, 0, st>>>(g, tier0, V, out);
+    return cudaGetLastError();
+}
+
 // explicit instantiations
 template cudaError_t launch_potential<double>(const GridInfo &, const PotTables<double> &, const double *, double *, int, int, cudaStream_t);
 template cudaError_t launch_potential<float>(const GridInfo &, const PotTables<float> &, const float *, float *, int, int, cudaStream_t);

@@ -30,7 +30,7 @@ EXPORTED = [
     "qhfpe_set_equilibrium", "qhfpe_response", "qhfpe_spectrum_absorption", "qhfpe_spectrum_2d",
     "qhfpe_kernel_timing", "qhfpe_kernel_timing_read", "qhfpe_potential_term_static",
     "qhfpe_closure_collect", "qhfpe_closure_load", "qhfpe_closure_coefficients", "qhfpe_closure_loss_grad",
-    "qhfpe_closure_train", "qhfpe_tile_rows", "qhfpe_wait_selftest",
+    "qhfpe_closure_train", "qhfpe_tile_rows", "qhfpe_wait_selftest", "qhfpe_adiabatic_marginals",
 ]
 
 CLOSURE_N_WEIGHTS = 135178
@@ -90,6 +90,7 @@ def lib():
     L.qhfpe_apply_dipole.argtypes = [vp, ctypes.c_int, ip, ctypes.c_int]
     L.qhfpe_apply_rhs.argtypes = [vp, ctypes.c_int, ctypes.c_int, vp]
     L.qhfpe_trace.argtypes = [vp, vp]
+    L.qhfpe_adiabatic_marginals.argtypes = [vp, ctypes.c_int, vp]
     L.qhfpe_equilibrate.argtypes = [vp, ctypes.c_long, dp]
     L.qhfpe_set_equilibrium.argtypes = [vp, vp, ctypes.c_int]
     L.qhfpe_response.argtypes = [vp, ctypes.POINTER(Schedule), vp]
@@ -297,6 +298,14 @@ class Propagator:
     def trace(self):
         out = np.zeros(self.n_replicas, dtype=np.complex128)
         self._check(self._L.qhfpe_trace(self._h, _ptr(out)))
+        return out
+
+    def adiabatic_marginals(self, replica=0):
+        """P^(ad)_ab(q_i) of the zeroth tier, complex [S][S][nq] (the adiabatic-basis coordinate
+        marginals of Sec. III)."""
+        S = self.shape[1]
+        out = np.zeros((S, S, self.shape[3]), dtype=np.complex128)
+        self._check(self._L.qhfpe_adiabatic_marginals(self._h, replica, _ptr(out)))
         return out
 
     def equilibrate(self, n_steps):

@@ -157,11 +157,16 @@ CONFIGS = {
 }
 
 
-def morse_photoisomerization(nq=512, n_p=128, qr=(-20.0, 80.0), pr=(-25.0, 25.0)):
+def morse_photoisomerization(nq=512, n_p=128, qr=(-20.0, 80.0), pr=(-25.0, 25.0), bath="underdamped"):
     """The paper's own model (Sec. III), in units of hbar*omega_0 with omega_0 = 100 cm^-1: displaced
     Morse diabats and a Gaussian diabatic coupling.  The printed exponent is read as
     -a_j (q - q_j) with a_j = omega_j / sqrt(2 D_j omega_0), which reproduces the printed resonance
-    frequencies (the literal printed form does not)."""
+    frequencies (the literal printed form does not).  Baths of Sec. III (T = 300 K, beta = 0.48):
+    underdamped zeta = 40 cm^-1, gamma = 500 cm^-1, depth 5; overdamped zeta = 400 cm^-1 with the
+    gamma -> infinity limit, i.e. the depth-0 hierarchy with the Eq. (GMFP) terminator (the quantum
+    Fokker-Planck equation, where gamma no longer enters)."""
+    if bath not in ("underdamped", "overdamped"):
+        raise ValueError(bath)
     w0, w1 = 1.0, 0.8
     D0, D1, dE, dV = 700.0, 500.0, 10.0, 6.0
     q0, q1, qs, sig = 0.0, 18.98, 10.28, 2.0
@@ -172,5 +177,5 @@ def morse_photoisomerization(nq=512, n_p=128, qr=(-20.0, 80.0), pr=(-25.0, 25.0)
     return dict(
         name="morse_photoisomerization", S=2, nq=nq, np=n_p, q_min=qr[0], q_max=qr[1], p_min=pr[0], p_max=pr[1],
         U=[[U00, U01], [U01, U11]], mu=np.array([[0.0, 1.0], [1.0, 0.0]]),
-        eta=0.4, gamma=5.0, beta=0.48, n_matsubara=0, high_temperature=1, use_cdelta=0,
-        depth=5, closure=1, dt=1e-3, periodic_q=0, q_minima=(q0, q1))
+        eta=0.4 if bath == "underdamped" else 4.0, gamma=5.0, beta=0.48, n_matsubara=0, high_temperature=1,
+        use_cdelta=0, depth=5 if bath == "underdamped" else 0, closure=1, dt=1e-3, periodic_q=0, q_minima=(q0, q1))
