@@ -162,6 +162,21 @@ qhfpe_status qhfpe_trace(qhfpe_t *h, double *out);
  * replica or NULL output. */
 qhfpe_status qhfpe_adiabatic_marginals(qhfpe_t *h, int replica, double *out);
 
+/* First-order perturbed Wigner distributions in the frequency domain, Sec. III (W'(omega_1), used for
+ * the 1D and 2D correlation spectra; W''(t2, omega_1) = G(t2) i [W'(omega_1) + W'(-omega_1)] follows from
+ * two of them):
+ *   W'(omega) = i [ mu^-> F(omega) - mu^<- F(-omega) ],
+ *   F(omega)  = sum_a w_a e^{i omega t_a} X(t_a),  X(t) = G(t) mu^x W_eq,  t_a = a t1_stride dt,
+ * a = 0 .. n_t1 - 1, with the trapezoid weights of the two-dimensional spectrum's t1 sum
+ * (w_a = dt1 / 2 at both ends, dt1 inside, all zero when n_t1 = 1).  Every hierarchy tier is returned.
+ * The propagation runs in the handle's arithmetic on an internal one-replica batch from the
+ * equilibrium state; the sums are FP64.  omega: host [n_omega].  out: host complex128
+ * [n_omega][n_elem][S][S][nq][np].  Needs an equilibrium state (QHFPE_EINVAL otherwise); QHFPE_EINVAL
+ * for n_t1 < 1, n_omega < 1, t1_stride < 1 with n_t1 > 1, NULL pointers or non-finite omega.
+ * Allocates device memory for 4 n_omega + 1 canonical states for the duration of the call. */
+qhfpe_status qhfpe_first_order_distribution(qhfpe_t *h, int n_t1, int t1_stride, const double *omega, int n_omega,
+                                            double *out);
+
 /* Equilibrium of Sec. III: the ground surface U_00 alone with the full hierarchy, started from the
  * classical Boltzmann distribution exp(-beta (p^2/2 + U_00(q))) normalised to unit trace, propagated
  * n_steps RK4 steps (FP64 always).  The result (ground block of every hierarchy element, all other

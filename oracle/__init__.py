@@ -174,6 +174,28 @@ class Oracle:
         _, tr = self.step(W, n_t)
         return 1j * tr
 
+    def first_order_distribution(self, W_eq, n_t1, t1_stride, omega):
+        """W'(omega) = (i/hbar) [mu^-> F(omega) - mu^<- F(-omega)] with F(omega) = int dt1 e^{i omega t1}
+        G(t1) mu^x W_eq (Sec. III, "One-dimensional spectrum"), the t1 integral by the trapezoid rule on
+        t1 = a*t1_stride*dt, a < n_t1 (n_t1 >= 2).  Returns [len(omega)][n_elem][S][S][nq][np]."""
+        assert n_t1 >= 2
+        dt1 = t1_stride * self.dt
+        wts = np.full(n_t1, dt1)
+        wts[0] *= 0.5
+        wts[-1] *= 0.5
+        omega = np.asarray(omega, dtype=np.float64)
+        Fp = np.zeros((len(omega),) + self.shape, dtype=np.complex128)
+        Fm = np.zeros_like(Fp)
+        X = self.apply_dipole(W_eq, COMMUTATOR)
+        for a in range(n_t1):
+            if a > 0:
+                X, _ = self.step(X, t1_stride)
+            for k, om in enumerate(omega):
+                Fp[k] += wts[a] * np.exp(1j * om * a * dt1) * X
+                Fm[k] += wts[a] * np.exp(-1j * om * a * dt1) * X
+        return np.stack([1j * (self.apply_dipole(Fp[k], LEFT) - self.apply_dipole(Fm[k], RIGHT))
+                         for k in range(len(omega))])
+
     def third_order_response(self, W_eq, n_t1, t1_stride, t2_steps, n_t3, first=COMMUTATOR):
         """R3(t3, t2, t1) = (i/hbar)^3 Tr{mu G(t3) mu^x G(t2) mu^x G(t1) mu^x W_eq} (Eq. (R3)) on the
         grid t1 = a*t1_stride*dt (a < n_t1), t2 in t2_steps*dt, t3 = c*dt (c <= n_t3).  `first`

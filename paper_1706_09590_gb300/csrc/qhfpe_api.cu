@@ -1191,6 +1191,61 @@ qhfpe_status qhfpe_adiabatic_marginals(qhfpe_t *h, int replica, double *out)
     return QHFPE_OK;
 }
 
+qhfpe_status qhfpe_first_order_distribution(qhfpe_t *h, int n_t1, int t1_stride, const double *omega, int n_omega,
+                                            double *out)
+{
+    qhfpe_status r = check_handle(h);
+    if (r != QHFPE_OK) return r;
+    if (!omega || !out || n_t1 < 1 || n_omega < 1 || t1_stride < 0 || (n_t1 > 1 && t1_stride < 1))
+        return h->fail(QHFPE_EINVAL, "first_order_distribution: need n_t1 >= 1, t1_stride >= 1, n_omega >= 1 and "
+                                     "non-NULL omega / out");
+    for (int w = 0; w < n_omega; ++w)
+        if (!std::isfinite(omega[w])) return h->fail(QHFPE_EINVAL, "first_order_distribution: non-finite omega");
+    if (!h->have_eq)
+        return h->fail(QHFPE_EINVAL, "first_order_distribution: no equilibrium state (call qhfpe_equilibrate or "
+                                     "qhfpe_set_equilibrium)");
+    cudaStream_t st = h->stream;
+    Prop *B;
+    if ((r = batch_prop(h, 1, &B)) != QHFPE_OK) return r;
+    const Model &M = *B->m;
+    const size_t n = (size_t)M.n_elem * M.S * M.S * B->g.blk;  // complex values of one canonical state
+    // trapezoid weights over the t1 grid (the convention of the two-dimensional spectrum) times
+    // cos / sin(omega t1)
+    const double dt1 = (double)t1_stride * h->p.dt;
+    std::vector<double> cs((size_t)n_t1 * 2 * n_omega);
+    for (int a = 0; a < n_t1; ++a) {
+        const double wgt = n_t1 == 1 ? 0.0 : ((a == 0 || a == n_t1 - 1) ? 0.5 * dt1 : dt1);
+        for (int w = 0; w < n_omega; ++w) {
+            cs[((size_t)a * 2) * n_omega + w] = wgt * std::cos(omega[w] * a * dt1);
+            cs[((size_t)a * 2 + 1) * n_omega + w] = wgt * std::sin(omega[w] * a * dt1);
+        }
+    }
+    struct Buf {
+        double *p = nullptr;
+        ~Buf() { if (p) cudaFree(p); }
+    } x, acc_c, acc_s, res, coef;
+    QH_CK(h, dalloc(&x.p, 2 * n));
+    QH_CK(h, dalloc(&acc_c.p, 2 * n * n_omega));
+    QH_CK(h, dalloc(&acc_s.p, 2 * n * n_omega));
+    QH_CK(h, dalloc(&res.p, 2 * n * n_omega));
+    QH_CK(h, dalloc(&coef.p, cs.size()));
+    QH_CK(h, cudaMemcpyAsync(coef.p, cs.data(), cs.size() * sizeof(double), cudaMemcpyHostToDevice, st));
+    QH_CK(h, cudaMemsetAsync(acc_c.p, 0, 2 * n * n_omega * sizeof(double), st));
+    QH_CK(h, cudaMemsetAsync(acc_s.p, 0, 2 * n * n_omega * sizeof(double), st));
+    // X(0) = mu^x W_eq, then X(t1) = G(t1) X(0) sampled every t1_stride steps
+    if ((r = set_from_canonical(h, *B, h->eq, 0, 1)) != QHFPE_OK) return r;
+    if ((r = apply_dipole_prop(h, *B, QHFPE_COMMUTATOR, nullptr, 1, 1.0)) != QHFPE_OK) return r;
+    for (int a = 0; a < n_t1; ++a) {
+        if (a > 0 && (r = run_steps(h, *B, t1_stride, nullptr, 0)) != QHFPE_OK) return r;
+        if ((r = get_to_canonical(h, *B, B->y, B->y0, x.p, 0)) != QHFPE_OK) return r;
+        QH_CK(h, launch_fourier_accumulate(x.p, n, coef.p + (size_t)a * 2 * n_omega, n_omega, acc_c.p, acc_s.p, st));
+    }
+    QH_CK(h, launch_first_order_combine(M.S, B->g.blk, M.n_elem, n_omega, M.mu, acc_c.p, acc_s.p, res.p, st));
+    QH_CK(h, cudaMemcpyAsync(out, res.p, 2 * n * n_omega * sizeof(double), cudaMemcpyDeviceToHost, st));
+    QH_CK(h, cudaStreamSynchronize(st));
+    return check_timeout(h);
+}
+
 qhfpe_status qhfpe_equilibrate(qhfpe_t *h, long n_steps, double *residual_out)
 {
     qhfpe_status r = check_handle(h);

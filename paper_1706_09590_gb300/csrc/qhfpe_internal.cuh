@@ -140,6 +140,12 @@ cudaError_t launch_to_canonical(const GridInfo &g, const T *src, const double *y
 // Adiabatic-basis coordinate marginals of one replica's zeroth tier (FP64, layout [S][S][re|im][q][p]);
 // V: [nq][S][S] eigenvector components; out: [S][S][nq] complex.
 cudaError_t launch_marginals(const GridInfo &g, const double *tier0, const double *V, double *out, cudaStream_t st);
+// W'(omega) of Sec. III: Fourier-weighted sums of canonical complex states (cs: [2][n_omega] weights of
+// this sample) and the dipole combination i [mu^-> (A_c + i A_s) - mu^<- (A_c - i A_s)].
+cudaError_t launch_fourier_accumulate(const double *x, size_t n, const double *cs, int n_omega, double *acc_c,
+                                      double *acc_s, cudaStream_t st);
+cudaError_t launch_first_order_combine(int S, size_t blk, int n_elem, int n_omega, const double *mu,
+                                       const double *acc_c, const double *acc_s, double *out, cudaStream_t st);
 cudaError_t launch_norm2(const double *x, size_t n, double *out_dev, cudaStream_t st);
 cudaError_t launch_wait_flag(const int *flag, unsigned long long limit_ns, int *status, cudaStream_t st);
 cudaError_t launch_absorption(const double *R1, long n_t, double dt, const double *omega, int n_omega,

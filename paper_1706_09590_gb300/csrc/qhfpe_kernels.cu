@@ -7,6 +7,7 @@
 // y0[rep][j][k][re|im][q][p].
 #include "qhfpe_internal.cuh"
 
+#include <algorithm>
 #include <mutex>
 
 namespace {
@@ -740,6 +741,76 @@ __global__ void marginal_kernel(GridInfo g, const double *__restrict__ state, co
 cudaError_t launch_marginals(const GridInfo &g, const double *tier0, const double *V, double *out, cudaStream_t st)
 {
     marginal_kernel<<<g.nq, 128, 0, st>>>(g, tier0, V, out);
+    return cudaGetLastError();
+}
+
+// Fourier-weighted accumulation of canonical complex states (W'(omega) of Sec. III): for each of
+// n_omega frequencies, acc_c[w] += cs[w] x and acc_s[w] += cs[n_omega + w] x, where cs holds this
+// sample's trapezoid weight times dt times cos / sin(omega_w t).
+__global__ void fourier_accumulate_kernel(const double *__restrict__ x, size_t n, const double *__restrict__ cs,
+                                          int n_omega, double *acc_c, double *acc_s)
+{
+    for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < n; idx += (size_t)gridDim.x * blockDim.x) {
+        const double xr = x[2 * idx], xi = x[2 * idx + 1];
+        for (int w = 0; w < n_omega; ++w) {
+            const double c = cs[w], s = cs[n_omega + w];
+            acc_c[2 * ((size_t)w * n + idx)] += c * xr;
+            acc_c[2 * ((size_t)w * n + idx) + 1] += c * xi;
+            acc_s[2 * ((size_t)w * n + idx)] += s * xr;
+            acc_s[2 * ((size_t)w * n + idx) + 1] += s * xi;
+        }
+    }
+}
+
+// W'(omega) = i [ mu^-> F(omega) - mu^<- F(-omega) ] with F(+-omega) = A_c +- i A_s, per frequency,
+// hierarchy element and cell (canonical layout [elem][j][k][cell] complex, cell = q * np + p).
+__global__ void first_order_combine_kernel(int S, size_t blk, int n_elem, int n_omega, const double *__restrict__ mu,
+                                           const double *__restrict__ acc_c, const double *__restrict__ acc_s,
+                                           double *__restrict__ out)
+{
+    const size_t per_elem = (size_t)S * S * blk, n = (size_t)n_elem * per_elem;
+    const size_t total = (size_t)n_omega * n_elem * blk;
+    for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total; t += (size_t)gridDim.x * blockDim.x) {
+        const size_t c = t % blk, e = (t / blk) % n_elem, w = t / (blk * n_elem);
+        const size_t base = w * n + e * per_elem + c;  // complex index of pair (0, 0)
+        double pr[QH_MAX_S * QH_MAX_S], pi[QH_MAX_S * QH_MAX_S], mr[QH_MAX_S * QH_MAX_S], mi[QH_MAX_S * QH_MAX_S];
+        for (int jk = 0; jk < S * S; ++jk) {
+            const size_t o = 2 * (base + (size_t)jk * blk);
+            const double cr = acc_c[o], ci = acc_c[o + 1], sr = acc_s[o], si = acc_s[o + 1];
+            pr[jk] = cr - si;  // A_c + i A_s
+            pi[jk] = ci + sr;
+            mr[jk] = cr + si;  // A_c - i A_s
+            mi[jk] = ci - sr;
+        }
+        for (int j = 0; j < S; ++j)
+            for (int k = 0; k < S; ++k) {
+                double zr = 0.0, zi = 0.0;
+                for (int l = 0; l < S; ++l) {
+                    zr += mu[j * S + l] * pr[l * S + k] - mr[j * S + l] * mu[l * S + k];
+                    zi += mu[j * S + l] * pi[l * S + k] - mi[j * S + l] * mu[l * S + k];
+                }
+                const size_t o = 2 * (base + (size_t)(j * S + k) * blk);
+                out[o] = -zi;  // times i
+                out[o + 1] = zr;
+            }
+    }
+}
+
+cudaError_t launch_fourier_accumulate(const double *x, size_t n, const double *cs, int n_omega, double *acc_c,
+                                      double *acc_s, cudaStream_t st)
+{
+    const long blocks = (long)std::min<size_t>((n + 255) / 256, 152 * 16);
+    fourier_accumulate_kernel<<<(unsigned)std::max(blocks, 1L), 256, 0, st>>>(x, n, cs, n_omega, acc_c, acc_s);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_first_order_combine(int S, size_t blk, int n_elem, int n_omega, const double *mu,
+                                       const double *acc_c, const double *acc_s, double *out, cudaStream_t st)
+{
+    const size_t total = (size_t)n_omega * n_elem * blk;
+    const long blocks = (long)std::min<size_t>((total + 255) / 256, 152 * 16);
+    first_order_combine_kernel<<<(unsigned)std::max(blocks, 1L), 256, 0, st>>>(S, blk, n_elem, n_omega, mu, acc_c,
+                                                                              acc_s, out);
     return cudaGetLastError();
 }
 

@@ -31,6 +31,7 @@ EXPORTED = [
     "qhfpe_kernel_timing", "qhfpe_kernel_timing_read", "qhfpe_potential_term_static",
     "qhfpe_closure_collect", "qhfpe_closure_load", "qhfpe_closure_coefficients", "qhfpe_closure_loss_grad",
     "qhfpe_closure_train", "qhfpe_tile_rows", "qhfpe_wait_selftest", "qhfpe_adiabatic_marginals",
+    "qhfpe_first_order_distribution",
 ]
 
 CLOSURE_N_WEIGHTS = 135178
@@ -91,6 +92,7 @@ def lib():
     L.qhfpe_apply_rhs.argtypes = [vp, ctypes.c_int, ctypes.c_int, vp]
     L.qhfpe_trace.argtypes = [vp, vp]
     L.qhfpe_adiabatic_marginals.argtypes = [vp, ctypes.c_int, vp]
+    L.qhfpe_first_order_distribution.argtypes = [vp, ctypes.c_int, ctypes.c_int, vp, ctypes.c_int, vp]
     L.qhfpe_equilibrate.argtypes = [vp, ctypes.c_long, dp]
     L.qhfpe_set_equilibrium.argtypes = [vp, vp, ctypes.c_int]
     L.qhfpe_response.argtypes = [vp, ctypes.POINTER(Schedule), vp]
@@ -306,6 +308,14 @@ class Propagator:
         S = self.shape[1]
         out = np.zeros((S, S, self.shape[3]), dtype=np.complex128)
         self._check(self._L.qhfpe_adiabatic_marginals(self._h, replica, _ptr(out)))
+        return out
+
+    def first_order_distribution(self, n_t1, t1_stride, omega):
+        """W'(omega_1) of Sec. III for each frequency: complex [n_omega][n_elem][S][S][nq][np]."""
+        om = np.ascontiguousarray(omega, dtype=np.float64)
+        out = np.zeros((len(om),) + self.shape, dtype=np.complex128)
+        self._check(self._L.qhfpe_first_order_distribution(self._h, int(n_t1), int(t1_stride), _ptr(om), len(om),
+                                                           _ptr(out)))
         return out
 
     def equilibrate(self, n_steps):
