@@ -150,6 +150,20 @@ qhfpe_status qhfpe_apply_rhs(qhfpe_t *h, int replica, int terms, double *out);
 /* Tr{mu W^(0)} of every replica now: host complex128 [n_replicas]. */
 qhfpe_status qhfpe_trace(qhfpe_t *h, double *out);
 
+/* Coordinate-dependent (non-Condon) dipole, Sec. III: "a non-Condon dipolar interaction can be
+ * included"; the dipole super-operators are the p-convolutions
+ *   (mu^-> W)_jk = sum_l mu_jl(p, q) * W_lk,   (mu^<- W)_jk = sum_l mu*_lk(p, q) * W_jl,
+ *   mu_jk(p, q) = (1 / 2 pi hbar) int dr e^{-i p r / hbar} mu_jk(q + r/2),
+ * which on the grid are circulants along p: after an FFT along p, products with mu_jl(q_i + r_m/2) and
+ * mu_lk(q_i - r_m/2) at the r-grid modes (Nyquist mode: the symmetric value, as for the potential).
+ * The trace Tr{mu W^(0)} weights W_jk(q_i, p) with mu_kj(q_i).  mu_table: host, [S][S][nq][np+1] in the
+ * U_table convention (mu_jk(q_i + s_t)), real and symmetric in (j, k); copied.  NULL restores the
+ * Condon dipole of qhfpe_params.mu.  Applies to every later dipole application and trace of the handle
+ * (qhfpe_apply_dipole, qhfpe_step traces, qhfpe_response, qhfpe_first_order_distribution); the mixed
+ * forms apply it to their FP64 zeroth tier in FP64.  Errors: QHFPE_EUNSUPPORTED unless np is 32, 64,
+ * 128 or 256 and S <= 3; QHFPE_EINVAL for non-finite or non-symmetric tables. */
+qhfpe_status qhfpe_set_dipole_table(qhfpe_t *h, const double *mu_table);
+
 /* Adiabatic-basis wavepacket marginals, Sec. III ("Wavepacket dynamics"): for replica `replica`,
  *   out[a][b][i] = sum_jk V_ja(q_i) V_kb(q_i) dp sum_l W^(0)_jk(q_i, p_l),
  * the coordinate marginal of the zeroth-tier Wigner distribution (the reduced density matrix on its

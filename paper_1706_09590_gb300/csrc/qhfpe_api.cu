@@ -170,6 +170,13 @@ struct Model {
     double max_rate = 0.0;     // Gershgorin estimate of the generator's spectral radius
     std::vector<double> adia_host;  // adiabatic eigenvectors of U(q_i): [nq][S][S], v[j][a]
     double *adia = nullptr;
+    // non-Condon dipole (qhfpe_set_dipole_table): r-space multipliers mu(q + r/2), mu(q - r/2) in the
+    // fused FFT's order (TL | TR, FP64 and FP32) and mu(q_i) at the grid points for the trace
+    bool noncondon = false;
+    double *dip64 = nullptr;
+    float *dip32 = nullptr;
+    double *mu_q = nullptr;
+    const double *trace_mu_q() const { return noncondon ? mu_q : nullptr; }
 
     PotTables<double> t64() const
     {
@@ -201,6 +208,9 @@ struct Model {
         if (tcN) cudaFree(tcN);
         if (tcB) cudaFree(tcB);
         if (adia) cudaFree(adia);
+        if (dip64) cudaFree(dip64);
+        if (dip32) cudaFree(dip32);
+        if (mu_q) cudaFree(mu_q);
     }
 };
 
@@ -233,6 +243,15 @@ struct Prop {
     size_t trace_cap = 0;
     cudaGraphExec_t graphs[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};  // [chunk][trace]
 
+    void drop_graphs()
+    {
+        for (auto &a : graphs)
+            for (auto &x : a)
+                if (x) {
+                    cudaGraphExecDestroy(x);
+                    x = nullptr;
+                }
+    }
     ~Prop()
     {
         for (auto &a : graphs)
@@ -627,8 +646,8 @@ qhfpe_status step_once(qhfpe *h, Prop &P, bool record)
     }
     if (record) {
         Bracket br(h, QH_KIND_AUX);
-        if (MIXED) QH_CK(h, launch_trace<double>(P.g, P.y0, P.g.tier0_rep_stride, M.mu, P.sink, 1, P.partial, st));
-        else QH_CK(h, launch_trace<double>(P.g, (const double *)P.y, P.g.rep_stride, M.mu, P.sink, 1, P.partial, st));
+        if (MIXED) QH_CK(h, launch_trace<double>(P.g, P.y0, P.g.tier0_rep_stride, M.mu, P.sink, 1, P.partial, st, M.trace_mu_q()));
+        else QH_CK(h, launch_trace<double>(P.g, (const double *)P.y, P.g.rep_stride, M.mu, P.sink, 1, P.partial, st, M.trace_mu_q()));
     }
     return QHFPE_OK;
 }
@@ -710,8 +729,8 @@ qhfpe_status run_steps(qhfpe *h, Prop &P, long n_steps, double *trace_dev, long 
     if (record) {
         set_sink_kernel<<<1, 1, 0, st>>>(P.sink, trace_dev, stride, 0);
         QH_CK(h, cudaGetLastError());
-        if (P.mixed) QH_CK(h, launch_trace<double>(P.g, P.y0, P.g.tier0_rep_stride, P.m->mu, P.sink, 1, P.partial, st));
-        else QH_CK(h, launch_trace<double>(P.g, (const double *)P.y, P.g.rep_stride, P.m->mu, P.sink, 1, P.partial, st));
+        if (P.mixed) QH_CK(h, launch_trace<double>(P.g, P.y0, P.g.tier0_rep_stride, P.m->mu, P.sink, 1, P.partial, st, P.m->trace_mu_q()));
+        else QH_CK(h, launch_trace<double>(P.g, (const double *)P.y, P.g.rep_stride, P.m->mu, P.sink, 1, P.partial, st, P.m->trace_mu_q()));
     }
     if (h->timing.enabled) {
         for (long s = 0; s < n_steps; ++s) {
@@ -796,6 +815,23 @@ qhfpe_status get_to_canonical(qhfpe *h, Prop &P, const void *src, const double *
 
 qhfpe_status apply_dipole_prop(qhfpe *h, Prop &P, int side, const int *reps_dev, int n, double scale)
 {
+    const Model &M = *P.m;
+    if (M.noncondon) {
+        const size_t tn = (size_t)M.S * M.S * M.nq * M.np;
+        if (P.mixed) {
+            // FP32 pass over every element, then the FP64 zeroth tier (which also rewrites its FP32 copy)
+            QH_CK(h, launch_dipole_fft<float>(P.g, M.dip32, M.dip32 + tn, M.ftab32 + 3 * tn, (float *)P.y, P.g.rep_stride,
+                                              M.n_elem, reps_dev, n, side, scale, nullptr, 0, h->stream));
+            QH_CK(h, launch_dipole_fft<double>(P.g, M.dip64, M.dip64 + tn, M.ftab64 + 3 * tn, P.y0,
+                                               P.g.tier0_rep_stride, 1, reps_dev, n, side, scale, (float *)P.y,
+                                               P.g.rep_stride, h->stream));
+        } else {
+            QH_CK(h, launch_dipole_fft<double>(P.g, M.dip64, M.dip64 + tn, M.ftab64 + 3 * tn, (double *)P.y,
+                                               P.g.rep_stride, M.n_elem, reps_dev, n, side, scale, nullptr, 0,
+                                               h->stream));
+        }
+        return QHFPE_OK;
+    }
     if (P.mixed) QH_CK(h, launch_dipole<float>(P.g, (float *)P.y, P.y0, reps_dev, n, P.m->mu, side, scale, h->stream));
     else QH_CK(h, launch_dipole<double>(P.g, (double *)P.y, nullptr, reps_dev, n, P.m->mu, side, scale, h->stream));
     return QHFPE_OK;
@@ -1166,10 +1202,72 @@ qhfpe_status qhfpe_trace(qhfpe_t *h, double *out)
     if (r != QHFPE_OK) return r;
     set_sink_kernel<<<1, 1, 0, h->stream>>>(P.sink, P.trace_buf, 1, 0);
     QH_CK(h, cudaGetLastError());
-    if (P.mixed) QH_CK(h, launch_trace<double>(P.g, P.y0, P.g.tier0_rep_stride, P.m->mu, P.sink, 0, P.partial, h->stream));
-    else QH_CK(h, launch_trace<double>(P.g, (const double *)P.y, P.g.rep_stride, P.m->mu, P.sink, 0, P.partial, h->stream));
+    if (P.mixed) QH_CK(h, launch_trace<double>(P.g, P.y0, P.g.tier0_rep_stride, P.m->mu, P.sink, 0, P.partial, h->stream, P.m->trace_mu_q()));
+    else QH_CK(h, launch_trace<double>(P.g, (const double *)P.y, P.g.rep_stride, P.m->mu, P.sink, 0, P.partial, h->stream, P.m->trace_mu_q()));
     QH_CK(h, cudaMemcpyAsync(out, P.trace_buf, (size_t)P.g.n_rep * 2 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
     QH_CK(h, cudaStreamSynchronize(h->stream));
+    return QHFPE_OK;
+}
+
+qhfpe_status qhfpe_set_dipole_table(qhfpe_t *h, const double *mu_table)
+{
+    qhfpe_status r = check_handle(h);
+    if (r != QHFPE_OK) return r;
+    Model &M = *h->model;
+    cudaStream_t st = h->stream;
+    const int S = M.S, nq = M.nq, N = M.np;
+    if (!mu_table) {
+        M.noncondon = false;
+    } else {
+        if (!fused_supported(N, S) || S > 3)
+            return h->fail(QHFPE_EUNSUPPORTED, "set_dipole_table: coordinate-dependent dipoles need np in {32, 64, "
+                                               "128, 256} and at most 3 states");
+        const size_t nt = (size_t)S * S * nq * (N + 1);
+        for (size_t x = 0; x < nt; ++x)
+            if (!std::isfinite(mu_table[x])) return h->fail(QHFPE_EINVAL, "set_dipole_table: non-finite entry");
+        for (int j = 0; j < S; ++j)
+            for (int k = 0; k < S; ++k)
+                for (size_t x = 0; x < (size_t)nq * (N + 1); ++x)
+                    if (mu_table[((size_t)j * S + k) * nq * (N + 1) + x] != mu_table[((size_t)k * S + j) * nq * (N + 1) + x])
+                        return h->fail(QHFPE_EINVAL, "set_dipole_table: the table must be symmetric in (j, k)");
+        // multipliers at r-grid mode m (the Nyquist mode takes the symmetric value, as the potential)
+        auto T = [&](int a, int b, int i, int t) { return mu_table[(((size_t)a * S + b) * nq + i) * (N + 1) + t]; };
+        auto ML = [&](int a, int b, int i, int m) {
+            return m == -N / 2 ? 0.5 * (T(a, b, i, 0) + T(a, b, i, N)) : T(a, b, i, m + N / 2);
+        };
+        auto MR = [&](int a, int b, int i, int m) {
+            return m == -N / 2 ? 0.5 * (T(a, b, i, 0) + T(a, b, i, N)) : T(a, b, i, N / 2 - m);
+        };
+        const size_t tn = (size_t)S * S * nq * N;
+        std::vector<double> tab(2 * tn);
+        std::vector<float> tab32(2 * tn);
+        for (int a = 0; a < S; ++a)
+            for (int b = 0; b < S; ++b)
+                for (int i = 0; i < nq; ++i)
+                    for (int pos = 0; pos < N; ++pos) {
+                        const int kk = fused_fft_frequency(N, pos);
+                        const int m = kk < N / 2 ? kk : kk - N;
+                        const size_t o = (((size_t)a * S + b) * nq + i) * N + pos;
+                        tab[o] = ML(a, b, i, m) / N;
+                        tab[tn + o] = MR(a, b, i, m) / N;
+                    }
+        for (size_t x = 0; x < 2 * tn; ++x) tab32[x] = (float)tab[x];
+        std::vector<double> muq((size_t)nq * S * S);
+        for (int i = 0; i < nq; ++i)
+            for (int a = 0; a < S; ++a)
+                for (int b = 0; b < S; ++b) muq[((size_t)i * S + a) * S + b] = T(a, b, i, N / 2);
+        if (!M.dip64) QH_CK(h, dalloc(&M.dip64, 2 * tn));
+        if (!M.dip32) QH_CK(h, dalloc(&M.dip32, 2 * tn));
+        if (!M.mu_q) QH_CK(h, dalloc(&M.mu_q, muq.size()));
+        QH_CK(h, cudaMemcpyAsync(M.dip64, tab.data(), tab.size() * sizeof(double), cudaMemcpyHostToDevice, st));
+        QH_CK(h, cudaMemcpyAsync(M.dip32, tab32.data(), tab32.size() * sizeof(float), cudaMemcpyHostToDevice, st));
+        QH_CK(h, cudaMemcpyAsync(M.mu_q, muq.data(), muq.size() * sizeof(double), cudaMemcpyHostToDevice, st));
+        QH_CK(h, cudaStreamSynchronize(st));
+        M.noncondon = true;
+    }
+    // captured step graphs hold the trace's dipole arguments: capture them again on next use
+    h->main->drop_graphs();
+    for (auto &b : h->batches) b.second->drop_graphs();
     return QHFPE_OK;
 }
 

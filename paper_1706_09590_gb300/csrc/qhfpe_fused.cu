@@ -705,6 +705,96 @@ fused_stage_kernel(GridInfo g, const ElemInfo *__restrict__ elems, FusedTables<T
     }
 }
 
+// Non-Condon dipole super-operators of Sec. III: (mu^-> W)_jk = sum_l mu_jl(p, q) * W_lk and
+// (mu^<- W)_jk = sum_l mu*_lk(p, q) * W_jl are p-convolutions with the Fourier transform of
+// mu(q + r/2); after an FFT along p they are products with mu_jl(q_i + r_m/2) (TL) and
+// mu_lk(q_i - r_m/2) (TR), both tabulated in the FFT's digit-reversed order and pre-scaled by 1/np.
+// side 1: mu^->, 2: mu^<-, 3: mu^x; times `scale`.  One block = (replica, element, tile of tq q rows),
+// all pairs, in place.  mirror (the mixed forms' FP32 copy of the zeroth tier): also written.
+template <typename T, int NP, int S>
+__global__ void __launch_bounds__(FTHREADS)
+dipole_fft_kernel(GridInfo g, const T *__restrict__ TL, const T *__restrict__ TR, const T *__restrict__ twt, T *state,
+                  size_t rep_stride, int n_elem, const int *__restrict__ reps, int n_rep, int side, double scale, int tq,
+                  float *mirror, size_t mirror_rep_stride)
+{
+    using C = typename V2<T>::type;
+    constexpr int S2 = S * S;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C *X = reinterpret_cast<C *>(smem_raw);  // [tq * S2][NP], padded (pad16)
+    C *tw = X + pad16(tq * S2 * NP) + 1;     // [NP]
+    const int nq = g.nq;
+    const int e = blockIdx.x % n_elem;
+    const int ri = (blockIdx.x / n_elem) % n_rep;
+    const int rep = reps ? reps[ri] : ri;
+    const int tile = blockIdx.x / (n_elem * n_rep);
+    const int i0 = tile * tq, rows = min(tq, nq - i0);
+    const size_t blk = g.blk;
+    T *base = state + (size_t)rep * rep_stride + (size_t)e * g.elem_stride;
+    for (int t = threadIdx.x; t < NP; t += FTHREADS) tw[t] = C{twt[2 * t], twt[2 * t + 1]};
+    for (int idx = threadIdx.x; idx < rows * S2 * NP; idx += FTHREADS) {
+        const int l = idx % NP, rp = idx / NP, pr = rp % S2, r = rp / S2;
+        const T *src = base + (size_t)pr * 2 * blk + (size_t)(i0 + r) * NP + l;
+        X[pad16((r * S2 + pr) * NP + l)] = C{src[0], src[blk]};
+    }
+    __syncthreads();
+    fft_all<NP, true>(X, rows * S2, tw);
+    const T cl = (side & 1) ? (T)1 : (T)0;                          // mu^-> part
+    const T cr = side == 2 ? (T)1 : (side == 3 ? (T)-1 : (T)0);     // mu^<- part
+    const T sc = (T)scale;
+    for (int idx = threadIdx.x; idx < rows * NP; idx += FTHREADS) {
+        const int pos = idx % NP, r = idx / NP, i = i0 + r;
+        C x[S2];
+#pragma unroll
+        for (int a = 0; a < S2; ++a) x[a] = X[pad16((r * S2 + a) * NP + pos)];
+#pragma unroll
+        for (int j = 0; j < S; ++j)
+#pragma unroll
+            for (int k = 0; k < S; ++k) {
+                T ar = (T)0, ai = (T)0;
+#pragma unroll
+                for (int l = 0; l < S; ++l) {
+                    const T a = cl * TL[((size_t)(j * S + l) * nq + i) * NP + pos];
+                    const T b = cr * TR[((size_t)(l * S + k) * nq + i) * NP + pos];
+                    ar += a * x[l * S + k].x + b * x[j * S + l].x;
+                    ai += a * x[l * S + k].y + b * x[j * S + l].y;
+                }
+                X[pad16((r * S2 + j * S + k) * NP + pos)] = C{sc * ar, sc * ai};
+            }
+    }
+    __syncthreads();
+    fft_all<NP, false>(X, rows * S2, tw);
+    float *mb = mirror ? mirror + (size_t)rep * mirror_rep_stride : nullptr;
+    for (int idx = threadIdx.x; idx < rows * S2 * NP; idx += FTHREADS) {
+        const int l = idx % NP, rp = idx / NP, pr = rp % S2, r = rp / S2;
+        const size_t o = (size_t)pr * 2 * blk + (size_t)(i0 + r) * NP + l;
+        const C v = X[pad16((r * S2 + pr) * NP + l)];
+        base[o] = v.x;
+        base[o + blk] = v.y;
+        if (mb) {
+            mb[o] = (float)v.x;
+            mb[o + blk] = (float)v.y;
+        }
+    }
+}
+
+template <typename T, int NP, int S>
+cudaError_t launch_dipole_fft_t(const GridInfo &g, const T *TL, const T *TR, const T *tw, T *state, size_t rep_stride,
+                                int n_elem, const int *reps, int n_rep, int side, double scale, float *mirror,
+                                size_t mirror_rep_stride, cudaStream_t st)
+{
+    // the largest tile (q rows, a power of two up to 16) whose shared memory stays within 44 KB
+    int tq = 16;
+    while (tq > 1 && fused_smem_bytes(tq, NP, S, sizeof(T)) > 44 * 1024) tq /= 2;
+    if (tq > g.nq) tq = g.nq;
+    const size_t smem = fused_smem_bytes(tq, NP, S, sizeof(T));
+    const long blocks = (long)((g.nq + tq - 1) / tq) * n_rep * n_elem;
+    if (blocks <= 0) return cudaSuccess;
+    dipole_fft_kernel<T, NP, S><<<(unsigned)blocks, FTHREADS, smem, st>>>(g, TL, TR, tw, state, rep_stride, n_elem, reps,
+                                                                         n_rep, side, scale, tq, mirror,
+                                                                         mirror_rep_stride);
+    return cudaGetLastError();
+}
+
 template <typename T, int NP, int S, bool MIXED>
 cudaError_t launch_fused_t(const GridInfo &g, const ElemInfo *elems, const FusedTables<T> &tab, const T *v_in,
                            const T *y, const double *y0, T *v_out, double *y0_out, double h, int mode, int terms,
@@ -811,6 +901,30 @@ cudaError_t prepare_fused(int np, int S)
     }
 }
 
+template <typename T>
+cudaError_t launch_dipole_fft(const GridInfo &g, const T *TL, const T *TR, const T *tw, T *state, size_t rep_stride,
+                              int n_elem, const int *reps, int n_rep, int side, double scale, float *mirror,
+                              size_t mirror_rep_stride, cudaStream_t st)
+{
+#define QH_CALL(NP_, S_) launch_dipole_fft_t<T, NP_, S_>(g, TL, TR, tw, state, rep_stride, n_elem, reps, n_rep, side, scale, mirror, mirror_rep_stride, st)
+    switch (g.np * 8 + g.S) {
+    case 32 * 8 + 1: return QH_CALL(32, 1);
+    case 32 * 8 + 2: return QH_CALL(32, 2);
+    case 32 * 8 + 3: return QH_CALL(32, 3);
+    case 64 * 8 + 1: return QH_CALL(64, 1);
+    case 64 * 8 + 2: return QH_CALL(64, 2);
+    case 64 * 8 + 3: return QH_CALL(64, 3);
+    case 128 * 8 + 1: return QH_CALL(128, 1);
+    case 128 * 8 + 2: return QH_CALL(128, 2);
+    case 128 * 8 + 3: return QH_CALL(128, 3);
+    case 256 * 8 + 1: return QH_CALL(256, 1);
+    case 256 * 8 + 2: return QH_CALL(256, 2);
+    case 256 * 8 + 3: return QH_CALL(256, 3);
+    default: return cudaErrorInvalidValue;
+    }
+#undef QH_CALL
+}
+
 // Position -> frequency index of the in-place mixed-radix DIF above: the pass with radix R_a at
 // sub-length M_a writes its output digit u_a at stride M_a / R_a, and that digit is the frequency's
 // a-th mixed-radix digit (weight R_0 ... R_{a-1}).
@@ -840,3 +954,5 @@ template cudaError_t launch_fused<float, true>(const GridInfo &, const ElemInfo 
 template cudaError_t launch_fused<double, false>(const GridInfo &, const ElemInfo *, const FusedTables<double> &, const double *, const double *, const double *, double *, double *, double, int, int, int, int, cudaStream_t, const double *, int);
 template cudaError_t prepare_fused<float, true>(int, int);
 template cudaError_t prepare_fused<double, false>(int, int);
+template cudaError_t launch_dipole_fft<float>(const GridInfo &, const float *, const float *, const float *, float *, size_t, int, const int *, int, int, double, float *, size_t, cudaStream_t);
+template cudaError_t launch_dipole_fft<double>(const GridInfo &, const double *, const double *, const double *, double *, size_t, int, const int *, int, int, double, float *, size_t, cudaStream_t);

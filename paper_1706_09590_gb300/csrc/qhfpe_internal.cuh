@@ -84,8 +84,10 @@ cudaError_t launch_stage(const GridInfo &g, const ElemInfo *elems, const T *v_in
 // partial: device scratch of 2 * n_rep * QH_TRACE_MAX_CHUNKS doubles
 #define QH_TRACE_MAX_CHUNKS 64
 template <typename T>
+// mu_q: non-Condon dipole at the grid points, [nq][S][S] (nullptr: the constant mu_dev)
 cudaError_t launch_trace(const GridInfo &g, const T *state, size_t rep_stride, const double *mu_dev,
-                         TraceSink *sink, int advance, double *partial, cudaStream_t st);
+                         TraceSink *sink, int advance, double *partial, cudaStream_t st,
+                         const double *mu_q = nullptr);
 
 cudaError_t launch_advance(TraceSink *sink, cudaStream_t st);
 cudaError_t prepare_potential(size_t smem_bytes_fp64);
@@ -102,6 +104,14 @@ cudaError_t launch_fused(const GridInfo &g, const ElemInfo *elems, const FusedTa
                          const T *y, const double *y0, T *v_out, double *y0_out, double h, int mode, int terms,
                          int rep0, int n_rep, cudaStream_t st, const T *Pg = nullptr, int tq = 0);
 int fused_max_rows(int np, int S, int elem_bytes);
+// Non-Condon dipole super-operator (side 1: mu^->, 2: mu^<-, 3: mu^x, times scale) on n_elem elements of
+// n_rep replicas (reps: device list or nullptr for 0..n_rep-1), in place, through an FFT along p.
+// TL, TR: [S][S][nq][np] r-space multipliers mu(q + r/2), mu(q - r/2) / np in the fused FFT's order;
+// tw: its np twiddles.  mirror: FP32 copy to update as well (nullptr: none).  np in {32..256}, S <= 3.
+template <typename T>
+cudaError_t launch_dipole_fft(const GridInfo &g, const T *TL, const T *TR, const T *tw, T *state, size_t rep_stride,
+                              int n_elem, const int *reps, int n_rep, int side, double scale, float *mirror,
+                              size_t mirror_rep_stride, cudaStream_t st);
 
 // ---- tensor-core potential term (qhfpe_tc.cu) ----------------------------------------------------------
 bool tc_supported(int np, int S);

@@ -292,7 +292,7 @@ pot_kernel(GridInfo g, PotTables<T> tab, const T *__restrict__ v, T *__restrict_
 template <typename T>
 __global__ void __launch_bounds__(256)
 trace_partial_kernel(GridInfo g, const T *__restrict__ state, size_t rep_stride, const double *__restrict__ mu,
-                     double *partial, int n_chunks)
+                     const double *__restrict__ mu_q, double *partial, int n_chunks)
 {
     __shared__ double red[2][256];
     const int chunk = blockIdx.x, rep = blockIdx.y;
@@ -304,9 +304,17 @@ trace_partial_kernel(GridInfo g, const T *__restrict__ state, size_t rep_stride,
     double sr = 0.0, si = 0.0;
     for (int j = 0; j < S; ++j)
         for (int k = 0; k < S; ++k) {
+            const T *b = W + (size_t)(j * S + k) * 2 * blk;
+            if (mu_q) {  // non-Condon: the Wigner function of mu(q) is mu_kj(q_i) at every p of row i
+                for (size_t c = c0 + threadIdx.x; c < c1; c += blockDim.x) {
+                    const double m = mu_q[(c / g.np) * S * S + k * S + j];
+                    sr += m * (double)b[c];
+                    si += m * (double)b[c + blk];
+                }
+                continue;
+            }
             const double m = mu[k * S + j];
             if (m == 0.0) continue;
-            const T *b = W + (size_t)(j * S + k) * 2 * blk;
             double ar = 0.0, ai = 0.0;
             for (size_t c = c0 + threadIdx.x; c < c1; c += blockDim.x) {
                 ar += (double)b[c];
@@ -600,10 +608,10 @@ int trace_chunks(int n_rep, size_t blk)
 
 template <typename T>
 cudaError_t launch_trace(const GridInfo &g, const T *state, size_t rep_stride, const double *mu_dev,
-                         TraceSink *sink, int advance, double *partial, cudaStream_t st)
+                         TraceSink *sink, int advance, double *partial, cudaStream_t st, const double *mu_q)
 {
     const int nc = trace_chunks(g.n_rep, g.blk);
-    trace_partial_kernel<T><<<dim3(nc, g.n_rep), 256, 0, st>>>(g, state, rep_stride, mu_dev, partial, nc);
+    trace_partial_kernel<T><<<dim3(nc, g.n_rep), 256, 0, st>>>(g, state, rep_stride, mu_dev, mu_q, partial, nc);
     cudaError_t err = cudaGetLastError();
     if (err != cudaSuccess) return err;
     trace_finish_kernel<<<1, 512, 0, st>>>(g, partial, nc, sink, advance);
@@ -819,7 +827,7 @@ template cudaError_t launch_potential<double>(const GridInfo &, const PotTables<
 template cudaError_t launch_potential<float>(const GridInfo &, const PotTables<float> &, const float *, float *, int, int, cudaStream_t);
 template cudaError_t launch_stage<double, false>(const GridInfo &, const ElemInfo *, const double *, const double *, const double *, const double *, double *, double *, double, int, int, int, int, cudaStream_t);
 template cudaError_t launch_stage<float, true>(const GridInfo &, const ElemInfo *, const float *, const float *, const float *, const double *, float *, double *, double, int, int, int, int, cudaStream_t);
-template cudaError_t launch_trace<double>(const GridInfo &, const double *, size_t, const double *, TraceSink *, int, double *, cudaStream_t);
+template cudaError_t launch_trace<double>(const GridInfo &, const double *, size_t, const double *, TraceSink *, int, double *, cudaStream_t, const double *);
 template cudaError_t launch_dipole<double>(const GridInfo &, double *, double *, const int *, int, const double *, int, double, cudaStream_t);
 template cudaError_t launch_dipole<float>(const GridInfo &, float *, double *, const int *, int, const double *, int, double, cudaStream_t);
 template cudaError_t launch_from_canonical<double>(const GridInfo &, const double *, double *, double *, int, int, cudaStream_t, int *);

@@ -31,7 +31,7 @@ EXPORTED = [
     "qhfpe_kernel_timing", "qhfpe_kernel_timing_read", "qhfpe_potential_term_static",
     "qhfpe_closure_collect", "qhfpe_closure_load", "qhfpe_closure_coefficients", "qhfpe_closure_loss_grad",
     "qhfpe_closure_train", "qhfpe_tile_rows", "qhfpe_wait_selftest", "qhfpe_adiabatic_marginals",
-    "qhfpe_first_order_distribution",
+    "qhfpe_first_order_distribution", "qhfpe_set_dipole_table",
 ]
 
 CLOSURE_N_WEIGHTS = 135178
@@ -92,6 +92,7 @@ def lib():
     L.qhfpe_apply_rhs.argtypes = [vp, ctypes.c_int, ctypes.c_int, vp]
     L.qhfpe_trace.argtypes = [vp, vp]
     L.qhfpe_adiabatic_marginals.argtypes = [vp, ctypes.c_int, vp]
+    L.qhfpe_set_dipole_table.argtypes = [vp, vp]
     L.qhfpe_first_order_distribution.argtypes = [vp, ctypes.c_int, ctypes.c_int, vp, ctypes.c_int, vp]
     L.qhfpe_equilibrate.argtypes = [vp, ctypes.c_long, dp]
     L.qhfpe_set_equilibrium.argtypes = [vp, vp, ctypes.c_int]
@@ -301,6 +302,16 @@ class Propagator:
         out = np.zeros(self.n_replicas, dtype=np.complex128)
         self._check(self._L.qhfpe_trace(self._h, _ptr(out)))
         return out
+
+    def set_dipole_table(self, mu_table):
+        """Coordinate-dependent dipole mu_jk(q_i + s_t), [S][S][nq][np+1] (None: the Condon dipole)."""
+        if mu_table is None:
+            self._check(self._L.qhfpe_set_dipole_table(self._h, None))
+            return
+        T = np.ascontiguousarray(mu_table, dtype=np.float64)
+        S = self.shape[1]
+        assert T.shape == (S, S, self.shape[3], self.shape[4] + 1)
+        self._check(self._L.qhfpe_set_dipole_table(self._h, _ptr(T)))
 
     def adiabatic_marginals(self, replica=0):
         """P^(ad)_ab(q_i) of the zeroth tier, complex [S][S][nq] (the adiabatic-basis coordinate

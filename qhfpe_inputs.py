@@ -57,6 +57,35 @@ def u_table(model):
     return np.ascontiguousarray(T)
 
 
+def function_table(model, F):
+    """T[j][k][i][t] = F[j][k](q_i + s_t) for an S x S array of functions of q (None: zero), in the
+    potential-table convention; used for coordinate-dependent (non-Condon) dipoles."""
+    S, nq, n_p = model["S"], model["nq"], model["np"]
+    q = axis(nq, model["q_min"], model["q_max"])
+    s = half_offsets(n_p, model["p_min"], model["p_max"])
+    pts = q[:, None] + s[None, :]
+    T = np.zeros((S, S, nq, n_p + 1), dtype=np.float64)
+    for j in range(S):
+        for k in range(S):
+            if F[j][k] is not None:
+                T[j, k] = F[j][k](pts)
+    return np.ascontiguousarray(T)
+
+
+def linear_dipole(model, slope=0.1, q_ref=0.0):
+    """A coordinate-dependent transition dipole mu_0j(q) = mu_j0(q) = mu_0j * (1 + slope (q - q_ref))
+    (a Herzberg-Teller-like linear dependence), zero elsewhere, on the model's Condon matrix."""
+    S = model["S"]
+    mu = np.asarray(model["mu"], dtype=np.float64)
+    F = [[None] * S for _ in range(S)]
+    for j in range(S):
+        for k in range(S):
+            if mu[j, k] != 0.0:
+                c = float(mu[j, k])
+                F[j][k] = (lambda c: (lambda q: c * (1.0 + slope * (np.asarray(q) - q_ref))))(c)
+    return F
+
+
 def _const(c):
     return lambda q: np.full(np.shape(q), float(c))
 
