@@ -67,6 +67,7 @@ struct TraceSink {
     double *base;   // [n_rep][stride] complex
     long stride;    // complex numbers per replica
     long counter;
+    int done;       // blocks of the running reduction that have finished (0 between launches)
 };
 
 enum { QH_KIND_STAGE = 0, QH_KIND_POT = 1, QH_KIND_AUX = 2, QH_KINDS = 3 };

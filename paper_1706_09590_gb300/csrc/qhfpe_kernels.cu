@@ -342,11 +342,13 @@ trace_partial_kernel(GridInfo g, const T *__restrict__ state, size_t rep_stride,
 __global__ void trace_finish_kernel(GridInfo g, const double *__restrict__ partial, int n_chunks, TraceSink *sink,
                                     int advance)
 {
-    // one warp per replica: lanes sum strided chunk partials, then a fixed butterfly over the lanes
-    // (the same order on every call, so the result is reproducible bit for bit)
+    // one warp per replica, replicas spread over the blocks: lanes sum strided chunk partials, then a
+    // fixed butterfly over the lanes (the same order on every call, so the result is reproducible bit
+    // for bit)
     const long slot = sink->counter;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, n_warps = blockDim.x >> 5;
-    for (int rep = warp; rep < g.n_rep; rep += n_warps) {
+    const int lane = threadIdx.x & 31, warps = blockDim.x >> 5;
+    const int n_warps = warps * gridDim.x;
+    for (int rep = blockIdx.x * warps + (threadIdx.x >> 5); rep < g.n_rep; rep += n_warps) {
         double sr = 0.0, si = 0.0;
         for (int c = lane; c < n_chunks; c += 32) {
             sr += partial[2 * ((size_t)rep * n_chunks + c)];
@@ -364,7 +366,11 @@ __global__ void trace_finish_kernel(GridInfo g, const double *__restrict__ parti
         }
     }
     __syncthreads();
-    if (advance && threadIdx.x == 0) sink->counter = slot + 1;
+    // the last block to finish advances the slot; every block read it before taking its ticket
+    if (threadIdx.x == 0 && atomicAdd(&sink->done, 1) == (int)gridDim.x - 1) {
+        sink->done = 0;
+        if (advance) sink->counter = slot + 1;
+    }
 }
 
 __global__ void advance_kernel(TraceSink *sink) { sink->counter += 1; }
@@ -614,7 +620,10 @@ cudaError_t launch_trace(const GridInfo &g, const T *state, size_t rep_stride, c
     trace_partial_kernel<T><<<dim3(nc, g.n_rep), 256, 0, st>>>(g, state, rep_stride, mu_dev, mu_q, partial, nc);
     cudaError_t err = cudaGetLastError();
     if (err != cudaSuccess) return err;
-    trace_finish_kernel<<<1, 512, 0, st>>>(g, partial, nc, sink, advance);
+    const int warps = 8;  // 256 threads, one warp per replica
+    int nb = (g.n_rep + warps - 1) / warps;
+    if (nb > 304) nb = 304;
+    trace_finish_kernel<<<nb, 32 * warps, 0, st>>>(g, partial, nc, sink, advance);
     return cudaGetLastError();
 }
 
