@@ -73,3 +73,26 @@ def linear_response(O, W_eq, mu_table, n_t):
         X, _ = O.step(X, 1)
         out[n] = 1j * trace(X, mu_table, O.dq, O.dp)
     return out
+
+
+def first_order_distribution(O, W_eq, mu_table, n_t1, t1_stride, omega):
+    """W'(omega) = i [mu^-> F(omega) - mu^<- F(-omega)], F(omega) = sum_a w_a e^{i omega t_a} X(t_a),
+    X(t) = G(t) mu^x W_eq, with the coordinate-dependent dipole (trapezoid weights on t_a = a t1_stride
+    dt, n_t1 >= 2); propagation by the oracle's RK4 O.step."""
+    assert n_t1 >= 2
+    dt1 = t1_stride * O.dt
+    wts = np.full(n_t1, dt1)
+    wts[0] *= 0.5
+    wts[-1] *= 0.5
+    omega = np.asarray(omega, dtype=np.float64)
+    X = apply_dipole(W_eq, mu_table, COMMUTATOR)
+    Fp = np.zeros((len(omega),) + X.shape, dtype=np.complex128)
+    Fm = np.zeros_like(Fp)
+    for a in range(n_t1):
+        if a > 0:
+            X, _ = O.step(X, t1_stride)
+        for k, om in enumerate(omega):
+            Fp[k] += wts[a] * np.exp(1j * om * a * dt1) * X
+            Fm[k] += wts[a] * np.exp(-1j * om * a * dt1) * X
+    return np.stack([1j * (apply_dipole(Fp[k], mu_table, LEFT) - apply_dipole(Fm[k], mu_table, RIGHT))
+                     for k in range(len(omega))])

@@ -1338,7 +1338,26 @@ qhfpe_status qhfpe_first_order_distribution(qhfpe_t *h, int n_t1, int t1_stride,
         if ((r = get_to_canonical(h, *B, B->y, B->y0, x.p, 0)) != QHFPE_OK) return r;
         QH_CK(h, launch_fourier_accumulate(x.p, n, coef.p + (size_t)a * 2 * n_omega, n_omega, acc_c.p, acc_s.p, st));
     }
-    QH_CK(h, launch_first_order_combine(M.S, B->g.blk, M.n_elem, n_omega, M.mu, acc_c.p, acc_s.p, res.p, st));
+    if (!M.noncondon) {
+        QH_CK(h, launch_first_order_combine(M.S, B->g.blk, M.n_elem, n_omega, M.mu, acc_c.p, acc_s.p, res.p, st));
+    } else {
+        // coordinate-dependent dipole: mu^-> and mu^<- are p-convolutions, applied through the batch's
+        // dipole path to F(omega) = A_c + i A_s and F(-omega) = A_c - i A_s, then W' = i (mu^-> F(omega)
+        // - mu^<- F(-omega)); x holds each input, out_w first the left part
+        for (int w = 0; w < n_omega; ++w) {
+            const double *ac = acc_c.p + 2 * n * w, *as = acc_s.p + 2 * n * w;
+            double *out_w = res.p + 2 * n * w;
+            QH_CK(h, launch_complex_combine(ac, as, 1.0, 0.0, 0.0, 1.0, x.p, n, st));
+            if ((r = set_from_canonical(h, *B, x.p, 0, 1)) != QHFPE_OK) return r;
+            if ((r = apply_dipole_prop(h, *B, QHFPE_LEFT, nullptr, 1, 1.0)) != QHFPE_OK) return r;
+            if ((r = get_to_canonical(h, *B, B->y, B->y0, out_w, 0)) != QHFPE_OK) return r;
+            QH_CK(h, launch_complex_combine(ac, as, 1.0, 0.0, 0.0, -1.0, x.p, n, st));
+            if ((r = set_from_canonical(h, *B, x.p, 0, 1)) != QHFPE_OK) return r;
+            if ((r = apply_dipole_prop(h, *B, QHFPE_RIGHT, nullptr, 1, 1.0)) != QHFPE_OK) return r;
+            if ((r = get_to_canonical(h, *B, B->y, B->y0, x.p, 0)) != QHFPE_OK) return r;
+            QH_CK(h, launch_complex_combine(out_w, x.p, 0.0, 1.0, 0.0, -1.0, out_w, n, st));
+        }
+    }
     QH_CK(h, cudaMemcpyAsync(out, res.p, 2 * n * n_omega * sizeof(double), cudaMemcpyDeviceToHost, st));
     QH_CK(h, cudaStreamSynchronize(st));
     return check_timeout(h);

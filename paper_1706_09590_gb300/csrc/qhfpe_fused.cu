@@ -18,7 +18,7 @@
 
 namespace {
 
-constexpr int FTHREADS = 256;
+constexpr int FTHREADS = 128;
 
 template <typename T> struct V2;
 template <> struct V2<float> { using type = float2; };
@@ -306,8 +306,10 @@ struct StageScalars {
     T inv12dp, fkin, fdelta, fterm, r0, h;
 };
 template <typename T, int NP, int S, bool MIXED>
-// FP32: three blocks per SM (80 registers); two for NP = 256, whose wider rows need more registers.
-__global__ void __launch_bounds__(FTHREADS, sizeof(T) == 4 ? (NP >= 256 ? 2 : 3) : 1)
+// 128-thread blocks (measured faster than 256: more independent blocks per SM keep phase A and phase B
+// of different blocks overlapping, and each barrier stalls four warps).  FP32: six blocks per SM (80
+// registers); four for NP = 256, whose wider rows need more registers.
+__global__ void __launch_bounds__(FTHREADS, sizeof(T) == 4 ? (NP >= 256 ? 4 : 6) : 2)
 fused_stage_kernel(GridInfo g, const ElemInfo *__restrict__ elems, FusedTables<T> tab, StageScalars<T> sc, const T *__restrict__ v_in,
                    const T *y, const double *y0, T *v_out, double *y0_out, double h, int mode, int terms, int rep0,
                    int n_rep, int tq, const T *__restrict__ Pg)
@@ -387,7 +389,7 @@ fused_stage_kernel(GridInfo g, const ElemInfo *__restrict__ elems, FusedTables<T
         }
         __syncthreads();
         fft_all<NP, true>(X, rows * S2, tw);
-        constexpr int MV = S >= 3 ? 1 : (S == 2 ? 2 : 4);  // modes per thread (vector table loads)
+        constexpr int MV = S >= 3 ? (NP > FTHREADS ? 2 : 1) : (S == 2 ? 2 : 4);  // modes per thread (vector table loads)
         static_assert(FTHREADS % (NP / MV) == 0, "mixing positions");
         const int pos0 = (threadIdx.x % (NP / MV)) * MV;
         for (int r = threadIdx.x / (NP / MV); r < rows; r += FTHREADS / (NP / MV)) {

@@ -155,6 +155,9 @@ cudaError_t launch_marginals(const GridInfo &g, const double *tier0, const doubl
 // this sample) and the dipole combination i [mu^-> (A_c + i A_s) - mu^<- (A_c - i A_s)].
 cudaError_t launch_fourier_accumulate(const double *x, size_t n, const double *cs, int n_omega, double *acc_c,
                                       double *acc_s, cudaStream_t st);
+// out = (ar + i ai) a + (br + i bi) b for n complex values (canonical states)
+cudaError_t launch_complex_combine(const double *a, const double *b, double ar, double ai, double br, double bi,
+                                   double *out, size_t n, cudaStream_t st);
 cudaError_t launch_first_order_combine(int S, size_t blk, int n_elem, int n_omega, const double *mu,
                                        const double *acc_c, const double *acc_s, double *out, cudaStream_t st);
 cudaError_t launch_norm2(const double *x, size_t n, double *out_dev, cudaStream_t st);

@@ -813,6 +813,25 @@ __global__ void first_order_combine_kernel(int S, size_t blk, int n_elem, int n_
     }
 }
 
+// out = (ar + i ai) a + (br + i bi) b over n complex values
+__global__ void complex_combine_kernel(const double *__restrict__ a, const double *__restrict__ b, double ar, double ai,
+                                       double br, double bi, double *__restrict__ out, size_t n)
+{
+    for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < n; idx += (size_t)gridDim.x * blockDim.x) {
+        const double xr = a[2 * idx], xi = a[2 * idx + 1], yr = b[2 * idx], yi = b[2 * idx + 1];
+        out[2 * idx] = ar * xr - ai * xi + br * yr - bi * yi;
+        out[2 * idx + 1] = ar * xi + ai * xr + br * yi + bi * yr;
+    }
+}
+
+cudaError_t launch_complex_combine(const double *a, const double *b, double ar, double ai, double br, double bi,
+                                   double *out, size_t n, cudaStream_t st)
+{
+    const long blocks = (long)std::min<size_t>((n + 255) / 256, 152 * 16);
+    complex_combine_kernel<<<(unsigned)std::max(blocks, 1L), 256, 0, st>>>(a, b, ar, ai, br, bi, out, n);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_fourier_accumulate(const double *x, size_t n, const double *cs, int n_omega, double *acc_c,
                                       double *acc_s, cudaStream_t st)
 {

@@ -116,3 +116,20 @@ def test_argument_checks():
     with pytest.raises(QhfpeError):
         P.set_dipole_table(bad)
     P.close()
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-10), ("mixed", 1e-5)])
+def test_first_order_distribution_with_a_coordinate_dependent_dipole(precision, tol):
+    m = qi.harmonic_two_state(nq=32, n_p=32, depth=2)
+    O = oracle.Oracle(m)
+    Weq, _ = O.equilibrate(200)
+    T = qi.function_table(m, qi.linear_dipole(m, slope=0.25))
+    omega = np.array([9.5, -9.5, 11.0])
+    ref = nc.first_order_distribution(O, Weq, T, 10, 4, omega)
+    P = _P(m, precision)
+    P.set_dipole_table(T)
+    P.set_equilibrium(Weq)
+    got = P.first_order_distribution(10, 4, omega)
+    for k in range(len(omega)):
+        assert rel(got[k], ref[k]) < tol, (precision, omega[k], rel(got[k], ref[k]))
+    P.close()

@@ -89,3 +89,16 @@ def test_constant_dipole_response_equals_condon_response():
     R_nc = nc.linear_response(O, Weq, qi.function_table(m, F), 30)
     R_c = O.linear_response(Weq, 30)
     assert np.linalg.norm(R_nc - R_c) <= 1e-12 * np.linalg.norm(R_c)
+
+
+def test_constant_dipole_first_order_distribution_equals_condon():
+    m = qi.harmonic_two_state(nq=16, n_p=16, depth=1)
+    O = oracle.Oracle(m)
+    Weq, _ = O.equilibrate(80)
+    mu = np.asarray(m["mu"], dtype=np.float64)
+    F = [[(lambda c: (lambda q: np.full_like(np.asarray(q, dtype=np.float64), c)))(mu[j, k]) for k in range(2)]
+         for j in range(2)]
+    om = [9.0, -9.0]
+    a = nc.first_order_distribution(O, Weq, qi.function_table(m, F), 6, 3, om)
+    b = O.first_order_distribution(Weq, 6, 3, om)
+    assert np.linalg.norm(a - b) <= 1e-12 * np.linalg.norm(b)
