@@ -307,31 +307,34 @@ pot_tc_kernel(GridInfo g, const float *__restrict__ v, float *__restrict__ P, co
                 i = (int)(rest % g.nq);
             }
             const int jj = pr / S, kk = pr % S;
+            // this row's 32 table entries of slice s, as 16-byte vectors (zero for rows past the end)
+            auto load_tables = [&](int s, float *td, float *tl, float *tr) {
+                const int c0 = s * 64 + grp * 32;
+                const float4 *pd = reinterpret_cast<const float4 *>(tD + ((size_t)pr * g.nq + i) * NP + c0);
+                const float4 *pl = reinterpret_cast<const float4 *>(
+                    tL + ((size_t)(jj * S + (S > 1 ? 1 - jj : 0)) * g.nq + i) * NP + c0);
+                const float4 *pq = reinterpret_cast<const float4 *>(
+                    tR + ((size_t)((S > 1 ? 1 - kk : 0) * S + kk) * g.nq + i) * NP + c0);
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    const float4 a = valid ? pd[q] : make_float4(0.f, 0.f, 0.f, 0.f);
+                    td[4 * q] = a.x; td[4 * q + 1] = a.y; td[4 * q + 2] = a.z; td[4 * q + 3] = a.w;
+                    if (S > 1) {
+                        const float4 b = valid ? pl[q] : make_float4(0.f, 0.f, 0.f, 0.f);
+                        const float4 c = valid ? pq[q] : make_float4(0.f, 0.f, 0.f, 0.f);
+                        tl[4 * q] = b.x; tl[4 * q + 1] = b.y; tl[4 * q + 2] = b.z; tl[4 * q + 3] = b.w;
+                        tr[4 * q] = c.x; tr[4 * q + 1] = c.y; tr[4 * q + 2] = c.z; tr[4 * q + 3] = c.w;
+                    }
+                }
+            };
+            float td[32], tl[32], tr[32];
+            load_tables(0, td, tl, tr);  // independent of D: in flight while the forward MMAs finish
             free_buf((sub - 1) & 1);  // the last forward commit: every forward MMA has completed
             ok = __syncthreads_and(ok);
             fence_after();
             for (int s = 0; s < KA && ok; ++s) {
                 const int c0 = s * 64 + grp * 32;  // 32 modes of this warp
-                // this row's 32 table entries, as 16-byte vectors
-                float td[32], tl[32], tr[32];
-                {
-                    const float4 *pd = reinterpret_cast<const float4 *>(tD + ((size_t)pr * g.nq + i) * NP + c0);
-                    const float4 *pl = reinterpret_cast<const float4 *>(
-                        tL + ((size_t)(jj * S + (S > 1 ? 1 - jj : 0)) * g.nq + i) * NP + c0);
-                    const float4 *pq = reinterpret_cast<const float4 *>(
-                        tR + ((size_t)((S > 1 ? 1 - kk : 0) * S + kk) * g.nq + i) * NP + c0);
-#pragma unroll
-                    for (int q = 0; q < 8; ++q) {
-                        const float4 a = valid ? pd[q] : make_float4(0.f, 0.f, 0.f, 0.f);
-                        td[4 * q] = a.x; td[4 * q + 1] = a.y; td[4 * q + 2] = a.z; td[4 * q + 3] = a.w;
-                        if (S > 1) {
-                            const float4 b = valid ? pl[q] : make_float4(0.f, 0.f, 0.f, 0.f);
-                            const float4 c = valid ? pq[q] : make_float4(0.f, 0.f, 0.f, 0.f);
-                            tl[4 * q] = b.x; tl[4 * q + 1] = b.y; tl[4 * q + 2] = b.z; tl[4 * q + 3] = b.w;
-                            tr[4 * q] = c.x; tr[4 * q + 1] = c.y; tr[4 * q + 2] = c.z; tr[4 * q + 3] = c.w;
-                        }
-                    }
-                }
+                if (s > 0) load_tables(s, td, tl, tr);
                 float dr[32], di[32];
                 tmem_load32(d_re + lane_off + c0, dr);
                 tmem_load32(d_im + lane_off + c0, di);
