@@ -242,8 +242,9 @@ qhfpe_status qhfpe_kernel_timing(qhfpe_t *h, int enable);
 qhfpe_status qhfpe_wait_selftest(qhfpe_t *h, int release, int limit_ms);
 /* Tile of the fused right-hand-side kernel (q rows per block) picked by the autotuner for the
  * handle's replicas: timed with CUDA events on the first propagation (0 before it, or when the
- * shape has no fused kernel).  The environment variable QHFPE_TILE_ROWS, when it holds a power of two
- * within the kernel's shared-memory limit, replaces the timing with that tile. */
+ * shape has no fused kernel; candidates 1, 2, 3, 4, 5, 6, 8, 12, 16 rows up to the kernel's
+ * shared-memory limit, a power of two).  The environment variable QHFPE_TILE_ROWS, when it holds a
+ * height from 1 to that limit, replaces the timing with that tile. */
 qhfpe_status qhfpe_tile_rows(const qhfpe_t *h, int *rows);
 qhfpe_status qhfpe_kernel_timing_read(qhfpe_t *h, long *launches, double *total_ms, int n_kinds);
 

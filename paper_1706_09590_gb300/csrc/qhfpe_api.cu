@@ -668,11 +668,11 @@ qhfpe_status autotune(qhfpe *h, Prop &P)
     cudaStream_t st = h->stream;
     const int esize = P.mixed ? 4 : 8;
     const int tmax = std::min(fused_max_rows(P.g.np, P.g.S, esize), P.g.nq);
-    // QHFPE_TILE_ROWS pins the tile (a power of two up to the limit) instead of timing the candidates,
-    // e.g. to profile the launch configuration that a timed run chose
+    // QHFPE_TILE_ROWS pins the tile (1 .. the limit) instead of timing the candidates, e.g. to profile
+    // the launch configuration that a timed run chose
     if (const char *env = std::getenv("QHFPE_TILE_ROWS")) {
         const int t = std::atoi(env);
-        if (t >= 1 && t <= tmax && (t & (t - 1)) == 0) {
+        if (t >= 1 && t <= tmax) {
             P.tq = t;
             return QHFPE_OK;
         }
@@ -682,7 +682,11 @@ qhfpe_status autotune(qhfpe *h, Prop &P)
     QH_CK(h, cudaEventCreate(&b));
     float best = 1e30f;
     int best_tq = 1;
-    for (int tq = 1; tq <= tmax; tq *= 2) {
+    // heights between the powers of two as well: the block count (tiles x elements x replicas) against
+    // the blocks resident at once decides how full the last wave is
+    static const int cand[] = {1, 2, 3, 4, 5, 6, 8, 12, 16};
+    for (int tq : cand) {
+        if (tq > tmax) break;
         float ms = 0.f;
         for (int rep = 0; rep < 4; ++rep) {
             if (rep == 1) QH_CK(h, cudaEventRecord(a, st));

@@ -307,9 +307,10 @@ struct StageScalars {
 };
 template <typename T, int NP, int S, bool MIXED>
 // 128-thread blocks (measured faster than 256: more independent blocks per SM keep phase A and phase B
-// of different blocks overlapping, and each barrier stalls four warps).  FP32: six blocks per SM (80
-// registers); four for NP = 256, whose wider rows need more registers.
-__global__ void __launch_bounds__(FTHREADS, sizeof(T) == 4 ? (NP >= 256 ? 4 : 6) : 2)
+// of different blocks overlapping, and each barrier stalls four warps).  The kernel waits mostly on L2
+// loads, so resident warps count: FP32 with one or two states runs seven blocks per SM (72 registers;
+// measured 5 % faster than six at 80), three states six (seven would spill), NP = 256 four (wider rows).
+__global__ void __launch_bounds__(FTHREADS, sizeof(T) == 4 ? (NP >= 256 ? 4 : (S >= 3 ? 6 : 7)) : 2)
 fused_stage_kernel(GridInfo g, const ElemInfo *__restrict__ elems, FusedTables<T> tab, StageScalars<T> sc, const T *__restrict__ v_in,
                    const T *y, const double *y0, T *v_out, double *y0_out, double h, int mode, int terms, int rep0,
                    int n_rep, int tq, const T *__restrict__ Pg)

@@ -110,7 +110,7 @@ TILE_MODELS = {
 }
 
 
-@pytest.mark.parametrize("tile", [1, 2, 4, 8, 16])
+@pytest.mark.parametrize("tile", [1, 2, 3, 4, 6, 8, 16])
 @pytest.mark.parametrize("name", list(TILE_MODELS))
 @pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("mixed", 2e-5)])
 def test_rhs_every_tile(name, tile, precision, tol, monkeypatch):
