@@ -248,51 +248,64 @@ pot_tc_kernel(GridInfo g, const float *__restrict__ v, float *__restrict__ P, co
     };
 
     const long n_tiles = (total_rows + TILE_M - 1) / TILE_M;
+    // Forward operand rows: this thread's row of the tile being loaded (offset, validity) and two
+    // sub-slices of it in registers.  The first two sub-slices of a tile are requested before the
+    // previous tile writes its P rows, so that their latency overlaps that store.
+    size_t f_rb = 0;
+    bool f_valid = false;
+    float x[2][32];
+    // this thread's 32 values of sub-slice j (one plane of its row, its half of the K slice)
+    auto load = [&](int j, float *xx) {
+        if (f_valid) {
+            const float4 *p4 =
+                reinterpret_cast<const float4 *>(v + f_rb + (size_t)(j & 1) * g.blk + (j >> 1) * 64 + half * 32);
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                const float4 a = p4[q];
+                xx[4 * q] = a.x;
+                xx[4 * q + 1] = a.y;
+                xx[4 * q + 2] = a.z;
+                xx[4 * q + 3] = a.w;
+            }
+        } else {
+#pragma unroll
+            for (int q = 0; q < 32; ++q) xx[q] = 0.f;
+        }
+    };
+    auto begin_tile = [&](long tl) {
+        const long row = tl * TILE_M + row_in_tile;
+        f_rb = 0;
+        f_valid = row < total_rows;
+        if (f_valid) {
+            long rest = row;
+            const int pr = (int)(rest % S2);
+            rest /= S2;
+            const int i = (int)(rest % g.nq);
+            rest /= g.nq;
+            const int e = (int)(rest % g.n_elem);
+            const int rep = (int)(rest / g.n_elem);
+            f_rb = (size_t)rep * g.rep_stride + (size_t)e * g.elem_stride + (size_t)pr * 2 * g.blk + (size_t)i * NP;
+        }
+        load(0, x[0]);
+        if (2 * KA > 1) load(1, x[1]);
+    };
+    if (blockIdx.x < n_tiles) begin_tile(blockIdx.x);
     for (long tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x) {
         // ---- forward transform: W rows -> D, sub-slices (slice, plane) ----------------------------
         {
-            const long row = tile * TILE_M + row_in_tile;
-            size_t rb = 0;
-            const bool valid = row < total_rows;
-            if (valid) {
-                long rest = row;
-                const int pr = (int)(rest % S2);
-                rest /= S2;
-                const int i = (int)(rest % g.nq);
-                rest /= g.nq;
-                const int e = (int)(rest % g.n_elem);
-                const int rep = (int)(rest / g.n_elem);
-                rb = (size_t)rep * g.rep_stride + (size_t)e * g.elem_stride + (size_t)pr * 2 * g.blk + (size_t)i * NP;
-            }
-            // this thread's 32 values (one plane of its row, its half of the K slice)
-            auto load = [&](int j, float *x) {
-                if (valid) {
-                    const float4 *p4 = reinterpret_cast<const float4 *>(v + rb + (size_t)(j & 1) * g.blk +
-                                                                        (j >> 1) * 64 + half * 32);
+            // two sub-slices in flight: sub-slice j + 2 is loaded while j is split, stored and multiplied
+            // (the loop is unrolled, so x[j & 1] is a fixed register set)
 #pragma unroll
-                    for (int q = 0; q < 8; ++q) {
-                        const float4 a = p4[q];
-                        x[4 * q] = a.x;
-                        x[4 * q + 1] = a.y;
-                        x[4 * q + 2] = a.z;
-                        x[4 * q + 3] = a.w;
-                    }
-                } else {
-#pragma unroll
-                    for (int q = 0; q < 32; ++q) x[q] = 0.f;
-                }
-            };
-            float x[32];
-            load(0, x);
             for (int j = 0; j < 2 * KA; ++j) {
                 const int b = sub & 1;
                 free_buf(b);
                 char *hi = A + (size_t)b * 2 * TILE;
 #pragma unroll
-                for (int cc = 0; cc < 4; ++cc) split_store8(x + 8 * cc, hi, hi + TILE, sw128_chunk(row_in_tile, half * 4 + cc));
+                for (int cc = 0; cc < 4; ++cc)
+                    split_store8(x[j & 1] + 8 * cc, hi, hi + TILE, sw128_chunk(row_in_tile, half * 4 + cc));
                 submit(j >> 1, false, j & 1, j == 0);
                 if (!ok) break;
-                if (j + 1 < 2 * KA) load(j + 1, x);  // in flight while the tensor core works
+                if (j + 2 < 2 * KA) load(j + 2, x[j & 1]);
             }
         }
         // ---- r-space mixing per slice of modes, then that slice of the inverse transform ------------
@@ -334,7 +347,6 @@ pot_tc_kernel(GridInfo g, const float *__restrict__ v, float *__restrict__ P, co
             fence_after();
             for (int s = 0; s < KA && ok; ++s) {
                 const int c0 = s * 64 + grp * 32;  // 32 modes of this warp
-                if (s > 0) load_tables(s, td, tl, tr);
                 float dr[32], di[32];
                 tmem_load32(d_re + lane_off + c0, dr);
                 tmem_load32(d_im + lane_off + c0, di);
@@ -355,6 +367,8 @@ pot_tc_kernel(GridInfo g, const float *__restrict__ v, float *__restrict__ P, co
                     y2[0][j] = ai;  // times -i
                     y2[1][j] = -ar;
                 }
+                // the next slice's tables, in flight while this slice is stored and multiplied
+                if (s + 1 < KA) load_tables(s + 1, td, tl, tr);
 #pragma unroll
                 for (int plane = 0; plane < 2; ++plane) {
                     const int b = sub & 1;
@@ -370,6 +384,7 @@ pot_tc_kernel(GridInfo g, const float *__restrict__ v, float *__restrict__ P, co
             free_buf((sub - 1) & 1);  // the last inverse commit: P is complete
             ok = __syncthreads_and(ok);
             fence_after();
+            if (ok && tile + gridDim.x < n_tiles) begin_tile(tile + gridDim.x);
             // ---- P rows to global -------------------------------------------------------------------
             if (ok) {
                 size_t rb = 0;
