@@ -143,6 +143,22 @@ __device__ __forceinline__ void split_store8(const float *x, char *hi_tile, char
     *reinterpret_cast<uint4 *>(lo_tile + off) = make_uint4(l[0], l[1], l[2], l[3]);
 }
 
+// split 4 floats into bf16 hi/lo and store them as 8 bytes each
+__device__ __forceinline__ void split_store4(const float *x, char *hi_tile, char *lo_tile, uint32_t off)
+{
+    uint32_t h[2], l[2];
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+        const __nv_bfloat16 h0 = __float2bfloat16_rn(x[2 * c]), h1 = __float2bfloat16_rn(x[2 * c + 1]);
+        const __nv_bfloat16 l0 = __float2bfloat16_rn(x[2 * c] - __bfloat162float(h0));
+        const __nv_bfloat16 l1 = __float2bfloat16_rn(x[2 * c + 1] - __bfloat162float(h1));
+        h[c] = (uint32_t)__bfloat16_as_ushort(h0) | ((uint32_t)__bfloat16_as_ushort(h1) << 16);
+        l[c] = (uint32_t)__bfloat16_as_ushort(l0) | ((uint32_t)__bfloat16_as_ushort(l1) << 16);
+    }
+    *reinterpret_cast<uint2 *>(hi_tile + off) = make_uint2(h[0], h[1]);
+    *reinterpret_cast<uint2 *>(lo_tile + off) = make_uint2(l[0], l[1]);
+}
+
 template <int NP, int S>
 __global__ void __launch_bounds__(TC_THREADS, 1)
 pot_tc_kernel(GridInfo g, const float *__restrict__ v, float *__restrict__ P, const uint4 *__restrict__ bmat,
@@ -162,10 +178,9 @@ pot_tc_kernel(GridInfo g, const float *__restrict__ v, float *__restrict__ P, co
     char *A = Bs + (size_t)KA * 4 * BT;
     uint64_t *mbar = reinterpret_cast<uint64_t *>(A + 4 * TILE);
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(mbar + 2);
+    long long *rbase_s = reinterpret_cast<long long *>(A + 4 * TILE + 64);  // [TILE_M] row offsets, -1 past the end
 
     const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
-    const int row_in_tile = t & (TILE_M - 1);   // A-load row of this thread
-    const int half = t >> 7;                    // which 32-wide half of a K slice this thread loads
     const int quad = warp & 3;                  // TMEM lane quadrant of this warp
     const int grp = warp >> 2;                  // column group of this warp in the epilogues
     const int erow = quad * 32 + lane;          // epilogue row (TMEM lane) of this thread
@@ -247,45 +262,47 @@ pot_tc_kernel(GridInfo g, const float *__restrict__ v, float *__restrict__ P, co
         ++sub;
     };
 
+    // Row order: pair fastest (the pairs of one state row sit in neighbouring TMEM lanes for the
+    // mixing), then (replica, element), then q, so that the rows of a warp share their q row and read
+    // the same few table rows in the mixing.
+    const long n_er = total_rows / ((long)g.nq * S2);  // replicas x elements
+    auto row_base = [&](long row) -> size_t {           // offset of a row's real plane in v and P
+        const int pr = (int)(row % S2);
+        const long rest = row / S2;
+        const long er = rest % n_er;
+        const int i = (int)(rest / n_er);
+        const int e = (int)(er % g.n_elem);
+        const long rep = er / g.n_elem;
+        return (size_t)rep * g.rep_stride + (size_t)e * g.elem_stride + (size_t)pr * 2 * g.blk + (size_t)i * NP;
+    };
     const long n_tiles = (total_rows + TILE_M - 1) / TILE_M;
-    // Forward operand rows: this thread's row of the tile being loaded (offset, validity) and two
-    // sub-slices of it in registers.  The first two sub-slices of a tile are requested before the
-    // previous tile writes its P rows, so that their latency overlaps that store.
-    size_t f_rb = 0;
-    bool f_valid = false;
+    // Forward operand: warp w loads rows 16w .. 16w + 15 of the tile, two per instruction (lanes 0-15
+    // one row, lanes 16-31 the next), four consecutive floats per lane, so that each request covers two
+    // 256-byte row segments; two sub-slices in registers.  The first two sub-slices of a tile are
+    // requested before the previous tile writes its P rows, so that their latency overlaps that store.
+    const int sl = lane & 15;
     float x[2][32];
-    // this thread's 32 values of sub-slice j (one plane of its row, its half of the K slice)
+    // sub-slice j (plane j & 1, K slice j >> 1) of this thread's 8 rows
     auto load = [&](int j, float *xx) {
-        if (f_valid) {
-            const float4 *p4 =
-                reinterpret_cast<const float4 *>(v + f_rb + (size_t)(j & 1) * g.blk + (j >> 1) * 64 + half * 32);
+        const size_t off = (size_t)(j & 1) * g.blk + (size_t)(j >> 1) * 64 + (size_t)sl * 4;
 #pragma unroll
-            for (int q = 0; q < 8; ++q) {
-                const float4 a = p4[q];
-                xx[4 * q] = a.x;
-                xx[4 * q + 1] = a.y;
-                xx[4 * q + 2] = a.z;
-                xx[4 * q + 3] = a.w;
-            }
-        } else {
-#pragma unroll
-            for (int q = 0; q < 32; ++q) xx[q] = 0.f;
+        for (int u = 0; u < 8; ++u) {
+            const long long rb = rbase_s[warp * 16 + 2 * u + (lane >> 4)];
+            float4 a = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (rb >= 0) a = *reinterpret_cast<const float4 *>(v + (size_t)rb + off);
+            xx[4 * u] = a.x;
+            xx[4 * u + 1] = a.y;
+            xx[4 * u + 2] = a.z;
+            xx[4 * u + 3] = a.w;
         }
     };
+    // (called by all threads together)
     auto begin_tile = [&](long tl) {
-        const long row = tl * TILE_M + row_in_tile;
-        f_rb = 0;
-        f_valid = row < total_rows;
-        if (f_valid) {
-            long rest = row;
-            const int pr = (int)(rest % S2);
-            rest /= S2;
-            const int i = (int)(rest % g.nq);
-            rest /= g.nq;
-            const int e = (int)(rest % g.n_elem);
-            const int rep = (int)(rest / g.n_elem);
-            f_rb = (size_t)rep * g.rep_stride + (size_t)e * g.elem_stride + (size_t)pr * 2 * g.blk + (size_t)i * NP;
+        if (t < TILE_M) {
+            const long row = tl * TILE_M + t;
+            rbase_s[t] = row < total_rows ? (long long)row_base(row) : -1ll;
         }
+        __syncthreads();
         load(0, x[0]);
         if (2 * KA > 1) load(1, x[1]);
     };
@@ -301,8 +318,9 @@ pot_tc_kernel(GridInfo g, const float *__restrict__ v, float *__restrict__ P, co
                 free_buf(b);
                 char *hi = A + (size_t)b * 2 * TILE;
 #pragma unroll
-                for (int cc = 0; cc < 4; ++cc)
-                    split_store8(x[j & 1] + 8 * cc, hi, hi + TILE, sw128_chunk(row_in_tile, half * 4 + cc));
+                for (int u = 0; u < 8; ++u)
+                    split_store4(x[j & 1] + 4 * u, hi, hi + TILE,
+                                 sw128_chunk(warp * 16 + 2 * u + (lane >> 4), sl >> 1) + (uint32_t)(sl & 1) * 8u);
                 submit(j >> 1, false, j & 1, j == 0);
                 if (!ok) break;
                 if (j + 2 < 2 * KA) load(j + 2, x[j & 1]);
@@ -314,10 +332,8 @@ pot_tc_kernel(GridInfo g, const float *__restrict__ v, float *__restrict__ P, co
             const bool valid = row < total_rows;
             int pr = 0, i = 0;
             if (valid) {
-                long rest = row;
-                pr = (int)(rest % S2);
-                rest /= S2;
-                i = (int)(rest % g.nq);
+                pr = (int)(row % S2);
+                i = (int)(row / S2 / n_er);
             }
             const int jj = pr / S, kk = pr % S;
             // this row's 32 table entries of slice s, as 16-byte vectors (zero for rows past the end)
@@ -387,14 +403,7 @@ pot_tc_kernel(GridInfo g, const float *__restrict__ v, float *__restrict__ P, co
             if (ok && tile + gridDim.x < n_tiles) begin_tile(tile + gridDim.x);
             // ---- P rows to global -------------------------------------------------------------------
             if (ok) {
-                size_t rb = 0;
-                if (valid) {
-                    long rest = row / S2 / g.nq;
-                    const int e = (int)(rest % g.n_elem);
-                    const int rep = (int)(rest / g.n_elem);
-                    rb = (size_t)rep * g.rep_stride + (size_t)e * g.elem_stride + (size_t)pr * 2 * g.blk +
-                         (size_t)i * NP;
-                }
+                const size_t rb = valid ? row_base(row) : 0;
                 for (int c0 = grp * (NP / 2); c0 < (grp + 1) * (NP / 2); c0 += 32) {
                     float pr_[32], pi_[32];
                     tmem_load32(p_re + lane_off + c0, pr_);
@@ -431,7 +440,8 @@ pot_tc_kernel(GridInfo g, const float *__restrict__ v, float *__restrict__ P, co
 template <int NP, int S>
 size_t tc_smem_bytes()
 {
-    return (size_t)(NP / 64) * 4 * NP * 64 * 2 + 4 * (size_t)TILE_M * 64 * 2 + 64 + 1024;  // B, 2 A buffers, barriers
+    // B, 2 A buffers, barriers, forward row offsets, alignment slack
+    return (size_t)(NP / 64) * 4 * NP * 64 * 2 + 4 * (size_t)TILE_M * 64 * 2 + 64 + 8 * TILE_M + 1024;
 }
 
 template <int NP, int S>
