@@ -179,6 +179,7 @@ pot_tc_kernel(GridInfo g, const float *__restrict__ v, float *__restrict__ P, co
     uint64_t *mbar = reinterpret_cast<uint64_t *>(A + 4 * TILE);
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(mbar + 2);
     long long *rbase_s = reinterpret_cast<long long *>(A + 4 * TILE + 64);  // [TILE_M] row offsets, -1 past the end
+    long long *pbase_s = rbase_s + TILE_M;  // the same for the tile whose P rows are being written
 
     const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
     const int quad = warp & 3;                  // TMEM lane quadrant of this warp
@@ -401,22 +402,43 @@ pot_tc_kernel(GridInfo g, const float *__restrict__ v, float *__restrict__ P, co
             ok = __syncthreads_and(ok);
             fence_after();
             if (ok && tile + gridDim.x < n_tiles) begin_tile(tile + gridDim.x);
-            // ---- P rows to global -------------------------------------------------------------------
+            // ---- P rows to global, through shared memory ---------------------------------------------
+            // Each pass stages 32 columns of each warp group's half, both planes, of all 128 rows in the
+            // (now idle) A buffers, as [group][plane][row][8 chunks of 16 B] with the chunk index XOR-ed
+            // by row & 7 (conflict-free both ways); then every warp writes four 128-byte row segments
+            // per instruction.
             if (ok) {
-                const size_t rb = valid ? row_base(row) : 0;
-                for (int c0 = grp * (NP / 2); c0 < (grp + 1) * (NP / 2); c0 += 32) {
-                    float pr_[32], pi_[32];
-                    tmem_load32(p_re + lane_off + c0, pr_);
-                    tmem_load32(p_im + lane_off + c0, pi_);
-                    if (valid) {
-                        float4 *o_r = reinterpret_cast<float4 *>(P + rb + c0);
-                        float4 *o_i = reinterpret_cast<float4 *>(P + rb + g.blk + c0);
+                if (grp == 0) pbase_s[erow] = valid ? (long long)row_base(row) : -1ll;
+                float *stg = reinterpret_cast<float *>(A);
+#pragma unroll
+                for (int it = 0; it < NP / 64; ++it) {
+                    const int c0 = grp * (NP / 2) + 32 * it;
+                    {
+                        float pr_[32], pi_[32];
+                        tmem_load32(p_re + lane_off + c0, pr_);
+                        tmem_load32(p_im + lane_off + c0, pi_);
+                        float4 *s_r = reinterpret_cast<float4 *>(stg + ((grp * 2 + 0) * TILE_M + erow) * 32);
+                        float4 *s_i = reinterpret_cast<float4 *>(stg + ((grp * 2 + 1) * TILE_M + erow) * 32);
 #pragma unroll
                         for (int q = 0; q < 8; ++q) {
-                            o_r[q] = make_float4(pr_[4 * q], pr_[4 * q + 1], pr_[4 * q + 2], pr_[4 * q + 3]);
-                            o_i[q] = make_float4(pi_[4 * q], pi_[4 * q + 1], pi_[4 * q + 2], pi_[4 * q + 3]);
+                            s_r[q ^ (erow & 7)] = make_float4(pr_[4 * q], pr_[4 * q + 1], pr_[4 * q + 2], pr_[4 * q + 3]);
+                            s_i[q ^ (erow & 7)] = make_float4(pi_[4 * q], pi_[4 * q + 1], pi_[4 * q + 2], pi_[4 * q + 3]);
                         }
                     }
+                    __syncthreads();
+                    const int ch = lane & 7;
+#pragma unroll 1
+                    for (int u = 0; u < 16; ++u) {
+                        const int seg = u * 32 + warp * 4 + (lane >> 3);  // (group, plane, row)
+                        const int gg = seg >> 8, pl = (seg >> 7) & 1, r = seg & (TILE_M - 1);
+                        const long long rb = pbase_s[r];
+                        if (rb >= 0) {
+                            const float4 val = reinterpret_cast<const float4 *>(stg + (size_t)seg * 32)[ch ^ (r & 7)];
+                            *reinterpret_cast<float4 *>(P + (size_t)rb + (size_t)pl * g.blk + gg * (NP / 2) + 32 * it +
+                                                        4 * ch) = val;
+                        }
+                    }
+                    __syncthreads();
                 }
             }
         }
@@ -440,8 +462,8 @@ pot_tc_kernel(GridInfo g, const float *__restrict__ v, float *__restrict__ P, co
 template <int NP, int S>
 size_t tc_smem_bytes()
 {
-    // B, 2 A buffers, barriers, forward row offsets, alignment slack
-    return (size_t)(NP / 64) * 4 * NP * 64 * 2 + 4 * (size_t)TILE_M * 64 * 2 + 64 + 8 * TILE_M + 1024;
+    // B, 2 A buffers, barriers, row offsets (forward and P), alignment slack
+    return (size_t)(NP / 64) * 4 * NP * 64 * 2 + 4 * (size_t)TILE_M * 64 * 2 + 64 + 16 * TILE_M + 1024;
 }
 
 template <int NP, int S>
