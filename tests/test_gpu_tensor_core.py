@@ -61,3 +61,22 @@ def test_linear_response_bf16x3():
     err = rel(got, ref)
     print("R1 relative L2 error (bf16x3)", err)
     assert err < 1e-4
+
+
+@pytest.mark.parametrize("name", ["np128_S2", "np64_S2"])
+def test_potential_term_replicas(name):
+    """Several replicas in one launch (tiles whose rows span replicas, elements and q rows, a ragged
+    last tile): each replica's right-hand side against the oracle on its own state."""
+    m = MODELS[name]
+    O = oracle.Oracle(m)
+    P = _P(m, n_replicas=3)
+    Ws = [qi.random_state(m, seed=90 + r) for r in range(3)]
+    for r, W in enumerate(Ws):
+        P.set_state(W, r)
+    for r in (2, 0, 1):
+        Win = P.get_state(r)
+        Win[1:] = Win[1:].astype(np.complex64).astype(np.complex128)
+        err = rel(P.apply_rhs(r, oracle.POTENTIAL), O.rhs(Win, oracle.POTENTIAL))
+        assert err < 2e-4, (name, r, err)
+        assert rel(P.apply_rhs(r), O.rhs(Win)) < 2e-4, (name, r)
+    P.close()
