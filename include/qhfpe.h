@@ -139,6 +139,30 @@ qhfpe_status qhfpe_fork(qhfpe_t *h, int src, const int *dst, int n);
  * first step and after each step (FP64 sums, Eqs. (R1), (R3)). */
 qhfpe_status qhfpe_step(qhfpe_t *h, long n_steps, double *trace_out);
 
+/* ---- Heterogeneous batch ------------------------------------------------------------------------
+ * Several handles advanced together: each Horner stage of the RK4 step (Sec. III's 4th-order
+ * integrator applied to Eq. (heom)) of every member is ONE launch of the fused stage kernel, whose
+ * blocks read their member's description (grid, tables, buffers, dt) from a device table, and whole
+ * steps are replayed from captured CUDA graphs.  Members may differ in nq, the q and p ranges, the
+ * surfaces, the bath (eta, gamma, beta, Matsubara count, delta-term), the depth, the closure
+ * (TRUNCATE or TERMINATOR), periodic_q, dt and n_replicas; they must share np, n_states and the
+ * precision (QHFPE_FP64 or QHFPE_MIXED; not the tensor-core form, not the learned closure), and np and
+ * n_states must have a fused kernel (np in {32, 64, 128, 256}, n_states <= 3).  Each member's result
+ * is that of qhfpe_step on the member alone (the same per-cell arithmetic).
+ * members: host array of n distinct handles; the batch keeps the pointers, does not own the handles,
+ * and must be destroyed before any of them.  Errors are reported through members[0]
+ * (qhfpe_last_error); EINVAL for mismatched or repeated members, EUNSUPPORTED for the forms above. */
+typedef struct qhfpe_batch qhfpe_batch_t;
+qhfpe_status qhfpe_batch_create(qhfpe_t *const *members, int n, qhfpe_batch_t **out);
+/* Advance every replica of every member n_steps RK4 steps (each member with its own dt), on members[0]'s
+ * stream after waiting for every member's stream.  trace_out: NULL, or a host array of n pointers, each
+ * NULL or a host complex128 [n_replicas][n_steps + 1] array receiving that member's Tr{mu W^(0)} as
+ * qhfpe_step does.  The tile height is timed on the first call (QHFPE_TILE_ROWS pins it). */
+qhfpe_status qhfpe_batch_step(qhfpe_batch_t *b, long n_steps, double *const *trace_out);
+/* Tile height (q rows per block) the batch runs with (0 before the first step). */
+qhfpe_status qhfpe_batch_tile_rows(const qhfpe_batch_t *b, int *rows);
+qhfpe_status qhfpe_batch_destroy(qhfpe_batch_t *b);
+
 /* Dipole super-operator on every hierarchy element of the listed replicas (replicas = NULL: all),
  * Sec. III (Condon: mu constant, so the p-convolution with mu(p, q) is a product). */
 qhfpe_status qhfpe_apply_dipole(qhfpe_t *h, int side, const int *replicas, int n);

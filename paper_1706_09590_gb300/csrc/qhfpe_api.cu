@@ -1706,5 +1706,250 @@ qhfpe_status qhfpe_closure_coefficients(const qhfpe_t *h, double *out)
 
 }  // extern "C"
 
+// ---- heterogeneous batch ---------------------------------------------------------------------------
+// Members are handles sharing np, S and the precision (FP64 or MIXED); every Horner stage of all of
+// them is one launch of the fused stage kernel over a device table of member descriptions (the
+// members' own buffers, tables and step sizes), and whole steps are replayed from captured graphs.
+struct qhfpe_batch {
+    std::vector<qhfpe *> mem;
+    bool mixed = false;
+    int np = 0, S = 0, tq = 0;
+    long blocks = 0;
+    void *desc = nullptr;  // device MultiMember<float or double>[n]
+    cudaGraphExec_t graphs[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};  // [chunk][trace]
+    ~qhfpe_batch()
+    {
+        for (auto &a : graphs)
+            for (auto &x : a)
+                if (x) cudaGraphExecDestroy(x);
+        if (desc) cudaFree(desc);
+    }
+};
+
+namespace {
+
+// descriptions of all members at tile height tq into b->desc (blocking copy); b->blocks set
+template <typename T>
+qhfpe_status batch_upload(qhfpe_batch *b, int tq)
+{
+    qhfpe *h0 = b->mem[0];
+    std::vector<MultiMember<T>> d(b->mem.size());
+    long blocks = 0;
+    for (size_t m = 0; m < b->mem.size(); ++m) {
+        Prop &P = *b->mem[m]->main;
+        const Model &M = *P.m;
+        MultiMember<T> &x = d[m];
+        std::memset(&x, 0, sizeof(x));
+        x.g = P.g;
+        x.elems = M.elems;
+        if constexpr (sizeof(T) == 4) x.tab = M.f32();
+        else x.tab = M.f64();
+        x.sc[0] = stage_scalars<T>(P.g, 0.0);
+        for (int k = 1; k <= 4; ++k) x.sc[k] = stage_scalars<T>(P.g, P.dt / k);
+        x.dt = P.dt;
+        x.y = (T *)P.y;
+        x.vA = (T *)P.vA;
+        x.vB = (T *)P.vB;
+        x.y0 = b->mixed ? P.y0 : nullptr;
+        x.block0 = blocks;
+        blocks += fused_blocks(P.g, tq);
+    }
+    if (blocks > 0x7fffffffL) return h0->fail(QHFPE_EUNSUPPORTED, "batch: more than 2^31 - 1 blocks per stage");
+    if (!b->desc) QH_CK(h0, cudaMalloc(&b->desc, d.size() * sizeof(MultiMember<T>)));
+    QH_CK(h0, cudaMemcpy(b->desc, d.data(), d.size() * sizeof(MultiMember<T>), cudaMemcpyHostToDevice));
+    b->blocks = blocks;
+    return QHFPE_OK;
+}
+
+qhfpe_status batch_launch(qhfpe_batch *b, int k, cudaStream_t st)
+{
+    qhfpe *h0 = b->mem[0];
+    const int n = (int)b->mem.size();
+    if (b->mixed)
+        QH_CK(h0, (launch_fused_multi<float, true>(b->np, b->S, (const MultiMember<float> *)b->desc, n, k, b->tq,
+                                                   b->blocks, st)));
+    else
+        QH_CK(h0, (launch_fused_multi<double, false>(b->np, b->S, (const MultiMember<double> *)b->desc, n, k, b->tq,
+                                                     b->blocks, st)));
+    return QHFPE_OK;
+}
+
+// the batch's tile height: every candidate evaluates every member's right-hand side (into its second
+// stage buffer, which holds no data between steps) a few times, timed with CUDA events
+qhfpe_status batch_autotune(qhfpe_batch *b, cudaStream_t st)
+{
+    qhfpe *h0 = b->mem[0];
+    int tmax = fused_max_rows(b->np, b->S, b->mixed ? 4 : 8), nq_max = 1;
+    for (qhfpe *h : b->mem) nq_max = std::max(nq_max, h->main->g.nq);
+    tmax = std::min(tmax, nq_max);
+    auto upload = [&](int tq) { return b->mixed ? batch_upload<float>(b, tq) : batch_upload<double>(b, tq); };
+    if (const char *env = std::getenv("QHFPE_TILE_ROWS")) {
+        const int t = std::atoi(env);
+        if (t >= 1 && t <= tmax) {
+            b->tq = t;
+            return upload(t);
+        }
+    }
+    cudaEvent_t e0, e1;
+    QH_CK(h0, cudaEventCreate(&e0));
+    QH_CK(h0, cudaEventCreate(&e1));
+    float best = 1e30f;
+    int best_tq = 1;
+    static const int cand[] = {1, 2, 3, 4, 5, 6, 8, 12, 16};
+    for (int tq : cand) {
+        if (tq > tmax) break;
+        qhfpe_status r = upload(tq);
+        if (r != QHFPE_OK) return r;
+        b->tq = tq;
+        float ms = 0.f;
+        for (int rep = 0; rep < 4; ++rep) {
+            if (rep == 1) QH_CK(h0, cudaEventRecord(e0, st));
+            r = batch_launch(b, 0, st);
+            if (r != QHFPE_OK) return r;
+        }
+        QH_CK(h0, cudaEventRecord(e1, st));
+        QH_CK(h0, cudaEventSynchronize(e1));
+        QH_CK(h0, cudaEventElapsedTime(&ms, e0, e1));
+        if (ms < best) {
+            best = ms;
+            best_tq = tq;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    b->tq = best_tq;
+    return upload(best_tq);
+}
+
+qhfpe_status batch_step_once(qhfpe_batch *b, bool record, cudaStream_t st)
+{
+    for (int k = 4; k >= 1; --k) {
+        qhfpe_status r = batch_launch(b, k, st);
+        if (r != QHFPE_OK) return r;
+    }
+    if (record)
+        for (qhfpe *h : b->mem) {
+            Prop &P = *h->main;
+            if (b->mixed)
+                QH_CK(h, launch_trace<double>(P.g, P.y0, P.g.tier0_rep_stride, P.m->mu, P.sink, 1, P.partial, st,
+                                              P.m->trace_mu_q()));
+            else
+                QH_CK(h, launch_trace<double>(P.g, (const double *)P.y, P.g.rep_stride, P.m->mu, P.sink, 1, P.partial,
+                                              st, P.m->trace_mu_q()));
+        }
+    return QHFPE_OK;
+}
+
+}  // namespace
+
 void qh_set_free_error(const std::string &msg) { g_create_error = msg; }
 
+
+extern "C" {
+
+qhfpe_status qhfpe_batch_create(qhfpe_t *const *members, int n, qhfpe_batch_t **out)
+{
+    if (!out || !members || n < 1) return QHFPE_EINVAL;
+    *out = nullptr;
+    qhfpe *h0 = members[0];
+    qhfpe_status r = check_handle(h0);
+    if (r != QHFPE_OK) return r;
+    std::unique_ptr<qhfpe_batch> b(new qhfpe_batch());
+    for (int m = 0; m < n; ++m) {
+        qhfpe *h = members[m];
+        if ((r = check_handle(h)) != QHFPE_OK) return h ? r : h0->fail(QHFPE_EINVAL, "batch_create: NULL member");
+        for (int a = 0; a < m; ++a)
+            if (members[a] == h) return h0->fail(QHFPE_EINVAL, "batch_create: a handle appears twice");
+        const Prop &P = *h->main;
+        if (P.tc || h->p.precision == QHFPE_MIXED_BF16X3)
+            return h0->fail(QHFPE_EUNSUPPORTED, "batch_create: the tensor-core form is not batched");
+        if (P.m->closure_slot >= 0)
+            return h0->fail(QHFPE_EUNSUPPORTED, "batch_create: the learned closure is not batched");
+        if (!P.m->fused) return h0->fail(QHFPE_EUNSUPPORTED, "batch_create: no fused stage kernel for this np and S");
+        if (m == 0) {
+            b->mixed = P.mixed;
+            b->np = P.g.np;
+            b->S = P.g.S;
+        } else if (P.mixed != b->mixed || P.g.np != b->np || P.g.S != b->S) {
+            return h0->fail(QHFPE_EINVAL, "batch_create: members must share np, the number of states and the precision");
+        }
+        b->mem.push_back(h);
+    }
+    *out = b.release();
+    return QHFPE_OK;
+}
+
+qhfpe_status qhfpe_batch_step(qhfpe_batch_t *b, long n_steps, double *const *trace_out)
+{
+    if (!b || b->mem.empty()) return QHFPE_EINVAL;
+    qhfpe *h0 = b->mem[0];
+    qhfpe_status r;
+    for (qhfpe *h : b->mem)
+        if ((r = check_handle(h)) != QHFPE_OK) return r;
+    if (n_steps < 0) return h0->fail(QHFPE_EINVAL, "batch_step: n_steps < 0");
+    // every member's earlier work (on its own stream) is complete before the batch touches its buffers
+    for (qhfpe *h : b->mem) QH_CK(h, cudaStreamSynchronize(h->stream));
+    cudaStream_t st = h0->stream;
+    if (!b->tq && n_steps > 0 && (r = batch_autotune(b, st)) != QHFPE_OK) return r;
+    const bool record = trace_out != nullptr;
+    const long stride = n_steps + 1;
+    if (record)
+        for (qhfpe *h : b->mem) {
+            Prop &P = *h->main;
+            if ((r = ensure_trace(h, P, (size_t)P.g.n_rep * stride)) != QHFPE_OK) return r;
+            set_sink_kernel<<<1, 1, 0, st>>>(P.sink, P.trace_buf, stride, 0);
+            QH_CK(h, cudaGetLastError());
+            if (b->mixed)
+                QH_CK(h, launch_trace<double>(P.g, P.y0, P.g.tier0_rep_stride, P.m->mu, P.sink, 1, P.partial, st,
+                                              P.m->trace_mu_q()));
+            else
+                QH_CK(h, launch_trace<double>(P.g, (const double *)P.y, P.g.rep_stride, P.m->mu, P.sink, 1, P.partial,
+                                              st, P.m->trace_mu_q()));
+        }
+    long done = 0;
+    while (done < n_steps) {
+        const int chunk = (n_steps - done >= kGraphChunk) ? 1 : 0;
+        const int len = chunk ? kGraphChunk : 1;
+        cudaGraphExec_t &ge = b->graphs[chunk][record ? 1 : 0];
+        if (!ge) {
+            cudaGraph_t graph;
+            QH_CK(h0, cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+            r = QHFPE_OK;
+            for (int s = 0; s < len && r == QHFPE_OK; ++s) r = batch_step_once(b, record, st);
+            cudaError_t e = cudaStreamEndCapture(st, &graph);
+            if (r != QHFPE_OK) return r;
+            QH_CK(h0, e);
+            e = cudaGraphInstantiate(&ge, graph, 0);
+            cudaGraphDestroy(graph);
+            QH_CK(h0, e);
+        }
+        QH_CK(h0, cudaGraphLaunch(ge, st));
+        done += len;
+    }
+    if (record)
+        for (size_t m = 0; m < b->mem.size(); ++m) {
+            Prop &P = *b->mem[m]->main;
+            if (trace_out[m])
+                QH_CK(h0, cudaMemcpyAsync(trace_out[m], P.trace_buf, (size_t)P.g.n_rep * stride * 2 * sizeof(double),
+                                          cudaMemcpyDeviceToHost, st));
+        }
+    QH_CK(h0, cudaStreamSynchronize(st));
+    return QHFPE_OK;
+}
+
+qhfpe_status qhfpe_batch_tile_rows(const qhfpe_batch_t *b, int *rows)
+{
+    if (!b || !rows) return QHFPE_EINVAL;
+    *rows = b->tq;
+    return QHFPE_OK;
+}
+
+qhfpe_status qhfpe_batch_destroy(qhfpe_batch_t *b)
+{
+    if (!b) return QHFPE_EINVAL;
+    if (!b->mem.empty()) cudaStreamSynchronize(b->mem[0]->stream);
+    delete b;
+    return QHFPE_OK;
+}
+
+}  // extern "C"

@@ -14,6 +14,7 @@
 // Grid order: the hierarchy element varies fastest, then the replica, then the q-tile, so the blocks
 // in flight cover all elements of a few q-tiles and the neighbour tiers and q-halos they re-read are
 // L2-resident.
+#include "qhfpe.h"
 #include "qhfpe_internal.cuh"
 
 namespace {
@@ -301,20 +302,61 @@ __device__ __forceinline__ void stv(T *p, const T *in)
     }
 }
 
-template <typename T>
-struct StageScalars {
-    T inv12dp, fkin, fdelta, fterm, r0, h;
-};
-template <typename T, int NP, int S, bool MIXED>
 // 128-thread blocks (measured faster than 256: more independent blocks per SM keep phase A and phase B
 // of different blocks overlapping, and each barrier stalls four warps).  The kernel waits mostly on L2
 // loads, so resident warps count: FP32 with one or two states runs seven blocks per SM (72 registers;
 // measured 5 % faster than six at 80), three states six (seven would spill), NP = 256 four (wider rows).
-__global__ void __launch_bounds__(FTHREADS, sizeof(T) == 4 ? (NP >= 256 ? 4 : (S >= 3 ? 6 : 7)) : 2)
+template <typename T, int NP, int S>
+struct FusedOcc {
+    static constexpr int blocks = sizeof(T) == 4 ? (NP >= 256 ? 4 : (S >= 3 ? 6 : 7)) : 2;
+};
+
+// MULTI: one Horner stage of several propagators at once (heterogeneous batch: members differ in q
+// grid, surfaces, bath, hierarchy depth, closure, dt and replica count, and share NP, S and the
+// precision).  Blocks are numbered member by member; a block finds its member (first block numbers
+// ascending), copies the member's description into shared memory and does that member's block of stage
+// k = 4..1 of the Horner form (k = 0: the right-hand side alone into the second stage buffer, for the
+// autotuner).  The other arguments are then taken from the member.
+template <typename T, int NP, int S, bool MIXED, bool MULTI>
+__global__ void __launch_bounds__(FTHREADS, FusedOcc<T, NP, S>::blocks - (MULTI && FusedOcc<T, NP, S>::blocks > 2 ? 1 : 0))
 fused_stage_kernel(GridInfo g, const ElemInfo *__restrict__ elems, FusedTables<T> tab, StageScalars<T> sc, const T *__restrict__ v_in,
                    const T *y, const double *y0, T *v_out, double *y0_out, double h, int mode, int terms, int rep0,
-                   int n_rep, int tq, const T *__restrict__ Pg)
+                   int n_rep, int tq, const T *__restrict__ Pg, const MultiMember<T> *__restrict__ mem, int n_mem, int k)
 {
+    unsigned bid = blockIdx.x;
+    if constexpr (MULTI) {
+        __shared__ MultiMember<T> M;
+        __shared__ int s_m;
+        if (threadIdx.x == 0) {
+            int m = 0;
+            while (m + 1 < n_mem && mem[m + 1].block0 <= (long)blockIdx.x) ++m;
+            s_m = m;
+        }
+        __syncthreads();
+        {
+            static_assert(sizeof(MultiMember<T>) % sizeof(int) == 0, "member size");
+            const int *src = reinterpret_cast<const int *>(mem + s_m);
+            int *dst = reinterpret_cast<int *>(&M);
+            for (int w = threadIdx.x; w < (int)(sizeof(MultiMember<T>) / sizeof(int)); w += FTHREADS) dst[w] = src[w];
+        }
+        __syncthreads();
+        g = M.g;
+        elems = M.elems;
+        tab = M.tab;
+        sc = M.sc[k];
+        v_in = k == 4 || k == 0 ? M.y : (k == 3 ? M.vA : (k == 2 ? M.vB : M.vA));
+        y = M.y;
+        y0 = M.y0;
+        v_out = k == 0 ? M.vB : (k == 1 ? M.y : (k == 4 ? M.vA : (k == 3 ? M.vB : M.vA)));
+        y0_out = k == 1 ? M.y0 : nullptr;
+        h = k == 0 ? 0.0 : M.dt / k;
+        mode = k == 0 ? 0 : (k == 1 ? 2 : 1);
+        terms = QHFPE_TERM_ALL;
+        rep0 = 0;
+        n_rep = M.g.n_rep;
+        Pg = nullptr;
+        bid -= (unsigned)M.block0;
+    }
     using C = typename V2<T>::type;
     constexpr int S2 = S * S;
     // phase B: a lane holds VEC consecutive p values of one row, a row spans LPR lanes, and a warp
@@ -328,9 +370,9 @@ fused_stage_kernel(GridInfo g, const ElemInfo *__restrict__ elems, FusedTables<T
     C *tw = X + pad16(tq * S2 * NP) + 1;             // [NP]
 
     const int nq = g.nq;
-    const int e = blockIdx.x % g.n_elem;
-    const int rep = rep0 + (blockIdx.x / g.n_elem) % n_rep;
-    const int tile = blockIdx.x / (g.n_elem * n_rep);
+    const int e = bid % g.n_elem;
+    const int rep = rep0 + (bid / g.n_elem) % n_rep;
+    const int tile = bid / (g.n_elem * n_rep);
     const int i0 = tile * tq;
     const int rows = min(tq, nq - i0);
     const size_t blk = g.blk;
@@ -811,15 +853,20 @@ cudaError_t launch_fused_t(const GridInfo &g, const ElemInfo *elems, const Fused
     const int tiles = (g.nq + tq - 1) / tq;
     const long blocks = (long)tiles * n_rep * g.n_elem;
     if (blocks <= 0) return cudaSuccess;
-    StageScalars<T> sc;
-    sc.inv12dp = (T)(1.0 / (12.0 * g.dp));
-    sc.fkin = (T)(1.0 / (60.0 * g.dq));
-    sc.fdelta = (T)(g.cdelta / (12.0 * g.dp * g.dp));
-    sc.fterm = (T)(g.term_c0 / (12.0 * g.dp * g.dp));
-    sc.r0 = (T)g.term_r0;
-    sc.h = (T)h;
-    fused_stage_kernel<T, NP, S, MIXED><<<(unsigned)blocks, FTHREADS, smem, st>>>(
-        g, elems, tab, sc, v_in, y, y0, v_out, y0_out, h, mode, terms, rep0, n_rep, tq, Pg);
+    const StageScalars<T> sc = stage_scalars<T>(g, h);
+    fused_stage_kernel<T, NP, S, MIXED, false><<<(unsigned)blocks, FTHREADS, smem, st>>>(
+        g, elems, tab, sc, v_in, y, y0, v_out, y0_out, h, mode, terms, rep0, n_rep, tq, Pg, nullptr, 0, 0);
+    return cudaGetLastError();
+}
+
+template <typename T, int NP, int S, bool MIXED>
+cudaError_t launch_fused_multi_t(const MultiMember<T> *mem, int n_mem, int k, int tq, long blocks, cudaStream_t st)
+{
+    if (blocks <= 0) return cudaSuccess;
+    const size_t smem = fused_smem_bytes(tq, NP, S, sizeof(T));
+    fused_stage_kernel<T, NP, S, MIXED, true><<<(unsigned)blocks, FTHREADS, smem, st>>>(
+        GridInfo{}, nullptr, FusedTables<T>{}, StageScalars<T>{}, nullptr, nullptr, nullptr, nullptr, nullptr, 0.0, 0, 0, 0,
+        1, tq, nullptr, mem, n_mem, k);
     return cudaGetLastError();
 }
 
@@ -828,11 +875,56 @@ cudaError_t prepare_fused_t()
 {
     const int tq = fused_max_rows(NP, S, sizeof(T));
     const size_t smem = fused_smem_bytes(tq, NP, S, sizeof(T));
-    return cudaFuncSetAttribute(fused_stage_kernel<T, NP, S, MIXED>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(fused_stage_kernel<T, NP, S, MIXED, false>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(fused_stage_kernel<T, NP, S, MIXED, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)smem);
 }
 
 }  // namespace
+
+template <typename T>
+StageScalars<T> stage_scalars(const GridInfo &g, double h)
+{
+    StageScalars<T> sc;
+    sc.inv12dp = (T)(1.0 / (12.0 * g.dp));
+    sc.fkin = (T)(1.0 / (60.0 * g.dq));
+    sc.fdelta = (T)(g.cdelta / (12.0 * g.dp * g.dp));
+    sc.fterm = (T)(g.term_c0 / (12.0 * g.dp * g.dp));
+    sc.r0 = (T)g.term_r0;
+    sc.h = (T)h;
+    return sc;
+}
+
+long fused_blocks(const GridInfo &g, int tq)
+{
+    if (tq > g.nq) tq = g.nq;
+    return (long)((g.nq + tq - 1) / tq) * g.n_rep * g.n_elem;
+}
+
+template <typename T, bool MIXED>
+cudaError_t launch_fused_multi(int np, int S, const MultiMember<T> *mem, int n_mem, int k, int tq, long blocks,
+                               cudaStream_t st)
+{
+#define QH_CALL(NP_, S_) launch_fused_multi_t<T, NP_, S_, MIXED>(mem, n_mem, k, tq, blocks, st)
+    switch (np * 8 + S) {
+    case 32 * 8 + 1: return QH_CALL(32, 1);
+    case 32 * 8 + 2: return QH_CALL(32, 2);
+    case 32 * 8 + 3: return QH_CALL(32, 3);
+    case 64 * 8 + 1: return QH_CALL(64, 1);
+    case 64 * 8 + 2: return QH_CALL(64, 2);
+    case 64 * 8 + 3: return QH_CALL(64, 3);
+    case 128 * 8 + 1: return QH_CALL(128, 1);
+    case 128 * 8 + 2: return QH_CALL(128, 2);
+    case 128 * 8 + 3: return QH_CALL(128, 3);
+    case 256 * 8 + 1: return QH_CALL(256, 1);
+    case 256 * 8 + 2: return QH_CALL(256, 2);
+    case 256 * 8 + 3: return QH_CALL(256, 3);
+    default: return cudaErrorInvalidValue;
+    }
+#undef QH_CALL
+}
 
 int fused_rows_per_tile(int np, int S, int elem_bytes)
 {
@@ -956,6 +1048,10 @@ int fused_fft_frequency(int np, int pos)
 template cudaError_t launch_fused<float, true>(const GridInfo &, const ElemInfo *, const FusedTables<float> &, const float *, const float *, const double *, float *, double *, double, int, int, int, int, cudaStream_t, const float *, int);
 template cudaError_t launch_fused<double, false>(const GridInfo &, const ElemInfo *, const FusedTables<double> &, const double *, const double *, const double *, double *, double *, double, int, int, int, int, cudaStream_t, const double *, int);
 template cudaError_t prepare_fused<float, true>(int, int);
+template StageScalars<float> stage_scalars<float>(const GridInfo &, double);
+template StageScalars<double> stage_scalars<double>(const GridInfo &, double);
+template cudaError_t launch_fused_multi<float, true>(int, int, const MultiMember<float> *, int, int, int, long, cudaStream_t);
+template cudaError_t launch_fused_multi<double, false>(int, int, const MultiMember<double> *, int, int, int, long, cudaStream_t);
 template cudaError_t prepare_fused<double, false>(int, int);
 template cudaError_t launch_dipole_fft<float>(const GridInfo &, const float *, const float *, const float *, float *, size_t, int, const int *, int, int, double, float *, size_t, cudaStream_t);
 template cudaError_t launch_dipole_fft<double>(const GridInfo &, const double *, const double *, const double *, double *, size_t, int, const int *, int, int, double, float *, size_t, cudaStream_t);

@@ -61,6 +61,27 @@ struct FusedTables {
     const T *tw;
 };
 
+// Scalars of one fused stage launch, rounded once on the host: 1/(12 dp), 1/(60 dq), the delta-term and
+// terminator coefficients of the 5-point d2/dp2, r_0 and the Horner step h.
+template <typename T>
+struct StageScalars {
+    T inv12dp, fkin, fdelta, fterm, r0, h;
+};
+
+// One member of a heterogeneous batch of fused stages (see launch_fused_multi): its grid and tables,
+// its Horner buffers, and the number of its first block in the batch launch.
+template <typename T>
+struct MultiMember {
+    GridInfo g;
+    const ElemInfo *elems;
+    FusedTables<T> tab;
+    StageScalars<T> sc[5];  // [k]: stage k = 1..4 (h = dt / k); [0]: the right-hand side alone (h = 0)
+    double dt;
+    T *y, *vA, *vB;
+    double *y0;             // FP64 zeroth tier (mixed form), else nullptr
+    long block0;
+};
+
 // Device-side trace sink: trace kernel writes slot `counter` of every replica then the counter
 // advances; keeps captured graphs independent of the call's output length.
 struct TraceSink {
@@ -105,6 +126,15 @@ cudaError_t launch_fused(const GridInfo &g, const ElemInfo *elems, const FusedTa
                          const T *y, const double *y0, T *v_out, double *y0_out, double h, int mode, int terms,
                          int rep0, int n_rep, cudaStream_t st, const T *Pg = nullptr, int tq = 0);
 int fused_max_rows(int np, int S, int elem_bytes);
+template <typename T>
+StageScalars<T> stage_scalars(const GridInfo &g, double h);
+// blocks of one fused launch over all replicas at tile height tq
+long fused_blocks(const GridInfo &g, int tq);
+// Horner stage k (4..1; 0: the right-hand side into vB) of every member of mem (device array, n_mem
+// members sharing np and S, block0 ascending from 0, blocks in total) as one launch.
+template <typename T, bool MIXED>
+cudaError_t launch_fused_multi(int np, int S, const MultiMember<T> *mem, int n_mem, int k, int tq, long blocks,
+                               cudaStream_t st);
 // Non-Condon dipole super-operator (side 1: mu^->, 2: mu^<-, 3: mu^x, times scale) on n_elem elements of
 // n_rep replicas (reps: device list or nullptr for 0..n_rep-1), in place, through an FFT along p.
 // TL, TR: [S][S][nq][np] r-space multipliers mu(q + r/2), mu(q - r/2) / np in the fused FFT's order;

@@ -31,7 +31,8 @@ EXPORTED = [
     "qhfpe_kernel_timing", "qhfpe_kernel_timing_read", "qhfpe_potential_term_static",
     "qhfpe_closure_collect", "qhfpe_closure_load", "qhfpe_closure_coefficients", "qhfpe_closure_loss_grad",
     "qhfpe_closure_train", "qhfpe_tile_rows", "qhfpe_wait_selftest", "qhfpe_adiabatic_marginals",
-    "qhfpe_first_order_distribution", "qhfpe_set_dipole_table",
+    "qhfpe_first_order_distribution", "qhfpe_set_dipole_table", "qhfpe_batch_create", "qhfpe_batch_step",
+    "qhfpe_batch_tile_rows", "qhfpe_batch_destroy",
 ]
 
 CLOSURE_N_WEIGHTS = 135178
@@ -105,6 +106,10 @@ def lib():
     L.qhfpe_potential_term_static.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double,
                                               ctypes.c_double, vp, ctypes.c_int, vp, vp, vp]
     L.qhfpe_tile_rows.argtypes = [vp, ip]
+    L.qhfpe_batch_create.argtypes = [ctypes.POINTER(vp), st, ctypes.POINTER(vp)]
+    L.qhfpe_batch_step.argtypes = [vp, ctypes.c_long, ctypes.POINTER(vp)]
+    L.qhfpe_batch_tile_rows.argtypes = [vp, ip]
+    L.qhfpe_batch_destroy.argtypes = [vp]
     L.qhfpe_wait_selftest.argtypes = [vp, ctypes.c_int, ctypes.c_int]
     L.qhfpe_closure_collect.argtypes = [vp, ctypes.c_int, vp]
     L.qhfpe_closure_load.argtypes = [vp, vp, ctypes.c_size_t]
@@ -408,3 +413,51 @@ class Propagator:
         self._check(self._L.qhfpe_kernel_timing_read(self._h, n, ms, 3))
         names = ("stage", "potential", "aux")
         return {names[k]: (n[k], ms[k]) for k in range(3)}
+
+
+class Batch:
+    """Several Propagators advanced together (a heterogeneous batch: each Horner stage of all members is
+    one fused kernel launch).  Members share np, the number of states and the precision; they may
+    differ in grid, bath, depth, closure, dt and replica count.  The Propagators must outlive it."""
+
+    def __init__(self, members):
+        self.members = list(members)
+        L = lib()
+        self._L = L
+        arr = (ctypes.c_void_p * len(self.members))(*[m._h.value for m in self.members])
+        b = ctypes.c_void_p()
+        s = L.qhfpe_batch_create(arr, len(self.members), ctypes.byref(b))
+        if s != 0:
+            raise QhfpeError(s, L.qhfpe_last_error(self.members[0]._h).decode())
+        self._b = b
+
+    def _check(self, s):
+        if s != 0:
+            raise QhfpeError(s, self._L.qhfpe_last_error(self.members[0]._h).decode())
+
+    def step(self, n_steps, record_trace=False):
+        """Advance every member n_steps RK4 steps; with record_trace, one [n_replicas][n_steps + 1]
+        complex trace per member (as Propagator.step)."""
+        if not record_trace:
+            self._check(self._L.qhfpe_batch_step(self._b, n_steps, None))
+            return None
+        outs = [np.zeros((m.n_replicas, n_steps + 1), dtype=np.complex128) for m in self.members]
+        ptrs = (ctypes.c_void_p * len(outs))(*[o.ctypes.data for o in outs])
+        self._check(self._L.qhfpe_batch_step(self._b, n_steps, ptrs))
+        return outs
+
+    def tile_rows(self):
+        v = ctypes.c_int()
+        self._check(self._L.qhfpe_batch_tile_rows(self._b, ctypes.byref(v)))
+        return v.value
+
+    def close(self):
+        if getattr(self, "_b", None):
+            self._L.qhfpe_batch_destroy(self._b)
+            self._b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
