@@ -222,6 +222,56 @@ def paper_workload_measure(stream):
     return out
 
 
+def hetero_batch_measure(stream):
+    """Eight config-1-shaped models that differ in q grid, depth, closure, bath and dt (np = 32, two
+    states, FP32 mixed form), advanced together as one heterogeneous batch (every Horner stage of all
+    eight one launch) and one after another on their own: wall time of the same RK4 steps, inputs
+    resident on the device."""
+    import numpy as np
+    import torch
+    import qhfpe_inputs as qi
+    from paper_1706_09590_gb300 import Batch, Propagator
+    specs = [(32, 3, 1, 0.5, 0.010), (24, 5, 0, 0.3, 0.008), (40, 4, 1, 1.0, 0.010), (48, 2, 1, 0.2, 0.012),
+             (32, 6, 0, 0.5, 0.009), (28, 3, 1, 2.0, 0.010), (36, 4, 1, 0.7, 0.011), (44, 5, 0, 0.4, 0.010)]
+    models = [qi.harmonic_two_state(nq=nq, n_p=32, depth=d, closure=c, eta=eta, dt=dt) for nq, d, c, eta, dt in specs]
+
+    def make():
+        Ps = [Propagator(m, qi.u_table(m), precision="mixed", stream=stream) for m in models]
+        for k, P in enumerate(Ps):
+            P.set_state(qi.random_state(P.model, seed=500 + k, hermitian=True))
+        return Ps
+
+    n = 400
+    Ps = make()
+    B = Batch(Ps)
+    B.step(20)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    B.step(n)
+    torch.cuda.synchronize()
+    t_batch = time.perf_counter() - t0
+    tq = B.tile_rows()
+    B.close()
+    cells = sum(P.n_replicas * int(np.prod(P.shape)) for P in Ps)
+    for P in Ps:
+        P.close()
+    Qs = make()
+    for Q in Qs:
+        Q.step(20)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for Q in Qs:
+        Q.step(n)
+    torch.cuda.synchronize()
+    t_seq = time.perf_counter() - t0
+    for Q in Qs:
+        Q.close()
+    return {"workload": "8 harmonic two-state models, np 32, nq 24-48, depth 2-6, terminator or truncation, "
+                        f"eta 0.2-2, dt 0.008-0.012 ({cells} cells), {n} RK4 steps, FP32 mixed form",
+            "batched_cell_updates_per_s": cells * n / t_batch, "one_by_one_cell_updates_per_s": cells * n / t_seq,
+            "batched_s": t_batch, "one_by_one_s": t_seq, "tile_rows": tq, "timer": "wall clock, device synchronised"}
+
+
 def cpu_baseline(m, T, seconds=15.0):
     """The FP64 oracle as it stands, on this host's cores, over a bounded number of RK4 steps of the
     same workload (full hierarchy, full grid)."""
@@ -289,6 +339,8 @@ def main():
     ap.add_argument("--no-spectrum", action="store_true", help="skip the batched 2D-spectrum measurement")
     ap.add_argument("--no-paper-workload", action="store_true",
                     help="skip the measurement on the paper's own Morse model")
+    ap.add_argument("--no-hetero-batch", action="store_true",
+                    help="skip the heterogeneous-batch measurement")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -424,6 +476,8 @@ def main():
         line["spectrum_2d"] = spectrum_2d_measure(stream)
     if not args.no_paper_workload:
         line["paper_workload"] = paper_workload_measure(stream)
+    if not args.no_hetero_batch:
+        line["hetero_batch"] = hetero_batch_measure(stream)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(m, T)
     if rank == 0:
