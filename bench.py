@@ -272,6 +272,46 @@ def hetero_batch_measure(stream):
             "batched_s": t_batch, "one_by_one_s": t_seq, "tile_rows": tq, "timer": "wall clock, device synchronised"}
 
 
+def three_state_measure(stream, hbm_peak):
+    """The three-state workload at full size (256 x 256, depth 10, three bath modes: 286 elements x 9
+    pairs, 168.7 M cells): RK4 throughput of the mixed and FP64 forms (CUDA events on the launching
+    stream), the mixed fused stage kernel's time per launch and its fraction of the HBM peak on the
+    algorithmic 22 B per cell per stage."""
+    import numpy as np
+    import torch
+    import qhfpe_inputs as qi
+    from paper_1706_09590_gb300 import Propagator
+    m = qi.three_state()
+    T = qi.u_table(m)
+    W = qi.random_state(m, seed=1706)
+    out = {"workload": "three_state_256x256_d10_K2 (3 states, 286 elements, 168.7 M cells)"}
+    s = torch.cuda.current_stream() if stream is None else stream
+    for prec, n in (("mixed", 20), ("fp64", 2)):
+        P = Propagator(m, T, precision=prec, stream=stream)
+        P.set_state(W)
+        P.step(2)
+        cells = int(np.prod(P.shape))
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(s)
+        P.step(n)
+        e1.record(s)
+        torch.cuda.synchronize()
+        out[prec + "_cell_updates_per_s"] = cells * n / (e0.elapsed_time(e1) / 1e3)
+        if prec == "mixed":
+            P.kernel_timing(True)
+            P.step(2)
+            kt = P.kernel_timing_read()
+            P.kernel_timing(False)
+            ms = kt["stage"][1] / max(kt["stage"][0], 1)
+            out["stage_ms_per_launch"] = ms
+            out["stage_hbm_frac_of_measured"] = 22.0 * cells / (ms / 1e3) / 1e9 / hbm_peak
+            out["tile_rows_autotuned"] = P.tile_rows()
+        out["cells"] = cells
+        P.close()
+    return out
+
+
 def cpu_baseline(m, T, seconds=15.0):
     """The FP64 oracle as it stands, on this host's cores, over a bounded number of RK4 steps of the
     same workload (full hierarchy, full grid)."""
@@ -341,6 +381,8 @@ def main():
                     help="skip the measurement on the paper's own Morse model")
     ap.add_argument("--no-hetero-batch", action="store_true",
                     help="skip the heterogeneous-batch measurement")
+    ap.add_argument("--no-three-state", action="store_true",
+                    help="skip the full-size three-state measurement")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -478,6 +520,8 @@ def main():
         line["paper_workload"] = paper_workload_measure(stream)
     if not args.no_hetero_batch:
         line["hetero_batch"] = hetero_batch_measure(stream)
+    if not args.no_three_state:
+        line["three_state"] = three_state_measure(stream, hbm_peak)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(m, T)
     if rank == 0:
