@@ -135,6 +135,9 @@ long fused_blocks(const GridInfo &g, int tq);
 template <typename T, bool MIXED>
 cudaError_t launch_fused_multi(int np, int S, const MultiMember<T> *mem, int n_mem, int k, int tq, long blocks,
                                cudaStream_t st);
+// shared-memory limit of the batch instantiation (called by prepare_fused)
+template <typename T, bool MIXED>
+cudaError_t prepare_fused_multi(int np, int S, size_t smem);
 // Non-Condon dipole super-operator (side 1: mu^->, 2: mu^<-, 3: mu^x, times scale) on n_elem elements of
 // n_rep replicas (reps: device list or nullptr for 0..n_rep-1), in place, through an FFT along p.
 // TL, TR: [S][S][nq][np] r-space multipliers mu(q + r/2), mu(q - r/2) / np in the fused FFT's order;
