@@ -435,13 +435,19 @@ def main():
     value = job_throughput(cells, args.steps, world, ms)
 
     # ---- end to end through the C ABI with host buffers --------------------------------------------
-    # every step: the state from pinned host memory, one RK4 step with its trace, the state back
+    # every step: the state from pinned host memory, one RK4 step with its trace, the state back; the
+    # mixed forms exchange complex64 states (their higher tiers are FP32 on the device), FP64 complex128
     n_e2e = max(2, min(args.steps, 10))
-    host_in = torch.from_numpy(W0.view(np.float64)).pin_memory()
+    if args.precision == "fp64":
+        host_in = torch.from_numpy(W0.view(np.float64)).pin_memory()
+        cdt = np.complex128
+    else:
+        host_in = torch.from_numpy(W0.astype(np.complex64).view(np.float32)).pin_memory()
+        cdt = np.complex64
     host_out = torch.empty_like(host_in).pin_memory()
-    w_in = host_in.numpy().view(np.complex128).reshape(P.shape)
-    w_out = host_out.numpy().view(np.complex128).reshape(P.shape)
-    state_bytes = host_in.numel() * 8
+    w_in = host_in.numpy().view(cdt).reshape(P.shape)
+    w_out = host_out.numpy().view(cdt).reshape(P.shape)
+    state_bytes = host_in.numel() * host_in.element_size()
     barrier()
     t0 = time.perf_counter()
     for _ in range(n_e2e):

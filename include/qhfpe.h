@@ -131,6 +131,11 @@ qhfpe_status qhfpe_max_stable_dt(const qhfpe_t *h, double *dt_out);
  * set_state checks the values on the device and returns QHFPE_ENUMERIC on NaN/Inf. */
 qhfpe_status qhfpe_set_state(qhfpe_t *h, int replica, const double *src, int is_device);
 qhfpe_status qhfpe_get_state(qhfpe_t *h, int replica, double *dst, int is_device);
+/* The same with a complex64 canonical state (half the bytes; for the mixed forms, whose higher tiers
+ * are FP32 anyway): set_state32 widens the values as given (the zeroth tier of the mixed forms becomes
+ * their FP64 value), get_state32 rounds each value, including the FP64 zeroth tier, to FP32. */
+qhfpe_status qhfpe_set_state32(qhfpe_t *h, int replica, const float *src, int is_device);
+qhfpe_status qhfpe_get_state32(qhfpe_t *h, int replica, float *dst, int is_device);
 /* Copy replica src onto each of dst[0..n-1] (host int array). */
 qhfpe_status qhfpe_fork(qhfpe_t *h, int src, const int *dst, int n);
 

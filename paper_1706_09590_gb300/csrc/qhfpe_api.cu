@@ -801,6 +801,24 @@ qhfpe_status ensure_scratch(qhfpe *h, size_t bytes)
     return QHFPE_OK;
 }
 
+template <typename H>
+qhfpe_status set_from_canonical_t(qhfpe *h, Prop &P, const H *src_dev, int rep, int n_rep, int *nonfinite)
+{
+    if (P.mixed)
+        QH_CK(h, (launch_from_canonical<float, H>(P.g, src_dev, (float *)P.y, P.y0, rep, n_rep, h->stream, nonfinite)));
+    else
+        QH_CK(h, (launch_from_canonical<double, H>(P.g, src_dev, (double *)P.y, nullptr, rep, n_rep, h->stream, nonfinite)));
+    return QHFPE_OK;
+}
+
+template <typename H>
+qhfpe_status get_to_canonical_t(qhfpe *h, Prop &P, const void *src, const double *y0, H *dst_dev, int rep)
+{
+    if (P.mixed) QH_CK(h, (launch_to_canonical<float, H>(P.g, (const float *)src, y0, dst_dev, rep, h->stream)));
+    else QH_CK(h, (launch_to_canonical<double, H>(P.g, (const double *)src, nullptr, dst_dev, rep, h->stream)));
+    return QHFPE_OK;
+}
+
 qhfpe_status set_from_canonical(qhfpe *h, Prop &P, const double *src_dev, int rep, int n_rep, int *nonfinite = nullptr)
 {
     if (P.mixed)
@@ -1044,23 +1062,28 @@ qhfpe_status qhfpe_max_stable_dt(const qhfpe_t *h, double *dt_out)
     return QHFPE_OK;
 }
 
-qhfpe_status qhfpe_set_state(qhfpe_t *h, int replica, const double *src, int is_device)
+}  // extern "C"
+
+namespace {
+
+template <typename H>
+qhfpe_status set_state_t(qhfpe_t *h, int replica, const H *src, int is_device)
 {
     qhfpe_status r = check_handle(h);
     if (r != QHFPE_OK) return r;
     Prop &P = *h->main;
     if (!src || replica < -1 || replica >= P.g.n_rep) return h->fail(QHFPE_EINVAL, "set_state: bad replica or NULL source");
     const size_t n = (size_t)P.g.n_elem * P.g.S * P.g.S * P.g.blk;
-    const double *dsrc = src;
+    const H *dsrc = src;
     if (!h->flag) QH_CK(h, cudaMalloc((void **)&h->flag, sizeof(int)));
     QH_CK(h, cudaMemsetAsync(h->flag, 0, sizeof(int), h->stream));
     if (!is_device) {
-        r = ensure_scratch(h, n * 2 * sizeof(double));
+        r = ensure_scratch(h, n * 2 * sizeof(H));
         if (r != QHFPE_OK) return r;
-        QH_CK(h, cudaMemcpyAsync(h->scratch, src, n * 2 * sizeof(double), cudaMemcpyHostToDevice, h->stream));
-        dsrc = h->scratch;
+        QH_CK(h, cudaMemcpyAsync(h->scratch, src, n * 2 * sizeof(H), cudaMemcpyHostToDevice, h->stream));
+        dsrc = reinterpret_cast<const H *>(h->scratch);
     }
-    r = set_from_canonical(h, P, dsrc, replica < 0 ? 0 : replica, replica < 0 ? P.g.n_rep : 1, h->flag);
+    r = set_from_canonical_t<H>(h, P, dsrc, replica < 0 ? 0 : replica, replica < 0 ? P.g.n_rep : 1, h->flag);
     if (r != QHFPE_OK) return r;
     int bad = 0;
     QH_CK(h, cudaMemcpyAsync(&bad, h->flag, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
@@ -1069,24 +1092,49 @@ qhfpe_status qhfpe_set_state(qhfpe_t *h, int replica, const double *src, int is_
     return QHFPE_OK;
 }
 
-qhfpe_status qhfpe_get_state(qhfpe_t *h, int replica, double *dst, int is_device)
+template <typename H>
+qhfpe_status get_state_t(qhfpe_t *h, int replica, H *dst, int is_device)
 {
     qhfpe_status r = check_handle(h);
     if (r != QHFPE_OK) return r;
     Prop &P = *h->main;
     if (!dst || replica < 0 || replica >= P.g.n_rep) return h->fail(QHFPE_EINVAL, "get_state: bad replica or NULL destination");
     const size_t n = (size_t)P.g.n_elem * P.g.S * P.g.S * P.g.blk;
-    double *ddst = dst;
+    H *ddst = dst;
     if (!is_device) {
-        r = ensure_scratch(h, n * 2 * sizeof(double));
+        r = ensure_scratch(h, n * 2 * sizeof(H));
         if (r != QHFPE_OK) return r;
-        ddst = h->scratch;
+        ddst = reinterpret_cast<H *>(h->scratch);
     }
-    r = get_to_canonical(h, P, P.y, P.y0, ddst, replica);
+    r = get_to_canonical_t<H>(h, P, P.y, P.y0, ddst, replica);
     if (r != QHFPE_OK) return r;
-    if (!is_device) QH_CK(h, cudaMemcpyAsync(dst, ddst, n * 2 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    if (!is_device) QH_CK(h, cudaMemcpyAsync(dst, ddst, n * 2 * sizeof(H), cudaMemcpyDeviceToHost, h->stream));
     QH_CK(h, cudaStreamSynchronize(h->stream));
     return QHFPE_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+qhfpe_status qhfpe_set_state(qhfpe_t *h, int replica, const double *src, int is_device)
+{
+    return set_state_t<double>(h, replica, src, is_device);
+}
+
+qhfpe_status qhfpe_get_state(qhfpe_t *h, int replica, double *dst, int is_device)
+{
+    return get_state_t<double>(h, replica, dst, is_device);
+}
+
+qhfpe_status qhfpe_set_state32(qhfpe_t *h, int replica, const float *src, int is_device)
+{
+    return set_state_t<float>(h, replica, src, is_device);
+}
+
+qhfpe_status qhfpe_get_state32(qhfpe_t *h, int replica, float *dst, int is_device)
+{
+    return get_state_t<float>(h, replica, dst, is_device);
 }
 
 qhfpe_status qhfpe_fork(qhfpe_t *h, int src, const int *dst, int n)

@@ -174,11 +174,12 @@ template <typename T>
 cudaError_t launch_dipole(const GridInfo &g, T *state, double *y0, const int *reps, int n_reps,
                           const double *mu_dev, int side, double scale, cudaStream_t st);
 
-template <typename T>
-cudaError_t launch_from_canonical(const GridInfo &g, const double *src, T *dst, double *y0_dst, int rep, int n_rep,
+// canonical layout [elem][j][k][q][p] complex with host element type H (double or float)
+template <typename T, typename H = double>
+cudaError_t launch_from_canonical(const GridInfo &g, const H *src, T *dst, double *y0_dst, int rep, int n_rep,
                                   cudaStream_t st, int *nonfinite = nullptr);
-template <typename T>
-cudaError_t launch_to_canonical(const GridInfo &g, const T *src, const double *y0_src, double *dst, int rep,
+template <typename T, typename H = double>
+cudaError_t launch_to_canonical(const GridInfo &g, const T *src, const double *y0_src, H *dst, int rep,
                                 cudaStream_t st);
 
 // Adiabatic-basis coordinate marginals of one replica's zeroth tier (FP64, layout [S][S][re|im][q][p]);

@@ -429,8 +429,8 @@ __global__ void dipole_kernel(GridInfo g, T *state, double *y0, const int *__res
 }
 
 // canonical complex128 [elem][j][k][q][p]  <->  internal planar layout of one replica
-template <typename T>
-__global__ void from_canonical_kernel(GridInfo g, const double *__restrict__ src, T *dst, double *y0, int rep0,
+template <typename T, typename H>
+__global__ void from_canonical_kernel(GridInfo g, const H *__restrict__ src, T *dst, double *y0, int rep0,
                                       int *nonfinite)
 {
     const size_t blk = g.blk;
@@ -439,7 +439,7 @@ __global__ void from_canonical_kernel(GridInfo g, const double *__restrict__ src
     for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < per; idx += (size_t)gridDim.x * blockDim.x) {
         const size_t cell = idx % blk;
         const size_t ep = idx / blk;  // e*S2 + pair
-        const double re = src[2 * idx], im = src[2 * idx + 1];
+        const double re = (double)src[2 * idx], im = (double)src[2 * idx + 1];
         if (nonfinite && !(isfinite(re) && isfinite(im))) *nonfinite = 1;
         const size_t o = (size_t)rep * g.rep_stride + ep * 2 * blk + cell;
         dst[o] = (T)re;
@@ -452,9 +452,9 @@ __global__ void from_canonical_kernel(GridInfo g, const double *__restrict__ src
     }
 }
 
-template <typename T>
+template <typename T, typename H>
 __global__ void to_canonical_kernel(GridInfo g, const T *__restrict__ src, const double *__restrict__ y0,
-                                    double *dst, int rep)
+                                    H *dst, int rep)
 {
     const size_t blk = g.blk;
     const size_t per = (size_t)g.n_elem * g.S * g.S * blk;
@@ -471,8 +471,8 @@ __global__ void to_canonical_kernel(GridInfo g, const T *__restrict__ src, const
             re = (double)src[o];
             im = (double)src[o + blk];
         }
-        dst[2 * idx] = re;
-        dst[2 * idx + 1] = im;
+        dst[2 * idx] = (H)re;
+        dst[2 * idx + 1] = (H)im;
     }
 }
 
@@ -662,22 +662,22 @@ cudaError_t launch_dipole(const GridInfo &g, T *state, double *y0, const int *re
     return cudaGetLastError();
 }
 
-template <typename T>
-cudaError_t launch_from_canonical(const GridInfo &g, const double *src, T *dst, double *y0_dst, int rep, int n_rep,
+template <typename T, typename H>
+cudaError_t launch_from_canonical(const GridInfo &g, const H *src, T *dst, double *y0_dst, int rep, int n_rep,
                                   cudaStream_t st, int *nonfinite)
 {
     const size_t per = (size_t)g.n_elem * g.S * g.S * g.blk;
     dim3 grid(grid_for(per, 256, 2048), n_rep);
-    from_canonical_kernel<T><<<grid, 256, 0, st>>>(g, src, dst, y0_dst, rep, nonfinite);
+    from_canonical_kernel<T, H><<<grid, 256, 0, st>>>(g, src, dst, y0_dst, rep, nonfinite);
     return cudaGetLastError();
 }
 
-template <typename T>
-cudaError_t launch_to_canonical(const GridInfo &g, const T *src, const double *y0_src, double *dst, int rep,
+template <typename T, typename H>
+cudaError_t launch_to_canonical(const GridInfo &g, const T *src, const double *y0_src, H *dst, int rep,
                                 cudaStream_t st)
 {
     const size_t per = (size_t)g.n_elem * g.S * g.S * g.blk;
-    to_canonical_kernel<T><<<grid_for(per, 256, 2048), 256, 0, st>>>(g, src, y0_src, dst, rep);
+    to_canonical_kernel<T, H><<<grid_for(per, 256, 2048), 256, 0, st>>>(g, src, y0_src, dst, rep);
     return cudaGetLastError();
 }
 
@@ -858,7 +858,11 @@ template cudaError_t launch_stage<float, true>(const GridInfo &, const ElemInfo 
 template cudaError_t launch_trace<double>(const GridInfo &, const double *, size_t, const double *, TraceSink *, int, double *, cudaStream_t, const double *);
 template cudaError_t launch_dipole<double>(const GridInfo &, double *, double *, const int *, int, const double *, int, double, cudaStream_t);
 template cudaError_t launch_dipole<float>(const GridInfo &, float *, double *, const int *, int, const double *, int, double, cudaStream_t);
-template cudaError_t launch_from_canonical<double>(const GridInfo &, const double *, double *, double *, int, int, cudaStream_t, int *);
-template cudaError_t launch_from_canonical<float>(const GridInfo &, const double *, float *, double *, int, int, cudaStream_t, int *);
-template cudaError_t launch_to_canonical<double>(const GridInfo &, const double *, const double *, double *, int, cudaStream_t);
-template cudaError_t launch_to_canonical<float>(const GridInfo &, const float *, const double *, double *, int, cudaStream_t);
+template cudaError_t launch_from_canonical<double, double>(const GridInfo &, const double *, double *, double *, int, int, cudaStream_t, int *);
+template cudaError_t launch_from_canonical<float, double>(const GridInfo &, const double *, float *, double *, int, int, cudaStream_t, int *);
+template cudaError_t launch_from_canonical<double, float>(const GridInfo &, const float *, double *, double *, int, int, cudaStream_t, int *);
+template cudaError_t launch_from_canonical<float, float>(const GridInfo &, const float *, float *, double *, int, int, cudaStream_t, int *);
+template cudaError_t launch_to_canonical<double, double>(const GridInfo &, const double *, const double *, double *, int, cudaStream_t);
+template cudaError_t launch_to_canonical<float, double>(const GridInfo &, const float *, const double *, double *, int, cudaStream_t);
+template cudaError_t launch_to_canonical<double, float>(const GridInfo &, const double *, const double *, float *, int, cudaStream_t);
+template cudaError_t launch_to_canonical<float, float>(const GridInfo &, const float *, const double *, float *, int, cudaStream_t);

@@ -32,7 +32,7 @@ EXPORTED = [
     "qhfpe_closure_collect", "qhfpe_closure_load", "qhfpe_closure_coefficients", "qhfpe_closure_loss_grad",
     "qhfpe_closure_train", "qhfpe_tile_rows", "qhfpe_wait_selftest", "qhfpe_adiabatic_marginals",
     "qhfpe_first_order_distribution", "qhfpe_set_dipole_table", "qhfpe_batch_create", "qhfpe_batch_step",
-    "qhfpe_batch_tile_rows", "qhfpe_batch_destroy",
+    "qhfpe_batch_tile_rows", "qhfpe_batch_destroy", "qhfpe_set_state32", "qhfpe_get_state32",
 ]
 
 CLOSURE_N_WEIGHTS = 135178
@@ -87,6 +87,8 @@ def lib():
     L.qhfpe_max_stable_dt.argtypes = [vp, dp]
     L.qhfpe_set_state.argtypes = [vp, ctypes.c_int, vp, ctypes.c_int]
     L.qhfpe_get_state.argtypes = [vp, ctypes.c_int, vp, ctypes.c_int]
+    L.qhfpe_set_state32.argtypes = [vp, ctypes.c_int, vp, ctypes.c_int]
+    L.qhfpe_get_state32.argtypes = [vp, ctypes.c_int, vp, ctypes.c_int]
     L.qhfpe_fork.argtypes = [vp, ctypes.c_int, ip, ctypes.c_int]
     L.qhfpe_step.argtypes = [vp, ctypes.c_long, vp]
     L.qhfpe_apply_dipole.argtypes = [vp, ctypes.c_int, ip, ctypes.c_int]
@@ -126,6 +128,10 @@ def lib():
 
 def _ptr(a):
     return ctypes.c_void_p(a.ctypes.data)
+
+
+def _is_c64(t):
+    return str(getattr(t, "dtype", "")) in ("torch.complex64", "torch.float32")
 
 
 def _c128(a):
@@ -254,9 +260,17 @@ class Propagator:
 
     # ---- state -----------------------------------------------------------------------------------
     def set_state(self, W, replica=-1):
+        """Canonical state into one replica (or all, replica = -1): complex128, or complex64 (half the
+        bytes; numpy array or CUDA tensor of that dtype)."""
         if hasattr(W, "is_cuda"):
             ptr, dev = _dev_ptr(W)
-            self._check(self._L.qhfpe_set_state(self._h, replica, ptr, dev))
+            f = self._L.qhfpe_set_state32 if _is_c64(W) else self._L.qhfpe_set_state
+            self._check(f(self._h, replica, ptr, dev))
+            return
+        if isinstance(W, np.ndarray) and W.dtype == np.complex64:
+            W = np.ascontiguousarray(W)
+            assert W.shape == self.shape, (W.shape, self.shape)
+            self._check(self._L.qhfpe_set_state32(self._h, replica, _ptr(W), 0))
             return
         W = _c128(W)
         assert W.shape == self.shape, (W.shape, self.shape)
@@ -264,14 +278,18 @@ class Propagator:
 
     def get_state(self, replica=0, out=None):
         """Canonical complex128 state of one replica.  out: optional destination (numpy array, e.g. a
-        view of pinned memory, or a contiguous CUDA tensor of matching size)."""
+        view of pinned memory, or a contiguous CUDA tensor of matching size); a complex64 destination
+        receives the state rounded to FP32."""
         if out is not None and hasattr(out, "is_cuda"):
             ptr, dev = _dev_ptr(out)
-            self._check(self._L.qhfpe_get_state(self._h, replica, ptr, dev))
+            f = self._L.qhfpe_get_state32 if _is_c64(out) else self._L.qhfpe_get_state
+            self._check(f(self._h, replica, ptr, dev))
             return out
         if out is not None:
-            assert out.dtype == np.complex128 and out.flags.c_contiguous and out.size == int(np.prod(self.shape))
-            self._check(self._L.qhfpe_get_state(self._h, replica, _ptr(out), 0))
+            assert out.dtype in (np.complex128, np.complex64) and out.flags.c_contiguous
+            assert out.size == int(np.prod(self.shape))
+            f = self._L.qhfpe_get_state32 if out.dtype == np.complex64 else self._L.qhfpe_get_state
+            self._check(f(self._h, replica, _ptr(out), 0))
             return out
         out = np.empty(self.shape, dtype=np.complex128)
         self._check(self._L.qhfpe_get_state(self._h, replica, _ptr(out), 0))
