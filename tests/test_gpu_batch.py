@@ -35,6 +35,13 @@ MEMBERS = [
 ]
 
 
+# np = 64, three states, different grids, depths and bath modes
+MEMBERS_S3 = [
+    (qi.three_state(nq=12, n_p=64, depth=1, n_matsubara=1), 2),
+    (qi.three_state(nq=20, n_p=64, qr=(-8.0, 9.0), depth=2, n_matsubara=0, dt=5e-4), 1),
+]
+
+
 def _fill(P, k):
     for r in range(P.n_replicas):
         P.set_state(qi.random_state(P.model, seed=300 + 10 * k + r, hermitian=True), r)
@@ -101,3 +108,21 @@ def test_batch_argument_checks():
         Batch([d])
     for P in (a, b, c, d):
         P.close()
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("mixed", 1e-5)])
+def test_three_state_batch_equals_members_alone(precision, tol):
+    from paper_1706_09590_gb300 import Batch
+    batched = [_P(m, precision, n) for m, n in MEMBERS_S3]
+    alone = [_P(m, precision, n) for m, n in MEMBERS_S3]
+    for k, (a, b) in enumerate(zip(batched, alone)):
+        _fill(a, k)
+        _fill(b, k)
+    B = Batch(batched)
+    tr_b = B.step(5, record_trace=True)
+    for k, (a, b) in enumerate(zip(batched, alone)):
+        tr_a = b.step(5, record_trace=True)
+        assert rel(tr_b[k], tr_a) <= tol, k
+        for r in range(a.n_replicas):
+            assert rel(a.get_state(r), b.get_state(r)) <= tol, (k, r)
+    B.close()
