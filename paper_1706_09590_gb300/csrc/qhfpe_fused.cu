@@ -108,9 +108,20 @@ cudaError_t launch_fused_t(const GridInfo &g, const ElemInfo *elems, const Fused
     const long blocks = (long)tiles * n_rep * g.n_elem;
     if (blocks <= 0) return cudaSuccess;
     const StageScalars<T> sc = stage_scalars<T>(g, h);
-    fused_stage_kernel<T, NP, S, MIXED, false><<<(unsigned)blocks, FTHREADS, smem, st>>>(
-        g, elems, tab, sc, v_in, y, y0, v_out, y0_out, h, mode, terms, rep0, n_rep, tq, Pg, nullptr, 0, 0);
-    return cudaGetLastError();
+    // launched with programmatic stream serialisation: its blocks may be scheduled while the previous
+    // kernel drains (the kernel waits for it before reading the state)
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)blocks);
+    cfg.blockDim = dim3(FTHREADS);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, fused_stage_kernel<T, NP, S, MIXED, false>, g, elems, tab, sc, v_in, y, y0, v_out,
+                              y0_out, h, mode, terms, rep0, n_rep, tq, Pg, (const MultiMember<T> *)nullptr, 0, 0);
 }
 
 template <typename T, int NP, int S, bool MIXED>

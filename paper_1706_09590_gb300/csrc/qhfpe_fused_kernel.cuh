@@ -327,6 +327,10 @@ fused_stage_kernel(GridInfo g, const ElemInfo *__restrict__ elems, FusedTables<T
                    const T *y, const double *y0, T *v_out, double *y0_out, double h, int mode, int terms, int rep0,
                    int n_rep, int tq, const T *__restrict__ Pg, const MultiMember<T> *__restrict__ mem, int n_mem, int k)
 {
+    // Programmatic dependent launch: the next stage may start its blocks (prologue only) once every
+    // block of this one has started; it waits below for this grid's completion before touching the
+    // state.  Both are no-ops for a plain launch.
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     unsigned bid = blockIdx.x;
     if constexpr (MULTI) {
         __shared__ MultiMember<T> M;
@@ -416,6 +420,10 @@ fused_stage_kernel(GridInfo g, const ElemInfo *__restrict__ elems, FusedTables<T
         tw[t] = C{tab.tw[2 * t], tab.tw[2 * t + 1]};
         pgrid[t] = (T)(g.p_min + t * g.dp);
     }
+
+    // the previous launch on the stream (the stage whose output this one reads) has completed and its
+    // writes are visible
+    asm volatile("griddepcontrol.wait;" ::: "memory");
 
     // ---- phase A: potential term -------------------------------------------------------------
     const bool want_pot = (terms & 2) != 0;
