@@ -295,6 +295,10 @@ trace_partial_kernel(GridInfo g, const T *__restrict__ state, size_t rep_stride,
                      const double *__restrict__ mu_q, double *partial, int n_chunks)
 {
     __shared__ double red[2][256];
+    // programmatic dependent launch (no-ops for a plain launch): let the next kernel be scheduled, then
+    // wait for the stage that wrote the state
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    asm volatile("griddepcontrol.wait;" ::: "memory");
     const int chunk = blockIdx.x, rep = blockIdx.y;
     const int S = g.S;
     const size_t blk = g.blk;
@@ -345,6 +349,8 @@ __global__ void trace_finish_kernel(GridInfo g, const double *__restrict__ parti
     // one warp per replica, replicas spread over the blocks: lanes sum strided chunk partials, then a
     // fixed butterfly over the lanes (the same order on every call, so the result is reproducible bit
     // for bit)
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    asm volatile("griddepcontrol.wait;" ::: "memory");  // the partials are complete
     const long slot = sink->counter;
     const int lane = threadIdx.x & 31, warps = blockDim.x >> 5;
     const int n_warps = warps * gridDim.x;
@@ -617,14 +623,24 @@ cudaError_t launch_trace(const GridInfo &g, const T *state, size_t rep_stride, c
                          TraceSink *sink, int advance, double *partial, cudaStream_t st, const double *mu_q)
 {
     const int nc = trace_chunks(g.n_rep, g.blk);
-    trace_partial_kernel<T><<<dim3(nc, g.n_rep), 256, 0, st>>>(g, state, rep_stride, mu_dev, mu_q, partial, nc);
-    cudaError_t err = cudaGetLastError();
+    // both launched with programmatic stream serialisation (each waits for its predecessor in-kernel)
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(nc, g.n_rep);
+    cfg.blockDim = dim3(256);
+    cfg.stream = st;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cudaError_t err = cudaLaunchKernelEx(&cfg, trace_partial_kernel<T>, g, state, rep_stride, mu_dev, mu_q, partial, nc);
     if (err != cudaSuccess) return err;
     const int warps = 8;  // 256 threads, one warp per replica
     int nb = (g.n_rep + warps - 1) / warps;
     if (nb > 304) nb = 304;
-    trace_finish_kernel<<<nb, 32 * warps, 0, st>>>(g, partial, nc, sink, advance);
-    return cudaGetLastError();
+    cfg.gridDim = dim3(nb);
+    cfg.blockDim = dim3(32 * warps);
+    return cudaLaunchKernelEx(&cfg, trace_finish_kernel, g, (const double *)partial, nc, sink, advance);
 }
 
 // Raises the dynamic shared-memory limit of the potential kernels; called at set-up, outside any
