@@ -97,3 +97,21 @@ def test_null_handle_calls_fail_cleanly():
     assert L.qhfpe_step(None, 1, None) == 1
     assert L.qhfpe_destroy(None) == 1
     assert L.qhfpe_trace(None, None) == 1
+
+
+def test_null_batch_and_state32_calls_fail_cleanly():
+    import paper_1706_09590_gb300.qhfpe as q
+    L = q.lib()
+    out = ctypes.c_void_p()
+    assert L.qhfpe_batch_create(None, 0, ctypes.byref(out)) == 1
+    assert out.value is None
+    arr = (ctypes.c_void_p * 1)(None)
+    assert L.qhfpe_batch_create(arr, 1, ctypes.byref(out)) == 1  # a NULL member
+    assert L.qhfpe_batch_create(arr, 0, None) == 1
+    assert L.qhfpe_batch_step(None, 1, None) == 1
+    rows = ctypes.c_int(-1)
+    assert L.qhfpe_batch_tile_rows(None, ctypes.byref(rows)) == 1
+    assert L.qhfpe_batch_destroy(None) == 1
+    buf = np.zeros(4, dtype=np.complex64)
+    assert L.qhfpe_set_state32(None, 0, buf.ctypes.data, 0) == 1
+    assert L.qhfpe_get_state32(None, 0, buf.ctypes.data, 0) == 1
