@@ -139,9 +139,15 @@ void sym_eigvec(int S, const double *A, double *v)
                 }
             }
     }
-    int order[QH_MAX_S];
-    for (int k = 0; k < S; ++k) order[k] = k;
-    std::sort(order, order + S, [&](int x, int y) { return a[x][x] < a[y][y]; });
+    int order[QH_MAX_S];  // ascending eigenvalue (insertion sort, S <= QH_MAX_S, stable)
+    for (int k = 0; k < S; ++k) {
+        int m = k;
+        while (m > 0 && a[k][k] < a[order[m - 1]][order[m - 1]]) {
+            order[m] = order[m - 1];
+            --m;
+        }
+        order[m] = k;
+    }
     for (int col = 0; col < S; ++col) {
         const int src = order[col];
         double mx = 0.0;
