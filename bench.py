@@ -167,6 +167,30 @@ def spectrum_2d_measure(stream):
     return out
 
 
+def cpu_spectrum_baseline(seconds_cap=60.0):
+    """The FP64 oracle as it stands on this host's cores, on a bounded sub-schedule of the batched 2D
+    spectrum (ket pathway, the first two t1 delays, the first two waiting times, full t3 = 512 steps),
+    extrapolated to the full schedule by the number of RK4 steps (every step of the schedule costs
+    the same: one full-hierarchy step of the 32 x 32, depth-3 model)."""
+    import oracle
+    import qhfpe_inputs as qi
+    m = qi.harmonic_two_state()
+    O = oracle.Oracle(m)
+    W_eq, _ = O.equilibrate(300)
+    n_t1, t2, n_t3, stride = 2, SPEC2D["t2"][:2], SPEC2D["n_t3"], SPEC2D["t1_stride"]
+    t0 = time.perf_counter()
+    O.third_order_response(W_eq, n_t1, stride, t2, n_t3, first=oracle.LEFT)
+    dt = time.perf_counter() - t0
+
+    def steps(n1, t2s, n3):  # RK4 steps of one pathway
+        return (n1 - 1) * stride + n1 * (max(t2s) + len(t2s) * n3)
+    full = 2 * steps(SPEC2D["n_t1"], SPEC2D["t2"], n_t3)
+    sample = steps(n_t1, t2, n_t3)
+    return {"sample_s": dt, "sample": f"ket pathway, {n_t1} t1 x {len(t2)} t2 x t3 {n_t3} ({sample} RK4 steps)",
+            "full_schedule_steps": full, "extrapolated_s": dt * full / sample, "cores": oracle.num_threads(),
+            "kind": "oracle"}
+
+
 def paper_workload_measure(stream):
     """The paper's own model (Sec. III: Morse diabats, Gaussian coupling, 512 x 128 mesh, underdamped
     bath at depth 5; 1.57 M cells, L2-resident): RK4 throughput of the mixed form (CUDA events on the
@@ -522,6 +546,8 @@ def main():
             "roofline": roof, "clocks": clk.summary()}
     if not args.no_spectrum:
         line["spectrum_2d"] = spectrum_2d_measure(stream)
+        if not args.no_cpu_baseline and rank == 0:
+            line["spectrum_2d"]["cpu_baseline"] = cpu_spectrum_baseline()
     if not args.no_paper_workload:
         line["paper_workload"] = paper_workload_measure(stream)
     if not args.no_hetero_batch:
