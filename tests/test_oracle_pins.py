@@ -547,3 +547,54 @@ def test_rhs_rows_equal_the_full_rhs():
             assert np.array_equal(got[r], full[e, j, k, i])
     with pytest.raises(ValueError):
         O.rhs_rows(W, [(0, 0, 0, nq)])
+
+
+# ------------------------------------------------------------------------------------------------
+# Brownian-oscillator absorption: displaced harmonic surfaces without diabatic coupling, Drude bath
+# at high temperature (the K = 0 coefficients of Sec. II), R1 of Eq. (R1)
+# ------------------------------------------------------------------------------------------------
+def _brownian_oscillator_r1(d, gap, zeta, gamma, beta, t):
+    """Closed form (hbar = m = omega_0 = 1).  The energy gap U_1 - U_0 = gap + d^2/2 - d q is linear in
+    q and the dynamics is Gaussian, so the second-order cumulant is exact:
+        R1(t) = i (K - K*),  K(t) = Tr{e^{i H_0 t} e^{-i H_1 t} rho_eq} = exp(-i (gap + d^2/2) t - g(t)),
+        g(t) = int_0^t (t - s) C(s) ds,  C(s) = d^2 [C_sym(s) - (i/2) chi(s)],
+    with chi the response of q to a unit momentum kick and C_sym the symmetrised q correlation of the
+    oscillator under Drude friction (memory zeta gamma e^{-gamma t}) and the bath force of the high-
+    temperature reading, <F(t) F(0)> = (zeta/beta) gamma e^{-gamma |t|}.  Both follow from the linear
+    Markovian embedding x = (q, p, z, F): q' = p, p' = -q - z + F, z' = zeta gamma p - gamma z,
+    F' = -gamma F + noise, whose stationary covariance solves a Lyapunov equation."""
+    from scipy.integrate import cumulative_trapezoid
+    from scipy.linalg import expm, solve_continuous_lyapunov
+    A = np.array([[0.0, 1.0, 0.0, 0.0], [-1.0, 0.0, -1.0, 1.0], [0.0, zeta * gamma, -gamma, 0.0],
+                  [0.0, 0.0, 0.0, -gamma]])
+    noise = np.zeros((4, 4))
+    noise[3, 3] = 2.0 * (zeta / beta) * gamma ** 2
+    Sig = solve_continuous_lyapunov(A, -noise)
+    tf = np.linspace(0.0, t[-1], 20001)
+    Eh, E3h = expm(A * (tf[1] - tf[0])), expm(A[:3, :3] * (tf[1] - tf[0]))
+    M, R = Sig.copy(), np.eye(3)
+    csym, chi = np.empty(len(tf)), np.empty(len(tf))
+    for k in range(len(tf)):
+        csym[k], chi[k] = M[0, 0], R[0, 1]
+        M, R = Eh @ M, E3h @ R
+    C = d * d * (csym - 0.5j * chi)
+    g = cumulative_trapezoid(cumulative_trapezoid(C, tf, initial=0.0), tf, initial=0.0)
+    gt = np.interp(t, tf, g.real) + 1j * np.interp(t, tf, g.imag)
+    K = np.exp(-1j * (gap + 0.5 * d * d) * t - gt)
+    return 1j * (K - np.conj(K)), Sig[0, 0]
+
+
+def test_brownian_oscillator_absorption_closed_form():
+    # small displacement and 15 time units, so that the vibrational recurrences and their damping by
+    # the bath shape R1: the closed form with zeta or gamma off by 10-20 % is 1.5e-2 - 2.6e-2 away,
+    # without the bath 0.87 away
+    d, gap, zeta, gamma, beta = 0.5, 10.0, 1.0, 1.0, 0.48
+    m = _model(nq=32, n_p=32, coupling=0.0, displacement=d, gap=gap, eta=zeta, gamma=gamma, beta=beta,
+               depth=4, dt=0.01)
+    O = oracle.Oracle(m)
+    W_eq, _ = O.equilibrate(3000)
+    n_t = 1500
+    R1 = O.linear_response(W_eq, n_t)
+    ref, q_var = _brownian_oscillator_r1(d, gap, zeta, gamma, beta, np.arange(n_t + 1) * m["dt"])
+    assert abs(q_var - 1.0 / beta) < 1e-9  # the high-temperature reading: classical <q^2> = 1 / beta
+    assert _relerr(R1, ref) < 1e-3  # measured 1.1e-4
