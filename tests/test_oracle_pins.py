@@ -600,6 +600,7 @@ def test_brownian_oscillator_absorption_closed_form():
     assert _relerr(R1, ref) < 1e-3  # measured 1.1e-4
 
 
+@pytest.mark.slow
 def test_third_order_response_against_vibrational_basis_heom():
     """Eq. (R3), R3 = i^3 Tr{mu G(t3) mu^x G(t2) mu^x G(t1) mu^x W_eq}, against the same hierarchy written
     for density matrices in a truncated vibrational basis (an independent method), on a small
@@ -643,3 +644,43 @@ def test_third_order_response_against_vibrational_basis_heom():
                 R3_h[b, a, c] = (1j) ** 3 * np.trace(B.mu @ Y[0])
     # the two truncations (48 x 48 phase-space grid vs 36 vibrational levels): measured 4.3e-5
     assert _relerr(R3_w, R3_h) < 5e-4
+
+
+@pytest.mark.slow
+def test_noncondon_linear_response_against_vibrational_basis_heom():
+    """A coordinate-dependent transition dipole mu_01(q) = 1 + s q (Sec. III: the dipole operators then
+    act as p-convolutions in the Wigner representation) against the vibrational-basis hierarchy, where
+    mu(q) is simply the operator 1 + s q."""
+    from oracle import noncondon as nc
+    beta, eta, gamma, depth, s = 1.0, 0.3, 1.0, 3, 0.2
+    d, E, V = [0.0, 1.0], [0.0, 2.0], [[0, 0.3], [0.3, 0]]
+    m = _model(nq=48, n_p=48, qr=(-8.0, 8.0), pr=(-8.0, 8.0), displacement=d[1], gap=E[1], coupling=0.3,
+               eta=eta, gamma=gamma, beta=beta, depth=depth, dt=0.01)
+    O = oracle.Oracle(m)
+    co = O.coefficients()
+    Weq, _ = O.equilibrate(4000)
+    n_t = 400
+    R1_w = nc.linear_response(O, Weq, qi.function_table(m, qi.linear_dipole(m, slope=s)), n_t)
+
+    n_v = 36
+    B1 = _HOBasisHEOM(1, n_v, [0.0], [0.0], [[0]], co, depth, np.array([[1.0]]))
+    rho0 = np.zeros((depth + 1, n_v, n_v), complex)
+    w, U = np.linalg.eigh(B1.H)
+    th = U @ np.diag(np.exp(-beta * w)) @ U.conj().T
+    rho0[0] = th / np.trace(th)
+    rho_eq = B1.rk4(rho0, 0.02, 2000)
+    B = _HOBasisHEOM(2, n_v, d, E, V, co, depth, m["mu"])
+    q = B.Q[:n_v, :n_v]
+    B.mu = np.kron(np.asarray(m["mu"], dtype=float), np.eye(n_v) + s * q)
+    R = np.zeros((depth + 1, 2 * n_v, 2 * n_v), complex)
+    R[:, :n_v, :n_v] = rho_eq
+    R = np.array([B.mu @ X - X @ B.mu for X in R])
+    R1_h = [1j * np.trace(B.mu @ R[0])]
+    for _ in range(n_t):
+        R = B.rk4(R, m["dt"], 1)
+        R1_h.append(1j * np.trace(B.mu @ R[0]))
+    R1_h = np.array(R1_h)
+    err = _relerr(R1_w, R1_h)
+    assert err < 1e-3  # measured 6.1e-4: the two truncations, as for the Condon R1
+    # and the coordinate dependence matters at this size: the Condon response is far away
+    assert _relerr(O.linear_response(Weq, n_t), R1_h) > 20 * err
