@@ -794,3 +794,40 @@ def test_first_order_distribution_marginals_against_vibrational_basis_heom():
         marg_h = np.array([[np.einsum("mi,mn,ni->i", phi, Wk[j * n_v:(j + 1) * n_v, l * n_v:(l + 1) * n_v], phi)
                             for l in range(2)] for j in range(2)])
         assert _relerr(marg_w[k], marg_h) < 2e-3, omega[k]  # measured 4.9e-4 at each omega
+
+
+@pytest.mark.slow
+def test_three_state_linear_response_against_vibrational_basis_heom():
+    """Three displaced harmonic diabats with pairwise constant couplings (the S x S mixing of the
+    potential kernel with S = 3) and mu_0j = mu_j0 = 1: R1 against the vibrational-basis hierarchy."""
+    beta, eta, gamma, depth = 1.0, 0.3, 1.0, 3
+    d, E = [0.0, 1.0, -0.8], [0.0, 2.0, 2.6]
+    V = [[0, 0.2, 0.15], [0.2, 0, 0.3], [0.15, 0.3, 0]]
+    U = [[(lambda j: (lambda q: 0.5 * (np.asarray(q) - d[j]) ** 2 + E[j]))(j) if j == k else
+          (lambda c: (lambda q: np.full(np.shape(q), float(c))))(V[j][k]) for k in range(3)] for j in range(3)]
+    mu = np.array([[0.0, 1.0, 1.0], [1.0, 0.0, 0.0], [1.0, 0.0, 0.0]])
+    m = dict(name="harmonic_three_state", S=3, nq=48, np=48, q_min=-8.0, q_max=8.0, p_min=-8.0, p_max=8.0,
+             U=U, mu=mu, eta=eta, gamma=gamma, beta=beta, n_matsubara=0, high_temperature=1, use_cdelta=0,
+             depth=depth, closure=1, dt=0.01, periodic_q=0)
+    O = oracle.Oracle(m, qi.u_table(m))
+    co = O.coefficients()
+    Weq, _ = O.equilibrate(4000)
+    n_t = 400
+    R1_w = O.linear_response(Weq, n_t)
+
+    n_v = 30
+    B1 = _HOBasisHEOM(1, n_v, [0.0], [0.0], [[0]], co, depth, np.array([[1.0]]))
+    rho0 = np.zeros((depth + 1, n_v, n_v), complex)
+    w, Uv = np.linalg.eigh(B1.H)
+    th = Uv @ np.diag(np.exp(-beta * w)) @ Uv.conj().T
+    rho0[0] = th / np.trace(th)
+    rho_eq = B1.rk4(rho0, 0.02, 2000)
+    B = _HOBasisHEOM(3, n_v, d, E, V, co, depth, mu)
+    R = np.zeros((depth + 1, 3 * n_v, 3 * n_v), complex)
+    R[:, :n_v, :n_v] = rho_eq
+    R = np.array([B.mu @ X - X @ B.mu for X in R])
+    R1_h = [1j * np.trace(B.mu @ R[0])]
+    for _ in range(n_t):
+        R = B.rk4(R, m["dt"], 1)
+        R1_h.append(1j * np.trace(B.mu @ R[0]))
+    assert _relerr(R1_w, np.array(R1_h)) < 1e-3  # measured 1.7e-4
