@@ -96,3 +96,30 @@ def first_order_distribution(O, W_eq, mu_table, n_t1, t1_stride, omega):
             Fm[k] += wts[a] * np.exp(-1j * om * a * dt1) * X
     return np.stack([1j * (apply_dipole(Fp[k], mu_table, LEFT) - apply_dipole(Fm[k], mu_table, RIGHT))
                      for k in range(len(omega))])
+
+
+def third_order_response(O, W_eq, mu_table, n_t1, t1_stride, t2_steps, n_t3, first=COMMUTATOR):
+    """R3(t3, t2, t1) = i^3 Tr{mu G(t3) mu^x G(t2) mu^x G(t1) mu^x W_eq} (Eq. (R3)) with the
+    coordinate-dependent dipole in every interaction and in the trace, on t1 = a t1_stride dt
+    (a < n_t1), t2 in t2_steps dt, t3 = c dt (c <= n_t3); `first` as in Oracle.third_order_response
+    (LEFT: mu^->, RIGHT: -mu^<-).  Propagation by the oracle's RK4 O.step.
+    Returns [len(t2_steps)][n_t1][n_t3 + 1]."""
+    W = apply_dipole(W_eq, mu_table, first)
+    if first == RIGHT:
+        W = -W
+    out = np.zeros((len(t2_steps), n_t1, n_t3 + 1), dtype=np.complex128)
+    for a in range(n_t1):
+        if a > 0:
+            W, _ = O.step(W, t1_stride)
+        X = apply_dipole(W, mu_table, COMMUTATOR)
+        done = 0
+        for b, t2 in enumerate(t2_steps):
+            if t2 > done:
+                X, _ = O.step(X, t2 - done)
+                done = t2
+            Y = apply_dipole(X, mu_table, COMMUTATOR)
+            out[b, a, 0] = (1j) ** 3 * trace(Y, mu_table, O.dq, O.dp)
+            for c in range(1, n_t3 + 1):
+                Y, _ = O.step(Y, 1)
+                out[b, a, c] = (1j) ** 3 * trace(Y, mu_table, O.dq, O.dp)
+    return out

@@ -912,3 +912,53 @@ def test_matsubara_linear_response_against_vibrational_basis_heom():
         R = g2.rk4(R, m["dt"], 1)
         R1_h.append(1j * np.trace(base.mu @ R[0]))
     assert _relerr(R1_w, np.array(R1_h)) < 1e-3  # measured 2.9e-4
+
+
+@pytest.mark.slow
+def test_noncondon_third_order_response_against_vibrational_basis_heom():
+    """Eq. (R3) with the coordinate-dependent dipole mu_01(q) = 1 + 0.2 q in all three interactions and
+    the trace, against the vibrational-basis hierarchy with the dipole operator 1 + 0.2 q."""
+    from oracle import noncondon as nc
+    beta, eta, gamma, depth, s = 1.0, 0.3, 1.0, 3, 0.2
+    d, E, V = [0.0, 1.0], [0.0, 2.0], [[0, 0.3], [0.3, 0]]
+    m = _model(nq=48, n_p=48, qr=(-8.0, 8.0), pr=(-8.0, 8.0), displacement=d[1], gap=E[1], coupling=0.3,
+               eta=eta, gamma=gamma, beta=beta, depth=depth, dt=0.01)
+    O = oracle.Oracle(m)
+    co = O.coefficients()
+    Weq, _ = O.equilibrate(4000)
+    n_t1, stride, t2_steps, n_t3 = 2, 20, [0, 30], 60
+    T = qi.function_table(m, qi.linear_dipole(m, slope=s))
+    R3_w = nc.third_order_response(O, Weq, T, n_t1, stride, t2_steps, n_t3)
+
+    n_v = 36
+    B1 = _HOBasisHEOM(1, n_v, [0.0], [0.0], [[0]], co, depth, np.array([[1.0]]))
+    rho0 = np.zeros((depth + 1, n_v, n_v), complex)
+    w, U = np.linalg.eigh(B1.H)
+    th = U @ np.diag(np.exp(-beta * w)) @ U.conj().T
+    rho0[0] = th / np.trace(th)
+    rho_eq = B1.rk4(rho0, 0.02, 2000)
+    B = _HOBasisHEOM(2, n_v, d, E, V, co, depth, m["mu"])
+    B.mu = np.kron(np.asarray(m["mu"], dtype=float), np.eye(n_v) + s * B.Q[:n_v, :n_v])
+    comm = lambda R: np.array([B.mu @ X - X @ B.mu for X in R])
+    R = np.zeros((depth + 1, 2 * n_v, 2 * n_v), complex)
+    R[:, :n_v, :n_v] = rho_eq
+    R = comm(R)
+    R3_h = np.zeros((len(t2_steps), n_t1, n_t3 + 1), complex)
+    for a in range(n_t1):
+        if a > 0:
+            R = B.rk4(R, m["dt"], stride)
+        X = comm(R)
+        done = 0
+        for b, t2 in enumerate(t2_steps):
+            if t2 > done:
+                X = B.rk4(X, m["dt"], t2 - done)
+                done = t2
+            Y = comm(X)
+            R3_h[b, a, 0] = (1j) ** 3 * np.trace(B.mu @ Y[0])
+            for c in range(1, n_t3 + 1):
+                Y = B.rk4(Y, m["dt"], 1)
+                R3_h[b, a, c] = (1j) ** 3 * np.trace(B.mu @ Y[0])
+    err = _relerr(R3_w, R3_h)
+    assert err < 5e-4  # measured 2.0e-5
+    # the coordinate dependence matters here: the Condon R3 is 7.4e-2 away
+    assert _relerr(O.third_order_response(Weq, n_t1, stride, t2_steps, n_t3), R3_h) > 100 * err
