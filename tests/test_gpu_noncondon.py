@@ -1,7 +1,8 @@
 """Coordinate-dependent (non-Condon) dipoles (Sec. III) through the C ABI: the dipole super-operators
 on every tier against the numpy oracle (two and three states, FP64 and mixed forms, a replica subset),
-a coordinate-independent table against the Condon path, the linear response R1 against the oracle, the
-return to the Condon dipole, and the argument checks."""
+a coordinate-independent table against the Condon path, the linear response R1, W'(omega) and the
+third-order response R3 (split pathways and plain) against the oracle, the return to the Condon
+dipole, and the argument checks."""
 import numpy as np
 import pytest
 
@@ -132,4 +133,25 @@ def test_first_order_distribution_with_a_coordinate_dependent_dipole(precision, 
     got = P.first_order_distribution(10, 4, omega)
     for k in range(len(omega)):
         assert rel(got[k], ref[k]) < tol, (precision, omega[k], rel(got[k], ref[k]))
+    P.close()
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-10), ("mixed", 1e-5)])
+def test_third_order_response_matches_the_oracle(precision, tol):
+    """Eq. (R3) with the coordinate-dependent dipole in every interaction and the trace: the batched
+    schedule (split pathways and the plain commutator) against the oracle's composition."""
+    m = qi.harmonic_two_state(nq=32, n_p=32, depth=2)
+    O = oracle.Oracle(m)
+    Weq, _ = O.equilibrate(300)
+    T = qi.function_table(m, qi.linear_dipole(m, slope=0.25))
+    args = (3, 4, [0, 6], 12)
+    ket = nc.third_order_response(O, Weq, T, *args, first=nc.LEFT)
+    bra = nc.third_order_response(O, Weq, T, *args, first=nc.RIGHT)
+    P = _P(m, precision)
+    P.set_dipole_table(T)
+    P.set_equilibrium(Weq)
+    got = P.third_order_response(*args, split_pathways=True)
+    assert rel(got[0], ket) < tol
+    assert rel(got[1], bra) < tol
+    assert rel(P.third_order_response(*args, split_pathways=False), ket + bra) < tol
     P.close()
