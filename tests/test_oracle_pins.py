@@ -4,6 +4,7 @@ Each test names what it pins.  None of them re-types the oracle's own formula: t
 (tests/golden), closed forms, exact discrete identities, invariants, special cases and an independent
 method (a density-matrix HEOM in a truncated vibrational basis).
 """
+import functools
 import itertools
 import math
 import os
@@ -382,27 +383,39 @@ class _HOBasisHEOM:
         return R
 
 
-@pytest.mark.slow
-def test_linear_response_against_vibrational_basis_heom():
+@functools.lru_cache(maxsize=1)
+def _vib_case():
+    """The two-state model shared by the comparisons with the vibrational-basis hierarchy (displaced
+    harmonic diabats, coupling 0.3, beta = 1, zeta = 0.3, gamma = 1, depth 3, 48 x 48 grid) with its
+    equilibrium in both representations: the oracle's (4000 RK4 steps from the Boltzmann start) and the
+    density-matrix one (the canonical state relaxed by the ground-state hierarchy, 2000 steps of 0.02).
+    Returns (model, oracle, bath coefficients, W_eq, rho_eq tiers, d, E, V, depth, n_v)."""
     beta, eta, gamma, depth = 1.0, 0.3, 1.0, 3
     d, E, V = [0.0, 1.0], [0.0, 2.0], [[0, 0.3], [0.3, 0]]
     m = _model(nq=48, n_p=48, qr=(-8.0, 8.0), pr=(-8.0, 8.0), displacement=d[1], gap=E[1], coupling=0.3,
                eta=eta, gamma=gamma, beta=beta, depth=depth, dt=0.01)
     O = oracle.Oracle(m)
     co = O.coefficients()
-    Weq, res = O.equilibrate(4000)
-    n_t = 400
-    R1_w = O.linear_response(Weq, n_t)
-
+    Weq, _ = O.equilibrate(4000)
+    Weq.setflags(write=False)
     n_v = 36
-    mu = m["mu"]
     B1 = _HOBasisHEOM(1, n_v, [0.0], [0.0], [[0]], co, depth, np.array([[1.0]]))
     rho0 = np.zeros((depth + 1, n_v, n_v), complex)
-    Hg = B1.H
-    w, U = np.linalg.eigh(Hg)
+    w, U = np.linalg.eigh(B1.H)
     th = U @ np.diag(np.exp(-beta * w)) @ U.conj().T
     rho0[0] = th / np.trace(th)
     rho_eq = B1.rk4(rho0, 0.02, 2000)
+    rho_eq.setflags(write=False)
+    return m, O, co, Weq, rho_eq, d, E, V, depth, n_v
+
+
+@pytest.mark.slow
+def test_linear_response_against_vibrational_basis_heom():
+    m, O, co, Weq, rho_eq, d, E, V, depth, n_v = _vib_case()
+    n_t = 400
+    R1_w = O.linear_response(Weq, n_t)
+
+    mu = m["mu"]
     B = _HOBasisHEOM(2, n_v, d, E, V, co, depth, mu)
     R = np.zeros((depth + 1, 2 * n_v, 2 * n_v), complex)
     R[:, :n_v, :n_v] = rho_eq
@@ -606,23 +619,10 @@ def test_third_order_response_against_vibrational_basis_heom():
     """Eq. (R3), R3 = i^3 Tr{mu G(t3) mu^x G(t2) mu^x G(t1) mu^x W_eq}, against the same hierarchy written
     for density matrices in a truncated vibrational basis (an independent method), on a small
     schedule: two t1 delays, two waiting times, 100 t3 steps."""
-    beta, eta, gamma, depth = 1.0, 0.3, 1.0, 3
-    d, E, V = [0.0, 1.0], [0.0, 2.0], [[0, 0.3], [0.3, 0]]
-    m = _model(nq=48, n_p=48, qr=(-8.0, 8.0), pr=(-8.0, 8.0), displacement=d[1], gap=E[1], coupling=0.3,
-               eta=eta, gamma=gamma, beta=beta, depth=depth, dt=0.01)
-    O = oracle.Oracle(m)
-    co = O.coefficients()
-    Weq, _ = O.equilibrate(4000)
+    m, O, co, Weq, rho_eq, d, E, V, depth, n_v = _vib_case()
     n_t1, stride, t2_steps, n_t3 = 2, 20, [0, 30], 100
     R3_w = O.third_order_response(Weq, n_t1, stride, t2_steps, n_t3)
 
-    n_v = 36
-    B1 = _HOBasisHEOM(1, n_v, [0.0], [0.0], [[0]], co, depth, np.array([[1.0]]))
-    rho0 = np.zeros((depth + 1, n_v, n_v), complex)
-    w, U = np.linalg.eigh(B1.H)
-    th = U @ np.diag(np.exp(-beta * w)) @ U.conj().T
-    rho0[0] = th / np.trace(th)
-    rho_eq = B1.rk4(rho0, 0.02, 2000)
     B = _HOBasisHEOM(2, n_v, d, E, V, co, depth, m["mu"])
     comm = lambda R: np.array([B.mu @ X - X @ B.mu for X in R])
     R = np.zeros((depth + 1, 2 * n_v, 2 * n_v), complex)
@@ -653,23 +653,11 @@ def test_noncondon_linear_response_against_vibrational_basis_heom():
     act as p-convolutions in the Wigner representation) against the vibrational-basis hierarchy, where
     mu(q) is simply the operator 1 + s q."""
     from oracle import noncondon as nc
-    beta, eta, gamma, depth, s = 1.0, 0.3, 1.0, 3, 0.2
-    d, E, V = [0.0, 1.0], [0.0, 2.0], [[0, 0.3], [0.3, 0]]
-    m = _model(nq=48, n_p=48, qr=(-8.0, 8.0), pr=(-8.0, 8.0), displacement=d[1], gap=E[1], coupling=0.3,
-               eta=eta, gamma=gamma, beta=beta, depth=depth, dt=0.01)
-    O = oracle.Oracle(m)
-    co = O.coefficients()
-    Weq, _ = O.equilibrate(4000)
+    s = 0.2
+    m, O, co, Weq, rho_eq, d, E, V, depth, n_v = _vib_case()
     n_t = 400
     R1_w = nc.linear_response(O, Weq, qi.function_table(m, qi.linear_dipole(m, slope=s)), n_t)
 
-    n_v = 36
-    B1 = _HOBasisHEOM(1, n_v, [0.0], [0.0], [[0]], co, depth, np.array([[1.0]]))
-    rho0 = np.zeros((depth + 1, n_v, n_v), complex)
-    w, U = np.linalg.eigh(B1.H)
-    th = U @ np.diag(np.exp(-beta * w)) @ U.conj().T
-    rho0[0] = th / np.trace(th)
-    rho_eq = B1.rk4(rho0, 0.02, 2000)
     B = _HOBasisHEOM(2, n_v, d, E, V, co, depth, m["mu"])
     q = B.Q[:n_v, :n_v]
     B.mu = np.kron(np.asarray(m["mu"], dtype=float), np.eye(n_v) + s * q)
@@ -695,25 +683,12 @@ def test_adiabatic_marginals_against_vibrational_basis_heom():
     eigenfunctions phi_n, rotated by the eigenvectors of the diabatic matrix U(q) (ascending
     eigenvalue, first largest-magnitude component positive)."""
     from oracle import marginals as mg
-    beta, eta, gamma, depth = 1.0, 0.3, 1.0, 3
-    d, E, V = [0.0, 1.0], [0.0, 2.0], [[0, 0.3], [0.3, 0]]
-    m = _model(nq=48, n_p=48, qr=(-8.0, 8.0), pr=(-8.0, 8.0), displacement=d[1], gap=E[1], coupling=0.3,
-               eta=eta, gamma=gamma, beta=beta, depth=depth, dt=0.01)
-    O = oracle.Oracle(m)
-    co = O.coefficients()
-    Weq, _ = O.equilibrate(4000)
+    m, O, co, Weq, rho_eq, d, E, V, depth, n_v = _vib_case()
     n_t = 200
     W, _ = O.step(O.apply_dipole(Weq, oracle.LEFT), n_t)
     dp = (m["p_max"] - m["p_min"]) / m["np"]
     P_w = mg.adiabatic_marginals(W, qi.u_table(m), dp)
 
-    n_v = 36
-    B1 = _HOBasisHEOM(1, n_v, [0.0], [0.0], [[0]], co, depth, np.array([[1.0]]))
-    rho0 = np.zeros((depth + 1, n_v, n_v), complex)
-    w, U = np.linalg.eigh(B1.H)
-    th = U @ np.diag(np.exp(-beta * w)) @ U.conj().T
-    rho0[0] = th / np.trace(th)
-    rho_eq = B1.rk4(rho0, 0.02, 2000)
     B = _HOBasisHEOM(2, n_v, d, E, V, co, depth, m["mu"])
     R = np.zeros((depth + 1, 2 * n_v, 2 * n_v), complex)
     R[:, :n_v, :n_v] = rho_eq
@@ -751,25 +726,12 @@ def test_first_order_distribution_marginals_against_vibrational_basis_heom():
     """The frequency-domain first-order distribution W'(omega_1) of Sec. III (trapezoid Fourier sums of
     the t1 propagation after mu^x, then i [mu^-> F(omega) - mu^<- F(-omega)]), integrated over p, against
     the same construction for density matrices in the vibrational basis, in position representation."""
-    beta, eta, gamma, depth = 1.0, 0.3, 1.0, 3
-    d, E, V = [0.0, 1.0], [0.0, 2.0], [[0, 0.3], [0.3, 0]]
-    m = _model(nq=48, n_p=48, qr=(-8.0, 8.0), pr=(-8.0, 8.0), displacement=d[1], gap=E[1], coupling=0.3,
-               eta=eta, gamma=gamma, beta=beta, depth=depth, dt=0.01)
-    O = oracle.Oracle(m)
-    co = O.coefficients()
-    Weq, _ = O.equilibrate(4000)
+    m, O, co, Weq, rho_eq, d, E, V, depth, n_v = _vib_case()
     n_t1, stride, omega = 6, 10, np.array([2.0, -2.0, 2.6])
     Wp = O.first_order_distribution(Weq, n_t1, stride, omega)
     dp = (m["p_max"] - m["p_min"]) / m["np"]
     marg_w = Wp[:, 0].sum(axis=-1) * dp  # [omega][S][S][nq]
 
-    n_v = 36
-    B1 = _HOBasisHEOM(1, n_v, [0.0], [0.0], [[0]], co, depth, np.array([[1.0]]))
-    rho0 = np.zeros((depth + 1, n_v, n_v), complex)
-    w, U = np.linalg.eigh(B1.H)
-    th = U @ np.diag(np.exp(-beta * w)) @ U.conj().T
-    rho0[0] = th / np.trace(th)
-    rho_eq = B1.rk4(rho0, 0.02, 2000)
     B = _HOBasisHEOM(2, n_v, d, E, V, co, depth, m["mu"])
     R = np.zeros((depth + 1, 2 * n_v, 2 * n_v), complex)
     R[:, :n_v, :n_v] = rho_eq
@@ -919,24 +881,12 @@ def test_noncondon_third_order_response_against_vibrational_basis_heom():
     """Eq. (R3) with the coordinate-dependent dipole mu_01(q) = 1 + 0.2 q in all three interactions and
     the trace, against the vibrational-basis hierarchy with the dipole operator 1 + 0.2 q."""
     from oracle import noncondon as nc
-    beta, eta, gamma, depth, s = 1.0, 0.3, 1.0, 3, 0.2
-    d, E, V = [0.0, 1.0], [0.0, 2.0], [[0, 0.3], [0.3, 0]]
-    m = _model(nq=48, n_p=48, qr=(-8.0, 8.0), pr=(-8.0, 8.0), displacement=d[1], gap=E[1], coupling=0.3,
-               eta=eta, gamma=gamma, beta=beta, depth=depth, dt=0.01)
-    O = oracle.Oracle(m)
-    co = O.coefficients()
-    Weq, _ = O.equilibrate(4000)
+    s = 0.2
+    m, O, co, Weq, rho_eq, d, E, V, depth, n_v = _vib_case()
     n_t1, stride, t2_steps, n_t3 = 2, 20, [0, 30], 60
     T = qi.function_table(m, qi.linear_dipole(m, slope=s))
     R3_w = nc.third_order_response(O, Weq, T, n_t1, stride, t2_steps, n_t3)
 
-    n_v = 36
-    B1 = _HOBasisHEOM(1, n_v, [0.0], [0.0], [[0]], co, depth, np.array([[1.0]]))
-    rho0 = np.zeros((depth + 1, n_v, n_v), complex)
-    w, U = np.linalg.eigh(B1.H)
-    th = U @ np.diag(np.exp(-beta * w)) @ U.conj().T
-    rho0[0] = th / np.trace(th)
-    rho_eq = B1.rk4(rho0, 0.02, 2000)
     B = _HOBasisHEOM(2, n_v, d, E, V, co, depth, m["mu"])
     B.mu = np.kron(np.asarray(m["mu"], dtype=float), np.eye(n_v) + s * B.Q[:n_v, :n_v])
     comm = lambda R: np.array([B.mu @ X - X @ B.mu for X in R])
