@@ -59,52 +59,133 @@ def cells_of(m, n_elem):
 
 
 class Clocks:
-    """Samples SM clocks and throttle reasons with nvidia-smi during the timed region."""
+    """SM clock, power and clock-event (throttle) reasons of THIS process's GPU, sampled every ~2 ms
+    while the benchmark runs; samples taken while the timed region is open are kept apart.
 
-    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+    The GPU is named by its UUID (from torch), never by an index: nvidia-smi and NVML do not see
+    CUDA_VISIBLE_DEVICES, so an index can name another user's GPU.  Queries are read-only: in-process
+    NVML through ctypes when the driver library loads, else `nvidia-smi -i GPU-<uuid>` at 20 ms."""
+
+    # clock-event reason bits of NVML
+    BITS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown", 0x40: "hw_thermal_slowdown",
+            0x80: "hw_power_brake_slowdown"}
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
          "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
          "clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, index):
-        self.index = index
-        self.rows = []
-        self.proc = None
-
-    def __enter__(self):
+    def __init__(self, local_index):
+        import torch
+        self.uuid = None
         try:
-            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
-                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
-            self.t = threading.Thread(target=self._read, daemon=True)
-            self.t.start()
-        except (OSError, FileNotFoundError):
-            self.proc = None
-        return self
+            u = str(torch.cuda.get_device_properties(local_index).uuid)
+            self.uuid = u if u.startswith("GPU-") else "GPU-" + u
+        except (AttributeError, RuntimeError):
+            pass
+        self.rows = []          # (sm_mhz, reasons bitmask or names, power_w, in_timed)
+        self.max_mhz = None
+        self.timed = False
+        self.source = None
+        self.error = None
+        self._stop = threading.Event()
+        self._nvml = None
+        self.proc = None
+        self.t = None
 
-    def _read(self):
+    # -- NVML through ctypes ------------------------------------------------------------------------
+    def _nvml_open(self):
+        import ctypes
+        lib = ctypes.CDLL("libnvidia-ml.so.1")
+        if lib.nvmlInit_v2() != 0:
+            raise OSError("nvmlInit_v2 failed")
+        h = ctypes.c_void_p()
+        if lib.nvmlDeviceGetHandleByUUID(self.uuid.encode(), ctypes.byref(h)) != 0:
+            raise OSError("no NVML device with UUID " + self.uuid)
+        mx = ctypes.c_uint()
+        if lib.nvmlDeviceGetMaxClockInfo(h, 1, ctypes.byref(mx)) == 0:  # NVML_CLOCK_SM
+            self.max_mhz = float(mx.value)
+        reasons = getattr(lib, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+            lib.nvmlDeviceGetCurrentClocksThrottleReasons
+        self._nvml = (ctypes, lib, h, reasons)
+
+    def _nvml_loop(self):
+        ctypes, lib, h, reasons = self._nvml
+        clk, pw, rs = ctypes.c_uint(), ctypes.c_uint(), ctypes.c_ulonglong()
+        while not self._stop.is_set():
+            ok = lib.nvmlDeviceGetClockInfo(h, 1, ctypes.byref(clk)) == 0
+            r = reasons(h, ctypes.byref(rs)) == 0
+            p = lib.nvmlDeviceGetPowerUsage(h, ctypes.byref(pw)) == 0
+            if ok:
+                self.rows.append((float(clk.value), int(rs.value) if r else 0, pw.value / 1e3 if p else None,
+                                  self.timed))
+            self._stop.wait(0.002)
+
+    # -- nvidia-smi fallback ------------------------------------------------------------------------
+    def _smi_loop(self):
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for line in self.proc.stdout:
             parts = [x.strip() for x in line.split(",")]
-            if len(parts) >= 9:
-                self.rows.append(parts)
+            if len(parts) < 7 or not parts[0].replace(".", "").isdigit():
+                continue
+            if parts[1].replace(".", "").isdigit():
+                self.max_mhz = float(parts[1])
+            act = [names[k] for k in range(4) if parts[3 + k].lower() == "active"]
+            pw = float(parts[2]) if parts[2].replace(".", "").isdigit() else None
+            self.rows.append((float(parts[0]), act, pw, self.timed))
+
+    def __enter__(self):
+        if self.uuid is None:
+            self.error = "no device UUID from torch"
+            return self
+        try:
+            self._nvml_open()
+            self.source = "nvml (in-process, read-only, ~2 ms)"
+            self.t = threading.Thread(target=self._nvml_loop, daemon=True)
+        except (OSError, AttributeError) as ex:
+            self.error = f"nvml: {ex}"
+            try:
+                self.proc = subprocess.Popen(["nvidia-smi", "-i", self.uuid, f"--query-gpu={self.Q}",
+                                              "--format=csv,noheader,nounits", "-lms", "20"],
+                                             stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+                self.source = "nvidia-smi -i <uuid> -lms 20"
+                self.t = threading.Thread(target=self._smi_loop, daemon=True)
+            except OSError as ex2:
+                self.error += f"; nvidia-smi: {ex2}"
+                return self
+        self.t.start()
+        return self
 
     def __exit__(self, *a):
+        self._stop.set()
         if self.proc:
             self.proc.terminate()
             try:
                 self.proc.wait(timeout=5)
             except subprocess.TimeoutExpired:
                 self.proc.kill()
+        if self.t:
             self.t.join(timeout=2)
+        if self._nvml:
+            self._nvml[1].nvmlShutdown()
+
+    def _names(self, r):
+        if isinstance(r, list):
+            return set(r)
+        return {n for b, n in self.BITS.items() if r & b}
 
     def summary(self):
-        if not self.rows:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
-        sm = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
-        mx = [float(r[2]) for r in self.rows if r[2].replace(".", "").isdigit()]
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({names[k] for r in self.rows for k in range(4) if r[5 + k].lower() == "active"})
-        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
-                "reasons": reasons, "samples": len(self.rows)}
+        timed = [r for r in self.rows if r[3]]
+        use = timed if timed else self.rows
+        out = {"sm_mhz": statistics.median(r[0] for r in use) if use else None, "sm_max_mhz": self.max_mhz,
+               "reasons": sorted(set().union(*[self._names(r[1]) for r in use])) if use else ["unsampled"],
+               "samples_timed": len(timed), "samples_total": len(self.rows), "source": self.source,
+               "gpu_uuid": self.uuid}
+        pw = [r[2] for r in use if r[2] is not None]
+        if pw:
+            out["power_w_max"] = max(pw)
+        if not timed:
+            out["note"] = "no sample inside the timed region; figures from the whole run" if use else \
+                (self.error or "no samples")
+        return out
 
 
 SPEC2D = dict(n_t1=64, t1_stride=8, t2=[0, 100, 200, 300], n_t3=512)
@@ -339,6 +420,128 @@ def three_state_measure(stream, hbm_peak):
     return out
 
 
+def tensor_core_measure(stream, m, T, tc_peak, peak_source):
+    """The tensor-core form (tcgen05 split-bf16 DFT-GEMM potential term + fused stencil/bath kernel) on
+    the benchmark workload: RK4 throughput (CUDA events on the launching stream) and the roofline of
+    its potential kernel against the bf16 tensor peak, on the tensor flops it issues (forward and
+    inverse DFT-GEMMs: 4 real products of [1 x np] x [np x np] per row, 3 bf16 products each)."""
+    import numpy as np
+    import torch
+    import qhfpe_inputs as qi
+    from paper_1706_09590_gb300 import Propagator
+    P = Propagator(m, T, precision="bf16x3", stream=stream)
+    P.set_state(qi.random_state(m, seed=1706))
+    P.step(4)
+    cells = int(np.prod(P.shape))
+    s = torch.cuda.current_stream() if stream is None else stream
+    n = 100
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(s)
+    P.step(n)
+    e1.record(s)
+    torch.cuda.synchronize()
+    P.kernel_timing(True)
+    P.step(n)
+    kt = P.kernel_timing_read()
+    P.kernel_timing(False)
+    P.close()
+    n_pot, ms_pot = kt["potential"]
+    n_stage, ms_stage = kt["stage"]
+    pot_ms = ms_pot / max(n_pot, 1)
+    flops = 2 * 3 * 4 * 2 * m["np"] * m["np"] * (cells / m["np"])
+    return {"workload": "photoiso_96x128_d8_K2, precision bf16x3", "cell_updates_per_s": cells * n / (e0.elapsed_time(e1) / 1e3),
+            "roofline": {"bound": "tensor", "kernel": "pot_tc_kernel (tcgen05 split-bf16 DFT-GEMM potential term)",
+                         "achieved": flops / (pot_ms / 1e3) / 1e12, "peak": tc_peak, "unit": "TFLOP/s",
+                         "frac": flops / (pot_ms / 1e3) / 1e12 / tc_peak, "peak_source": peak_source,
+                         "ms_per_launch": pot_ms, "flops_per_launch": flops,
+                         "share": ms_pot / max(ms_pot + ms_stage + kt["aux"][1], 1e-9)},
+            "stage_ms_per_launch": ms_stage / max(n_stage, 1)}
+
+
+def fp64_form_measure(stream, m, T, fp64_peak_tflops, peak_source):
+    """The FP64 form on the benchmark workload: RK4 throughput and the fused stage kernel against the
+    FP64 pipe (FP64 flops per launch as counted by ncu on this workload, FMA = 2)."""
+    import numpy as np
+    import torch
+    import qhfpe_inputs as qi
+    from paper_1706_09590_gb300 import Propagator
+    P = Propagator(m, T, precision="fp64", stream=stream)
+    P.set_state(qi.random_state(m, seed=1706))
+    P.step(2)
+    cells = int(np.prod(P.shape))
+    s = torch.cuda.current_stream() if stream is None else stream
+    n = 20
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(s)
+    P.step(n)
+    e1.record(s)
+    torch.cuda.synchronize()
+    P.kernel_timing(True)
+    P.step(4)
+    kt = P.kernel_timing_read()
+    P.kernel_timing(False)
+    P.close()
+    stage_ms = kt["stage"][1] / max(kt["stage"][0], 1)
+    fl = FP64_FLOPS_PER_CELL_STAGE * cells
+    return {"workload": "photoiso_96x128_d8_K2, precision fp64", "cell_updates_per_s": cells * n / (e0.elapsed_time(e1) / 1e3),
+            "roofline": {"bound": "alu", "kernel": "fused_stage_kernel<double> (FP64 pipe)",
+                         "achieved": fl / (stage_ms / 1e3) / 1e12, "peak": fp64_peak_tflops, "unit": "TFLOP/s",
+                         "frac": fl / (stage_ms / 1e3) / 1e12 / fp64_peak_tflops, "peak_source": peak_source,
+                         "ms_per_launch": stage_ms, "flops_per_launch": fl}}
+
+
+CONFIG2_ETAS = (0.1, 1.0, 5.0)
+CONFIG2_COUPLINGS = (0.2, 0.5, 1.0, 2.0)
+
+
+def config2_sweep_measure(stream):
+    """The benchmark model over its stated parameter ranges (eta in {0.1, 1, 5} x diabatic coupling in
+    {0.2, 0.5, 1, 2}, 96 x 128, depth 8, two Matsubara terms + delta-term, dt = 0.8 x the stability
+    bound): linear response over one time unit and the transient-absorption response (t1 = 0, waiting
+    times 0 and 0.25, detection over 0.5) from one FP64 equilibrium, in the FP64 and the mixed form;
+    each form's wall time and the mixed form's relative L2 error against FP64."""
+    import numpy as np
+    import torch
+    import qhfpe_inputs as qi
+    from paper_1706_09590_gb300 import Propagator
+    rows = []
+    for eta in CONFIG2_ETAS:
+        for coupling in CONFIG2_COUPLINGS:
+            m = qi.photoisomerization_two_state(eta=eta, coupling=coupling)
+            T = qi.u_table(m)
+            E = Propagator(m, T, precision="fp64", stream=stream)
+            dt = 0.8 * E.max_stable_dt()
+            E.close()
+            E = Propagator(m, T, precision="fp64", stream=stream, dt=dt)
+            E.equilibrate(300)
+            Weq = E.get_state(0)
+            E.close()
+            # at eta = 5 the truncated hierarchy has growing modes (about e^(10 t)): compared up to t = 0.5
+            t_r1, t_T, t_t3 = (0.5, 0.125, 0.375) if eta >= 5 else (1.0, 0.25, 0.5)
+            n_r1, t2, n_t3 = int(round(t_r1 / dt)), [0, int(round(t_T / dt))], int(round(t_t3 / dt))
+            R1, R3, wall = {}, {}, {}
+            for prec in ("fp64", "mixed"):
+                P = Propagator(m, T, precision=prec, stream=stream, dt=dt)
+                P.set_equilibrium(Weq)
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                R1[prec] = P.linear_response(n_r1)
+                R3[prec] = P.third_order_response(1, 1, t2, n_t3)
+                torch.cuda.synchronize()
+                wall[prec] = time.perf_counter() - t0
+                P.close()
+            rel = lambda a, b: float(np.linalg.norm(a - b) / np.linalg.norm(b))
+            rows.append({"eta": eta, "coupling": coupling, "dt": dt, "rel_err_R1": rel(R1["mixed"], R1["fp64"]),
+                         "rel_err_TAS_R3": rel(R3["mixed"], R3["fp64"]), "fp64_s": wall["fp64"],
+                         "mixed_s": wall["mixed"]})
+    return {"workload": "photoiso_96x128_d8_K2 at eta x coupling, R1 (1 time unit) + TAS R3 (T = 0, 0.25; t3 0.5); "
+                        "eta 5: R1 0.5, T = 0, 0.125, t3 0.375 (growing modes of the truncated hierarchy)",
+            "cases": rows, "max_rel_err": max(max(r["rel_err_R1"], r["rel_err_TAS_R3"]) for r in rows),
+            "fp64_s_total": sum(r["fp64_s"] for r in rows), "mixed_s_total": sum(r["mixed_s"] for r in rows)}
+
+
 def cpu_baseline(m, T, seconds=15.0):
     """The FP64 oracle as it stands, on this host's cores, over a bounded number of RK4 steps of the
     same workload (full hierarchy, full grid)."""
@@ -410,6 +613,10 @@ def main():
                     help="skip the heterogeneous-batch measurement")
     ap.add_argument("--no-three-state", action="store_true",
                     help="skip the full-size three-state measurement")
+    ap.add_argument("--no-forms", action="store_true",
+                    help="skip the tensor-core and FP64 forms on the benchmark workload")
+    ap.add_argument("--no-config2-sweep", action="store_true",
+                    help="skip the eta x coupling sweep of the benchmark model (FP64 vs mixed spectra)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -447,13 +654,16 @@ def main():
     P.kernel_timing(True)
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with Clocks(local) as clk:
+        time.sleep(0.02)  # a few samples before the timed region
         barrier()
+        clk.timed = True
         with torch.cuda.stream(stream):
             ev0.record(stream)
         tr = P.step(args.steps, record_trace=True)
         with torch.cuda.stream(stream):
             ev1.record(stream)
         barrier()
+        clk.timed = False
     ms = ev0.elapsed_time(ev1)
     kt = P.kernel_timing_read()
     P.kernel_timing(False)
@@ -494,6 +704,15 @@ def main():
         pass
     hbm_peak = peaks.get("hbm_gbs", 6800.0)
     tc_peak = peaks.get("bf16_tflops_sustained", 1700.0)
+    tc_src = "MEASURED_PEAKS.json bf16_tflops_sustained (of measured)" if "bf16_tflops_sustained" in peaks else \
+        "fallback 1.7 PFLOP/s sustained"
+    # FP64 peak: the DFMA rate measured on this device now (CUDA events; clocks as they are)
+    from paper_1706_09590_gb300.qhfpe import fp64_fma_rate
+    try:
+        fp64_peak = fp64_fma_rate(stream, repeats=5) / 1e12
+        fp64_src = "measured DFMA rate on this device (qhfpe_fp64_fma_rate, best of 5, of measured)"
+    except RuntimeError:
+        fp64_peak, fp64_src = FP64_PEAK_TFLOPS, "nominal FP64 rate (2 FMA / clock / SM, 152 SMs, 2.07 GHz)"
     n_stage, ms_stage = kt["stage"]
     n_pot, ms_pot = kt["potential"]
     esize = 8 if args.precision == "fp64" else 4
@@ -513,13 +732,11 @@ def main():
                   "algorithmic_bytes_per_launch": alg_bytes_stage}
     if args.precision == "fp64":
         # the FP64 form is bound by the FP64 pipe (ncu: 86 % of its cycles active, DRAM 3 %): FP64 flops
-        # per launch (FMA = 2) as counted by ncu on this workload, against the nominal FP64 rate of
-        # 2 FMA per clock per SM x 152 SMs x 2.07 GHz = 1.259 TFLOP/s
+        # per launch (FMA = 2) as counted by ncu on this workload, against the DFMA rate measured here
         fl = FP64_FLOPS_PER_CELL_STAGE * cells
-        stage_roof.update({"bound": "alu", "achieved": fl / (stage_ms / 1e3) / 1e12, "peak": FP64_PEAK_TFLOPS,
-                           "unit": "TFLOP/s", "frac": fl / (stage_ms / 1e3) / 1e12 / FP64_PEAK_TFLOPS,
-                           "peak_source": "nominal FP64 rate (2 FMA / clock / SM, 152 SMs, 2.07 GHz)",
-                           "flops_per_launch": fl})
+        stage_roof.update({"bound": "alu", "achieved": fl / (stage_ms / 1e3) / 1e12, "peak": fp64_peak,
+                           "unit": "TFLOP/s", "frac": fl / (stage_ms / 1e3) / 1e12 / fp64_peak,
+                           "peak_source": fp64_src, "flops_per_launch": fl})
         stage_roof.pop("algorithmic_bytes_per_launch")
     # DRAM bytes per launch from the committed ncu capture, valid only for the kernel source it was
     # taken from
@@ -539,8 +756,8 @@ def main():
         tc_roof = {"bound": "tensor", "kernel": "pot_tc_kernel (tcgen05 split-bf16 DFT-GEMM potential term)",
                    "achieved": flops / (pot_ms / 1e3) / 1e12, "peak": tc_peak, "unit": "TFLOP/s",
                    "frac": flops / (pot_ms / 1e3) / 1e12 / tc_peak, "traffic": None,
-                   "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained (of measured)",
-                   "ms_per_launch": pot_ms, "share": ms_pot / total, "flops_per_launch": flops}
+                   "peak_source": tc_src, "ms_per_launch": pot_ms, "share": ms_pot / total,
+                   "flops_per_launch": flops}
         roof = dict(tc_roof) if ms_pot >= ms_stage else dict(stage_roof)
         roof["other_kernel"] = stage_roof if ms_pot >= ms_stage else tc_roof
 
@@ -556,7 +773,13 @@ def main():
             "e2e": {"value": e2e, "unit": "cell-updates/s", "h2d_bytes_per_step": state_bytes,
                     "d2h_bytes_per_step": state_bytes + 16 * 2},
             "gpu_launches": int(n_stage + n_pot + 2 * args.steps + 2),
-            "roofline": roof, "clocks": clk.summary()}
+            "roofline": roof, "clocks": clk.summary(),
+            "fp64_peak": {"tflops": fp64_peak, "source": fp64_src}}
+    if args.precision == "mixed" and not args.no_forms:
+        line["tensor_core"] = tensor_core_measure(stream, m, T, tc_peak, tc_src)
+        line["fp64_form"] = fp64_form_measure(stream, m, T, fp64_peak, fp64_src)
+    if not args.no_config2_sweep:
+        line["config2_sweep"] = config2_sweep_measure(stream)
     if not args.no_spectrum:
         line["spectrum_2d"] = spectrum_2d_measure(stream)
         if not args.no_cpu_baseline and rank == 0:

@@ -226,6 +226,16 @@ qhfpe_status qhfpe_first_order_distribution(qhfpe_t *h, int n_t1, int t1_stride,
  * blocks zero) is kept as the handle's equilibrium state and written to every replica.
  * residual_out (may be NULL): ||L W|| / ||W|| of the final ground problem (2-norm, all elements). */
 qhfpe_status qhfpe_equilibrate(qhfpe_t *h, long n_steps, double *residual_out);
+/* The same equilibration run until it is stationary, Sec. III ("a sufficiently long time to obtain a
+ * true thermal equilibrium state"): the residual ||L W|| / ||W|| of the ground problem is evaluated
+ * before the first step and after every check_every steps (one right-hand side and two FP64 norms on
+ * the device, two scalars to the host), and the propagation stops at the first check where it is
+ * below tol, or when the steps reach t_max / dt (rounded to the nearest step).  steps_taken (may be
+ * NULL): the RK4 steps propagated, a multiple of check_every unless t_max ended the run.
+ * residual_out (may be NULL): the residual at the stop.  The result is that of qhfpe_equilibrate with
+ * n_steps = *steps_taken.  Errors: EINVAL for t_max < 0 or not finite, tol <= 0, check_every < 1. */
+qhfpe_status qhfpe_equilibrate_tol(qhfpe_t *h, double t_max, double tol, long check_every, long *steps_taken,
+                                   double *residual_out);
 /* Provide the equilibrium state directly (canonical layout, one replica). */
 qhfpe_status qhfpe_set_equilibrium(qhfpe_t *h, const double *src, int is_device);
 
@@ -276,6 +286,13 @@ qhfpe_status qhfpe_wait_selftest(qhfpe_t *h, int release, int limit_ms);
  * height from 1 to that limit, replaces the timing with that tile. */
 qhfpe_status qhfpe_tile_rows(const qhfpe_t *h, int *rows);
 qhfpe_status qhfpe_kernel_timing_read(qhfpe_t *h, long *launches, double *total_ms, int n_kinds);
+/* Measurement aid with no counterpart in the paper: the FP64 fused multiply-add rate of the current
+ * device, the denominator of the FP64 form's roofline.  8 blocks of 256 threads per SM each run eight
+ * independent chains of 4096 x 8 DFMAs; the best of `repeats` (1..100) launches timed with CUDA events
+ * on `stream` (NULL: legacy default stream) gives flops_per_s = 2 x DFMAs / time.  No clock or other
+ * device setting is touched: the rate is at whatever clock the device runs.  Allocates and frees a
+ * small output buffer.  Errors: EINVAL (bad repeats or NULL output), ECUDA. */
+qhfpe_status qhfpe_fp64_fma_rate(void *stream, int repeats, double *flops_per_s);
 
 /* ---- Learned closure (one Drude mode, K = 0) --------------------------------------------------
  * With closure = QHFPE_LEARNED the deepest tier's missing element W^(N+1) is the Eq. (GMFP)
@@ -319,9 +336,9 @@ qhfpe_status qhfpe_closure_train(float *w, const double *X, const double *stats,
 
 /* ---- Potential term without allocation -----------------------------------------------------
  * No counterpart in the paper: this entry point exists for callers that cannot allocate device
- * memory -- code running while a stream is captured into a CUDA graph (cudaMalloc cannot be captured),
- * code with a fixed device-memory budget owned by another allocator, or code that must not
- * synchronise the device (which cudaMalloc/cudaFree may do).  It needs no handle.
+ * memory -- code whose device memory is a fixed budget owned by another allocator (an embedding
+ * application or framework that hands out all of the GPU's memory itself), or code that must not
+ * synchronise the device, which cudaMalloc/cudaFree may do.  It needs no handle.
  *
  * out_dev = -i [U, W] in Wigner space (the QHFPE_TERM_POTENTIAL part of qhfpe_apply_rhs, FP64) for
  * n_elem hierarchy elements of one state.  W_dev, out_dev: device, canonical complex128 layout

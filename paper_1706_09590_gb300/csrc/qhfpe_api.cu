@@ -201,8 +201,14 @@ struct Model {
     bool fused = false;         // fused stage kernel available for (np, S)
     double *ftab64 = nullptr;   // its tables (digit-reversed order, np twiddles)
     float *ftab32 = nullptr;
-    FusedTables<double> f64() const { return {ftab64, ftab64 + tab_n, ftab64 + 2 * tab_n, ftab64 + 3 * tab_n}; }
-    FusedTables<float> f32() const { return {ftab32, ftab32 + tab_n, ftab32 + 2 * tab_n, ftab32 + 3 * tab_n}; }
+    FusedTables<double> f64() const
+    {
+        return {ftab64, ftab64 + tab_n, ftab64 + 2 * tab_n, ftab64 + 3 * tab_n, ftab64 + 3 * tab_n + 2 * np};
+    }
+    FusedTables<float> f32() const
+    {
+        return {ftab32, ftab32 + tab_n, ftab32 + 2 * tab_n, ftab32 + 3 * tab_n, ftab32 + 3 * tab_n + 2 * np};
+    }
     ~Model()
     {
         if (elems) cudaFree(elems);
@@ -335,11 +341,11 @@ cudaError_t dalloc(T **p, size_t n)
 // Potential tables (Eq. (quantum-liouvillian) in r-space) for an FFT's output order, pre-scaled by
 // 1/np.  freq(pos) gives the frequency index sitting at position pos; n_tw twiddles e^{2 pi i t/np}.
 template <typename F>
-void build_tables(const Model &M, const double *U, std::vector<double> &out, F freq, int n_tw)
+void build_tables(const Model &M, const double *U, std::vector<double> &out, F freq, int n_tw, bool with_lpp = false)
 {
     const int S = M.S, nq = M.nq, N = M.np;
     const size_t n = (size_t)S * S * nq * N;
-    out.assign(3 * n + 2 * n_tw, 0.0);
+    out.assign(3 * n + 2 * n_tw + (with_lpp ? N : 0), 0.0);
     auto T = [&](int j, int k, int i, int t) { return U[(((size_t)j * S + k) * nq + i) * (N + 1) + t]; };
     auto UL = [&](int j, int s, int i, int m) {
         return m == -N / 2 ? 0.5 * (T(j, s, i, 0) + T(j, s, i, N)) : T(j, s, i, m + N / 2);
@@ -362,6 +368,14 @@ void build_tables(const Model &M, const double *U, std::vector<double> &out, F f
         out[3 * n + 2 * t] = std::cos(2.0 * kPi * t / N);
         out[3 * n + 2 * t + 1] = std::sin(2.0 * kPi * t / N);
     }
+    // eigenvalues of the periodic 5-point second difference (-1, 16, -30, 16, -1) along p at the mode
+    // of each FFT position, divided by N (the inverse transform's normalisation): the delta-term and
+    // the terminator's c_0 d2/dp2 act as products in r-space
+    if (with_lpp)
+        for (int pos = 0; pos < N; ++pos) {
+            const double th = 2.0 * kPi * freq(pos) / N;
+            out[3 * n + 2 * n_tw + pos] = (-2.0 * std::cos(2.0 * th) + 32.0 * std::cos(th) - 30.0) / N;
+        }
 }
 
 qhfpe_status build_model(qhfpe *h, Model &M, int S, const double *U, const double *mu)
@@ -439,6 +453,8 @@ qhfpe_status build_model(qhfpe *h, Model &M, int S, const double *U, const doubl
     g.elem_stride = (size_t)S * S * 2 * g.blk;
     g.rep_stride = (size_t)(M.n_elem + (M.closure_slot >= 0 ? 1 : 0)) * g.elem_stride;
     g.tier0_rep_stride = g.elem_stride;
+    g.max_nb = 0;
+    for (const ElemInfo &E : M.elems_host) g.max_nb = std::max(g.max_nb, E.n_up + E.n_dn);
 
     M.mu_host.assign(mu, mu + S * S);
     std::vector<double> tab;
@@ -496,7 +512,7 @@ qhfpe_status build_model(qhfpe *h, Model &M, int S, const double *U, const doubl
     QH_CK(h, cudaMemcpyAsync(M.tab32, tab32.data(), sizeof(float) * tab32.size(), cudaMemcpyHostToDevice, st));
     if (M.fused) {
         std::vector<double> ft;
-        build_tables(M, U, ft, [&](int pos) { return fused_fft_frequency(p.np, pos); }, p.np);
+        build_tables(M, U, ft, [&](int pos) { return fused_fft_frequency(p.np, pos); }, p.np, true);
         QH_CK(h, dalloc(&M.ftab64, ft.size()));
         QH_CK(h, cudaMemcpyAsync(M.ftab64, ft.data(), sizeof(double) * ft.size(), cudaMemcpyHostToDevice, st));
         std::vector<float> ft32(ft.begin(), ft.end());
@@ -1421,14 +1437,16 @@ qhfpe_status qhfpe_first_order_distribution(qhfpe_t *h, int n_t1, int t1_stride,
     return check_timeout(h);
 }
 
-qhfpe_status qhfpe_equilibrate(qhfpe_t *h, long n_steps, double *residual_out)
+namespace {
+
+// The ground problem of the equilibration (Sec. III): U_00 alone with the full hierarchy, started
+// from the classical Boltzmann distribution with unit trace.
+qhfpe_status equilibrium_start(qhfpe_t *h, std::unique_ptr<Prop> &GP)
 {
-    qhfpe_status r = check_handle(h);
-    if (r != QHFPE_OK) return r;
-    if (n_steps < 0) return h->fail(QHFPE_EINVAL, "equilibrate: n_steps < 0");
     const qhfpe_params &p = h->p;
     const int nq = p.nq, np = p.np, S = p.n_states;
     cudaStream_t st = h->stream;
+    qhfpe_status r;
     if (!h->ground) {
         std::vector<double> U00((size_t)nq * (np + 1));
         for (int i = 0; i < nq; ++i)
@@ -1439,10 +1457,8 @@ qhfpe_status qhfpe_equilibrate(qhfpe_t *h, long n_steps, double *residual_out)
         if (r != QHFPE_OK) return r;
     }
     Model &G = *h->ground;
-    std::unique_ptr<Prop> GP;
     r = make_prop(h, &G, 1, false, p.dt, GP);
     if (r != QHFPE_OK) return r;
-    // classical Boltzmann start, unit trace
     const size_t blk = (size_t)nq * np;
     const size_t gn = (size_t)G.n_elem * blk;
     std::vector<double> w0(2 * gn, 0.0);
@@ -1461,34 +1477,49 @@ qhfpe_status qhfpe_equilibrate(qhfpe_t *h, long n_steps, double *residual_out)
     r = ensure_scratch(h, std::max(gn, full) * 2 * sizeof(double) + 64);
     if (r != QHFPE_OK) return r;
     QH_CK(h, cudaMemcpyAsync(h->scratch, w0.data(), gn * 2 * sizeof(double), cudaMemcpyHostToDevice, st));
-    r = set_from_canonical(h, *GP, h->scratch, 0, 1);
-    if (r != QHFPE_OK) return r;
-    r = run_steps(h, *GP, n_steps, nullptr, 0);
-    if (r != QHFPE_OK) return r;
-    // residual ||L W|| / ||W|| (the closure slot is not part of the state)
-    r = closure_fill<double>(h, *GP, (double *)GP->y, 0, 1);
+    return set_from_canonical(h, *GP, h->scratch, 0, 1);
+}
+
+// ||L W|| / ||W|| of the ground problem's current state (2-norm over all elements; the closure slot
+// is not part of the state): one right-hand side into vA, two norms, two scalars to the host.
+qhfpe_status equilibrium_residual(qhfpe_t *h, Prop &GP, double *res)
+{
+    Model &G = *h->ground;
+    cudaStream_t st = h->stream;
+    qhfpe_status r = closure_fill<double>(h, GP, (double *)GP.y, 0, 1);
     if (r != QHFPE_OK) return r;
     if (G.fused) {
-        QH_CK(h, (launch_fused<double, false>(GP->g, G.elems, G.f64(), (const double *)GP->y, (const double *)GP->y,
-                                              nullptr, (double *)GP->vA, nullptr, 0.0, 0, QHFPE_TERM_ALL, 0, 1, st)));
+        QH_CK(h, (launch_fused<double, false>(GP.g, G.elems, G.f64(), (const double *)GP.y, (const double *)GP.y,
+                                              nullptr, (double *)GP.vA, nullptr, 0.0, 0, QHFPE_TERM_ALL, 0, 1, st)));
     } else {
-        QH_CK(h, launch_potential<double>(GP->g, G.t64(), (const double *)GP->y, (double *)GP->P, 0, 1, st));
-        QH_CK(h, (launch_stage<double, false>(GP->g, G.elems, (const double *)GP->y, (const double *)GP->P,
-                                              (const double *)GP->y, nullptr, (double *)GP->vA, nullptr, 0.0, 0,
+        QH_CK(h, launch_potential<double>(GP.g, G.t64(), (const double *)GP.y, (double *)GP.P, 0, 1, st));
+        QH_CK(h, (launch_stage<double, false>(GP.g, G.elems, (const double *)GP.y, (const double *)GP.P,
+                                              (const double *)GP.y, nullptr, (double *)GP.vA, nullptr, 0.0, 0,
                                               QHFPE_TERM_ALL, 0, 1, st)));
     }
-    const size_t real = (size_t)G.n_elem * GP->g.elem_stride;
-    QH_CK(h, launch_norm2((const double *)GP->vA, real, h->scratch, st));
-    QH_CK(h, launch_norm2((const double *)GP->y, real, h->scratch + 1, st));
+    const size_t real = (size_t)G.n_elem * GP.g.elem_stride;
+    QH_CK(h, launch_norm2((const double *)GP.vA, real, h->scratch, st));
+    QH_CK(h, launch_norm2((const double *)GP.y, real, h->scratch + 1, st));
     double nn[2];
     QH_CK(h, cudaMemcpyAsync(nn, h->scratch, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
     QH_CK(h, cudaStreamSynchronize(st));
-    if (residual_out) *residual_out = std::sqrt(nn[0] / nn[1]);
     if (!std::isfinite(nn[0]) || !std::isfinite(nn[1])) return h->fail(QHFPE_ENUMERIC, "equilibrate: state not finite");
-    // embed in the 00 block of every element
+    *res = std::sqrt(nn[0] / nn[1]);
+    return check_timeout(h);
+}
+
+// Embeds the ground problem's state in the 00 block of every element: the handle's equilibrium state,
+// also written to every replica.
+qhfpe_status equilibrium_embed(qhfpe_t *h, Prop &GP)
+{
+    const int S = h->p.n_states;
+    const Model &G = *h->ground;
+    const size_t blk = (size_t)h->p.nq * h->p.np;
+    const size_t full = (size_t)G.n_elem * S * S * blk;
+    cudaStream_t st = h->stream;
     if (!h->eq) QH_CK(h, cudaMalloc((void **)&h->eq, full * 2 * sizeof(double)));
     QH_CK(h, cudaMemsetAsync(h->eq, 0, full * 2 * sizeof(double), st));
-    r = get_to_canonical(h, *GP, GP->y, nullptr, h->scratch, 0);
+    qhfpe_status r = get_to_canonical(h, GP, GP.y, nullptr, h->scratch, 0);
     if (r != QHFPE_OK) return r;
     QH_CK(h, cudaMemcpy2DAsync(h->eq, (size_t)S * S * blk * 2 * sizeof(double), h->scratch, blk * 2 * sizeof(double),
                                blk * 2 * sizeof(double), G.n_elem, cudaMemcpyDeviceToDevice, st));
@@ -1497,6 +1528,47 @@ qhfpe_status qhfpe_equilibrate(qhfpe_t *h, long n_steps, double *residual_out)
     if (r != QHFPE_OK) return r;
     QH_CK(h, cudaStreamSynchronize(st));
     return QHFPE_OK;
+}
+
+}  // namespace
+
+qhfpe_status qhfpe_equilibrate(qhfpe_t *h, long n_steps, double *residual_out)
+{
+    qhfpe_status r = check_handle(h);
+    if (r != QHFPE_OK) return r;
+    if (n_steps < 0) return h->fail(QHFPE_EINVAL, "equilibrate: n_steps < 0");
+    std::unique_ptr<Prop> GP;
+    if ((r = equilibrium_start(h, GP)) != QHFPE_OK) return r;
+    if ((r = run_steps(h, *GP, n_steps, nullptr, 0)) != QHFPE_OK) return r;
+    double res = 0.0;
+    if ((r = equilibrium_residual(h, *GP, &res)) != QHFPE_OK) return r;
+    if (residual_out) *residual_out = res;
+    return equilibrium_embed(h, *GP);
+}
+
+qhfpe_status qhfpe_equilibrate_tol(qhfpe_t *h, double t_max, double tol, long check_every, long *steps_taken,
+                                   double *residual_out)
+{
+    qhfpe_status r = check_handle(h);
+    if (r != QHFPE_OK) return r;
+    if (!(t_max >= 0.0) || !std::isfinite(t_max) || !(tol > 0.0) || check_every < 1)
+        return h->fail(QHFPE_EINVAL, "equilibrate_tol: need finite t_max >= 0, tol > 0, check_every >= 1");
+    // the last step may end at most half a step past t_max
+    const long max_steps = (long)std::floor(t_max / h->p.dt + 0.5);
+    std::unique_ptr<Prop> GP;
+    if ((r = equilibrium_start(h, GP)) != QHFPE_OK) return r;
+    long done = 0;
+    double res = 0.0;
+    if ((r = equilibrium_residual(h, *GP, &res)) != QHFPE_OK) return r;
+    while (res >= tol && done < max_steps) {
+        const long n = std::min(check_every, max_steps - done);
+        if ((r = run_steps(h, *GP, n, nullptr, 0)) != QHFPE_OK) return r;
+        done += n;
+        if ((r = equilibrium_residual(h, *GP, &res)) != QHFPE_OK) return r;
+    }
+    if (steps_taken) *steps_taken = done;
+    if (residual_out) *residual_out = res;
+    return equilibrium_embed(h, *GP);
 }
 
 qhfpe_status qhfpe_set_equilibrium(qhfpe_t *h, const double *src, int is_device)
@@ -1674,6 +1746,44 @@ qhfpe_status qhfpe_wait_selftest(qhfpe_t *h, int release, int limit_ms)
     QH_CK(h, e);
     if (status == 2) return h->fail(QHFPE_ETIMEOUT, "wait_selftest: the device wait gave up (flag never set)");
     return status == 1 ? QHFPE_OK : h->fail(QHFPE_ECUDA, "wait_selftest: no status written");
+}
+
+qhfpe_status qhfpe_fp64_fma_rate(void *stream, int repeats, double *flops_per_s)
+{
+    if (!flops_per_s || repeats < 1 || repeats > 100) {
+        qh_set_free_error("fp64_fma_rate: need repeats in [1, 100] and an output");
+        return QHFPE_EINVAL;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    int dev = 0, sms = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int blocks = 8 * (sms > 0 ? sms : 1), n_iter = 4096;
+    double *out = nullptr;
+    if (e == cudaSuccess) e = cudaMalloc((void **)&out, (size_t)blocks * 256 * sizeof(double));
+    cudaEvent_t a = nullptr, b = nullptr;
+    if (e == cudaSuccess) e = cudaEventCreate(&a);
+    if (e == cudaSuccess) e = cudaEventCreate(&b);
+    if (e == cudaSuccess) e = launch_dfma_rate(blocks, 64, out, st);  // warm-up
+    float best = 0.0f;
+    for (int r = 0; r < repeats && e == cudaSuccess; ++r) {
+        e = cudaEventRecord(a, st);
+        if (e == cudaSuccess) e = launch_dfma_rate(blocks, n_iter, out, st);
+        if (e == cudaSuccess) e = cudaEventRecord(b, st);
+        if (e == cudaSuccess) e = cudaEventSynchronize(b);
+        float ms = 0.0f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, a, b);
+        if (e == cudaSuccess && (best == 0.0f || ms < best)) best = ms;
+    }
+    if (a) cudaEventDestroy(a);
+    if (b) cudaEventDestroy(b);
+    if (out) cudaFree(out);
+    if (e != cudaSuccess || best <= 0.0f) {
+        qh_set_free_error(std::string("fp64_fma_rate: ") + cudaGetErrorString(e));
+        return QHFPE_ECUDA;
+    }
+    *flops_per_s = 2.0 * 64.0 * n_iter * (double)blocks * 256.0 / (best * 1e-3);
+    return QHFPE_OK;
 }
 
 qhfpe_status qhfpe_tile_rows(const qhfpe_t *h, int *rows)

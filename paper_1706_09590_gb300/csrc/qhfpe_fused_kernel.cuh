@@ -315,6 +315,79 @@ struct FusedOcc {
     static constexpr int blocks = sizeof(T) == 4 ? (NP >= 256 ? 4 : (S >= 3 ? 6 : 7)) : 2;
 };
 
+// Phase A of the fused stage kernels: the potential term of Eq. (quantum-liouvillian) in place on the
+// block's rows * S^2 p-rows in X (padded, complex): forward FFT (sign +, digit-reversed), per r-mode
+// mixing across the S x S blocks with the tables D, L, R (pre-scaled by 1/NP) times -i, plus the
+// p-diagonal bath terms (f_pp lambda_pp(m) - ngam) / NP (damping, delta-term, terminator d2/dp2, which
+// are circulants along p), and the inverse FFT (sign -, natural order).  Called by all threads of the
+// block after a barrier that makes X complete; ends with the inverse FFT's barrier.
+template <typename T, int NP, int S>
+__device__ __forceinline__ void potential_in_place(typename V2<T>::type *X, const typename V2<T>::type *tw,
+                                                   const FusedTables<T> &tab, int nq, int i0, int rows, T fpp,
+                                                   T ngam, const T *s_lpp)
+{
+    using C = typename V2<T>::type;
+    constexpr int S2 = S * S;
+    fft_all<NP, true>(X, rows * S2, tw);
+    constexpr int MV = S >= 3 ? (NP > FTHREADS ? 2 : 1) : (S == 2 ? 2 : 4);  // modes per thread (vector table loads)
+    static_assert(FTHREADS % (NP / MV) == 0, "mixing positions");
+    const int pos0 = (threadIdx.x % (NP / MV)) * MV;
+    // r-space coefficient of the bath terms diagonal in p (already over NP, like the tables):
+    // (f_pp lambda_pp(m) - sum n_k gamma_k) / NP
+    T cf[MV];
+    {
+        const T ng_a = ngam / (T)NP;
+#pragma unroll
+        for (int v = 0; v < MV; ++v) cf[v] = fpp * s_lpp[pos0 + v] - ng_a;
+    }
+    for (int r = threadIdx.x / (NP / MV); r < rows; r += FTHREADS / (NP / MV)) {
+        const int i = i0 + r;
+        C rho[S2][MV];
+#pragma unroll
+        for (int a = 0; a < S2; ++a)
+#pragma unroll
+            for (int v = 0; v < MV; ++v) rho[a][v] = X[pad16((r * S2 + a) * NP + pos0 + v)];
+#pragma unroll
+        for (int j = 0; j < S; ++j)
+#pragma unroll
+            for (int k = 0; k < S; ++k) {
+                T d[MV];
+                ldv<T, MV>(tab.D + ((size_t)(j * S + k) * nq + i) * NP + pos0, d);
+                C acc[MV];
+#pragma unroll
+                for (int v = 0; v < MV; ++v) acc[v] = C{d[v] * rho[j * S + k][v].x, d[v] * rho[j * S + k][v].y};
+#pragma unroll
+                for (int s = 0; s < S; ++s) {
+                    if (s != j) {
+                        T u[MV];
+                        ldv<T, MV>(tab.L + ((size_t)(j * S + s) * nq + i) * NP + pos0, u);
+#pragma unroll
+                        for (int v = 0; v < MV; ++v) {
+                            acc[v].x += u[v] * rho[s * S + k][v].x;
+                            acc[v].y += u[v] * rho[s * S + k][v].y;
+                        }
+                    }
+                    if (s != k) {
+                        T u[MV];
+                        ldv<T, MV>(tab.R + ((size_t)(s * S + k) * nq + i) * NP + pos0, u);
+#pragma unroll
+                        for (int v = 0; v < MV; ++v) {
+                            acc[v].x -= u[v] * rho[j * S + s][v].x;
+                            acc[v].y -= u[v] * rho[j * S + s][v].y;
+                        }
+                    }
+                }
+#pragma unroll
+                for (int v = 0; v < MV; ++v) {  // times -i, plus the p-diagonal bath terms
+                    const C w = rho[j * S + k][v];
+                    X[pad16((r * S2 + j * S + k) * NP + pos0 + v)] = C{acc[v].y + cf[v] * w.x, cf[v] * w.y - acc[v].x};
+                }
+            }
+    }
+    __syncthreads();
+    fft_all<NP, false>(X, rows * S2, tw);
+}
+
 // MULTI: one Horner stage of several propagators at once (heterogeneous batch: members differ in q
 // grid, surfaces, bath, hierarchy depth, closure, dt and replica count, and share NP, S and the
 // precision).  Blocks are numbered member by member; a block finds its member (first block numbers
@@ -391,6 +464,7 @@ fused_stage_kernel(GridInfo g, const ElemInfo *__restrict__ elems, FusedTables<T
     __shared__ int s_cnt[4];
     __shared__ T s_ngam;
     __shared__ __align__(16) T pgrid[NP];
+    __shared__ __align__(16) T s_lpp[NP];
     if (threadIdx.x == 0) {
         const ElemInfo &E = elems[e];
         int n = 0;
@@ -419,6 +493,7 @@ fused_stage_kernel(GridInfo g, const ElemInfo *__restrict__ elems, FusedTables<T
     for (int t = threadIdx.x; t < NP; t += FTHREADS) {
         tw[t] = C{tab.tw[2 * t], tab.tw[2 * t + 1]};
         pgrid[t] = (T)(g.p_min + t * g.dp);
+        s_lpp[t] = tab.lpp[t];
     }
 
     // the previous launch on the stream (the stage whose output this one reads) has completed and its
@@ -426,8 +501,12 @@ fused_stage_kernel(GridInfo g, const ElemInfo *__restrict__ elems, FusedTables<T
     asm volatile("griddepcontrol.wait;" ::: "memory");
 
     // ---- phase A: potential term -------------------------------------------------------------
+    // With the potential term computed here, the p-diagonal parts of the bath terms ride along in
+    // r-space: the damping -(sum n_k gamma_k) W and the 5-point d2/dp2 of the delta-term and of the
+    // terminator are circulants along p, i.e. products with their eigenvalues after the FFT.
     const bool want_pot = (terms & 2) != 0;
-    if (want_pot && !Pg) {
+    const bool fold = want_pot && !Pg;
+    if (fold) {
         constexpr int LV = 4;  // p values per load
         constexpr int PL = NP / LV;
         static_assert(FTHREADS % PL == 0, "load positions");
@@ -443,54 +522,9 @@ fused_stage_kernel(GridInfo g, const ElemInfo *__restrict__ elems, FusedTables<T
             for (int v = 0; v < LV; ++v) X[pad16(base + v)] = C{re[v], im[v]};
         }
         __syncthreads();
-        fft_all<NP, true>(X, rows * S2, tw);
-        constexpr int MV = S >= 3 ? (NP > FTHREADS ? 2 : 1) : (S == 2 ? 2 : 4);  // modes per thread (vector table loads)
-        static_assert(FTHREADS % (NP / MV) == 0, "mixing positions");
-        const int pos0 = (threadIdx.x % (NP / MV)) * MV;
-        for (int r = threadIdx.x / (NP / MV); r < rows; r += FTHREADS / (NP / MV)) {
-            const int i = i0 + r;
-            C rho[S2][MV];
-#pragma unroll
-            for (int a = 0; a < S2; ++a)
-#pragma unroll
-                for (int v = 0; v < MV; ++v) rho[a][v] = X[pad16((r * S2 + a) * NP + pos0 + v)];
-#pragma unroll
-            for (int j = 0; j < S; ++j)
-#pragma unroll
-                for (int k = 0; k < S; ++k) {
-                    T d[MV];
-                    ldv<T, MV>(tab.D + ((size_t)(j * S + k) * nq + i) * NP + pos0, d);
-                    C acc[MV];
-#pragma unroll
-                    for (int v = 0; v < MV; ++v) acc[v] = C{d[v] * rho[j * S + k][v].x, d[v] * rho[j * S + k][v].y};
-#pragma unroll
-                    for (int s = 0; s < S; ++s) {
-                        if (s != j) {
-                            T u[MV];
-                            ldv<T, MV>(tab.L + ((size_t)(j * S + s) * nq + i) * NP + pos0, u);
-#pragma unroll
-                            for (int v = 0; v < MV; ++v) {
-                                acc[v].x += u[v] * rho[s * S + k][v].x;
-                                acc[v].y += u[v] * rho[s * S + k][v].y;
-                            }
-                        }
-                        if (s != k) {
-                            T u[MV];
-                            ldv<T, MV>(tab.R + ((size_t)(s * S + k) * nq + i) * NP + pos0, u);
-#pragma unroll
-                            for (int v = 0; v < MV; ++v) {
-                                acc[v].x -= u[v] * rho[j * S + s][v].x;
-                                acc[v].y -= u[v] * rho[j * S + s][v].y;
-                            }
-                        }
-                    }
-#pragma unroll
-                    for (int v = 0; v < MV; ++v)
-                        X[pad16((r * S2 + j * S + k) * NP + pos0 + v)] = C{acc[v].y, -acc[v].x};  // times -i
-                }
-        }
-        __syncthreads();
-        fft_all<NP, false>(X, rows * S2, tw);
+        potential_in_place<T, NP, S>(X, tw, tab, nq, i0, rows,
+                                     ((terms & 4) ? sc.fdelta : (T)0) + ((s_cnt[3] != 0) ? sc.fterm : (T)0), s_ngam,
+                                     s_lpp);
     }
 
     // ---- phase B: one warp per p-row ------------------------------------------------------------
@@ -498,10 +532,11 @@ fused_stage_kernel(GridInfo g, const ElemInfo *__restrict__ elems, FusedTables<T
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int n_up = s_cnt[0], n_d0 = s_cnt[1], n_nb = s_cnt[2];
     const bool term = s_cnt[3] != 0;
-    const T ngam = s_ngam;
+    // (folded into phase A when it ran)
+    const T ngam = fold ? (T)0 : s_ngam;
     const T inv12dp = sc.inv12dp;
     const T fkin = sc.fkin;
-    const T fpp = ((terms & 4) ? sc.fdelta : (T)0) + (term ? sc.fterm : (T)0);
+    const T fpp = fold ? (T)0 : ((terms & 4) ? sc.fdelta : (T)0) + (term ? sc.fterm : (T)0);
     const int lr = lane / LPR;            // this lane's row among the warp's RPW rows
     const int l0 = (lane % LPR) * VEC;    // its first p index
     T pcol[VEC];
@@ -621,8 +656,10 @@ fused_stage_kernel(GridInfo g, const ElemInfo *__restrict__ elems, FusedTables<T
             ldv<T, VEC>(Vre + (size_t)i * NP + l0, wr);
             ldv<T, VEC>(Vim + (size_t)i * NP + l0, wi);
         }
-        v_axpy<VEC>(ar, -ngam, wr);
-        v_axpy<VEC>(ai, -ngam, wi);
+        if (ngam != (T)0) {
+            v_axpy<VEC>(ar, -ngam, wr);
+            v_axpy<VEC>(ai, -ngam, wi);
+        }
         // G = sum_up W^(n+e_k) + sum_dn wc W^(n-e_k) [+ r_0 p W at the terminator]; d/dp of G below
         T gr[VEC], gi[VEC], hr[VEC], hi[VEC];
 #pragma unroll

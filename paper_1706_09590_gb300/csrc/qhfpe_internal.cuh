@@ -41,6 +41,7 @@ struct GridInfo {
     size_t elem_stride;    // S*S*2*blk reals per element
     size_t rep_stride;     // n_elem*elem_stride reals per replica
     size_t tier0_rep_stride;  // S*S*2*blk reals per replica in the FP64 tier-0 buffer
+    int max_nb;        // most tier neighbours (up + down) of any element
 };
 
 // Potential-kernel tables in FFT output (bit-reversed) order, pre-scaled by 1/np:
@@ -54,11 +55,13 @@ struct PotTables {
 };
 
 // Tables of the fused stage kernel: same D, L, R as PotTables but in the fused FFT's
-// digit-reversed order (fused_fft_frequency), and np twiddles e^{2 pi i t/np}, t < np.
+// digit-reversed order (fused_fft_frequency), np twiddles e^{2 pi i t/np}, t < np, and lpp: the
+// eigenvalues of the periodic 5-point d2/dp2 stencil (without 1/(12 dp^2)) at each FFT position, over np.
 template <typename T>
 struct FusedTables {
     const T *D, *L, *R;
     const T *tw;
+    const T *lpp;
 };
 
 // Scalars of one fused stage launch, rounded once on the host: 1/(12 dp), 1/(60 dq), the delta-term and
@@ -195,6 +198,8 @@ cudaError_t launch_complex_combine(const double *a, const double *b, double ar, 
 cudaError_t launch_first_order_combine(int S, size_t blk, int n_elem, int n_omega, const double *mu,
                                        const double *acc_c, const double *acc_s, double *out, cudaStream_t st);
 cudaError_t launch_norm2(const double *x, size_t n, double *out_dev, cudaStream_t st);
+// DFMA throughput probe: blocks x 256 threads, each n_iter x 64 DFMAs; out: blocks * 256 doubles
+cudaError_t launch_dfma_rate(int blocks, int n_iter, double *out, cudaStream_t st);
 cudaError_t launch_wait_flag(const int *flag, unsigned long long limit_ns, int *status, cudaStream_t st);
 cudaError_t launch_absorption(const double *R1, long n_t, double dt, const double *omega, int n_omega,
                               double *out, cudaStream_t st);

@@ -576,6 +576,25 @@ __global__ void wait_flag_kernel(const volatile int *flag, unsigned long long li
     }
 }
 
+// FP64 fused multiply-add throughput: every thread runs eight independent dependency chains of
+// n_iter x 8 DFMAs (a = a * x + y); one result per thread is stored so nothing is dropped.
+__global__ void __launch_bounds__(256) dfma_rate_kernel(double x, double y, int n_iter, double *out)
+{
+    double a[8];
+#pragma unroll
+    for (int c = 0; c < 8; ++c) a[c] = (double)(threadIdx.x + c) * 1e-3;
+    for (int it = 0; it < n_iter; ++it) {
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+#pragma unroll
+            for (int c = 0; c < 8; ++c) a[c] = fma(a[c], x, y);
+    }
+    double s = 0.0;
+#pragma unroll
+    for (int c = 0; c < 8; ++c) s += a[c];
+    out[blockIdx.x * (size_t)blockDim.x + threadIdx.x] = s;
+}
+
 inline int grid_for(size_t n, int threads, int cap = 152 * 32)
 {
     size_t b = (n + threads - 1) / threads;
@@ -700,6 +719,12 @@ cudaError_t launch_to_canonical(const GridInfo &g, const T *src, const double *y
 cudaError_t launch_wait_flag(const int *flag, unsigned long long limit_ns, int *status, cudaStream_t st)
 {
     wait_flag_kernel<<<1, 1, 0, st>>>(flag, limit_ns, status);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_dfma_rate(int blocks, int n_iter, double *out, cudaStream_t st)
+{
+    dfma_rate_kernel<<<blocks, 256, 0, st>>>(0.999999, 1e-7, n_iter, out);
     return cudaGetLastError();
 }
 

@@ -1,10 +1,9 @@
 // qhfpe_potential_term_static: the potential term of the right-hand side for callers that cannot
 // allocate device memory.
 //
-// Some callers cannot call cudaMalloc: code that runs while a CUDA stream is being captured into a graph
-// (allocation is not a capturable operation), code that must run with a fixed, pre-planned device
-// footprint (embedded or real-time loops, memory owned by another allocator), or code that must not
-// synchronise the device, which cudaMalloc/cudaFree can do.  The handle-based calls allocate their
+// Some callers cannot call cudaMalloc: code that must run with a fixed, pre-planned device footprint
+// (embedded or real-time loops, memory owned by another allocator), or code that must not synchronise
+// the device, which cudaMalloc/cudaFree can do.  The handle-based calls allocate their
 // buffers in qhfpe_create; this entry point needs no handle.  It works in a file-scope device array of
 // fixed size instead of allocated scratch.
 //

@@ -27,6 +27,7 @@ EXPORTED = [
     "qhfpe_create", "qhfpe_destroy", "qhfpe_last_error", "qhfpe_sizes", "qhfpe_hierarchy",
     "qhfpe_bath_coefficients", "qhfpe_max_stable_dt", "qhfpe_set_state", "qhfpe_get_state", "qhfpe_fork",
     "qhfpe_step", "qhfpe_apply_dipole", "qhfpe_apply_rhs", "qhfpe_trace", "qhfpe_equilibrate",
+    "qhfpe_equilibrate_tol", "qhfpe_fp64_fma_rate",
     "qhfpe_set_equilibrium", "qhfpe_response", "qhfpe_spectrum_absorption", "qhfpe_spectrum_2d",
     "qhfpe_kernel_timing", "qhfpe_kernel_timing_read", "qhfpe_potential_term_static",
     "qhfpe_closure_collect", "qhfpe_closure_load", "qhfpe_closure_coefficients", "qhfpe_closure_loss_grad",
@@ -98,6 +99,8 @@ def lib():
     L.qhfpe_set_dipole_table.argtypes = [vp, vp]
     L.qhfpe_first_order_distribution.argtypes = [vp, ctypes.c_int, ctypes.c_int, vp, ctypes.c_int, vp]
     L.qhfpe_equilibrate.argtypes = [vp, ctypes.c_long, dp]
+    L.qhfpe_equilibrate_tol.argtypes = [vp, ctypes.c_double, ctypes.c_double, ctypes.c_long,
+                                        ctypes.POINTER(ctypes.c_long), dp]
     L.qhfpe_set_equilibrium.argtypes = [vp, vp, ctypes.c_int]
     L.qhfpe_response.argtypes = [vp, ctypes.POINTER(Schedule), vp]
     L.qhfpe_spectrum_absorption.argtypes = [vp, vp, ctypes.c_long, ctypes.c_double, vp, ctypes.c_int, vp]
@@ -108,6 +111,7 @@ def lib():
     L.qhfpe_potential_term_static.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double,
                                               ctypes.c_double, vp, ctypes.c_int, vp, vp, vp]
     L.qhfpe_tile_rows.argtypes = [vp, ip]
+    L.qhfpe_fp64_fma_rate.argtypes = [vp, ctypes.c_int, dp]
     L.qhfpe_batch_create.argtypes = [ctypes.POINTER(vp), st, ctypes.POINTER(vp)]
     L.qhfpe_batch_step.argtypes = [vp, ctypes.c_long, ctypes.POINTER(vp)]
     L.qhfpe_batch_tile_rows.argtypes = [vp, ip]
@@ -357,6 +361,14 @@ class Propagator:
         self._check(self._L.qhfpe_equilibrate(self._h, n_steps, ctypes.byref(res)))
         return res.value
 
+    def equilibrate_to(self, tol, t_max, check_every=100):
+        """Equilibrate until ||L W|| / ||W|| < tol (checked every check_every steps) or t_max; returns
+        (steps taken, residual)."""
+        n, res = ctypes.c_long(), ctypes.c_double()
+        self._check(self._L.qhfpe_equilibrate_tol(self._h, float(t_max), float(tol), int(check_every),
+                                                  ctypes.byref(n), ctypes.byref(res)))
+        return n.value, res.value
+
     def set_equilibrium(self, W):
         W = _c128(W)
         assert W.shape == self.shape
@@ -479,3 +491,14 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+def fp64_fma_rate(stream=None, repeats=5):
+    """FP64 FMA throughput of the current device in flop/s (2 per DFMA), timed with CUDA events."""
+    L = lib()
+    out = ctypes.c_double()
+    st = None if stream is None else ctypes.c_void_p(stream.cuda_stream)
+    s = L.qhfpe_fp64_fma_rate(st, int(repeats), ctypes.byref(out))
+    if s != 0:
+        raise QhfpeError(s, L.qhfpe_last_error(None).decode())
+    return out.value

@@ -97,6 +97,8 @@ def test_null_handle_calls_fail_cleanly():
     assert L.qhfpe_step(None, 1, None) == 1
     assert L.qhfpe_destroy(None) == 1
     assert L.qhfpe_trace(None, None) == 1
+    n = ctypes.c_long(-1)
+    assert L.qhfpe_equilibrate_tol(None, 1.0, 1e-6, 10, ctypes.byref(n), None) == 1
 
 
 def test_null_batch_and_state32_calls_fail_cleanly():

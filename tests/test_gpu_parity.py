@@ -184,6 +184,30 @@ def test_equilibrate_fp64():
     assert res == pytest.approx(ref_res, rel=1e-6)
 
 
+def test_equilibrate_to_tolerance_fp64():
+    """Stationarity-driven equilibration (Sec. III): the run stops at the first check where the
+    residual ||L W|| / ||W|| is below tol.  The oracle, propagated the same number of steps, gives the
+    same state, a residual below tol, and a residual at tol or above one check earlier."""
+    m = MODELS["harmonic"]
+    O = oracle.Oracle(m)
+    P = _P(m)
+    M = 40
+    tol = 1e-4  # the Boltzmann start is at 1.9e-3; the oracle passes 1e-4 between 320 and 640 steps
+    n, res = P.equilibrate_to(tol, t_max=60.0, check_every=M)
+    assert 320 < n <= 640 and n % M == 0
+    ref, ref_res = O.equilibrate(n)
+    assert rel(P.get_state(0), ref) < 1e-11
+    assert res == pytest.approx(ref_res, rel=1e-6)
+    assert ref_res < tol
+    assert O.equilibrate(n - M)[1] >= tol
+    # t_max ends the run when tol cannot be met: 1.05 time units = 105 steps of 0.01 (a partial check)
+    n2, res2 = P.equilibrate_to(1e-300, t_max=1.05, check_every=M)
+    assert n2 == 105
+    ref2, ref_res2 = O.equilibrate(105)
+    assert rel(P.get_state(0), ref2) < 1e-11
+    assert res2 == pytest.approx(ref_res2, rel=1e-6)
+
+
 @pytest.mark.parametrize("precision,tol", [("fp64", 1e-10), ("mixed", 1e-4)])
 def test_linear_response(precision, tol):
     m = MODELS["harmonic"]
