@@ -1,6 +1,10 @@
 // Fused right-hand-side stage: launchers of the single-model kernel (qhfpe_fused_kernel.cuh) and the
 // non-Condon dipole kernel, which shares its FFT.
 #include "qhfpe_fused_kernel.cuh"
+#include "qhfpe_fused_window.cuh"
+
+#include <cstdlib>
+#include <cstring>
 
 namespace {
 
@@ -94,11 +98,59 @@ cudaError_t launch_dipole_fft_t(const GridInfo &g, const T *TL, const T *TR, con
     return cudaGetLastError();
 }
 
+// The q-window kernel serves FP32 states with np = 128 and one or two electronic states when the stage
+// computes every term with the potential term in the kernel, each lane's four p values share a sign
+// (p = 0 on a multiple of four, or off the grid), and no element has more than six tier neighbours.
+// QHFPE_FUSED_WINDOW=0 in the environment selects fused_stage_kernel instead.
+bool window_enabled()
+{
+    const char *v = std::getenv("QHFPE_FUSED_WINDOW");
+    return !(v && std::strcmp(v, "0") == 0);
+}
+
+bool window_applies(const GridInfo &g, int np, int S, int terms, bool have_pg)
+{
+    if (np != 128 || S < 1 || S > 2 || have_pg || terms != QHFPE_TERM_ALL || g.max_nb > WIN_MAXNB) return false;
+    for (int c = 0; c < np; c += 4) {
+        const bool a = (float)(g.p_min + c * g.dp) < 0.0f, b = (float)(g.p_min + (c + 3) * g.dp) < 0.0f;
+        if (a != b) return false;
+    }
+    return window_enabled();
+}
+
+template <int S, bool MIXED>
+cudaError_t launch_window_t(const GridInfo &g, const ElemInfo *elems, const FusedTables<float> &tab, const float *v_in,
+                            const float *y, const double *y0, float *v_out, double *y0_out, double h, int mode,
+                            int rep0, int n_rep, cudaStream_t st)
+{
+    constexpr int NP = 128, TQ = WinTile<S>::TQ;
+    const size_t smem = win_kin_offset<NP, S, TQ>() + WIN_KIN_BYTES;
+    const long blocks = (long)((g.nq + TQ - 1) / TQ) * n_rep * g.n_elem;
+    if (blocks <= 0) return cudaSuccess;
+    const StageScalars<float> sc = stage_scalars<float>(g, h);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)blocks);
+    cfg.blockDim = dim3(FTHREADS);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, fused_window_kernel<NP, S, MIXED>, g, elems, tab, sc, v_in, y, y0, v_out, y0_out, h,
+                              mode, rep0, n_rep);
+}
+
 template <typename T, int NP, int S, bool MIXED>
 cudaError_t launch_fused_t(const GridInfo &g, const ElemInfo *elems, const FusedTables<T> &tab, const T *v_in,
                            const T *y, const double *y0, T *v_out, double *y0_out, double h, int mode, int terms,
                            int rep0, int n_rep, cudaStream_t st, const T *Pg, int tq_req)
 {
+    if constexpr (sizeof(T) == 4 && NP == 128 && S <= 2) {
+        if (window_applies(g, NP, S, terms, Pg != nullptr))
+            return launch_window_t<S, MIXED>(g, elems, tab, v_in, y, y0, v_out, y0_out, h, mode, rep0, n_rep, st);
+    }
     int tq = tq_req > 0 ? tq_req : fused_rows_per_tile(NP, S, sizeof(T));
     const int tmax = fused_max_rows(NP, S, sizeof(T));  // the shared-memory limit set at preparation
     if (tq > tmax) tq = tmax;
@@ -132,6 +184,12 @@ cudaError_t prepare_fused_t()
     cudaError_t e = cudaFuncSetAttribute(fused_stage_kernel<T, NP, S, MIXED, false>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
+    if constexpr (sizeof(T) == 4 && NP == 128 && S <= 2) {
+        constexpr int TQ = WinTile<S>::TQ;
+        e = cudaFuncSetAttribute(fused_window_kernel<NP, S, MIXED>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)(win_kin_offset<NP, S, TQ>() + WIN_KIN_BYTES));
+        if (e != cudaSuccess) return e;
+    }
     return prepare_fused_multi<T, MIXED>(NP, S, smem);
 }
 
