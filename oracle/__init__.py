@@ -35,6 +35,7 @@ class _Params(ctypes.Structure):
         ("n_matsubara", ctypes.c_int), ("high_temperature", ctypes.c_int), ("use_cdelta", ctypes.c_int),
         ("depth", ctypes.c_int), ("closure", ctypes.c_int), ("periodic_q", ctypes.c_int),
         ("dt", ctypes.c_double), ("closure_coef", ctypes.POINTER(ctypes.c_double)),
+        ("v_c2", ctypes.c_double),
     ]
 
 
@@ -90,7 +91,7 @@ class Oracle:
                           model["p_min"], model["p_max"], self.T.ctypes.data_as(dp), self.mu.ctypes.data_as(dp),
                           model["eta"], model["gamma"], model["beta"], model["n_matsubara"],
                           model["high_temperature"], model["use_cdelta"], model["depth"], model["closure"],
-                          int(per), model["dt"], None)
+                          int(per), model["dt"], None, float(model.get("v_c2", 0.0)))
         if closure_coef is not None:
             self._coef = np.ascontiguousarray(closure_coef, dtype=np.float64)
             assert self._coef.shape == (model["nq"], model["np"], 10)

@@ -62,6 +62,7 @@ typedef struct {
     int periodic_q;
     double dt;
     const double *closure_coef; /* closure 2 (learned): [nq][np][10] coefficients, see oq_rhs */
+    double v_c2;           /* system side of the system-bath coupling, V(q) = q + v_c2 q^2 (Sec. II) */
 } oq_params;
 
 typedef struct {
@@ -197,6 +198,7 @@ oq_ctx *oq_create(const oq_params *P)
     if (P->S < 1 || P->S > 8 || P->nq < 1 || P->np < 2 || (P->np & 1) || P->depth < 0) return NULL;
     if ((P->closure == 1 || P->closure == 2) && P->n_matsubara != 0) return NULL; /* K = 0 closures only */
     if (P->closure == 2 && !P->closure_coef) return NULL;
+    if (P->v_c2 != 0.0 && P->closure != 0) return NULL; /* the Eq. (GMFP) terminator assumes V(q) = q */
     oq_ctx *C = (oq_ctx *)calloc(1, sizeof(oq_ctx));
     C->P = *P;
     int S = P->S, nq = P->nq, np = P->np;
@@ -351,6 +353,22 @@ static cplx dpp_central(const oq_ctx *C, const cplx *row, int l)
             + 16.0 * Xp(C, row, l + 1, 0) - Xp(C, row, l + 2, 0)) / (12.0 * C->dp * C->dp);
 }
 
+/* d^2 W/dp dq at (q_i, p_l): 4th-order central differences along q (zero ghost cells, or periodic)
+ * and along p (periodic), the q-difference taken first. */
+static cplx dq_central(const oq_ctx *C, const cplx *blk, int i, int l)
+{
+    return (Wq(C, blk, i - 2, l) - 8.0 * Wq(C, blk, i - 1, l) + 8.0 * Wq(C, blk, i + 1, l) - Wq(C, blk, i + 2, l))
+           / (12.0 * C->dq);
+}
+
+static cplx dpq_central(const oq_ctx *C, const cplx *blk, int i, int l)
+{
+    int np = C->P.np;
+    cplx v[5];
+    for (int b = -2; b <= 2; ++b) v[b + 2] = dq_central(C, blk, i, ((l + b) % np + np) % np);
+    return (v[0] - 8.0 * v[1] + 8.0 * v[3] - v[4]) / (12.0 * C->dp);
+}
+
 /* ------------------------------------------------------------------------------------------------
  * Right-hand side of Eq. (heom) with the linear-coupling operators of Sec. II:
  *   Phi = -d/dp, Psi = q, Lambda^(1) = -p/m, Lambda^(2) = 0  (so only m = e_k survives in the sum,
@@ -360,6 +378,19 @@ static cplx dpp_central(const oq_ctx *C, const cplx *row, int l)
  *               - (sum_k n_k gamma_k) W^n_jk + c_delta d^2W^n_jk/dp^2
  *               + sum_k dW^(n+e_k)_jk/dp
  *               + sum_k n_k gamma_k ( r_k p W^(n-e_k)_jk + c_k dW^(n-e_k)_jk/dp ).
+ * Nonlinear coupling V(q) = q + c2 q^2 (Sec. II keeps V general; with hbar = m = 1).  From the
+ * definitions there -- Phi = i (V(p,q) - V*(p,q)) *, Psi = (V(p,q) + V*(p,q))/2 *, K = p d/dq,
+ * Lambda^(l) = (Psi^x)^l K with the commutator A^x B = AB - BA -- and r <-> i d/dp under the Wigner
+ * transform along p:  V(q + r/2) - V(q - r/2) = r phi(q),  phi(q) = 1 + 2 c2 q, and
+ * (V(q + r/2) + V(q - r/2))/2 = V(q) + c2 r^2/4, so
+ *   Phi        = -phi(q) d/dp,
+ *   Psi        = V(q) - (c2/4) d^2/dp^2,
+ *   Lambda^(1) = [Psi, p d/dq] = -p phi(q) - (c2/2) d^2/dp dq,
+ *   Lambda^(2) = [Psi, Lambda^(1)] = c2 phi(q) d/dp,   Lambda^(l >= 3) = 0,
+ *   Phi^2      = phi(q)^2 d^2/dp^2.
+ * In Eq. (heom) the sum over m then keeps |m| = 1 (weight n_k) and |m| = 2 (weight n!/(m!(n-m)!)
+ * gamma^m r^m: C(n_k, 2) gamma_k^2 r_k^2 for m = 2 e_k, n_k n_l gamma_k gamma_l r_k r_l for
+ * m = e_k + e_l).  c2 = 0 gives back the linear form above exactly.  Closure: truncation only.
  * At the deepest tier with the terminator closure (Eq. (GMFP), K = 0), the missing W^(N+1) in the
  * tier-up term is replaced by r_0 p W^N + c_0 dW^N/dp, i.e. the term becomes
  *   d/dp (r_0 p W^N) + c_0 d^2 W^N/dp^2.
@@ -380,6 +411,8 @@ static void rhs_row(const oq_ctx *C, const cplx *W, int e, int j, int k, int i, 
     for (int a = 0; a < M; ++a) { tier += n[a]; ngam += n[a] * C->gam[a]; }
     const cplx *Wjk = W + e * elem + ((size_t)j * S + k) * blk;
     const cplx *row = Wjk + (size_t)i * np;
+    const double c2 = P->v_c2;
+    const double phi = 1.0 + 2.0 * c2 * C->qv[i];   /* Phi = -phi d/dp */
     for (int l = 0; l < np; ++l) {
         cplx acc = 0.0;
         if (terms & OQ_KINETIC) acc += -C->pv[l] * dq_upwind(C, Wjk, i, l);
@@ -399,14 +432,14 @@ static void rhs_row(const oq_ctx *C, const cplx *W, int e, int j, int k, int i, 
         }
         if (terms & OQ_DAMPING) {
             acc += -ngam * row[l];
-            if (C->cdelta != 0.0) acc += C->cdelta * dpp_central(C, row, l);
+            if (C->cdelta != 0.0) acc += C->cdelta * phi * phi * dpp_central(C, row, l);
         }
         if (terms & OQ_TIER_UP) {
             for (int a = 0; a < M; ++a) {
                 int u = C->up[e * M + a];
                 if (u >= 0) {
                     const cplx *urow = W + u * elem + ((size_t)j * S + k) * blk + (size_t)i * np;
-                    acc += dp_central(C, urow, l, 0);
+                    acc += phi * dp_central(C, urow, l, 0);
                 } else if (P->closure == 1 && tier == P->depth) {
                     acc += C->r[0] * dp_central(C, row, l, 1) + C->c[0] * dpp_central(C, row, l);
                 } else if (P->closure == 2 && tier == P->depth) {
@@ -423,7 +456,29 @@ static void rhs_row(const oq_ctx *C, const cplx *W, int e, int j, int k, int i, 
                 if (dn < 0) continue;
                 const cplx *drow = W + dn * elem + ((size_t)j * S + k) * blk + (size_t)i * np;
                 double w = n[a] * C->gam[a];
-                acc += w * (C->r[a] * C->pv[l] * drow[l] + C->c[a] * dp_central(C, drow, l, 0));
+                acc += w * (C->r[a] * phi * C->pv[l] * drow[l] + C->c[a] * phi * dp_central(C, drow, l, 0));
+                if (c2 != 0.0 && C->r[a] != 0.0) {  /* the d^2/dp dq part of -r_k Lambda^(1) */
+                    const cplx *dblk = W + dn * elem + ((size_t)j * S + k) * blk;
+                    acc += w * C->r[a] * 0.5 * c2 * dpq_central(C, dblk, i, l);
+                }
+            }
+            /* |m| = 2: -(n!/(m!(n-m)!)) gamma^m r^m Lambda^(2) W^(n-m), Lambda^(2) = c2 phi d/dp */
+            if (c2 != 0.0) {
+                int v[64];
+                for (int a = 0; a < M; ++a)
+                    for (int b = a; b < M; ++b) {
+                        double wgt;
+                        if (a == b) wgt = 0.5 * n[a] * (n[a] - 1) * C->gam[a] * C->gam[a] * C->r[a] * C->r[a];
+                        else wgt = (double)n[a] * n[b] * C->gam[a] * C->gam[b] * C->r[a] * C->r[b];
+                        if (wgt == 0.0) continue;
+                        memcpy(v, n, sizeof(int) * M);
+                        v[a] -= 1;
+                        v[b] -= 1;
+                        if (v[a] < 0 || v[b] < 0) continue;
+                        int d2 = find_element(C, v);
+                        const cplx *drow = W + d2 * elem + ((size_t)j * S + k) * blk + (size_t)i * np;
+                        acc += -wgt * c2 * phi * dp_central(C, drow, l, 0);
+                    }
             }
         }
         out[l] = acc;
