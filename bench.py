@@ -213,16 +213,27 @@ def spectrum_2d_measure(stream):
     eqp.close()
     out = {}
     R = {}
+    args = (SPEC2D["n_t1"], SPEC2D["t1_stride"], SPEC2D["t2"], SPEC2D["n_t3"])
     for prec in ("mixed", "fp64"):
         P = Propagator(m, T, precision=prec, stream=stream)
         P.set_equilibrium(W_eq)
-        args = (SPEC2D["n_t1"], SPEC2D["t1_stride"], SPEC2D["t2"], SPEC2D["n_t3"])
         P.third_order_response(*args, split_pathways=True)  # builds the batches and graphs
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         R[prec] = P.third_order_response(*args, split_pathways=True)
         torch.cuda.synchronize()
         out[prec + "_s"] = time.perf_counter() - t0
+        if prec == "mixed":
+            # the same schedule with every phase's propagation as one persistent cooperative launch
+            P.set_persistent(True)
+            P.third_order_response(*args, split_pathways=True)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            Rp = P.third_order_response(*args, split_pathways=True)
+            torch.cuda.synchronize()
+            out["mixed_persistent_s"] = time.perf_counter() - t0
+            out["rel_err_R3_persistent_vs_graphs"] = float(np.linalg.norm(Rp - R[prec]) / np.linalg.norm(R[prec]))
+            P.set_persistent(False)
         if prec == "mixed":
             w = np.linspace(5.0, 16.0, 111)
             spec = {}
@@ -248,6 +259,40 @@ def spectrum_2d_measure(stream):
     out["workload"] = ("harmonic_32x32_d3, 64 t1 x 4 t2 x 2 pathways = 512 t3 jobs of 512 steps "
                        f"({512 * cells} cells per detection stage)")
     out["t3_cell_updates"] = 512 * cells * SPEC2D["n_t3"]
+    return out
+
+
+def linear_absorption_measure(stream):
+    """Linear absorption of the two-state harmonic model (32 x 32, depth 3, terminator, dt 0.01, 2000 RK4
+    steps of one 16,384-cell propagation): wall time of R1 with graph-replayed stage launches and with one
+    persistent cooperative launch (FP64 and mixed), and the mixed form's R1 error against FP64."""
+    import numpy as np
+    import torch
+    import qhfpe_inputs as qi
+    from paper_1706_09590_gb300 import Propagator
+    m = qi.harmonic_two_state()
+    T = qi.u_table(m)
+    E = Propagator(m, T, precision="fp64", stream=stream)
+    E.equilibrate(1000)
+    Weq = E.get_state(0)
+    E.close()
+    out = {"workload": "harmonic_32x32_d3, R1 over 2000 RK4 steps (one propagation, 16384 cells)"}
+    R = {}
+    for prec in ("fp64", "mixed"):
+        for persistent in (False, True):
+            P = Propagator(m, T, precision=prec, stream=stream)
+            P.set_persistent(persistent)
+            P.set_equilibrium(Weq)
+            P.linear_response(2000)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            R[(prec, persistent)] = P.linear_response(2000)
+            torch.cuda.synchronize()
+            out[prec + ("_persistent_s" if persistent else "_graphs_s")] = time.perf_counter() - t0
+            P.close()
+    ref = R[("fp64", False)]
+    out["rel_err_R1_mixed_vs_fp64"] = float(np.linalg.norm(R[("mixed", False)] - ref) / np.linalg.norm(ref))
+    out["rel_err_R1_persistent_vs_graphs_fp64"] = float(np.linalg.norm(R[("fp64", True)] - ref) / np.linalg.norm(ref))
     return out
 
 
@@ -722,7 +767,8 @@ def main():
     stage_ms = ms_stage / max(n_stage, 1)
     pot_ms = ms_pot / max(n_pot, 1)
     total = max(ms_stage + ms_pot + kt["aux"][1], 1e-9)
-    stage_roof = {"bound": "hbm", "kernel": "fused_stage_kernel (FFT potential term, stencil, bath, tier couplings, "
+    stage_name = "fused_window_kernel" if P.stage_form() == 1 else "fused_stage_kernel"
+    stage_roof = {"bound": "hbm", "kernel": stage_name + " (FFT potential term, stencil, bath, tier couplings, "
                   "Horner update)" if args.precision != "bf16x3" else
                   "fused_stage_kernel (stencil, bath, tier couplings, Horner update; potential term read)",
                   "achieved": alg_bytes_stage / (stage_ms / 1e3) / 1e9, "peak": hbm_peak, "unit": "GB/s",
@@ -738,13 +784,14 @@ def main():
                            "unit": "TFLOP/s", "frac": fl / (stage_ms / 1e3) / 1e12 / fp64_peak,
                            "peak_source": fp64_src, "flops_per_launch": fl})
         stage_roof.pop("algorithmic_bytes_per_launch")
-    # DRAM bytes per launch from the committed ncu capture, valid only for the kernel source it was
-    # taken from
+    # DRAM bytes per launch from the committed ncu capture of the kernel this run times, valid only for
+    # the kernel sources it was taken from
     try:
         import hashlib
-        tr = json.load(open(os.path.join(ROOT, "profiles", "ncu_traffic_fused_stage_photoiso_96x128_d8.json")))
-        src = open(os.path.join(ROOT, tr["source"]), "rb").read()
-        if hashlib.sha256(src).hexdigest() == tr["source_sha256"] and args.precision == "mixed":
+        tr = json.load(open(os.path.join(ROOT, "profiles", "ncu_traffic_fused_window_photoiso_96x128_d8.json")))
+        same = all(hashlib.sha256(open(os.path.join(ROOT, f), "rb").read()).hexdigest() == h
+                   for f, h in zip(tr["sources"], tr["sources_sha256"]))
+        if same and args.precision == "mixed" and P.stage_form() == 1:
             stage_roof["traffic"] = tr["dram_bytes_per_launch"]
     except (OSError, ValueError, KeyError):
         pass
@@ -769,6 +816,7 @@ def main():
                                    f"{cells} cells per GPU)", "precision": args.precision,
                        "l2": f"working set {4 * cells * 2 * esize / 1e6:.0f} MB per step > 129 MB L2 (no flush)",
                        "tile_rows_autotuned": P.tile_rows(),
+                       "stage_form_autotuned": {1: "q-window", 0: "general", -1: "none"}[P.stage_form()],
                        "parallelism": f"replicas x{world}"},
             "e2e": {"value": e2e, "unit": "cell-updates/s", "h2d_bytes_per_step": state_bytes,
                     "d2h_bytes_per_step": state_bytes + 16 * 2},
@@ -781,6 +829,7 @@ def main():
     if not args.no_config2_sweep:
         line["config2_sweep"] = config2_sweep_measure(stream)
     if not args.no_spectrum:
+        line["linear_absorption"] = linear_absorption_measure(stream)
         line["spectrum_2d"] = spectrum_2d_measure(stream)
         if not args.no_cpu_baseline and rank == 0:
             line["spectrum_2d"]["cpu_baseline"] = cpu_spectrum_baseline()

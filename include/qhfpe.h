@@ -68,7 +68,9 @@ typedef enum {
 typedef enum {
     QHFPE_TRUNCATE = 0,   /* W^(n + e_k) = 0 beyond the deepest tier */
     QHFPE_TERMINATOR = 1, /* Eq. (GMFP) at the deepest tier; requires n_matsubara = 0 */
-    QHFPE_LEARNED = 2     /* learned closure, n_matsubara = 0 (see qhfpe_closure_load) */
+    QHFPE_LEARNED = 2,    /* learned closure, n_matsubara = 0 (see qhfpe_closure_load) */
+    QHFPE_LEARNED_STATE = 3 /* state-input learned closure (see qhfpe_closure_state_load): n_matsubara = 0,
+                             * QHFPE_FP64, n_states <= 2, np in {32, 64, 128, 256}; classic RK4 */
 } qhfpe_closure;
 
 typedef enum {
@@ -103,6 +105,15 @@ typedef struct {
     int precision;           /* qhfpe_precision */
     double dt;               /* RK4 step > 0 */
     int n_replicas;          /* independent propagations held by the handle, >= 1 */
+    /* System side of the system-bath coupling, Sec. II: V(q) = q + v_c2 q^2 (0: the linear coupling
+     * the paper works with).  With hbar = m = 1 and phi(q) = 1 + 2 v_c2 q the operators of Eq. (heom)
+     * become Phi = -phi d/dp, Lambda^(1) = -p phi - (v_c2/2) d2/dp dq, Lambda^(2) = v_c2 phi d/dp
+     * (Lambda^(>=3) = 0), and Phi^2 = phi^2 d2/dp2; the |m| = 2 couplings of Eq. (heom) to
+     * W^(n - e_k - e_l) enter with their multinomial weights.  d/dq in the mixed derivative: 4th-order
+     * central differences (zero ghost cells, or periodic).  Nonzero v_c2 requires closure =
+     * QHFPE_TRUNCATE (the Eq. (GMFP) terminator assumes V = q), a fused shape (np in {32, 64, 128, 256},
+     * n_states <= 3) and a finite value; EINVAL / EUNSUPPORTED otherwise. */
+    double v_c2;
 } qhfpe_params;
 
 typedef struct qhfpe qhfpe_t;
@@ -282,9 +293,32 @@ qhfpe_status qhfpe_wait_selftest(qhfpe_t *h, int release, int limit_ms);
 /* Tile of the fused right-hand-side kernel (q rows per block) picked by the autotuner for the
  * handle's replicas: timed with CUDA events on the first propagation (0 before it, or when the
  * shape has no fused kernel; candidates 1, 2, 3, 4, 5, 6, 8, 12, 16 rows up to the kernel's
- * shared-memory limit, a power of two).  The environment variable QHFPE_TILE_ROWS, when it holds a
- * height from 1 to that limit, replaces the timing with that tile. */
+ * shared-memory limit, a power of two, and the q-window form's fixed tile, see qhfpe_stage_form).
+ * The environment variable QHFPE_TILE_ROWS, when it holds a height from 1 to that limit, replaces
+ * the timing with that tile (the q-window form then serves the shapes it applies to). */
 qhfpe_status qhfpe_tile_rows(const qhfpe_t *h, int *rows);
+/* Persistent propagation (on = 1), Sec. III protocol on the device: every later run of RK4 steps of
+ * the handle -- qhfpe_step and the propagations of qhfpe_response, whose phases pack all delays as
+ * replicas -- runs as ONE cooperative launch that stays resident: each Horner stage is a grid-stride
+ * loop over the blocks of the fused stage kernel, grid-wide barriers separate the stages, and the
+ * FP64 trace Tr{mu W^(0)} is reduced in the same launch after each step (fixed order).  Results equal
+ * those of the graph-replayed launches (on = 0, the default) to rounding of the trace sums (the state is
+ * the same arithmetic).  It covers the shapes with a fused kernel (np in {32, 64, 128, 256}, n_states
+ * <= 3), the FP64 and QHFPE_MIXED forms, the Condon dipole and the TRUNCATE / TERMINATOR closures; other
+ * handles keep the graph replay.  Every barrier wait is bounded (2 s): when one gives up the call
+ * returns QHFPE_ETIMEOUT and the handle turns sticky.  Kernel timing (qhfpe_kernel_timing) uses the
+ * per-stage launches. */
+qhfpe_status qhfpe_set_persistent(qhfpe_t *h, int on);
+/* Failure-detection self-test of the persistent kernel's grid barrier: four blocks meet at one barrier
+ * with the bounded wait (limit_ms, 1..10000); withhold = 1 keeps one block away, so the others give up
+ * and the call returns QHFPE_ETIMEOUT while the handle and the CUDA context stay usable. */
+qhfpe_status qhfpe_barrier_selftest(qhfpe_t *h, int withhold, int limit_ms);
+/* Form of the fused right-hand-side kernel the autotuner picked for the handle's replicas, timed
+ * together with the tile heights: 1 the q-window form (FP32 states with np = 128 and one or two
+ * states, each warp one electronic pair and four q rows; candidate only where it applies), 0 the
+ * general form; -1 before the first propagation or without a fused kernel.  QHFPE_FUSED_WINDOW=0
+ * removes the q-window form from the candidates. */
+qhfpe_status qhfpe_stage_form(const qhfpe_t *h, int *form);
 qhfpe_status qhfpe_kernel_timing_read(qhfpe_t *h, long *launches, double *total_ms, int n_kinds);
 /* Measurement aid with no counterpart in the paper: the FP64 fused multiply-add rate of the current
  * device, the denominator of the FP64 form's roofline.  8 blocks of 256 threads per SM each run eight
@@ -313,6 +347,11 @@ qhfpe_status qhfpe_fp64_fma_rate(void *stream, int repeats, double *flops_per_s)
 #define QHFPE_CLOSURE_N_OUT 10
 #define QHFPE_CLOSURE_N_WEIGHTS 135178
 #define QHFPE_CLOSURE_N_STATS 67
+/* The network's inputs on a grid (host, [nq*np][3] doubles, row-major [q][p]): (q_i / 8, p_l / 8, ln eta)
+ * with the grid convention above; the same values the library's inference uses.  EINVAL for an empty
+ * grid, eta <= 0 or a NULL output. */
+qhfpe_status qhfpe_closure_inputs(int nq, int np, double q_min, double q_max, double p_min, double p_max, double eta,
+                                  double *X);
 /* Add the statistics of target tier t (1 <= t <= depth, n_matsubara = 0) over every replica's current
  * state to stats_dev (device, caller-owned, nq*np*67 doubles, accumulated into). */
 qhfpe_status qhfpe_closure_collect(qhfpe_t *h, int target_tier, double *stats_dev);
@@ -333,6 +372,40 @@ qhfpe_status qhfpe_closure_loss_grad(const float *w, const double *X, const doub
                                      double ridge, double *loss, float *grad);
 qhfpe_status qhfpe_closure_train(float *w, const double *X, const double *stats, int n_points, int n_iters,
                                  int batch, double lr, double ridge, unsigned seed, double *loss_history);
+
+/* ---- State-input learned closure (BASELINE's literal network; no counterpart in the paper) ---------
+ * With closure = QHFPE_LEARNED_STATE the missing element W^(N+1) of the deepest tier (one Drude mode,
+ * a chain) is predicted at every grid point (q_i, p_l) by a perceptron of the state itself: inputs
+ * (q_i / 8, p_l / 8, ln eta) followed by the 3 x 3 patches (q_{i+a}, p_{l+b}), a, b in {-1, 0, 1} (q: zero
+ * outside the grid, or periodic; p periodic), of tiers N and N-1, pair by pair (j, k row-major), patch
+ * row-major over (a, b), (re, im) innermost -- 36 S^2 + 3 values; three tanh layers of width 256 and a
+ * linear output of 2 S^2 values, W^(N+1)_jk(q_i, p_l) (re, im) pair by pair.  The closed hierarchy is
+ * nonlinear in the state, so the step is classic RK4 (four right-hand sides, FP64) and pathway
+ * additivity no longer holds exactly.  Inference runs in every right-hand side with bf16 weights and
+ * activations and FP32 accumulation.  Until weights are loaded the slot is zero (the truncated
+ * hierarchy).  The equilibrium (qhfpe_equilibrate) uses the Eq. (GMFP) terminator.  Weights (float):
+ * W1[256][36 S^2 + 3], b1[256], W2[256][256], b2, W3[256][256], b3, W4[2 S^2][256], b4, then three scales
+ * (tier-N inputs, tier-(N-1) inputs, outputs: the network sees the values divided by them) --
+ * qhfpe_closure_state_n_weights(S) floats. */
+size_t qhfpe_closure_state_n_weights(int n_states);
+qhfpe_status qhfpe_closure_state_load(qhfpe_t *h, const float *weights, size_t n);
+/* Training samples from the handle's current state (FP64, n_matsubara = 0, any closure): for every
+ * replica and grid point, the inputs of the target tier t (1 <= t <= depth; tiers t-1, t-2, unscaled) into
+ * X_dev [..][36 S^2 + 3] and the tier-t values into Y_dev [..][2 S^2] (device, floats), starting at sample
+ * `offset`, at most up to `capacity`; count_out: samples written. */
+qhfpe_status qhfpe_closure_state_collect(qhfpe_t *h, int target_tier, float *X_dev, float *Y_dev, long offset,
+                                         long capacity, long *count_out);
+/* The mean squared error over the n_points samples and all outputs, and its gradient (FP32 kernels),
+ * for weights w (the scales are not used: X and Y as given).  grad: qhfpe_closure_state_n_weights(S) - 3
+ * floats.  Host arrays. */
+qhfpe_status qhfpe_closure_state_loss_grad(int n_states, const float *w, const float *X, const float *Y,
+                                           int n_points, double *loss, float *grad);
+/* Adam training (beta1 0.9, beta2 0.999, eps 1e-8, minibatches drawn without replacement per epoch,
+ * seeded) on the samples scaled by the RMS of the tier-N inputs, of the tier-(N-1) inputs and of the
+ * outputs; w (host, qhfpe_closure_state_n_weights(S) floats) updated in place, the three scales written
+ * at its end; loss_history (may be NULL) gets each minibatch's mean squared error (scaled values). */
+qhfpe_status qhfpe_closure_state_train(int n_states, float *w, const float *X, const float *Y, int n_points,
+                                       int n_iters, int batch, double lr, unsigned seed, double *loss_history);
 
 /* ---- Potential term without allocation -----------------------------------------------------
  * No counterpart in the paper: this entry point exists for callers that cannot allocate device

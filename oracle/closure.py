@@ -158,3 +158,130 @@ def statistics(W, tier, r0=0.0, c0=0.0, p=None, dp=1.0):
     out[..., 65] = yy
     out[..., 66] = phi.shape[2]
     return out.reshape(nq * n_p, N_STATS)
+
+
+# ------------------------------------------------------------------------------------------------
+# State-input closure (the literal network): W^(N+1) at (q_i, p_l), all pairs, from the 3 x 3 patches
+# of tiers N and N-1 of the state itself and (q/8, p/8, ln eta).  Input layout: the three features,
+# then tier N then tier N-1, each pair by pair (j, k row-major), patch row-major over (a, b) in
+# {-1, 0, 1}^2 (q offset a: zero outside the grid unless periodic; p offset b: periodic), (re, im)
+# innermost -- 36 S^2 + 3 values.  Output: (re, im) of W^(N+1)_jk pair by pair -- 2 S^2 values.  Weights:
+# W1[256][n_in], b1, W2[256][256], b2, W3[256][256], b3, W4[n_out][256], b4, then three scales (tier-N
+# inputs, tier-(N-1) inputs, outputs).
+# ------------------------------------------------------------------------------------------------
+def state_sizes(S):
+    return 36 * S * S + 3, 2 * S * S
+
+
+def state_shapes(S):
+    n_in, n_out = state_sizes(S)
+    return [(N_HID, n_in), (N_HID,), (N_HID, N_HID), (N_HID,), (N_HID, N_HID), (N_HID,), (n_out, N_HID), (n_out,)]
+
+
+def state_n_weights(S):
+    return int(sum(np.prod(s) for s in state_shapes(S))) + 3
+
+
+def state_unpack(w, S):
+    out, o = [], 0
+    for s in state_shapes(S):
+        n = int(np.prod(s))
+        out.append(np.asarray(w[o:o + n], dtype=np.float64).reshape(s))
+        o += n
+    return out, np.asarray(w[o:o + 3], dtype=np.float64)
+
+
+def state_inputs(W, tier, model):
+    """Unscaled network inputs [nq][np][36 S^2 + 3] of the target tier `tier` from a K = 0 state W
+    ([n_elem][S][S][nq][np], element e = tier e): tiers tier-1 and tier-2 (zeros below tier 0)."""
+    from qhfpe_inputs import axis
+    n_elem, S, _, nq, n_p = W.shape
+    periodic = model.get("periodic_q", 0)
+    q = axis(nq, model["q_min"], model["q_max"])
+    p = axis(n_p, model["p_min"], model["p_max"])
+    out = np.zeros((nq, n_p, 36 * S * S + 3))
+    out[..., 0] = q[:, None] / 8.0
+    out[..., 1] = p[None, :] / 8.0
+    out[..., 2] = np.log(model["eta"])
+    c = 3
+    for t in (tier - 1, tier - 2):
+        X = W[t] if t >= 0 else np.zeros_like(W[0])
+        for j in range(S):
+            for k in range(S):
+                blk = X[j, k]
+                for a in (-1, 0, 1):
+                    sh = np.roll(blk, -a, axis=0)
+                    if not periodic:
+                        if a == 1:
+                            sh[-1] = 0
+                        elif a == -1:
+                            sh[0] = 0
+                    for b in (-1, 0, 1):
+                        v = np.roll(sh, -b, axis=1)
+                        out[..., c] = v.real
+                        out[..., c + 1] = v.imag
+                        c += 2
+    return out
+
+
+def state_targets(W, tier):
+    """[nq][np][2 S^2] targets: (re, im) of W^(tier)_jk pair by pair."""
+    n_elem, S, _, nq, n_p = W.shape
+    Y = np.zeros((nq, n_p, 2 * S * S))
+    for j in range(S):
+        for k in range(S):
+            Y[..., 2 * (j * S + k)] = W[tier, j, k].real
+            Y[..., 2 * (j * S + k) + 1] = W[tier, j, k].imag
+    return Y
+
+
+def state_forward(w, X, S, quantize=None, scaled=True):
+    """Network output for inputs X [..][n_in].  scaled: divide the tier inputs by their scales and
+    multiply the outputs by the output scale (the deployed network); quantize (optional) rounds the
+    inputs, weights and activations (e.g. to bf16)."""
+    (W1, b1, W2, b2, W3, b3, W4, b4), sc = state_unpack(w, S)
+    qz = quantize or (lambda a: a)
+    n_in, _ = state_sizes(S)
+    half = (n_in - 3) // 2
+    X = np.array(X, dtype=np.float64)
+    if scaled:
+        X[..., 3:3 + half] /= sc[0]
+        X[..., 3 + half:] /= sc[1]
+    h = qz(X)
+    for Wl, bl in ((W1, b1), (W2, b2), (W3, b3)):
+        h = qz(np.tanh(h @ qz(Wl).T + bl))
+    out = h @ qz(W4).T + b4
+    return out * sc[2] if scaled else out
+
+
+def state_loss_and_grad(w, X, Y, S):
+    """Mean squared error over all samples and outputs (unscaled X, Y) and its gradient with respect to
+    the flat weights (without the three scales)."""
+    (W1, b1, W2, b2, W3, b3, W4, b4), _ = state_unpack(w, S)
+    h1 = np.tanh(X @ W1.T + b1)
+    h2 = np.tanh(h1 @ W2.T + b2)
+    h3 = np.tanh(h2 @ W3.T + b3)
+    o = h3 @ W4.T + b4
+    d = o - Y
+    L = (d * d).mean()
+    do = 2.0 * d / d.size
+    dW4 = do.T @ h3
+    db4 = do.sum(0)
+    dz3 = (do @ W4) * (1 - h3 ** 2)
+    dW3 = dz3.T @ h2
+    db3 = dz3.sum(0)
+    dz2 = (dz3 @ W3) * (1 - h2 ** 2)
+    dW2 = dz2.T @ h1
+    db2 = dz2.sum(0)
+    dz1 = (dz2 @ W2) * (1 - h1 ** 2)
+    dW1 = dz1.T @ X
+    db1 = dz1.sum(0)
+    return L, np.concatenate([a.ravel() for a in (dW1, db1, dW2, db2, dW3, db3, dW4, db4)])
+
+
+def bf16(a):
+    """Round to the nearest bf16 (ties to even), returned as float64."""
+    x = np.asarray(a, dtype=np.float32)
+    u = x.view(np.uint32).astype(np.uint64)
+    u = (u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000
+    return u.astype(np.uint32).view(np.float32).astype(np.float64)

@@ -8,17 +8,15 @@ of depth target-1 truncates) against its two lower tiers are accumulated per gri
 """
 import numpy as np
 
-from .qhfpe import CLOSURE_N_STATS, CLOSURE_N_WEIGHTS, COMMUTATOR, TERMINATOR, Propagator, closure_train
+from .qhfpe import (CLOSURE_N_STATS, CLOSURE_N_WEIGHTS, COMMUTATOR, TERMINATOR, Propagator, closure_inputs,
+                    closure_train)
 
 N_IN, N_HID, N_OUT = 3, 256, 10
 
 
 def network_inputs(model, eta):
-    """(q/8, p/8, ln eta) for every grid point, [nq*np][3]."""
-    q = model["q_min"] + np.arange(model["nq"]) * (model["q_max"] - model["q_min"]) / model["nq"]
-    p = model["p_min"] + np.arange(model["np"]) * (model["p_max"] - model["p_min"]) / model["np"]
-    Q, P = np.meshgrid(q, p, indexing="ij")
-    return np.stack([Q / 8.0, P / 8.0, np.full(Q.shape, np.log(eta))], -1).reshape(-1, 3)
+    """(q/8, p/8, ln eta) for every grid point, [nq*np][3], from the library."""
+    return closure_inputs(model, eta)
 
 
 def initial_weights(seed=1706):
@@ -62,3 +60,54 @@ def training_set(model, U_table, etas, deep_depth, target_tier, n_eq=1500, n_pro
 def train(X, stats, n_iters=3000, batch=4096, lr=1e-3, ridge=0.01, seed=1706, weights=None):
     w0 = initial_weights(seed) if weights is None else weights
     return closure_train(w0, X, stats, n_iters, batch=batch, lr=lr, ridge=ridge, seed=seed)
+
+
+# ---- state-input network (BASELINE's literal closure; QHFPE_LEARNED_STATE) -------------------------
+def initial_state_weights(S, seed=1706):
+    """Glorot-uniform hidden layers, zero output layer (the untrained network predicts zero: truncation),
+    unit scales."""
+    from .qhfpe import closure_state_n_weights
+    n_in, n_out = 36 * S * S + 3, 2 * S * S
+    rng = np.random.default_rng(seed)
+    parts = []
+    for fan_out, fan_in in ((N_HID, n_in), (N_HID, N_HID), (N_HID, N_HID)):
+        lim = np.sqrt(6.0 / (fan_in + fan_out))
+        parts += [rng.uniform(-lim, lim, fan_out * fan_in), np.zeros(fan_out)]
+    parts += [np.zeros(n_out * N_HID), np.zeros(n_out), np.ones(3)]
+    w = np.concatenate(parts).astype(np.float32)
+    assert w.size == closure_state_n_weights(S)
+    return w
+
+
+def state_training_set(model, U_table, etas, deep_depth, target_tier, n_eq, n_prop, every, stream=None):
+    """Samples (X, Y) of the target tier from depth-`deep_depth` FP64 runs (Eq. (GMFP) terminator) at each
+    eta, excited like the statistics of the coefficient form: every grid point of both replicas every
+    `every` steps.  Returns host float32 arrays."""
+    import torch
+    S = model["S"]
+    n_in, n_out = 36 * S * S + 3, 2 * S * S
+    Xs, Ys = [], []
+    for eta in etas:
+        m = dict(model, eta=eta, depth=deep_depth, closure=TERMINATOR)
+        P = Propagator(m, U_table, precision="fp64", n_replicas=2, stream=stream)
+        n_snap = n_prop // every + 1
+        cap = n_snap * 2 * m["nq"] * m["np"]
+        X = torch.zeros((cap, n_in), dtype=torch.float32, device="cuda")
+        Y = torch.zeros((cap, n_out), dtype=torch.float32, device="cuda")
+        P.equilibrate(n_eq)
+        off = P.closure_state_collect(target_tier, X, Y, 0, cap)
+        P.apply_dipole(COMMUTATOR, [0, 1])
+        P.apply_dipole(COMMUTATOR, [1])
+        for _ in range(n_prop // every):
+            P.step(every)
+            off += P.closure_state_collect(target_tier, X, Y, off, cap)
+        P.close()
+        Xs.append(X[:off].cpu().numpy())
+        Ys.append(Y[:off].cpu().numpy())
+    return np.concatenate(Xs), np.concatenate(Ys)
+
+
+def train_state(S, X, Y, n_iters=3000, batch=4096, lr=1e-3, seed=1706, weights=None):
+    from .qhfpe import closure_state_train
+    w0 = initial_state_weights(S, seed) if weights is None else weights
+    return closure_state_train(S, w0, X, Y, n_iters, batch=batch, lr=lr, seed=seed)

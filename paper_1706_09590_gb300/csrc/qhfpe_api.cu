@@ -193,6 +193,7 @@ struct Model {
         return {tab32, tab32 + tab_n, tab32 + 2 * tab_n, tab32 + 3 * tab_n};
     }
     int closure_slot = -1;      // learned closure: element slot holding W^(N+1) (after the real elements)
+    bool closure_state = false; // the slot is predicted from the state (QHFPE_LEARNED_STATE)
     int closure_n = -1, closure_n1 = -1;  // elements of tiers N and N-1 (chain, K = 0)
     double *coef64 = nullptr;   // closure coefficients [nq][np][10] (owned by the handle)
     float *coef32 = nullptr;
@@ -246,6 +247,7 @@ struct Prop {
     bool mixed = false;
     bool tc = false;        // potential term on the tensor cores (bf16 x3)
     int tq = 0;             // fused stage kernel: q rows per block (autotuned on first use; 0 = not yet)
+    int form = -1;          // fused stage kernel form (launch_fused): -1 rule, 0 general, 1 q-window
     double dt = 0.0;
     void *y = nullptr, *vA = nullptr, *vB = nullptr, *P = nullptr;
     double *y0 = nullptr;
@@ -254,6 +256,9 @@ struct Prop {
     double *trace_buf = nullptr;
     size_t trace_cap = 0;
     cudaGraphExec_t graphs[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};  // [chunk][trace]
+    void *pdesc = nullptr;      // persistent propagation: this propagator as a one-member batch
+    int pdesc_tq = 0;           // its tile height
+    unsigned *pbar = nullptr;   // barrier words (count, generation) and the give-up flag
 
     void drop_graphs()
     {
@@ -269,7 +274,8 @@ struct Prop {
         for (auto &a : graphs)
             for (auto &x : a)
                 if (x) cudaGraphExecDestroy(x);
-        for (void *b : {y, vA, vB, P, (void *)y0, (void *)sink, (void *)partial, (void *)trace_buf})
+        for (void *b : {y, vA, vB, P, (void *)y0, (void *)sink, (void *)partial, (void *)trace_buf, pdesc,
+                        (void *)pbar})
             if (b) cudaFree(b);
     }
 };
@@ -293,6 +299,8 @@ struct qhfpe {
     double *coef64 = nullptr;  // learned-closure coefficient table [nq][np][10]
     float *coef32 = nullptr;
     float *closure_w = nullptr;
+    bool persistent = false;   // qhfpe_set_persistent: whole runs of steps in one cooperative launch
+    float *state_w = nullptr;  // state-input closure weights (device), nullptr until loaded
     Timing timing;
 
     ~qhfpe()
@@ -308,6 +316,7 @@ struct qhfpe {
         if (coef64) cudaFree(coef64);
         if (coef32) cudaFree(coef32);
         if (closure_w) cudaFree(closure_w);
+        if (state_w) cudaFree(state_w);
         if (own_stream && stream) cudaStreamDestroy(stream);
     }
 
@@ -378,9 +387,10 @@ void build_tables(const Model &M, const double *U, std::vector<double> &out, F f
         }
 }
 
-qhfpe_status build_model(qhfpe *h, Model &M, int S, const double *U, const double *mu)
+qhfpe_status build_model(qhfpe *h, Model &M, int S, const double *U, const double *mu, int closure_override = -1)
 {
-    const qhfpe_params &p = h->p;
+    qhfpe_params p = h->p;
+    if (closure_override >= 0) p.closure = closure_override;
     M.S = S;
     M.nq = p.nq;
     M.np = p.np;
@@ -406,7 +416,7 @@ qhfpe_status build_model(qhfpe *h, Model &M, int S, const double *U, const doubl
         }
         E.ngam = ngam;
         E.tier = tier;
-        E.terminator = ((p.closure == QHFPE_TERMINATOR || p.closure == QHFPE_LEARNED) && tier == p.depth) ? 1 : 0;
+        E.terminator = ((p.closure == QHFPE_TERMINATOR || p.closure == QHFPE_LEARNED) && tier == p.depth) ? 1 : 0;  // not LEARNED_STATE
         for (int k = 0; k < M.n_modes; ++k) {
             std::vector<int> v = n;
             v[k] += 1;
@@ -420,8 +430,38 @@ qhfpe_status build_model(qhfpe *h, Model &M, int S, const double *U, const doubl
                 E.n_dn++;
             }
         }
+        // nonlinear coupling: -r_k Lambda^(1) brings (v_c2/2) d2/dp dq of W^(n - e_k) (weight
+        // n_k gamma_k r_k v_c2 / 2), and the |m| = 2 terms bring -(multinomial) gamma^m r^m v_c2 phi
+        // d/dp W^(n - m), which joins the tier sum G (differentiated as phi d/dp) with weight
+        // -(multinomial) gamma^m r^m v_c2
+        E.n_mx = E.n_d2 = 0;
+        if (p.v_c2 != 0.0) {
+            for (int k = 0; k < M.n_modes; ++k) {
+                const double w = n[k] * M.bath.gamma[k] * M.bath.r[k] * 0.5 * p.v_c2;
+                if (n[k] > 0 && w != 0.0) {
+                    std::vector<int> v = n;
+                    v[k] -= 1;
+                    E.mx[E.n_mx] = index.at(v);
+                    E.wmx[E.n_mx] = w;
+                    E.n_mx++;
+                }
+                for (int l = k; l < M.n_modes; ++l) {
+                    const double gr = M.bath.gamma[k] * M.bath.r[k] * M.bath.gamma[l] * M.bath.r[l];
+                    const double mult = (k == l) ? 0.5 * n[k] * (n[k] - 1) : (double)n[k] * n[l];
+                    if (gr == 0.0 || mult == 0.0) continue;
+                    std::vector<int> v = n;
+                    v[k] -= 1;
+                    v[l] -= 1;
+                    if (v[k] < 0 || v[l] < 0 || E.n_d2 >= QH_MAX_MODES) continue;
+                    E.d2[E.n_d2] = index.at(v);
+                    E.w2[E.n_d2] = -mult * gr * p.v_c2;
+                    E.n_d2++;
+                }
+            }
+        }
     }
-    if (p.closure == QHFPE_LEARNED) {
+    if (p.closure == QHFPE_LEARNED || p.closure == QHFPE_LEARNED_STATE) {
+        M.closure_state = p.closure == QHFPE_LEARNED_STATE;
         M.closure_slot = M.n_elem;
         for (int e = 0; e < M.n_elem; ++e) {
             ElemInfo &E = M.elems_host[e];
@@ -455,6 +495,7 @@ qhfpe_status build_model(qhfpe *h, Model &M, int S, const double *U, const doubl
     g.tier0_rep_stride = g.elem_stride;
     g.max_nb = 0;
     for (const ElemInfo &E : M.elems_host) g.max_nb = std::max(g.max_nb, E.n_up + E.n_dn);
+    g.c2 = p.v_c2;
 
     M.mu_host.assign(mu, mu + S * S);
     std::vector<double> tab;
@@ -480,10 +521,15 @@ qhfpe_status build_model(qhfpe *h, Model &M, int S, const double *U, const doubl
                     pot = std::max(pot, r * p.np);
                 }
     double bathr = 0.0;
+    // nonlinear coupling: Phi = -phi d/dp with |phi| <= phimax on the grid
+    const double phimax = 1.0 + 2.0 * std::fabs(p.v_c2) * std::max(std::fabs(p.q_min), std::fabs(p.q_max));
     for (const ElemInfo &E : M.elems_host) {
-        double r = E.ngam + (std::fabs(g.cdelta) + (E.terminator ? g.term_c0 : 0.0)) * 64.0 / (12.0 * g.dp * g.dp);
-        r += E.n_up * 1.5 / g.dp + (E.terminator ? g.term_r0 * (pmax / g.dp * 1.5 + 1.0) : 0.0);
-        for (int a = 0; a < E.n_dn; ++a) r += std::fabs(E.wr[a]) * pmax + std::fabs(E.wc[a]) * 1.5 / g.dp;
+        double r = E.ngam + (std::fabs(g.cdelta) * phimax * phimax + (E.terminator ? g.term_c0 : 0.0)) * 64.0 /
+                                (12.0 * g.dp * g.dp);
+        r += E.n_up * 1.5 / g.dp * phimax + (E.terminator ? g.term_r0 * (pmax / g.dp * 1.5 + 1.0) : 0.0);
+        for (int a = 0; a < E.n_dn; ++a) r += (std::fabs(E.wr[a]) * pmax + std::fabs(E.wc[a]) * 1.5 / g.dp) * phimax;
+        for (int a = 0; a < E.n_mx; ++a) r += std::fabs(E.wmx[a]) * (1.5 / g.dp) * (1.5 / g.dq);
+        for (int a = 0; a < E.n_d2; ++a) r += std::fabs(E.w2[a]) * 1.5 / g.dp * phimax;
         bathr = std::max(bathr, r);
     }
     M.max_rate = kin + pot + bathr;
@@ -611,6 +657,14 @@ qhfpe_status closure_fill(qhfpe *h, const Prop &P, T *in, int rep0, int n_rep)
 {
     const Model &M = *P.m;
     if (M.closure_slot < 0) return QHFPE_OK;
+    if (M.closure_state) {  // predicted from the state; zero (truncation) until weights are loaded
+        if constexpr (sizeof(T) == 8) {
+            if (h->state_w)
+                QH_CK(h, launch_closure_state_fill<double>(P.g, in, M.closure_n, M.closure_n1, M.closure_slot,
+                                                           h->state_w, h->p.eta, rep0, n_rep, h->stream));
+        }
+        return QHFPE_OK;
+    }
     const T *coef = std::is_same<T, float>::value ? (const T *)M.coef32 : (const T *)M.coef64;
     QH_CK(h, launch_closure_apply<T>(P.g, in, M.closure_n, M.closure_n1, M.closure_slot, coef, rep0, n_rep, h->stream));
     return QHFPE_OK;
@@ -640,7 +694,7 @@ qhfpe_status step_once(qhfpe *h, Prop &P, bool record)
             Bracket br(h, QH_KIND_STAGE);
             QH_CK(h, (launch_fused<float, true>(P.g, M.elems, M.f32(), (const float *)in, (const float *)y, P.y0,
                                                (float *)out, k == 1 ? P.y0 : nullptr, P.dt / k, k == 1 ? 2 : 1,
-                                               QHFPE_TERM_ALL, 0, P.g.n_rep, st, (const float *)Pt, P.tq)));
+                                               QHFPE_TERM_ALL, 0, P.g.n_rep, st, (const float *)Pt, P.tq, P.form)));
             continue;
         }
         if (M.fused) {
@@ -648,7 +702,7 @@ qhfpe_status step_once(qhfpe *h, Prop &P, bool record)
             if (MIXED)
                 QH_CK(h, (launch_fused<float, true>(P.g, M.elems, M.f32(), (const float *)in, (const float *)y, P.y0,
                                                    (float *)out, k == 1 ? P.y0 : nullptr, P.dt / k, k == 1 ? 2 : 1,
-                                                   QHFPE_TERM_ALL, 0, P.g.n_rep, st, nullptr, P.tq)));
+                                                   QHFPE_TERM_ALL, 0, P.g.n_rep, st, nullptr, P.tq, P.form)));
             else
                 QH_CK(h, (launch_fused<double, false>(P.g, M.elems, M.f64(), (const double *)in, (const double *)y,
                                                      nullptr, (double *)out, nullptr, P.dt / k, k == 1 ? 2 : 1,
@@ -674,8 +728,39 @@ qhfpe_status step_once(qhfpe *h, Prop &P, bool record)
     return QHFPE_OK;
 }
 
+// ---- one classic RK4 step (the state-input closure makes the right-hand side nonlinear) ------------
+//   k1 = L(y), k2 = L(y + dt/2 k1), k3 = L(y + dt/2 k2), k4 = L(y + dt k3),
+//   y <- y + dt/6 (k1 + 2 k2 + 2 k3 + k4); FP64, k in vA, the stage input in vB, the sum in P.
+qhfpe_status step_rk4(qhfpe *h, Prop &P, bool record)
+{
+    cudaStream_t st = h->stream;
+    const Model &M = *P.m;
+    double *y = (double *)P.y, *K = (double *)P.vA, *V = (double *)P.vB, *A = (double *)P.P;
+    const size_t n = (size_t)P.g.n_rep * P.g.rep_stride;
+    const double dt = P.dt;
+    const double a_acc[4] = {dt / 6, dt / 3, dt / 3, dt / 6}, a_v[4] = {dt / 2, dt / 2, dt, 0.0};
+    for (int j = 0; j < 4; ++j) {
+        double *in = j == 0 ? y : V;
+        qhfpe_status r = closure_fill<double>(h, P, in, 0, P.g.n_rep);
+        if (r != QHFPE_OK) return r;
+        {
+            Bracket br(h, QH_KIND_STAGE);
+            QH_CK(h, (launch_fused<double, false>(P.g, M.elems, M.f64(), in, in, nullptr, K, nullptr, 0.0, 0,
+                                                  QHFPE_TERM_ALL, 0, P.g.n_rep, st, nullptr, P.tq, P.form)));
+        }
+        QH_CK(h, launch_rk4_combine(n, y, K, A, V, a_acc[j], a_v[j], j == 0, j == 3, st));
+    }
+    if (record) {
+        Bracket br(h, QH_KIND_AUX);
+        QH_CK(h, launch_trace<double>(P.g, (const double *)P.y, P.g.rep_stride, M.mu, P.sink, 1, P.partial, st,
+                                      M.trace_mu_q()));
+    }
+    return QHFPE_OK;
+}
+
 qhfpe_status step_dispatch(qhfpe *h, Prop &P, bool record)
 {
+    if (P.m->closure_state) return step_rk4(h, P, record);
     return P.mixed ? step_once<float, true>(h, P, record) : step_once<double, false>(h, P, record);
 }
 
@@ -702,38 +787,53 @@ qhfpe_status autotune(qhfpe *h, Prop &P)
     cudaEvent_t a, b;
     QH_CK(h, cudaEventCreate(&a));
     QH_CK(h, cudaEventCreate(&b));
-    float best = 1e30f;
-    int best_tq = 1;
-    // heights between the powers of two as well: the block count (tiles x elements x replicas) against
-    // the blocks resident at once decides how full the last wave is
-    static const int cand[] = {1, 2, 3, 4, 5, 6, 8, 12, 16};
-    for (int tq : cand) {
-        if (tq > tmax) break;
-        float ms = 0.f;
+    // one right-hand side of every replica into vB with the given form and tile, timed over three launches
+    auto time_one = [&](int form, int tq, float *ms) -> qhfpe_status {
         for (int rep = 0; rep < 4; ++rep) {
             if (rep == 1) QH_CK(h, cudaEventRecord(a, st));
             cudaError_t e;
             if (P.mixed)
                 e = launch_fused<float, true>(P.g, M.elems, M.f32(), (const float *)P.y, (const float *)P.y, P.y0,
                                               (float *)P.vB, nullptr, 0.0, 0, QHFPE_TERM_ALL, 0, P.g.n_rep, st,
-                                              P.tc ? (const float *)P.P : nullptr, tq);
+                                              P.tc ? (const float *)P.P : nullptr, tq, form);
             else
                 e = launch_fused<double, false>(P.g, M.elems, M.f64(), (const double *)P.y, (const double *)P.y,
                                                 nullptr, (double *)P.vB, nullptr, 0.0, 0, QHFPE_TERM_ALL, 0, P.g.n_rep,
-                                                st, nullptr, tq);
+                                                st, nullptr, tq, form);
             QH_CK(h, e);
         }
         QH_CK(h, cudaEventRecord(b, st));
         QH_CK(h, cudaEventSynchronize(b));
-        QH_CK(h, cudaEventElapsedTime(&ms, a, b));
+        QH_CK(h, cudaEventElapsedTime(ms, a, b));
+        return QHFPE_OK;
+    };
+    float best = 1e30f, ms = 0.f;
+    int best_tq = 1, best_form = 0;
+    // the kernel form: the q-window kernel (fixed tile) where it applies, against the general kernel
+    if (P.mixed && !P.tc && fused_window_applies(P.g, QHFPE_TERM_ALL, false)) {
+        qhfpe_status r = time_one(1, 0, &ms);
+        if (r != QHFPE_OK) return r;
+        best = ms;
+        best_tq = fused_window_rows(P.g.S);
+        best_form = 1;
+    }
+    // tile heights of the general kernel, between the powers of two as well: the block count (tiles x
+    // elements x replicas) against the blocks resident at once decides how full the last wave is
+    static const int cand[] = {1, 2, 3, 4, 5, 6, 8, 12, 16};
+    for (int tq : cand) {
+        if (tq > tmax) break;
+        qhfpe_status r = time_one(0, tq, &ms);
+        if (r != QHFPE_OK) return r;
         if (ms < best) {
             best = ms;
             best_tq = tq;
+            best_form = 0;
         }
     }
     cudaEventDestroy(a);
     cudaEventDestroy(b);
     P.tq = best_tq;
+    P.form = best_form;
     return QHFPE_OK;
 }
 
@@ -742,6 +842,80 @@ __global__ void set_sink_kernel(TraceSink *s, double *base, long stride, long co
     s->base = base;
     s->stride = stride;
     s->counter = counter;
+}
+
+// Persistent propagation (qhfpe_set_persistent) covers the fused shapes with the shared-memory FFT
+// potential, linear closures without the learned slot and the Condon trace.
+bool persistent_ok(const qhfpe *h, const Prop &P)
+{
+    const Model &M = *P.m;
+    return h->persistent && M.fused && !P.tc && M.closure_slot < 0 && !M.noncondon && !h->timing.enabled;
+}
+
+template <typename T>
+qhfpe_status persistent_desc(qhfpe *h, Prop &P)
+{
+    if (P.pdesc) return QHFPE_OK;
+    const Model &M = *P.m;
+    const int esize = sizeof(T);
+    // the general stage kernel's tile: the autotuned one when the general form won, else the default
+    int tq = P.form == 0 && P.tq > 0 ? P.tq : fused_rows_per_tile(P.g.np, P.g.S, esize);
+    tq = std::min(std::min(tq, fused_max_rows(P.g.np, P.g.S, esize)), P.g.nq);
+    MultiMember<T> x;
+    std::memset(&x, 0, sizeof(x));
+    x.g = P.g;
+    x.elems = M.elems;
+    if constexpr (sizeof(T) == 4) x.tab = M.f32();
+    else x.tab = M.f64();
+    x.sc[0] = stage_scalars<T>(P.g, 0.0);
+    for (int k = 1; k <= 4; ++k) x.sc[k] = stage_scalars<T>(P.g, P.dt / k);
+    x.dt = P.dt;
+    x.y = (T *)P.y;
+    x.vA = (T *)P.vA;
+    x.vB = (T *)P.vB;
+    x.y0 = P.mixed ? P.y0 : nullptr;
+    x.block0 = 0;
+    QH_CK(h, cudaMalloc(&P.pdesc, sizeof(x)));
+    QH_CK(h, cudaMemcpy(P.pdesc, &x, sizeof(x), cudaMemcpyHostToDevice));
+    QH_CK(h, cudaMalloc((void **)&P.pbar, 4 * sizeof(unsigned)));
+    P.pdesc_tq = tq;
+    return QHFPE_OK;
+}
+
+qhfpe_status run_persistent(qhfpe *h, Prop &P, long n_steps, double *trace_dev, long stride)
+{
+    cudaStream_t st = h->stream;
+    qhfpe_status r = P.mixed ? persistent_desc<float>(h, P) : persistent_desc<double>(h, P);
+    if (r != QHFPE_OK) return r;
+    const long n_items = fused_blocks(P.g, P.pdesc_tq);
+    const int nc = trace_chunks(P.g.n_rep, P.g.blk);
+    const unsigned long long limit = 2000000000ull;  // 2 s per barrier wait
+    for (long done = 0; done < n_steps;) {
+        const int len = (int)std::min<long>(n_steps - done, 1 << 20);
+        QH_CK(h, cudaMemsetAsync(P.pbar, 0, 4 * sizeof(unsigned), st));
+        int *err = reinterpret_cast<int *>(P.pbar + 2);
+        const double *ts = P.mixed ? P.y0 : (const double *)P.y;
+        const size_t trs = P.mixed ? P.g.tier0_rep_stride : P.g.rep_stride;
+        cudaError_t e;
+        if (P.mixed)
+            e = launch_persistent<float, true>(P.g.np, P.g.S, (const MultiMember<float> *)P.pdesc, n_items, P.pdesc_tq,
+                                               len, ts, trs, P.m->mu, P.partial, nc, trace_dev, stride, 1 + done,
+                                               P.pbar, err, limit, st);
+        else
+            e = launch_persistent<double, false>(P.g.np, P.g.S, (const MultiMember<double> *)P.pdesc, n_items,
+                                                 P.pdesc_tq, len, ts, trs, P.m->mu, P.partial, nc, trace_dev, stride,
+                                                 1 + done, P.pbar, err, limit, st);
+        QH_CK(h, e);
+        int bad = 0;
+        QH_CK(h, cudaMemcpyAsync(&bad, err, sizeof(int), cudaMemcpyDeviceToHost, st));
+        QH_CK(h, cudaStreamSynchronize(st));
+        if (bad) {
+            h->sticky = true;
+            return h->fail(QHFPE_ETIMEOUT, "persistent propagation: a grid barrier wait gave up");
+        }
+        done += len;
+    }
+    return QHFPE_OK;
 }
 
 qhfpe_status run_steps(qhfpe *h, Prop &P, long n_steps, double *trace_dev, long stride)
@@ -758,6 +932,7 @@ qhfpe_status run_steps(qhfpe *h, Prop &P, long n_steps, double *trace_dev, long 
         if (P.mixed) QH_CK(h, launch_trace<double>(P.g, P.y0, P.g.tier0_rep_stride, P.m->mu, P.sink, 1, P.partial, st, P.m->trace_mu_q()));
         else QH_CK(h, launch_trace<double>(P.g, (const double *)P.y, P.g.rep_stride, P.m->mu, P.sink, 1, P.partial, st, P.m->trace_mu_q()));
     }
+    if (n_steps > 0 && persistent_ok(h, P)) return run_persistent(h, P, n_steps, trace_dev, stride);
     if (h->timing.enabled) {
         for (long s = 0; s < n_steps; ++s) {
             qhfpe_status r = step_dispatch(h, P, record);
@@ -949,8 +1124,12 @@ qhfpe_status qhfpe_create(const qhfpe_params *params, void *stream, qhfpe_t **ou
     if (p.depth < 0) return bad("depth must be >= 0");
     if (p.closure == QHFPE_TERMINATOR && p.n_matsubara != 0) return bad("the terminator closure needs n_matsubara = 0");
     if (p.closure == QHFPE_LEARNED && p.n_matsubara != 0) return bad("the learned closure needs n_matsubara = 0");
-    if (p.closure != QHFPE_TRUNCATE && p.closure != QHFPE_TERMINATOR && p.closure != QHFPE_LEARNED)
+    if (p.closure != QHFPE_TRUNCATE && p.closure != QHFPE_TERMINATOR && p.closure != QHFPE_LEARNED &&
+        p.closure != QHFPE_LEARNED_STATE)
         return bad("unknown closure");
+    if (p.closure == QHFPE_LEARNED_STATE &&
+        (p.n_matsubara != 0 || p.precision != QHFPE_FP64 || p.n_states > 2 || !fused_supported(p.np, p.n_states)))
+        return bad("the state-input closure needs n_matsubara = 0, QHFPE_FP64, n_states <= 2 and np in {32, 64, 128, 256}");
     if (p.precision != QHFPE_FP64 && p.precision != QHFPE_MIXED && p.precision != QHFPE_MIXED_BF16X3)
         return bad("unknown precision");
     if (p.precision == QHFPE_MIXED_BF16X3 && !tc_supported(p.np, p.n_states)) {
@@ -958,6 +1137,13 @@ qhfpe_status qhfpe_create(const qhfpe_params *params, void *stream, qhfpe_t **ou
         return QHFPE_EUNSUPPORTED;
     }
     if (p.n_replicas < 1) return bad("n_replicas must be >= 1");
+    if (!std::isfinite(p.v_c2)) return bad("v_c2 must be finite");
+    if (p.v_c2 != 0.0 && p.closure != QHFPE_TRUNCATE)
+        return bad("a nonlinear coupling (v_c2 != 0) needs closure = QHFPE_TRUNCATE");
+    if (p.v_c2 != 0.0 && !fused_supported(p.np, p.n_states)) {
+        create_err = "a nonlinear coupling (v_c2 != 0) needs np in {32, 64, 128, 256} and n_states <= 3";
+        return QHFPE_EUNSUPPORTED;
+    }
     if (!(p.beta > 0.0) || !(p.gamma > 0.0) || !(p.eta >= 0.0)) return bad("bath parameters out of range");
     if (!p.high_temperature && std::fabs(std::sin(p.beta * p.gamma / 2.0)) < 1e-12)
         return bad("beta*gamma/2 is a multiple of pi (cot diverges)");
@@ -1453,7 +1639,10 @@ qhfpe_status equilibrium_start(qhfpe_t *h, std::unique_ptr<Prop> &GP)
             for (int t = 0; t <= np; ++t) U00[(size_t)i * (np + 1) + t] = h->U[(size_t)i * (np + 1) + t];
         const double zero = 0.0;
         h->ground.reset(new Model());
-        r = build_model(h, *h->ground, 1, U00.data(), &zero);
+        // the state-input closure's network is for n_states pairs: the ground problem is closed by the
+        // Eq. (GMFP) terminator
+        r = build_model(h, *h->ground, 1, U00.data(), &zero,
+                        p.closure == QHFPE_LEARNED_STATE ? (int)QHFPE_TERMINATOR : -1);
         if (r != QHFPE_OK) return r;
     }
     Model &G = *h->ground;
@@ -1793,6 +1982,44 @@ qhfpe_status qhfpe_tile_rows(const qhfpe_t *h, int *rows)
     return QHFPE_OK;
 }
 
+qhfpe_status qhfpe_set_persistent(qhfpe_t *h, int on)
+{
+    qhfpe_status r = check_handle(h);
+    if (r != QHFPE_OK) return r;
+    h->persistent = on != 0;
+    return QHFPE_OK;
+}
+
+qhfpe_status qhfpe_barrier_selftest(qhfpe_t *h, int withhold, int limit_ms)
+{
+    qhfpe_status r = check_handle(h);
+    if (r != QHFPE_OK) return r;
+    if (limit_ms < 1 || limit_ms > 10000) return h->fail(QHFPE_EINVAL, "barrier_selftest: limit_ms must be in [1, 10000]");
+    unsigned *buf = nullptr;
+    QH_CK(h, cudaMalloc((void **)&buf, 4 * sizeof(unsigned)));
+    cudaError_t e = cudaMemsetAsync(buf, 0, 4 * sizeof(unsigned), h->stream);
+    if (e == cudaSuccess)
+        e = launch_barrier_selftest(buf, reinterpret_cast<int *>(buf + 2), (unsigned long long)limit_ms * 1000000ull,
+                                    withhold != 0, h->stream);
+    int bad = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&bad, buf + 2, sizeof(int), cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    cudaFree(buf);
+    QH_CK(h, e);
+    if (bad) return h->fail(QHFPE_ETIMEOUT, "barrier_selftest: the grid barrier wait gave up (a block never arrived)");
+    return QHFPE_OK;
+}
+
+qhfpe_status qhfpe_stage_form(const qhfpe_t *h, int *form)
+{
+    if (!h || !form) return QHFPE_EINVAL;
+    const Prop &P = *h->main;
+    if (!P.tq) *form = -1;
+    else if (P.form >= 0) *form = P.form;
+    else *form = (P.mixed && !P.tc && fused_window_applies(P.g, QHFPE_TERM_ALL, false)) ? 1 : 0;  // pinned tile
+    return QHFPE_OK;
+}
+
 qhfpe_status qhfpe_kernel_timing(qhfpe_t *h, int enable)
 {
     qhfpe_status r = check_handle(h);
@@ -1858,6 +2085,56 @@ qhfpe_status qhfpe_closure_load(qhfpe_t *h, const float *weights, size_t n)
     return QHFPE_OK;
 }
 
+size_t qhfpe_closure_state_n_weights(int n_states)
+{
+    return (n_states >= 1 && n_states <= 2) ? closure_state_n_weights(n_states) : 0;
+}
+
+qhfpe_status qhfpe_closure_state_load(qhfpe_t *h, const float *weights, size_t n)
+{
+    qhfpe_status r = check_handle(h);
+    if (r != QHFPE_OK) return r;
+    if (h->p.closure != QHFPE_LEARNED_STATE)
+        return h->fail(QHFPE_EINVAL, "closure_state_load: the handle was not created with QHFPE_LEARNED_STATE");
+    if (!weights || n != closure_state_n_weights(h->p.n_states))
+        return h->fail(QHFPE_EINVAL, "closure_state_load: expected qhfpe_closure_state_n_weights(n_states) floats");
+    for (size_t i = 0; i < n; ++i)
+        if (!std::isfinite(weights[i])) return h->fail(QHFPE_ENUMERIC, "closure_state_load: non-finite weight");
+    for (size_t i = n - 3; i < n; ++i)
+        if (!(weights[i] > 0.f)) return h->fail(QHFPE_EINVAL, "closure_state_load: the three scales must be positive");
+    if (!h->state_w) QH_CK(h, cudaMalloc((void **)&h->state_w, n * sizeof(float)));
+    QH_CK(h, cudaMemcpyAsync(h->state_w, weights, n * sizeof(float), cudaMemcpyHostToDevice, h->stream));
+    QH_CK(h, cudaStreamSynchronize(h->stream));
+    for (auto &kv : h->batches) kv.second->drop_graphs();
+    h->main->drop_graphs();
+    return QHFPE_OK;
+}
+
+qhfpe_status qhfpe_closure_state_collect(qhfpe_t *h, int target_tier, float *X_dev, float *Y_dev, long offset,
+                                         long capacity, long *count_out)
+{
+    qhfpe_status r = check_handle(h);
+    if (r != QHFPE_OK) return r;
+    const Model &M = *h->model;
+    Prop &P = *h->main;
+    if (h->p.n_matsubara != 0 || h->p.precision != QHFPE_FP64 || h->p.n_states > 2)
+        return h->fail(QHFPE_EINVAL, "closure_state_collect: needs n_matsubara = 0, QHFPE_FP64 and n_states <= 2");
+    if (target_tier < 1 || target_tier > h->p.depth || !X_dev || !Y_dev || offset < 0 || capacity < offset)
+        return h->fail(QHFPE_EINVAL, "closure_state_collect: invalid argument");
+    // chain: the element of tier t is the one with n_0 = t
+    auto elem_of = [&](int t) -> int {
+        for (int e = 0; e < M.n_elem; ++e)
+            if (M.hier[e][0] == t) return e;
+        return -1;
+    };
+    const int et = elem_of(target_tier), et1 = elem_of(target_tier - 1), et2 = target_tier >= 2 ? elem_of(target_tier - 2) : -1;
+    QH_CK(h, launch_closure_state_collect<double>(P.g, (const double *)P.y, et, et1, et2, h->p.eta, X_dev, Y_dev, offset,
+                                                  capacity, h->stream));
+    QH_CK(h, cudaStreamSynchronize(h->stream));
+    if (count_out) *count_out = std::min<long>((long)P.g.n_rep * (long)P.g.blk, capacity - offset);
+    return QHFPE_OK;
+}
+
 qhfpe_status qhfpe_closure_coefficients(const qhfpe_t *h, double *out)
 {
     if (!h || !out) return QHFPE_EINVAL;
@@ -1881,6 +2158,9 @@ struct qhfpe_batch {
     long blocks = 0;
     void *desc = nullptr;  // device MultiMember<float or double>[n]
     cudaGraphExec_t graphs[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};  // [chunk][trace]
+    void *pdesc = nullptr;      // persistent propagation: this propagator as a one-member batch
+    int pdesc_tq = 0;           // its tile height
+    unsigned *pbar = nullptr;   // barrier words (count, generation) and the give-up flag
     ~qhfpe_batch()
     {
         for (auto &a : graphs)

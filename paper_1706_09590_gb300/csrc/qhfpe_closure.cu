@@ -224,6 +224,16 @@ __global__ void adam_kernel(size_t n, float *w, const float *__restrict__ g, flo
 // ---------------------------------------------------------------------------------------------------
 __device__ __forceinline__ float rnd(float x, int bf16) { return bf16 ? __bfloat162float(__float2bfloat16_rn(x)) : x; }
 
+// The network's inputs at grid point (i, l): x = (q_i / 8, p_l / 8, ln eta); the one definition used by
+// inference here and by the training inputs (qhfpe_closure_inputs).
+__host__ __device__ __forceinline__ void closure_features(double q_min, double dq, double p_min, double dp, double log_eta,
+                                                          int i, int l, double *x)
+{
+    x[0] = (q_min + i * dq) / 8.0;
+    x[1] = (p_min + l * dp) / 8.0;
+    x[2] = log_eta;
+}
+
 constexpr int IPTS = 16;  // points per inference block
 
 __global__ void __launch_bounds__(256) infer_kernel(int n_points, int np, double q_min, double dq, double p_min,
@@ -240,8 +250,9 @@ __global__ void __launch_bounds__(256) infer_kernel(int n_points, int np, double
         float v = 0.f;
         if (x < n_points) {
             const int i = x / np, l = x % np;
-            const float in[3] = {rnd((float)((q_min + i * dq) / 8.0), bf16), rnd((float)((p_min + l * dp) / 8.0), bf16),
-                                 rnd((float)log_eta, bf16)};
+            double xf[3];
+            closure_features(q_min, dq, p_min, dp, log_eta, i, l, xf);
+            const float in[3] = {rnd((float)xf[0], bf16), rnd((float)xf[1], bf16), rnd((float)xf[2], bf16)};
             v = w[OB1 + u];
             for (int k = 0; k < NIN; ++k) v += rnd(w[OW1 + (size_t)u * NIN + k], bf16) * in[k];
             v = rnd(tanhf(v), bf16);
@@ -430,6 +441,19 @@ cudaError_t launch_closure_infer(const GridInfo &g, double eta, const float *w_d
 }
 
 // ---- C ABI ----------------------------------------------------------------------------------------
+extern "C" qhfpe_status qhfpe_closure_inputs(int nq, int np, double q_min, double q_max, double p_min, double p_max,
+                                             double eta, double *X)
+{
+    if (nq < 1 || np < 1 || !(q_max > q_min) || !(p_max > p_min) || !(eta > 0.0) || !X) {
+        qh_set_free_error("closure_inputs: invalid argument");
+        return QHFPE_EINVAL;
+    }
+    const double dq = (q_max - q_min) / nq, dp = (p_max - p_min) / np, le = std::log(eta);
+    for (int i = 0; i < nq; ++i)
+        for (int l = 0; l < np; ++l) closure_features(q_min, dq, p_min, dp, le, i, l, X + ((size_t)i * np + l) * NIN);
+    return QHFPE_OK;
+}
+
 extern "C" qhfpe_status qhfpe_closure_loss_grad(const float *w, const double *X, const double *stats, int n_points,
                                                 double ridge, double *loss, float *grad)
 {
@@ -509,5 +533,389 @@ extern "C" qhfpe_status qhfpe_closure_train(float *w, const double *X, const dou
         qh_set_free_error(std::string("closure_train: ") + cudaGetErrorString(e));
         return QHFPE_ECUDA;
     }
+    return QHFPE_OK;
+}
+
+// ===================================================================================================
+// State-input closure: the network reads the state itself.  For the deepest element n (one Drude
+// mode, a chain), at grid point (q_i, p_l) the inputs are (q_i / 8, p_l / 8, ln eta) followed by the
+// 3 x 3 patches (q_{i+a}, p_{l+b}), a, b in {-1, 0, 1}, of tiers N and N-1 for every electronic pair
+// (re, im) -- 36 S^2 + 3 values -- and the outputs are W^(N+1)_jk(q_i, p_l) for every pair (re, im),
+// 2 S^2 values, written to the closure slot that the deepest element's tier-up term reads.  The closed
+// hierarchy is then nonlinear in the state (no terminator is added: the network predicts the whole
+// element).  Weights (float): W1[256][n_in], b1, W2[256][256], b2, W3[256][256], b3, W4[n_out][256],
+// b4, then three scales: tier-N inputs, tier-(N-1) inputs and outputs (the network works on the
+// values divided by them).
+// ===================================================================================================
+namespace {
+
+__host__ __device__ constexpr int sc_nin(int S) { return 36 * S * S + 3; }
+__host__ __device__ constexpr int sc_nout(int S) { return 2 * S * S; }
+__host__ __device__ constexpr size_t sc_nweights(int S)
+{
+    return (size_t)NH * sc_nin(S) + NH + 2 * ((size_t)NH * NH + NH) + (size_t)sc_nout(S) * NH + sc_nout(S) + 3;
+}
+
+constexpr int SPTS = 8;  // points per inference block
+
+// inputs of one point into x (length sc_nin(S)), unscaled; tier elements e_n, e_n1 (-1: zeros)
+template <typename T>
+__device__ __forceinline__ void sc_gather(const GridInfo &g, const T *rep_state, int e_n, int e_n1, int i, int l,
+                                          double log_eta, float *x, float sN, float sN1)
+{
+    const int S2 = g.S * g.S, nq = g.nq, np = g.np;
+    double f[3];
+    closure_features(g.q_min, g.dq, g.p_min, g.dp, log_eta, i, l, f);
+    x[0] = (float)f[0];
+    x[1] = (float)f[1];
+    x[2] = (float)f[2];
+    int c = 3;
+    for (int tier = 0; tier < 2; ++tier) {
+        const int e = tier == 0 ? e_n : e_n1;
+        const float s = tier == 0 ? sN : sN1;
+        for (int pr = 0; pr < S2; ++pr)
+            for (int a = -1; a <= 1; ++a)
+                for (int b = -1; b <= 1; ++b) {
+                    int ii = i + a;
+                    bool ok = e >= 0 && ii >= 0 && ii < nq;
+                    if (e >= 0 && !ok && g.periodic_q) {
+                        ii = (ii + nq) % nq;
+                        ok = true;
+                    }
+                    const int lb = (l + b + np) % np;
+                    float re = 0.f, im = 0.f;
+                    if (ok) {
+                        const T *blk = rep_state + (size_t)e * g.elem_stride + (size_t)pr * 2 * g.blk;
+                        re = (float)blk[(size_t)ii * np + lb];
+                        im = (float)blk[g.blk + (size_t)ii * np + lb];
+                    }
+                    x[c++] = re / s;
+                    x[c++] = im / s;
+                }
+    }
+}
+
+// One block evaluates SPTS points of one replica: bf16 weights and activations, FP32 accumulation.
+template <typename T, int S>
+__global__ void __launch_bounds__(256) state_closure_kernel(GridInfo g, T *state, int e_n, int e_n1, int e_slot,
+                                                            const float *__restrict__ w, double log_eta, int rep0)
+{
+    constexpr int NI = sc_nin(S), NO = sc_nout(S), S2 = S * S;
+    __shared__ float xin[SPTS][NI];
+    __shared__ float h[2][SPTS][NH + 1];
+    const size_t OW1s = 0, OB1s = OW1s + (size_t)NH * NI, OW2s = OB1s + NH, OB2s = OW2s + (size_t)NH * NH,
+                 OW3s = OB2s + NH, OB3s = OW3s + (size_t)NH * NH, OW4s = OB3s + NH, OB4s = OW4s + (size_t)NO * NH,
+                 OSC = OB4s + NO;
+    const float sN = w[OSC], sN1 = w[OSC + 1], sO = w[OSC + 2];
+    const int rep = rep0 + blockIdx.y;
+    T *rs = state + (size_t)rep * g.rep_stride;
+    const int n_pts = (int)g.blk;
+    const int p0 = blockIdx.x * SPTS;
+    for (int pt = threadIdx.x; pt < SPTS; pt += blockDim.x) {
+        const int x = p0 + pt;
+        if (x < n_pts) {
+            sc_gather<T>(g, rs, e_n, e_n1, x / g.np, x % g.np, log_eta, xin[pt], sN, sN1);
+            for (int k = 0; k < NI; ++k) xin[pt][k] = rnd(xin[pt][k], 1);
+        } else {
+            for (int k = 0; k < NI; ++k) xin[pt][k] = 0.f;
+        }
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < SPTS * NH; t += blockDim.x) {
+        const int pt = t / NH, u = t % NH;
+        float v = w[OB1s + u];
+        const float *wr = w + OW1s + (size_t)u * NI;
+        for (int k = 0; k < NI; ++k) v += rnd(wr[k], 1) * xin[pt][k];
+        h[0][pt][u] = rnd(tanhf(v), 1);
+    }
+    __syncthreads();
+    int cur = 0;
+    for (int layer = 0; layer < 2; ++layer) {
+        const size_t OW = layer == 0 ? OW2s : OW3s, OB = layer == 0 ? OB2s : OB3s;
+        for (int t = threadIdx.x; t < SPTS * NH; t += blockDim.x) {
+            const int pt = t / NH, u = t % NH;
+            float v = w[OB + u];
+            const float *wr = w + OW + (size_t)u * NH;
+            for (int k = 0; k < NH; ++k) v += rnd(wr[k], 1) * h[cur][pt][k];
+            h[cur ^ 1][pt][u] = rnd(tanhf(v), 1);
+        }
+        __syncthreads();
+        cur ^= 1;
+    }
+    for (int t = threadIdx.x; t < SPTS * NO; t += blockDim.x) {
+        const int pt = t / NO, o = t % NO;
+        const int x = p0 + pt;
+        if (x >= n_pts) continue;
+        float v = w[OB4s + o];
+        const float *wr = w + OW4s + (size_t)o * NH;
+        for (int k = 0; k < NH; ++k) v += rnd(wr[k], 1) * h[cur][pt][k];
+        const int pr = o / 2, part = o % 2;
+        if (pr < S2) rs[(size_t)e_slot * g.elem_stride + (size_t)pr * 2 * g.blk + (size_t)part * g.blk + x] = (T)(v * sO);
+    }
+}
+
+// training samples of target tier t from every replica and grid point: X [n][n_in] unscaled inputs of
+// tiers t-1, t-2, Y [n][n_out] the tier-t values
+template <typename T, int S>
+__global__ void state_collect_kernel(GridInfo g, const T *state, int e_t, int e_t1, int e_t2, double log_eta, float *X,
+                                     float *Y, long offset, long capacity)
+{
+    constexpr int NI = sc_nin(S), NO = sc_nout(S), S2 = S * S;
+    const long total = (long)g.n_rep * g.blk;
+    for (long idx = blockIdx.x * (long)blockDim.x + threadIdx.x; idx < total; idx += (long)gridDim.x * blockDim.x) {
+        const long o = offset + idx;
+        if (o >= capacity) return;
+        const int rep = (int)(idx / g.blk);
+        const int x = (int)(idx % g.blk);
+        const T *rs = state + (size_t)rep * g.rep_stride;
+        sc_gather<T>(g, rs, e_t1, e_t2, x / g.np, x % g.np, log_eta, X + (size_t)o * NI, 1.f, 1.f);
+        for (int pr = 0; pr < S2; ++pr) {
+            const T *blk = rs + (size_t)e_t * g.elem_stride + (size_t)pr * 2 * g.blk;
+            Y[(size_t)o * NO + 2 * pr] = (float)blk[x];
+            Y[(size_t)o * NO + 2 * pr + 1] = (float)blk[g.blk + x];
+        }
+    }
+}
+
+// per point: MSE loss contribution and dOut = 2 (out - y) / (B n_out)
+__global__ void mse_loss_kernel(int B, int n_out, const float *__restrict__ out, const float *__restrict__ Y,
+                                const int *__restrict__ idx, float inv, float *dOut, double *loss)
+{
+    __shared__ double red[256];
+    double part = 0.0;
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < B * n_out; t += gridDim.x * blockDim.x) {
+        const int b = t / n_out, o = t % n_out;
+        const float d = out[t] - Y[(size_t)idx[b] * n_out + o];
+        dOut[t] = 2.f * d * inv;
+        part += (double)d * d;
+    }
+    red[threadIdx.x] = part;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if ((int)threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) atomicAdd(loss, red[0] * inv);
+}
+
+__global__ void gather_rows_kernel(int B, int n, const float *__restrict__ X, const int *__restrict__ idx, float *out)
+{
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < B * n; t += gridDim.x * blockDim.x)
+        out[t] = X[(size_t)idx[t / n] * n + t % n];
+}
+
+// the generic MLP (n_in -> 256 -> 256 -> 256 -> n_out, tanh, linear output) with the MSE loss
+struct MLP {
+    int n_in = 0, n_out = 0, B = 0;
+    size_t ow1, ob1, ow2, ob2, ow3, ob3, ow4, ob4, nw;
+    float *w = nullptr, *g = nullptr, *m = nullptr, *v = nullptr, *X = nullptr, *Y = nullptr, *Xb = nullptr,
+          *H1 = nullptr, *H2 = nullptr, *H3 = nullptr, *O = nullptr, *dO = nullptr, *d3 = nullptr, *d2 = nullptr,
+          *d1 = nullptr;
+    double *loss = nullptr;
+    int *idx = nullptr;
+    void layout(int ni, int no)
+    {
+        n_in = ni;
+        n_out = no;
+        ow1 = 0;
+        ob1 = ow1 + (size_t)NH * ni;
+        ow2 = ob1 + NH;
+        ob2 = ow2 + (size_t)NH * NH;
+        ow3 = ob2 + NH;
+        ob3 = ow3 + (size_t)NH * NH;
+        ow4 = ob3 + NH;
+        ob4 = ow4 + (size_t)no * NH;
+        nw = ob4 + no;
+    }
+    ~MLP()
+    {
+        for (void *p : {(void *)w, (void *)g, (void *)m, (void *)v, (void *)X, (void *)Y, (void *)Xb, (void *)H1,
+                        (void *)H2, (void *)H3, (void *)O, (void *)dO, (void *)d3, (void *)d2, (void *)d1,
+                        (void *)loss, (void *)idx})
+            if (p) cudaFree(p);
+    }
+};
+
+cudaError_t mlp_setup(MLP &T, const float *w, const float *X, const float *Y, int n, int B, cudaStream_t st)
+{
+    cudaError_t e;
+    T.B = B;
+    auto al = [&](float **p, size_t cnt) { return cudaMalloc((void **)p, cnt * sizeof(float)); };
+    if ((e = al(&T.w, T.nw)) || (e = al(&T.g, T.nw)) || (e = al(&T.m, T.nw)) || (e = al(&T.v, T.nw)) ||
+        (e = al(&T.X, (size_t)n * T.n_in)) || (e = al(&T.Y, (size_t)n * T.n_out)) || (e = al(&T.Xb, (size_t)B * T.n_in)) ||
+        (e = al(&T.H1, (size_t)B * NH)) || (e = al(&T.H2, (size_t)B * NH)) || (e = al(&T.H3, (size_t)B * NH)) ||
+        (e = al(&T.O, (size_t)B * T.n_out)) || (e = al(&T.dO, (size_t)B * T.n_out)) || (e = al(&T.d3, (size_t)B * NH)) ||
+        (e = al(&T.d2, (size_t)B * NH)) || (e = al(&T.d1, (size_t)B * NH)) ||
+        (e = cudaMalloc((void **)&T.loss, 8)) || (e = cudaMalloc((void **)&T.idx, (size_t)std::max(B, n) * 4)))
+        return e;
+    if ((e = cudaMemcpyAsync(T.w, w, T.nw * 4, cudaMemcpyHostToDevice, st))) return e;
+    if ((e = cudaMemcpyAsync(T.X, X, (size_t)n * T.n_in * 4, cudaMemcpyHostToDevice, st))) return e;
+    if ((e = cudaMemcpyAsync(T.Y, Y, (size_t)n * T.n_out * 4, cudaMemcpyHostToDevice, st))) return e;
+    if ((e = cudaMemsetAsync(T.m, 0, T.nw * 4, st))) return e;
+    if ((e = cudaMemsetAsync(T.v, 0, T.nw * 4, st))) return e;
+    return cudaStreamSynchronize(st);
+}
+
+// forward, MSE loss (mean over the B points and n_out outputs) and backward for idx[0..B)
+cudaError_t mlp_forward_backward(MLP &T, int B, cudaStream_t st)
+{
+    cudaError_t e;
+    const float *w = T.w;
+    float *g = T.g;
+    const int NI = T.n_in, NO = T.n_out;
+    gather_rows_kernel<<<gsz((size_t)B * NI), 256, 0, st>>>(B, NI, T.X, T.idx, T.Xb);
+    if ((e = gemm<false, true>(B, NH, NI, T.Xb, NI, w + T.ow1, NI, w + T.ob1, T.H1, NH, 1, st))) return e;
+    if ((e = gemm<false, true>(B, NH, NH, T.H1, NH, w + T.ow2, NH, w + T.ob2, T.H2, NH, 1, st))) return e;
+    if ((e = gemm<false, true>(B, NH, NH, T.H2, NH, w + T.ow3, NH, w + T.ob3, T.H3, NH, 1, st))) return e;
+    if ((e = gemm<false, true>(B, NO, NH, T.H3, NH, w + T.ow4, NH, w + T.ob4, T.O, NO, 0, st))) return e;
+    if ((e = cudaMemsetAsync(T.loss, 0, sizeof(double), st))) return e;
+    mse_loss_kernel<<<gsz((size_t)B * NO), 256, 0, st>>>(B, NO, T.O, T.Y, T.idx, 1.f / ((float)B * NO), T.dO, T.loss);
+    if ((e = gemm<true, false>(NO, NH, B, T.dO, NO, T.H3, NH, nullptr, g + T.ow4, NH, 0, st))) return e;
+    colsum_kernel<<<1, 32, 0, st>>>(B, NO, T.dO, g + T.ob4);
+    if ((e = gemm<false, false>(B, NH, NO, T.dO, NO, w + T.ow4, NH, nullptr, T.d3, NH, 0, st))) return e;
+    tanh_back_kernel<<<gsz((size_t)B * NH), 256, 0, st>>>((size_t)B * NH, T.H3, T.d3);
+    if ((e = gemm<true, false>(NH, NH, B, T.d3, NH, T.H2, NH, nullptr, g + T.ow3, NH, 0, st))) return e;
+    colsum_kernel<<<(NH + 127) / 128, 128, 0, st>>>(B, NH, T.d3, g + T.ob3);
+    if ((e = gemm<false, false>(B, NH, NH, T.d3, NH, w + T.ow3, NH, nullptr, T.d2, NH, 0, st))) return e;
+    tanh_back_kernel<<<gsz((size_t)B * NH), 256, 0, st>>>((size_t)B * NH, T.H2, T.d2);
+    if ((e = gemm<true, false>(NH, NH, B, T.d2, NH, T.H1, NH, nullptr, g + T.ow2, NH, 0, st))) return e;
+    colsum_kernel<<<(NH + 127) / 128, 128, 0, st>>>(B, NH, T.d2, g + T.ob2);
+    if ((e = gemm<false, false>(B, NH, NH, T.d2, NH, w + T.ow2, NH, nullptr, T.d1, NH, 0, st))) return e;
+    tanh_back_kernel<<<gsz((size_t)B * NH), 256, 0, st>>>((size_t)B * NH, T.H1, T.d1);
+    if ((e = gemm<true, false>(NH, NI, B, T.d1, NH, T.Xb, NI, nullptr, g + T.ow1, NI, 0, st))) return e;
+    colsum_kernel<<<(NH + 127) / 128, 128, 0, st>>>(B, NH, T.d1, g + T.ob1);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+size_t closure_state_n_weights(int S) { return sc_nweights(S); }
+
+template <typename T>
+cudaError_t launch_closure_state_fill(const GridInfo &g, T *state, int e_n, int e_n1, int e_slot, const float *w,
+                                      double eta, int rep0, int n_rep, cudaStream_t st)
+{
+    dim3 grid((unsigned)((g.blk + SPTS - 1) / SPTS), (unsigned)n_rep);
+    const double le = std::log(eta);
+    switch (g.S) {
+    case 1: state_closure_kernel<T, 1><<<grid, 256, 0, st>>>(g, state, e_n, e_n1, e_slot, w, le, rep0); break;
+    case 2: state_closure_kernel<T, 2><<<grid, 256, 0, st>>>(g, state, e_n, e_n1, e_slot, w, le, rep0); break;
+    default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+template cudaError_t launch_closure_state_fill<double>(const GridInfo &, double *, int, int, int, const float *, double,
+                                                       int, int, cudaStream_t);
+
+template <typename T>
+cudaError_t launch_closure_state_collect(const GridInfo &g, const T *state, int e_t, int e_t1, int e_t2, double eta,
+                                         float *X, float *Y, long offset, long capacity, cudaStream_t st)
+{
+    const long total = (long)g.n_rep * g.blk;
+    const int blocks = (int)std::min<long>((total + 255) / 256, 152 * 16);
+    switch (g.S) {
+    case 1: state_collect_kernel<T, 1><<<blocks, 256, 0, st>>>(g, state, e_t, e_t1, e_t2, std::log(eta), X, Y, offset, capacity); break;
+    case 2: state_collect_kernel<T, 2><<<blocks, 256, 0, st>>>(g, state, e_t, e_t1, e_t2, std::log(eta), X, Y, offset, capacity); break;
+    default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+template cudaError_t launch_closure_state_collect<double>(const GridInfo &, const double *, int, int, int, double,
+                                                          float *, float *, long, long, cudaStream_t);
+
+extern "C" qhfpe_status qhfpe_closure_state_loss_grad(int n_states, const float *w, const float *X, const float *Y,
+                                                      int n_points, double *loss, float *grad)
+{
+    if (n_states < 1 || n_states > 2 || !w || !X || !Y || n_points < 1 || !loss || !grad) {
+        qh_set_free_error("closure_state_loss_grad: invalid argument");
+        return QHFPE_EINVAL;
+    }
+    MLP T;
+    T.layout(sc_nin(n_states), sc_nout(n_states));
+    cudaStream_t st = nullptr;
+    cudaError_t e = mlp_setup(T, w, X, Y, n_points, n_points, st);
+    std::vector<int> idx(n_points);
+    for (int x = 0; x < n_points; ++x) idx[x] = x;
+    if (!e) e = cudaMemcpy(T.idx, idx.data(), (size_t)n_points * 4, cudaMemcpyHostToDevice);
+    if (!e) e = mlp_forward_backward(T, n_points, st);
+    if (!e) e = cudaMemcpy(loss, T.loss, 8, cudaMemcpyDeviceToHost);
+    if (!e) e = cudaMemcpy(grad, T.g, T.nw * 4, cudaMemcpyDeviceToHost);
+    if (e) {
+        qh_set_free_error(std::string("closure_state_loss_grad: ") + cudaGetErrorString(e));
+        return QHFPE_ECUDA;
+    }
+    return QHFPE_OK;
+}
+
+extern "C" qhfpe_status qhfpe_closure_state_train(int n_states, float *w, const float *X, const float *Y, int n_points,
+                                                  int n_iters, int batch, double lr, unsigned seed, double *loss_history)
+{
+    if (n_states < 1 || n_states > 2 || !w || !X || !Y || n_points < 1 || n_iters < 0 || batch < 1 || !(lr > 0.0)) {
+        qh_set_free_error("closure_state_train: invalid argument");
+        return QHFPE_EINVAL;
+    }
+    MLP T;
+    const int NI = sc_nin(n_states), NO = sc_nout(n_states);
+    T.layout(NI, NO);
+    // scales: RMS of the tier-N inputs, of the tier-(N-1) inputs and of the outputs; the network is
+    // trained on the scaled values and the scales travel with the weights
+    const int half = (NI - 3) / 2;
+    double s[3] = {0.0, 0.0, 0.0};
+    for (long x = 0; x < n_points; ++x) {
+        for (int k = 0; k < half; ++k) {
+            s[0] += (double)X[x * NI + 3 + k] * X[x * NI + 3 + k];
+            s[1] += (double)X[x * NI + 3 + half + k] * X[x * NI + 3 + half + k];
+        }
+        for (int o = 0; o < NO; ++o) s[2] += (double)Y[x * NO + o] * Y[x * NO + o];
+    }
+    float sc[3];
+    sc[0] = (float)std::sqrt(s[0] / ((double)n_points * half));
+    sc[1] = (float)std::sqrt(s[1] / ((double)n_points * half));
+    sc[2] = (float)std::sqrt(s[2] / ((double)n_points * NO));
+    for (float &v : sc)
+        if (!(v > 0.f) || !std::isfinite(v)) v = 1.f;
+    std::vector<float> Xs((size_t)n_points * NI), Ys((size_t)n_points * NO);
+    for (long x = 0; x < n_points; ++x) {
+        for (int k = 0; k < NI; ++k)
+            Xs[x * NI + k] = k < 3 ? X[x * NI + k] : X[x * NI + k] / (k < 3 + half ? sc[0] : sc[1]);
+        for (int o = 0; o < NO; ++o) Ys[x * NO + o] = Y[x * NO + o] / sc[2];
+    }
+    const int B = std::min(batch, n_points);
+    cudaStream_t st = nullptr;
+    cudaError_t e = mlp_setup(T, w, Xs.data(), Ys.data(), n_points, B, st);
+    std::mt19937 rng(seed);
+    std::vector<int> perm(n_points);
+    for (int x = 0; x < n_points; ++x) perm[x] = x;
+    size_t pos = n_points;
+    const float b1 = 0.9f, b2 = 0.999f;
+    double c1 = 1.0, c2 = 1.0;
+    for (int it = 0; it < n_iters && !e; ++it) {
+        if (pos + B > (size_t)n_points) {
+            std::shuffle(perm.begin(), perm.end(), rng);
+            pos = 0;
+        }
+        e = cudaMemcpyAsync(T.idx, perm.data() + pos, (size_t)B * 4, cudaMemcpyHostToDevice, st);
+        pos += B;
+        if (!e) e = mlp_forward_backward(T, B, st);
+        c1 *= b1;
+        c2 *= b2;
+        if (!e) {
+            adam_kernel<<<gsz(T.nw), 256, 0, st>>>(T.nw, T.w, T.g, T.m, T.v, (float)lr, b1, b2, 1e-8f, (float)(1.0 - c1),
+                                                   (float)(1.0 - c2));
+            e = cudaGetLastError();
+        }
+        if (!e && loss_history) {
+            e = cudaMemcpyAsync(loss_history + it, T.loss, 8, cudaMemcpyDeviceToHost, st);
+            if (!e) e = cudaStreamSynchronize(st);
+        }
+    }
+    if (!e) e = cudaMemcpy(w, T.w, T.nw * 4, cudaMemcpyDeviceToHost);
+    if (e) {
+        qh_set_free_error(std::string("closure_state_train: ") + cudaGetErrorString(e));
+        return QHFPE_ECUDA;
+    }
+    w[T.nw] = sc[0];
+    w[T.nw + 1] = sc[1];
+    w[T.nw + 2] = sc[2];
     return QHFPE_OK;
 }

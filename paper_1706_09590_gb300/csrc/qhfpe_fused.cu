@@ -108,15 +108,23 @@ bool window_enabled()
     return !(v && std::strcmp(v, "0") == 0);
 }
 
-bool window_applies(const GridInfo &g, int np, int S, int terms, bool have_pg)
+}  // namespace
+
+int fused_window_rows(int S) { return S == 1 ? WinTile<1>::TQ : WinTile<2>::TQ; }
+
+bool fused_window_applies(const GridInfo &g, int terms, bool have_pg)
 {
-    if (np != 128 || S < 1 || S > 2 || have_pg || terms != QHFPE_TERM_ALL || g.max_nb > WIN_MAXNB) return false;
+    const int np = g.np, S = g.S;
+    if (np != 128 || S < 1 || S > 2 || have_pg || terms != QHFPE_TERM_ALL || g.max_nb > WIN_MAXNB || g.c2 != 0.0)
+        return false;
     for (int c = 0; c < np; c += 4) {
         const bool a = (float)(g.p_min + c * g.dp) < 0.0f, b = (float)(g.p_min + (c + 3) * g.dp) < 0.0f;
         if (a != b) return false;
     }
     return window_enabled();
 }
+
+namespace {
 
 template <int S, bool MIXED>
 cudaError_t launch_window_t(const GridInfo &g, const ElemInfo *elems, const FusedTables<float> &tab, const float *v_in,
@@ -145,10 +153,10 @@ cudaError_t launch_window_t(const GridInfo &g, const ElemInfo *elems, const Fuse
 template <typename T, int NP, int S, bool MIXED>
 cudaError_t launch_fused_t(const GridInfo &g, const ElemInfo *elems, const FusedTables<T> &tab, const T *v_in,
                            const T *y, const double *y0, T *v_out, double *y0_out, double h, int mode, int terms,
-                           int rep0, int n_rep, cudaStream_t st, const T *Pg, int tq_req)
+                           int rep0, int n_rep, cudaStream_t st, const T *Pg, int tq_req, int form)
 {
     if constexpr (sizeof(T) == 4 && NP == 128 && S <= 2) {
-        if (window_applies(g, NP, S, terms, Pg != nullptr))
+        if (form != 0 && fused_window_applies(g, terms, Pg != nullptr))
             return launch_window_t<S, MIXED>(g, elems, tab, v_in, y, y0, v_out, y0_out, h, mode, rep0, n_rep, st);
     }
     int tq = tq_req > 0 ? tq_req : fused_rows_per_tile(NP, S, sizeof(T));
@@ -243,9 +251,9 @@ bool fused_supported(int np, int S) { return (np == 32 || np == 64 || np == 128 
 template <typename T, bool MIXED>
 cudaError_t launch_fused(const GridInfo &g, const ElemInfo *elems, const FusedTables<T> &tab, const T *v_in,
                          const T *y, const double *y0, T *v_out, double *y0_out, double h, int mode, int terms,
-                         int rep0, int n_rep, cudaStream_t st, const T *Pg, int tq)
+                         int rep0, int n_rep, cudaStream_t st, const T *Pg, int tq, int form)
 {
-#define QH_CALL(T_, NP_, S_, M_) launch_fused_t<T_, NP_, S_, M_>(g, elems, tab, v_in, y, y0, v_out, y0_out, h, mode, terms, rep0, n_rep, st, Pg, tq)
+#define QH_CALL(T_, NP_, S_, M_) launch_fused_t<T_, NP_, S_, M_>(g, elems, tab, v_in, y, y0, v_out, y0_out, h, mode, terms, rep0, n_rep, st, Pg, tq, form)
     switch (g.np * 8 + g.S) {
     case 32 * 8 + 1: return QH_CALL(T, 32, 1, MIXED);
     case 32 * 8 + 2: return QH_CALL(T, 32, 2, MIXED);
@@ -333,8 +341,8 @@ int fused_fft_frequency(int np, int pos)
     return k;
 }
 
-template cudaError_t launch_fused<float, true>(const GridInfo &, const ElemInfo *, const FusedTables<float> &, const float *, const float *, const double *, float *, double *, double, int, int, int, int, cudaStream_t, const float *, int);
-template cudaError_t launch_fused<double, false>(const GridInfo &, const ElemInfo *, const FusedTables<double> &, const double *, const double *, const double *, double *, double *, double, int, int, int, int, cudaStream_t, const double *, int);
+template cudaError_t launch_fused<float, true>(const GridInfo &, const ElemInfo *, const FusedTables<float> &, const float *, const float *, const double *, float *, double *, double, int, int, int, int, cudaStream_t, const float *, int, int);
+template cudaError_t launch_fused<double, false>(const GridInfo &, const ElemInfo *, const FusedTables<double> &, const double *, const double *, const double *, double *, double *, double, int, int, int, int, cudaStream_t, const double *, int, int);
 template cudaError_t prepare_fused<float, true>(int, int);
 template StageScalars<float> stage_scalars<float>(const GridInfo &, double);
 template StageScalars<double> stage_scalars<double>(const GridInfo &, double);

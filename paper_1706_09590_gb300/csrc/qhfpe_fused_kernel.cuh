@@ -321,10 +321,13 @@ struct FusedOcc {
 // p-diagonal bath terms (f_pp lambda_pp(m) - ngam) / NP (damping, delta-term, terminator d2/dp2, which
 // are circulants along p), and the inverse FFT (sign -, natural order).  Called by all threads of the
 // block after a barrier that makes X complete; ends with the inverse FFT's barrier.
+// c2 != 0 (nonlinear coupling V = q + c2 q^2): the d2/dp2 coefficient of row i is fpp phi(q_i)^2,
+// phi = 1 + 2 c2 q (Phi^2 = phi^2 d2/dp2); q_i = q_min + i dq.
 template <typename T, int NP, int S>
 __device__ __forceinline__ void potential_in_place(typename V2<T>::type *X, const typename V2<T>::type *tw,
                                                    const FusedTables<T> &tab, int nq, int i0, int rows, T fpp,
-                                                   T ngam, const T *s_lpp)
+                                                   T ngam, const T *s_lpp, double c2 = 0.0, double q_min = 0.0,
+                                                   double dq = 0.0)
 {
     using C = typename V2<T>::type;
     constexpr int S2 = S * S;
@@ -342,6 +345,12 @@ __device__ __forceinline__ void potential_in_place(typename V2<T>::type *X, cons
     }
     for (int r = threadIdx.x / (NP / MV); r < rows; r += FTHREADS / (NP / MV)) {
         const int i = i0 + r;
+        if (c2 != 0.0) {  // block-uniform
+            const T ph = (T)(1.0 + 2.0 * c2 * (q_min + i * dq));
+            const T ng_a = ngam / (T)NP;
+#pragma unroll
+            for (int v = 0; v < MV; ++v) cf[v] = fpp * ph * ph * s_lpp[pos0 + v] - ng_a;
+        }
         C rho[S2][MV];
 #pragma unroll
         for (int a = 0; a < S2; ++a)
@@ -394,23 +403,21 @@ __device__ __forceinline__ void potential_in_place(typename V2<T>::type *X, cons
 // ascending), copies the member's description into shared memory and does that member's block of stage
 // k = 4..1 of the Horner form (k = 0: the right-hand side alone into the second stage buffer, for the
 // autotuner).  The other arguments are then taken from the member.
+// The block `bid` of a fused stage launch (see fused_stage_kernel below); also called in a loop by the
+// persistent kernel (a barrier must separate two calls of one block: shared memory is reused).
 template <typename T, int NP, int S, bool MIXED, bool MULTI>
-__global__ void __launch_bounds__(FTHREADS, FusedOcc<T, NP, S>::blocks - (MULTI && FusedOcc<T, NP, S>::blocks > 2 ? 1 : 0))
-fused_stage_kernel(GridInfo g, const ElemInfo *__restrict__ elems, FusedTables<T> tab, StageScalars<T> sc, const T *__restrict__ v_in,
-                   const T *y, const double *y0, T *v_out, double *y0_out, double h, int mode, int terms, int rep0,
-                   int n_rep, int tq, const T *__restrict__ Pg, const MultiMember<T> *__restrict__ mem, int n_mem, int k)
+__device__ __forceinline__ void
+fused_stage_body(unsigned bid, GridInfo g, const ElemInfo *__restrict__ elems, FusedTables<T> tab, StageScalars<T> sc,
+                 const T *__restrict__ v_in, const T *y, const double *y0, T *v_out, double *y0_out, double h, int mode,
+                 int terms, int rep0, int n_rep, int tq, const T *__restrict__ Pg, const MultiMember<T> *__restrict__ mem,
+                 int n_mem, int k)
 {
-    // Programmatic dependent launch: the next stage may start its blocks (prologue only) once every
-    // block of this one has started; it waits below for this grid's completion before touching the
-    // state.  Both are no-ops for a plain launch.
-    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
-    unsigned bid = blockIdx.x;
     if constexpr (MULTI) {
         __shared__ MultiMember<T> M;
         __shared__ int s_m;
         if (threadIdx.x == 0) {
             int m = 0;
-            while (m + 1 < n_mem && mem[m + 1].block0 <= (long)blockIdx.x) ++m;
+            while (m + 1 < n_mem && mem[m + 1].block0 <= (long)bid) ++m;
             s_m = m;
         }
         __syncthreads();
@@ -459,8 +466,11 @@ fused_stage_kernel(GridInfo g, const ElemInfo *__restrict__ elems, FusedTables<T
     const size_t blk = g.blk;
     const size_t ebase = (size_t)rep * g.rep_stride + (size_t)e * g.elem_stride;
 
-    __shared__ long long nb_off[2 * QH_MAX_MODES];
-    __shared__ T nb_wg[2 * QH_MAX_MODES], nb_wa[2 * QH_MAX_MODES];
+    __shared__ long long nb_off[3 * QH_MAX_MODES];
+    __shared__ T nb_wg[3 * QH_MAX_MODES], nb_wa[3 * QH_MAX_MODES];
+    __shared__ long long mx_off[QH_MAX_MODES];  // nonlinear coupling: mixed-derivative neighbours
+    __shared__ T mx_w[QH_MAX_MODES];
+    __shared__ int s_nmx;
     __shared__ int s_cnt[4];
     __shared__ T s_ngam;
     __shared__ __align__(16) T pgrid[NP];
@@ -476,6 +486,13 @@ fused_stage_kernel(GridInfo g, const ElemInfo *__restrict__ elems, FusedTables<T
         }
         const int n_dn = (terms & 16) ? E.n_dn : 0;
         for (int pass = 0; pass < 2; ++pass) {
+            if (pass == 0 && (terms & 16)) {  // |m| = 2 couplings of the nonlinear coupling: G only
+                for (int a = 0; a < E.n_d2; ++a, ++n) {
+                    nb_off[n] = (long long)(E.d2[a] - e) * (long long)g.elem_stride;
+                    nb_wg[n] = (T)E.w2[a];
+                    nb_wa[n] = (T)0;
+                }
+            }
             for (int a = 0; a < n_dn; ++a) {
                 if ((E.wr[a] != 0.0) != (pass == 1)) continue;
                 nb_off[n] = (long long)(E.dn[a] - e) * (long long)g.elem_stride;
@@ -485,6 +502,12 @@ fused_stage_kernel(GridInfo g, const ElemInfo *__restrict__ elems, FusedTables<T
             }
             if (pass == 0) s_cnt[1] = n;
         }
+        const int n_mx = (terms & 16) ? E.n_mx : 0;
+        for (int a = 0; a < n_mx; ++a) {
+            mx_off[a] = (long long)(E.mx[a] - e) * (long long)g.elem_stride;
+            mx_w[a] = (T)(E.wmx[a] / (12.0 * g.dq));
+        }
+        s_nmx = n_mx;
         s_cnt[0] = n_up;
         s_cnt[2] = n;
         s_cnt[3] = (terms & 8) && E.terminator;
@@ -524,7 +547,7 @@ fused_stage_kernel(GridInfo g, const ElemInfo *__restrict__ elems, FusedTables<T
         __syncthreads();
         potential_in_place<T, NP, S>(X, tw, tab, nq, i0, rows,
                                      ((terms & 4) ? sc.fdelta : (T)0) + ((s_cnt[3] != 0) ? sc.fterm : (T)0), s_ngam,
-                                     s_lpp);
+                                     s_lpp, g.c2, g.q_min, g.dq);
     }
 
     // ---- phase B: one warp per p-row ------------------------------------------------------------
@@ -681,6 +704,9 @@ fused_stage_kernel(GridInfo g, const ElemInfo *__restrict__ elems, FusedTables<T
             v_axpy<VEC>(gr, wg, xr);
             v_axpy<VEC>(gi, wg, xi);
         }
+        // nonlinear coupling V = q + c2 q^2: phi = 1 + 2 c2 q_i multiplies Phi = -phi d/dp and the
+        // p phi part of Lambda^(1); its d2/dp dq part enters G below (block-uniform branches)
+        const T phi = g.c2 != 0.0 ? (T)(1.0 + 2.0 * g.c2 * (g.q_min + i * g.dq)) : (T)1;
         if (n_d0 < n_nb) {
             for (int a = n_d0; a < n_nb; ++a) {
                 const T *u = v_in + (long long)o + nb_off[a];
@@ -693,10 +719,46 @@ fused_stage_kernel(GridInfo g, const ElemInfo *__restrict__ elems, FusedTables<T
                 v_axpy<VEC>(hr, wa, xr);
                 v_axpy<VEC>(hi, wa, xi);
             }
+            if (g.c2 != 0.0) {
+#pragma unroll
+                for (int v = 0; v < VEC; ++v) {
+                    hr[v] *= phi;
+                    hi[v] *= phi;
+                }
+            }
             v_fma<VEC>(ar, pcol, hr);
             v_fma<VEC>(ai, pcol, hi);
         }
-        const bool have_g = n_nb > 0 || term;
+        const int n_mx = s_nmx;
+        if (g.c2 != 0.0) {
+            // G' = phi G + sum_a wmx_a d/dq W^(mx_a) (4th-order central in q, rows i-2..i+2), so that
+            // d/dp G' = phi dG/dp + wmx d2/dp dq W: the p-stencil below covers both
+#pragma unroll
+            for (int v = 0; v < VEC; ++v) {
+                gr[v] *= phi;
+                gi[v] *= phi;
+            }
+            for (int a = 0; a < n_mx; ++a) {
+                const T *Ere = v_in + poff + mx_off[a];
+                const T w = mx_w[a];
+                const T cq[4] = {(T)1, (T)-8, (T)8, (T)-1};
+                const int dqo[4] = {-2, -1, 1, 2};
+#pragma unroll
+                for (int b = 0; b < 4; ++b) {
+                    int ii = i + dqo[b];
+                    if (ii < 0 || ii >= nq) {
+                        if (!g.periodic_q) continue;
+                        ii = ii < 0 ? ii + nq : ii - nq;
+                    }
+                    T xr[VEC], xi[VEC];
+                    ldv<T, VEC>(Ere + (size_t)ii * NP + l0, xr);
+                    ldv<T, VEC>(Ere + blk + (size_t)ii * NP + l0, xi);
+                    v_axpy<VEC>(gr, w * cq[b], xr);
+                    v_axpy<VEC>(gi, w * cq[b], xi);
+                }
+            }
+        }
+        const bool have_g = n_nb > 0 || term || n_mx > 0;
         if (term) {
             T r0p[VEC];
 #pragma unroll
@@ -743,7 +805,7 @@ fused_stage_kernel(GridInfo g, const ElemInfo *__restrict__ elems, FusedTables<T
         if (fpp != (T)0) {
             T er[VEC + 4], ei[VEC + 4];
             stencil(wr, wi, er, ei);
-            const T f = fpp;
+            const T f = fpp * phi * phi;
 #pragma unroll
             for (int v = 0; v < VEC; ++v) {
                 ar[v] += f * (-er[v] + (T)16 * er[v + 1] - (T)30 * er[v + 2] + (T)16 * er[v + 3] - er[v + 4]);
@@ -797,6 +859,20 @@ fused_stage_kernel(GridInfo g, const ElemInfo *__restrict__ elems, FusedTables<T
             stv<T, VEC>(v_out + o + blk, bi);
         }
     }
+}
+
+template <typename T, int NP, int S, bool MIXED, bool MULTI>
+__global__ void __launch_bounds__(FTHREADS, FusedOcc<T, NP, S>::blocks - (MULTI && FusedOcc<T, NP, S>::blocks > 2 ? 1 : 0))
+fused_stage_kernel(GridInfo g, const ElemInfo *__restrict__ elems, FusedTables<T> tab, StageScalars<T> sc, const T *__restrict__ v_in,
+                   const T *y, const double *y0, T *v_out, double *y0_out, double h, int mode, int terms, int rep0,
+                   int n_rep, int tq, const T *__restrict__ Pg, const MultiMember<T> *__restrict__ mem, int n_mem, int k)
+{
+    // Programmatic dependent launch: the next stage may start its blocks (prologue only) once every
+    // block of this one has started; the body waits (griddepcontrol.wait) for this grid's completion
+    // before touching the state.  Both are no-ops for a plain launch.
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    fused_stage_body<T, NP, S, MIXED, MULTI>(blockIdx.x, g, elems, tab, sc, v_in, y, y0, v_out, y0_out, h, mode, terms,
+                                             rep0, n_rep, tq, Pg, mem, n_mem, k);
 }
 
 }  // namespace

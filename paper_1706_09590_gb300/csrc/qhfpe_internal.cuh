@@ -18,6 +18,9 @@
 //   damping   : - (sum_k n_k gamma_k) W
 //   terminator: at the deepest tier with the Eq. (GMFP) closure, d/dp (r_0 p W) + c_0 d2W/dp2 replaces
 //               the missing tier-up term.
+//   nonlinear coupling V(q) = q + c2 q^2 (GridInfo::c2 != 0): the mixed derivative
+//               + wmx d2/dp dq W^(n-e_k) (element mx[a]) and the |m| = 2 couplings, terms of
+//               phi d/dp W^(n-m) with weight w2 (element d2[a]), where phi = 1 + 2 c2 q
 struct ElemInfo {
     int up[QH_MAX_MODES];
     int dn[QH_MAX_MODES];
@@ -27,6 +30,11 @@ struct ElemInfo {
     int n_up, n_dn;
     int terminator;
     int tier;
+    int mx[QH_MAX_MODES];
+    double wmx[QH_MAX_MODES];
+    int d2[QH_MAX_MODES];
+    double w2[QH_MAX_MODES];
+    int n_mx, n_d2;
 };
 
 // Geometry and bath scalars shared by every kernel of one propagator.
@@ -42,6 +50,7 @@ struct GridInfo {
     size_t rep_stride;     // n_elem*elem_stride reals per replica
     size_t tier0_rep_stride;  // S*S*2*blk reals per replica in the FP64 tier-0 buffer
     int max_nb;        // most tier neighbours (up + down) of any element
+    double c2;         // nonlinear system-bath coupling V(q) = q + c2 q^2 (0: linear)
 };
 
 // Potential-kernel tables in FFT output (bit-reversed) order, pre-scaled by 1/np:
@@ -124,10 +133,17 @@ size_t fused_smem_bytes(int tq, int np, int S, int elem_bytes);
 int fused_fft_frequency(int np, int pos);
 // Pg: potential term computed elsewhere (same layout as v_in), or nullptr to compute it in the kernel.
 // tq: q rows per block (0: the default heuristic), at most fused_max_rows.
+// form: -1 the q-window kernel where it applies (fused_window_applies), 0 always fused_stage_kernel,
+// 1 the q-window kernel where it applies (the autotuner's choice).
 template <typename T, bool MIXED>
 cudaError_t launch_fused(const GridInfo &g, const ElemInfo *elems, const FusedTables<T> &tab, const T *v_in,
                          const T *y, const double *y0, T *v_out, double *y0_out, double h, int mode, int terms,
-                         int rep0, int n_rep, cudaStream_t st, const T *Pg = nullptr, int tq = 0);
+                         int rep0, int n_rep, cudaStream_t st, const T *Pg = nullptr, int tq = 0, int form = -1);
+// The q-window form of the fused stage kernel (FP32, np 128, one or two states, every term with the
+// potential in the kernel, lanes of one p sign, at most six tier neighbours, linear coupling), unless
+// QHFPE_FUSED_WINDOW=0; its q rows per block.
+bool fused_window_applies(const GridInfo &g, int terms, bool have_pg);
+int fused_window_rows(int S);
 int fused_max_rows(int np, int S, int elem_bytes);
 template <typename T>
 StageScalars<T> stage_scalars(const GridInfo &g, double h);
@@ -150,6 +166,23 @@ cudaError_t launch_dipole_fft(const GridInfo &g, const T *TL, const T *TR, const
                               int n_elem, const int *reps, int n_rep, int side, double scale, float *mirror,
                               size_t mirror_rep_stride, cudaStream_t st);
 
+// ---- persistent propagation (qhfpe_persistent.cu) ---------------------------------------------------------
+// n_steps RK4 steps of the one-member batch `mem` (device, block0 = 0) in one cooperative launch: every
+// Horner stage a grid-stride loop over the n_items blocks of a fused stage launch at tile height tq,
+// grid barriers between stages (bar_words: two zeroed words, count and generation; *err set to 1 when a
+// wait exceeded limit_ns).  trace_out (device, may be nullptr): Tr{mu W^(0)} of every replica after
+// each step into slots slot0 .. slot0 + n_steps - 1 of [n_rep][trace_stride] complex, from the FP64
+// trace_state (Condon mu), chunk partials in `partial` ([n_rep][n_chunks][2]).
+template <typename T, bool MIXED>
+cudaError_t launch_persistent(int np, int S, const MultiMember<T> *mem, long n_items, int tq, int n_steps,
+                              const double *trace_state, size_t trace_rep_stride, const double *mu, double *partial,
+                              int n_chunks, double *trace_out, long trace_stride, long slot0, unsigned *bar_words,
+                              int *err, unsigned long long limit_ns, cudaStream_t st);
+// The barrier alone on four one-warp blocks; withhold = 1 keeps block 0 away, so the others give up.
+cudaError_t launch_barrier_selftest(unsigned *bar_words, int *err, unsigned long long limit_ns, int withhold,
+                                    cudaStream_t st);
+int trace_chunks(int n_rep, size_t blk);
+
 // ---- tensor-core potential term (qhfpe_tc.cu) ----------------------------------------------------------
 bool tc_supported(int np, int S);
 cudaError_t prepare_tc(int np, int S);
@@ -169,6 +202,20 @@ cudaError_t launch_closure_collect(const GridInfo &g, const T *state, int e_t, i
                                    cudaStream_t st);
 cudaError_t launch_closure_infer(const GridInfo &g, double eta, const float *w_dev, int bf16, double *out64,
                                  float *out32, cudaStream_t st);
+
+// State-input closure (qhfpe_closure.cu): weights per S; fill the W^(N+1) slot of `state` from tiers
+// e_n, e_n1 of replicas rep0 .. rep0 + n_rep - 1; training samples of the tier e_t from e_t1, e_t2.
+size_t closure_state_n_weights(int S);
+template <typename T>
+cudaError_t launch_closure_state_fill(const GridInfo &g, T *state, int e_n, int e_n1, int e_slot, const float *w,
+                                      double eta, int rep0, int n_rep, cudaStream_t st);
+template <typename T>
+cudaError_t launch_closure_state_collect(const GridInfo &g, const T *state, int e_t, int e_t1, int e_t2, double eta,
+                                         float *X, float *Y, long offset, long capacity, cudaStream_t st);
+// classic RK4 combination over n values: first: acc = y + a_acc k; else acc += a_acc k; then v = y + a_v k;
+// last: y = acc + a_acc k (v untouched)
+cudaError_t launch_rk4_combine(size_t n, double *y, const double *k, double *acc, double *v, double a_acc, double a_v,
+                               int first, int last, cudaStream_t st);
 
 // Error text for calls without a handle (failed create, the static-scratch entry point).
 void qh_set_free_error(const std::string &msg);

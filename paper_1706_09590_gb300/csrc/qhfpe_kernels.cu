@@ -595,6 +595,21 @@ __global__ void __launch_bounds__(256) dfma_rate_kernel(double x, double y, int 
     out[blockIdx.x * (size_t)blockDim.x + threadIdx.x] = s;
 }
 
+__global__ void rk4_combine_kernel(size_t n, double *y, const double *__restrict__ k, double *acc, double *v, double a_acc,
+                                   double a_v, int first, int last)
+{
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        const double kv = k[i];
+        if (last) {
+            y[i] = acc[i] + a_acc * kv;
+            continue;
+        }
+        const double yv = y[i];
+        acc[i] = (first ? yv : acc[i]) + a_acc * kv;
+        v[i] = yv + a_v * kv;
+    }
+}
+
 inline int grid_for(size_t n, int threads, int cap = 152 * 32)
 {
     size_t b = (n + threads - 1) / threads;
@@ -725,6 +740,13 @@ cudaError_t launch_wait_flag(const int *flag, unsigned long long limit_ns, int *
 cudaError_t launch_dfma_rate(int blocks, int n_iter, double *out, cudaStream_t st)
 {
     dfma_rate_kernel<<<blocks, 256, 0, st>>>(0.999999, 1e-7, n_iter, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_rk4_combine(size_t n, double *y, const double *k, double *acc, double *v, double a_acc, double a_v,
+                               int first, int last, cudaStream_t st)
+{
+    rk4_combine_kernel<<<grid_for(n, 256), 256, 0, st>>>(n, y, k, acc, v, a_acc, a_v, first, last);
     return cudaGetLastError();
 }
 

@@ -27,7 +27,9 @@ EXPORTED = [
     "qhfpe_create", "qhfpe_destroy", "qhfpe_last_error", "qhfpe_sizes", "qhfpe_hierarchy",
     "qhfpe_bath_coefficients", "qhfpe_max_stable_dt", "qhfpe_set_state", "qhfpe_get_state", "qhfpe_fork",
     "qhfpe_step", "qhfpe_apply_dipole", "qhfpe_apply_rhs", "qhfpe_trace", "qhfpe_equilibrate",
-    "qhfpe_equilibrate_tol", "qhfpe_fp64_fma_rate",
+    "qhfpe_equilibrate_tol", "qhfpe_fp64_fma_rate", "qhfpe_stage_form", "qhfpe_set_persistent",
+    "qhfpe_barrier_selftest", "qhfpe_closure_inputs", "qhfpe_closure_state_n_weights", "qhfpe_closure_state_load",
+    "qhfpe_closure_state_collect", "qhfpe_closure_state_loss_grad", "qhfpe_closure_state_train",
     "qhfpe_set_equilibrium", "qhfpe_response", "qhfpe_spectrum_absorption", "qhfpe_spectrum_2d",
     "qhfpe_kernel_timing", "qhfpe_kernel_timing_read", "qhfpe_potential_term_static",
     "qhfpe_closure_collect", "qhfpe_closure_load", "qhfpe_closure_coefficients", "qhfpe_closure_loss_grad",
@@ -37,6 +39,7 @@ EXPORTED = [
 ]
 
 CLOSURE_N_WEIGHTS = 135178
+LEARNED_STATE = 3
 CLOSURE_N_STATS = 67
 
 
@@ -56,6 +59,7 @@ class Params(ctypes.Structure):
         ("n_matsubara", ctypes.c_int), ("high_temperature", ctypes.c_int), ("use_cdelta", ctypes.c_int),
         ("depth", ctypes.c_int), ("closure", ctypes.c_int), ("periodic_q", ctypes.c_int),
         ("precision", ctypes.c_int), ("dt", ctypes.c_double), ("n_replicas", ctypes.c_int),
+        ("v_c2", ctypes.c_double),
     ]
 
 
@@ -111,6 +115,19 @@ def lib():
     L.qhfpe_potential_term_static.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double,
                                               ctypes.c_double, vp, ctypes.c_int, vp, vp, vp]
     L.qhfpe_tile_rows.argtypes = [vp, ip]
+    L.qhfpe_stage_form.argtypes = [vp, ip]
+    L.qhfpe_set_persistent.argtypes = [vp, ctypes.c_int]
+    L.qhfpe_closure_inputs.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                       ctypes.c_double, ctypes.c_double, vp]
+    L.qhfpe_closure_state_n_weights.argtypes = [ctypes.c_int]
+    L.qhfpe_closure_state_n_weights.restype = ctypes.c_size_t
+    L.qhfpe_closure_state_load.argtypes = [vp, vp, ctypes.c_size_t]
+    L.qhfpe_closure_state_collect.argtypes = [vp, ctypes.c_int, vp, vp, ctypes.c_long, ctypes.c_long,
+                                              ctypes.POINTER(ctypes.c_long)]
+    L.qhfpe_closure_state_loss_grad.argtypes = [ctypes.c_int, vp, vp, vp, ctypes.c_int, dp, vp]
+    L.qhfpe_closure_state_train.argtypes = [ctypes.c_int, vp, vp, vp, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                            ctypes.c_double, ctypes.c_uint, vp]
+    L.qhfpe_barrier_selftest.argtypes = [vp, ctypes.c_int, ctypes.c_int]
     L.qhfpe_fp64_fma_rate.argtypes = [vp, ctypes.c_int, dp]
     L.qhfpe_batch_create.argtypes = [ctypes.POINTER(vp), st, ctypes.POINTER(vp)]
     L.qhfpe_batch_step.argtypes = [vp, ctypes.c_long, ctypes.POINTER(vp)]
@@ -181,6 +198,50 @@ def closure_loss_grad(w, X, stats, ridge=0.0):
     return loss.value, grad
 
 
+def closure_inputs(model, eta):
+    """The closure network's inputs (q/8, p/8, ln eta) at every grid point, [nq*np][3], computed by the library."""
+    L = lib()
+    X = np.zeros((model["nq"] * model["np"], 3))
+    s = L.qhfpe_closure_inputs(model["nq"], model["np"], model["q_min"], model["q_max"], model["p_min"],
+                               model["p_max"], float(eta), _ptr(X))
+    if s != 0:
+        raise QhfpeError(s, L.qhfpe_last_error(None).decode())
+    return X
+
+
+def closure_state_n_weights(n_states):
+    return int(lib().qhfpe_closure_state_n_weights(int(n_states)))
+
+
+def closure_state_loss_grad(n_states, w, X, Y):
+    """Mean squared error of the state-input network on (X, Y) and its gradient (FP32 kernels)."""
+    L = lib()
+    w = np.ascontiguousarray(w, dtype=np.float32)
+    X = np.ascontiguousarray(X, dtype=np.float32)
+    Y = np.ascontiguousarray(Y, dtype=np.float32)
+    loss = ctypes.c_double()
+    grad = np.zeros(closure_state_n_weights(n_states) - 3, dtype=np.float32)
+    s = L.qhfpe_closure_state_loss_grad(int(n_states), _ptr(w), _ptr(X), _ptr(Y), X.shape[0], ctypes.byref(loss),
+                                        _ptr(grad))
+    if s != 0:
+        raise QhfpeError(s, L.qhfpe_last_error(None).decode())
+    return loss.value, grad
+
+
+def closure_state_train(n_states, w, X, Y, n_iters, batch=4096, lr=1e-3, seed=1706):
+    """Adam training of the state-input network on the device; returns (weights with scales, loss history)."""
+    L = lib()
+    w = np.ascontiguousarray(w, dtype=np.float32).copy()
+    X = np.ascontiguousarray(X, dtype=np.float32)
+    Y = np.ascontiguousarray(Y, dtype=np.float32)
+    hist = np.zeros(max(n_iters, 1))
+    s = L.qhfpe_closure_state_train(int(n_states), _ptr(w), _ptr(X), _ptr(Y), X.shape[0], n_iters, batch, lr, seed,
+                                    _ptr(hist))
+    if s != 0:
+        raise QhfpeError(s, L.qhfpe_last_error(None).decode())
+    return w, hist[:n_iters]
+
+
 def closure_train(w, X, stats, n_iters, batch=4096, lr=1e-3, ridge=0.0, seed=1706):
     """Adam training of the closure network on the device; returns (weights, per-iteration loss)."""
     L = lib()
@@ -211,7 +272,7 @@ class Propagator:
                              model["eta"], model["gamma"], model["beta"], model["n_matsubara"],
                              model["high_temperature"], model["use_cdelta"], model["depth"],
                              model["closure"] if closure is None else closure, model.get("periodic_q", 0),
-                             prec, model["dt"] if dt is None else dt, n_replicas)
+                             prec, model["dt"] if dt is None else dt, n_replicas, float(model.get("v_c2", 0.0)))
         self.model = model
         self.n_replicas = n_replicas
         self.dt = self.params.dt
@@ -419,6 +480,19 @@ class Propagator:
         w = np.ascontiguousarray(weights, dtype=np.float32)
         self._check(self._L.qhfpe_closure_load(self._h, _ptr(w), w.size))
 
+    def closure_state_load(self, weights):
+        w = np.ascontiguousarray(weights, dtype=np.float32)
+        self._check(self._L.qhfpe_closure_state_load(self._h, _ptr(w), w.size))
+
+    def closure_state_collect(self, target_tier, X_dev, Y_dev, offset, capacity):
+        """Samples of the target tier into device tensors X_dev [capacity][36 S^2 + 3], Y_dev [capacity][2 S^2]
+        from sample `offset`; returns the number written."""
+        n = ctypes.c_long()
+        self._check(self._L.qhfpe_closure_state_collect(self._h, int(target_tier), ctypes.c_void_p(X_dev.data_ptr()),
+                                                        ctypes.c_void_p(Y_dev.data_ptr()), int(offset), int(capacity),
+                                                        ctypes.byref(n)))
+        return n.value
+
     def closure_coefficients(self):
         out = np.zeros((self.model["nq"], self.model["np"], 10))
         self._check(self._L.qhfpe_closure_coefficients(self._h, _ptr(out)))
@@ -428,6 +502,19 @@ class Propagator:
     def wait_selftest(self, release, limit_ms=200):
         """Status of the bounded device wait self-test (0 = OK, 5 = ETIMEOUT)."""
         return self._L.qhfpe_wait_selftest(self._h, int(release), int(limit_ms))
+
+    def set_persistent(self, on=True):
+        """Whole runs of steps (and the response schedule's phases) in one cooperative, resident launch."""
+        self._check(self._L.qhfpe_set_persistent(self._h, int(bool(on))))
+
+    def barrier_selftest(self, withhold, limit_ms=200):
+        return self._L.qhfpe_barrier_selftest(self._h, int(withhold), int(limit_ms))
+
+    def stage_form(self):
+        """1: q-window stage kernel, 0: general, -1: not yet chosen."""
+        f = ctypes.c_int()
+        self._check(self._L.qhfpe_stage_form(self._h, ctypes.byref(f)))
+        return f.value
 
     def tile_rows(self):
         v = ctypes.c_int()

@@ -113,3 +113,54 @@ def test_correction_can_cancel_the_terminator_momentum_part():
     diff = L_term - L_learned
     assert np.allclose(diff[2], dpw, atol=1e-11)
     assert np.abs(diff[:2]).max() < 1e-12
+
+
+# ------------------------------------------------------------------------------------------------
+# State-input network (the literal closure): inputs layout, backpropagation, bf16 rounding
+# ------------------------------------------------------------------------------------------------
+def test_state_inputs_layout_on_an_impulse():
+    """A single nonzero value of tier N-1 at (i0, l0) of pair (0, 1) appears in the inputs of exactly
+    the nine neighbouring points, at the patch position of its offset (q zero-padded, p periodic)."""
+    m = qi.harmonic_two_state(nq=6, n_p=8, depth=3)
+    W = np.zeros(qi.state_shape(m), complex)
+    i0, l0 = 2, 7
+    W[2, 0, 1, i0, l0] = 3.0 - 1.0j
+    X = cl.state_inputs(W, 3, m)
+    base = 3  # tier N (= tier 2 of the state) comes first
+    pair = 0 * 2 + 1
+    hits = np.argwhere(np.abs(X[..., 3:]) > 0)
+    assert len(hits) == 2 * 9
+    for a in (-1, 0, 1):
+        for b in (-1, 0, 1):
+            i, l = i0 - a, (l0 - b) % 8  # the point whose (a, b) neighbour is (i0, l0)
+            c = base + 2 * (9 * pair + 3 * (a + 1) + (b + 1))
+            assert X[i, l, c] == 3.0 and X[i, l, c + 1] == -1.0
+    assert X[0, 0, 0] == m["q_min"] / 8 and X[0, 1, 1] == (m["p_min"] + 2.0) / 8
+
+
+def test_state_gradient_matches_finite_differences():
+    S = 1
+    n_in, n_out = cl.state_sizes(S)
+    rng = np.random.default_rng(7)
+    w = np.concatenate([rng.normal(size=int(np.prod(s))) * (0.3 / np.sqrt(s[-1]) if len(s) == 2 else 0.1)
+                        for s in cl.state_shapes(S)] + [np.ones(3)])
+    X = rng.normal(size=(5, n_in))
+    Y = rng.normal(size=(5, n_out))
+    L, g = cl.state_loss_and_grad(w, X, Y, S)
+    n = len(g)
+    for idx in rng.choice(n, 25, replace=False):
+        e = np.zeros_like(w)
+        e[idx] = 1e-6
+        fd = (cl.state_loss_and_grad(w + e, X, Y, S)[0] - cl.state_loss_and_grad(w - e, X, Y, S)[0]) / 2e-6
+        assert fd == pytest.approx(g[idx], rel=1e-5, abs=1e-9)
+
+
+def test_bf16_rounding():
+    v = np.array([1.0, 1.0 + 2 ** -8, 1.0 + 2 ** -7, 1.0 + 3 * 2 ** -8, -2.5, 1e-3])
+    got = cl.bf16(v)
+    assert got[0] == 1.0
+    assert got[1] == 1.0                  # halfway between 1 and 1 + 2^-7: ties to even
+    assert got[2] == 1.0 + 2 ** -7
+    assert got[3] == 1.0 + 2 * 2 ** -7    # halfway: ties to even (odd mantissa rounds up)
+    assert got[4] == -2.5
+    assert abs(got[5] - 1e-3) < 1e-3 * 2 ** -8
