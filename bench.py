@@ -296,6 +296,71 @@ def linear_absorption_measure(stream):
     return out
 
 
+def learned_closure_measure(stream):
+    """Learned closures on the config-1 model at 96 x 128 (q, p in [-8, 8)): trained on depth-12 FP64 runs
+    at eta in {0.2, 0.5, 1}, deployed at depth 4, judged at the held-out eta = 0.3 against depth 12: R1
+    over 10 time units for the truncation, the Eq. (GMFP) terminator, the coefficient form (QHFPE_LEARNED)
+    and the state-input network (QHFPE_LEARNED_STATE); their training times (device kernels), the wall
+    time of R1 at depth 4 and at depth 12, and the pathway-additivity defect of a small third-order
+    schedule (ket + bra against the full commutator) of each form."""
+    import numpy as np
+    import torch
+    import qhfpe_inputs as qi
+    from paper_1706_09590_gb300 import Propagator
+    from paper_1706_09590_gb300 import closure as pcl
+    base = qi.harmonic_two_state(nq=96, n_p=128, qr=(-8.0, 8.0), pr=(-8.0, 8.0), depth=12, eta=1.0)
+    T = qi.u_table(base)
+    probe = Propagator(base, T, precision="fp64", stream=stream)
+    dt = 0.8 * probe.max_stable_dt()
+    probe.close()
+    base["dt"] = dt
+    etas = (0.2, 0.5, 1.0)
+    args = dict(deep_depth=12, target_tier=5, n_eq=int(10 / dt), n_prop=int(6 / dt), every=max(1, int(0.2 / dt)))
+    out = {"workload": "harmonic two-state 96x128, depth 12 -> 4, train eta 0.2/0.5/1, judged at eta 0.3, R1 over 10 "
+                       "time units", "dt": dt}
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    Xc, Sc = pcl.training_set(base, T, etas, stream=stream, **args)
+    out["coef_data_s"] = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    wc, _ = pcl.train(Xc, Sc, n_iters=3000, batch=4096, lr=1e-3)
+    out["coef_train_s"] = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    Xs, Ys = pcl.state_training_set(base, T, etas, stream=stream, **dict(args, every=max(1, int(0.5 / dt))))
+    out["state_data_s"] = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    ws, _ = pcl.train_state(2, Xs, Ys, n_iters=3000, batch=4096, lr=1e-3)
+    out["state_train_s"] = time.perf_counter() - t0
+    out["state_samples"] = int(Xs.shape[0])
+    n_t = int(10 / dt)
+    R1, defect = {}, {}
+    for name, depth, closure in (("depth12", 12, 1), ("truncate", 4, 0), ("terminator", 4, 1), ("learned_coef", 4, 2),
+                                 ("learned_state", 4, 3)):
+        m = dict(base, eta=0.3, depth=depth, closure=closure)
+        P = Propagator(m, T, precision="fp64", stream=stream)
+        if closure == 2:
+            P.closure_load(wc)
+        if closure == 3:
+            P.closure_state_load(ws)
+        P.equilibrate(int(10 / dt))
+        P.set_equilibrium(P.get_state(0))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        R1[name] = P.linear_response(n_t)
+        torch.cuda.synchronize()
+        out[name + "_R1_s"] = time.perf_counter() - t0
+        sched = (2, int(0.5 / dt), [0, int(1.0 / dt)], int(2 / dt))
+        full = P.third_order_response(*sched)
+        split = P.third_order_response(*sched, split_pathways=True)
+        defect[name] = float(np.linalg.norm(split[0] + split[1] - full) / np.linalg.norm(full))
+        P.close()
+    ref = R1["depth12"]
+    out["rel_err_R1_vs_depth12"] = {k: float(np.linalg.norm(v - ref) / np.linalg.norm(ref)) for k, v in R1.items()
+                                    if k != "depth12"}
+    out["additivity_defect"] = defect
+    return out
+
+
 def cpu_spectrum_baseline(seconds_cap=60.0):
     """The FP64 oracle as it stands on this host's cores, on a bounded sub-schedule of the batched 2D
     spectrum (ket pathway, the first two t1 delays, the first two waiting times, full t3 = 512 steps),
@@ -660,6 +725,8 @@ def main():
                     help="skip the full-size three-state measurement")
     ap.add_argument("--no-forms", action="store_true",
                     help="skip the tensor-core and FP64 forms on the benchmark workload")
+    ap.add_argument("--no-closure", action="store_true",
+                    help="skip the learned-closure measurement (config-5 shape)")
     ap.add_argument("--no-config2-sweep", action="store_true",
                     help="skip the eta x coupling sweep of the benchmark model (FP64 vs mixed spectra)")
     args = ap.parse_args()
@@ -828,6 +895,8 @@ def main():
         line["fp64_form"] = fp64_form_measure(stream, m, T, fp64_peak, fp64_src)
     if not args.no_config2_sweep:
         line["config2_sweep"] = config2_sweep_measure(stream)
+    if not args.no_closure:
+        line["learned_closure"] = learned_closure_measure(stream)
     if not args.no_spectrum:
         line["linear_absorption"] = linear_absorption_measure(stream)
         line["spectrum_2d"] = spectrum_2d_measure(stream)

@@ -79,10 +79,12 @@ def initial_state_weights(S, seed=1706):
     return w
 
 
-def state_training_set(model, U_table, etas, deep_depth, target_tier, n_eq, n_prop, every, stream=None):
+def state_training_set(model, U_table, etas, deep_depth, target_tier, n_eq, n_prop, every, stream=None,
+                       max_samples=400000, seed=1706):
     """Samples (X, Y) of the target tier from depth-`deep_depth` FP64 runs (Eq. (GMFP) terminator) at each
     eta, excited like the statistics of the coefficient form: every grid point of both replicas every
-    `every` steps.  Returns host float32 arrays."""
+    `every` steps, then at most max_samples of them drawn at random (seeded).  Returns host float32
+    arrays."""
     import torch
     S = model["S"]
     n_in, n_out = 36 * S * S + 3, 2 * S * S
@@ -104,7 +106,11 @@ def state_training_set(model, U_table, etas, deep_depth, target_tier, n_eq, n_pr
         P.close()
         Xs.append(X[:off].cpu().numpy())
         Ys.append(Y[:off].cpu().numpy())
-    return np.concatenate(Xs), np.concatenate(Ys)
+    X, Y = np.concatenate(Xs), np.concatenate(Ys)
+    if X.shape[0] > max_samples:
+        keep = np.sort(np.random.default_rng(seed).choice(X.shape[0], max_samples, replace=False))
+        X, Y = X[keep], Y[keep]
+    return X, Y
 
 
 def train_state(S, X, Y, n_iters=3000, batch=4096, lr=1e-3, seed=1706, weights=None):

@@ -156,7 +156,7 @@ def test_state_closure_additivity_defect_and_error(torch):
         r1 = P.linear_response(1000)
         full = P.third_order_response(3, 20, [0, 100], 200)
         split = P.third_order_response(3, 20, [0, 100], 200, split_pathways=True)
-        res[name] = (r1, rel(split[0] + split[1], full[0]))
+        res[name] = (r1, rel(split[0] + split[1], full))
         P.close()
     err = {k: rel(v[0], res["truth"][0]) for k, v in res.items() if k != "truth"}
     defect = {k: v[1] for k, v in res.items()}
