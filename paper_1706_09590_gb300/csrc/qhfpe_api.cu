@@ -2102,8 +2102,11 @@ qhfpe_status qhfpe_closure_state_load(qhfpe_t *h, const float *weights, size_t n
         if (!std::isfinite(weights[i])) return h->fail(QHFPE_ENUMERIC, "closure_state_load: non-finite weight");
     for (size_t i = n - 3; i < n; ++i)
         if (!(weights[i] > 0.f)) return h->fail(QHFPE_EINVAL, "closure_state_load: the three scales must be positive");
-    if (!h->state_w) QH_CK(h, cudaMalloc((void **)&h->state_w, n * sizeof(float)));
+    const size_t off = closure_state_prepared_offset(h->p.n_states);
+    if (!h->state_w)
+        QH_CK(h, cudaMalloc((void **)&h->state_w, (off + closure_state_prepared_floats(h->p.n_states)) * sizeof(float)));
     QH_CK(h, cudaMemcpyAsync(h->state_w, weights, n * sizeof(float), cudaMemcpyHostToDevice, h->stream));
+    QH_CK(h, launch_closure_state_prepare(h->p.n_states, h->state_w, h->state_w + off, h->stream));
     QH_CK(h, cudaStreamSynchronize(h->stream));
     for (auto &kv : h->batches) kv.second->drop_graphs();
     h->main->drop_graphs();

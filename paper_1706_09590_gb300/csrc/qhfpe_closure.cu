@@ -556,8 +556,6 @@ __host__ __device__ constexpr size_t sc_nweights(int S)
     return (size_t)NH * sc_nin(S) + NH + 2 * ((size_t)NH * NH + NH) + (size_t)sc_nout(S) * NH + sc_nout(S) + 3;
 }
 
-constexpr int SPTS = 8;  // points per inference block
-
 // inputs of one point into x (length sc_nin(S)), unscaled; tier elements e_n, e_n1 (-1: zeros)
 template <typename T>
 __device__ __forceinline__ void sc_gather(const GridInfo &g, const T *rep_state, int e_n, int e_n1, int i, int l,
@@ -595,60 +593,128 @@ __device__ __forceinline__ void sc_gather(const GridInfo &g, const T *rep_state,
     }
 }
 
+// input c of one point (the order of sc_gather: features, then tier, pair, a, b, re/im), unscaled
+template <typename T>
+__device__ __forceinline__ float sc_input(const GridInfo &g, const T *rep_state, int e_n, int e_n1, int i, int l,
+                                          double log_eta, int c, float sN, float sN1)
+{
+    if (c < 3) {
+        double f[3];
+        closure_features(g.q_min, g.dq, g.p_min, g.dp, log_eta, i, l, f);
+        return (float)f[c];
+    }
+    const int S2 = g.S * g.S, nq = g.nq, np = g.np;
+    const int cc = c - 3, tier = cc / (18 * S2), rem = cc % (18 * S2), pr = rem / 18, ab = (rem % 18) / 2,
+              part = rem % 2;
+    const int e = tier == 0 ? e_n : e_n1;
+    const float s = tier == 0 ? sN : sN1;
+    int ii = i + ab / 3 - 1;
+    bool ok = e >= 0 && ii >= 0 && ii < nq;
+    if (e >= 0 && !ok && g.periodic_q) {
+        ii = (ii + nq) % nq;
+        ok = true;
+    }
+    if (!ok) return 0.f;
+    const int lb = (l + ab % 3 - 1 + np) % np;
+    const T *blk = rep_state + (size_t)e * g.elem_stride + (size_t)pr * 2 * g.blk + (size_t)part * g.blk;
+    return (float)blk[(size_t)ii * np + lb] / s;
+}
+
+// The matrices of the network, bf16-rounded and transposed ([k][unit]) once per weight load, so that a
+// warp reads consecutive units of one input k: Wt1[NI][NH], Wt2[NH][NH], Wt3[NH][NH], Wt4[NH][NO].
+__global__ void state_weights_prepare_kernel(int NI, int NO, const float *__restrict__ w, float *wt)
+{
+    const size_t n1 = (size_t)NI * NH, n2 = (size_t)NH * NH, n4 = (size_t)NH * NO;
+    const size_t OW2 = n1 + NH, OW3 = OW2 + n2 + NH, OW4 = OW3 + n2 + NH;
+    for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < n1 + 2 * n2 + n4; t += (size_t)gridDim.x * blockDim.x) {
+        float v;
+        if (t < n1) {
+            const size_t k = t / NH, u = t % NH;
+            v = w[u * NI + k];
+        } else if (t < n1 + 2 * n2) {
+            const size_t tt = (t - n1) % n2, k = tt / NH, u = tt % NH;
+            v = w[(t < n1 + n2 ? OW2 : OW3) + u * NH + k];
+        } else {
+            const size_t tt = t - n1 - 2 * n2, k = tt / NO, o = tt % NO;
+            v = w[OW4 + o * NH + k];
+        }
+        wt[t] = rnd(v, 1);
+    }
+}
+
+constexpr int SPTS = 32;          // points per state-closure inference block
+constexpr int ILD = NH + 4;       // padded activation row (floats)
+
+// one hidden layer for SPTS points: out[pt][u] = bf16(tanh(b[u] + sum_k in[pt][k] Wt[k][u])), the sum in
+// k order from the bias (as the oracle's quantised forward); thread (ty, tx) owns points 4 ty .. 4 ty + 3
+// and units 8 tx .. 8 tx + 7
+template <int K>
+__device__ __forceinline__ void state_dense_tanh(const float *in, float *out, const float *__restrict__ Wt,
+                                                 const float *__restrict__ b)
+{
+    const int ty = threadIdx.x >> 5, tx = threadIdx.x & 31;
+    float acc[4][8];
+    {
+        const float4 b0 = *reinterpret_cast<const float4 *>(b + 8 * tx), b1 = *reinterpret_cast<const float4 *>(b + 8 * tx + 4);
+        const float bb[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 8; ++j) acc[i][j] = bb[j];
+    }
+#pragma unroll 4
+    for (int k = 0; k < K; ++k) {
+        const float4 w0 = __ldg(reinterpret_cast<const float4 *>(Wt + (size_t)k * NH + 8 * tx));
+        const float4 w1 = __ldg(reinterpret_cast<const float4 *>(Wt + (size_t)k * NH + 8 * tx + 4));
+        const float ww[8] = {w0.x, w0.y, w0.z, w0.w, w1.x, w1.y, w1.z, w1.w};
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const float a = in[(4 * ty + i) * ILD + k];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(ww[j], a, acc[i][j]);
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) out[(4 * ty + i) * ILD + 8 * tx + j] = rnd(tanhf(acc[i][j]), 1);
+}
+
 // One block evaluates SPTS points of one replica: bf16 weights and activations, FP32 accumulation.
 template <typename T, int S>
 __global__ void __launch_bounds__(256) state_closure_kernel(GridInfo g, T *state, int e_n, int e_n1, int e_slot,
-                                                            const float *__restrict__ w, double log_eta, int rep0)
+                                                            const float *__restrict__ w, const float *__restrict__ wt,
+                                                            double log_eta, int rep0)
 {
     constexpr int NI = sc_nin(S), NO = sc_nout(S), S2 = S * S;
-    __shared__ float xin[SPTS][NI];
-    __shared__ float h[2][SPTS][NH + 1];
-    const size_t OW1s = 0, OB1s = OW1s + (size_t)NH * NI, OW2s = OB1s + NH, OB2s = OW2s + (size_t)NH * NH,
-                 OW3s = OB2s + NH, OB3s = OW3s + (size_t)NH * NH, OW4s = OB3s + NH, OB4s = OW4s + (size_t)NO * NH,
-                 OSC = OB4s + NO;
+    static_assert(NI <= ILD, "inputs fit an activation row");
+    extern __shared__ __align__(16) float sact[];
+    float *hA = sact, *hB = sact + SPTS * ILD;  // [SPTS][ILD] each
+    const size_t OB1s = (size_t)NH * NI, OB2s = OB1s + NH + (size_t)NH * NH, OB3s = OB2s + NH + (size_t)NH * NH,
+                 OB4s = OB3s + NH + (size_t)NO * NH, OSC = OB4s + NO;
+    const size_t T2 = (size_t)NI * NH, T3 = T2 + (size_t)NH * NH, T4 = T3 + (size_t)NH * NH;
     const float sN = w[OSC], sN1 = w[OSC + 1], sO = w[OSC + 2];
     const int rep = rep0 + blockIdx.y;
     T *rs = state + (size_t)rep * g.rep_stride;
     const int n_pts = (int)g.blk;
     const int p0 = blockIdx.x * SPTS;
-    for (int pt = threadIdx.x; pt < SPTS; pt += blockDim.x) {
-        const int x = p0 + pt;
-        if (x < n_pts) {
-            sc_gather<T>(g, rs, e_n, e_n1, x / g.np, x % g.np, log_eta, xin[pt], sN, sN1);
-            for (int k = 0; k < NI; ++k) xin[pt][k] = rnd(xin[pt][k], 1);
-        } else {
-            for (int k = 0; k < NI; ++k) xin[pt][k] = 0.f;
-        }
+    for (int t = threadIdx.x; t < SPTS * NI; t += blockDim.x) {
+        const int pt = t / NI, c = t % NI, x = p0 + pt;
+        hA[pt * ILD + c] = x < n_pts ? rnd(sc_input<T>(g, rs, e_n, e_n1, x / g.np, x % g.np, log_eta, c, sN, sN1), 1) : 0.f;
     }
     __syncthreads();
-    for (int t = threadIdx.x; t < SPTS * NH; t += blockDim.x) {
-        const int pt = t / NH, u = t % NH;
-        float v = w[OB1s + u];
-        const float *wr = w + OW1s + (size_t)u * NI;
-        for (int k = 0; k < NI; ++k) v += rnd(wr[k], 1) * xin[pt][k];
-        h[0][pt][u] = rnd(tanhf(v), 1);
-    }
+    state_dense_tanh<NI>(hA, hB, wt, w + OB1s);
     __syncthreads();
-    int cur = 0;
-    for (int layer = 0; layer < 2; ++layer) {
-        const size_t OW = layer == 0 ? OW2s : OW3s, OB = layer == 0 ? OB2s : OB3s;
-        for (int t = threadIdx.x; t < SPTS * NH; t += blockDim.x) {
-            const int pt = t / NH, u = t % NH;
-            float v = w[OB + u];
-            const float *wr = w + OW + (size_t)u * NH;
-            for (int k = 0; k < NH; ++k) v += rnd(wr[k], 1) * h[cur][pt][k];
-            h[cur ^ 1][pt][u] = rnd(tanhf(v), 1);
-        }
-        __syncthreads();
-        cur ^= 1;
-    }
+    state_dense_tanh<NH>(hB, hA, wt + T2, w + OB2s);
+    __syncthreads();
+    state_dense_tanh<NH>(hA, hB, wt + T3, w + OB3s);
+    __syncthreads();
     for (int t = threadIdx.x; t < SPTS * NO; t += blockDim.x) {
         const int pt = t / NO, o = t % NO;
         const int x = p0 + pt;
         if (x >= n_pts) continue;
         float v = w[OB4s + o];
-        const float *wr = w + OW4s + (size_t)o * NH;
-        for (int k = 0; k < NH; ++k) v += rnd(wr[k], 1) * h[cur][pt][k];
+        for (int k = 0; k < NH; ++k) v = fmaf(wt[T4 + (size_t)k * NO + o], hB[pt * ILD + k], v);
         const int pr = o / 2, part = o % 2;
         if (pr < S2) rs[(size_t)e_slot * g.elem_stride + (size_t)pr * 2 * g.blk + (size_t)part * g.blk + x] = (T)(v * sO);
     }
@@ -797,11 +863,35 @@ cudaError_t launch_closure_state_fill(const GridInfo &g, T *state, int e_n, int 
 {
     dim3 grid((unsigned)((g.blk + SPTS - 1) / SPTS), (unsigned)n_rep);
     const double le = std::log(eta);
+    const size_t smem = 2 * SPTS * ILD * sizeof(float);
+    const float *wt = w + closure_state_prepared_offset(g.S);  // the prepared matrices follow the weights
     switch (g.S) {
-    case 1: state_closure_kernel<T, 1><<<grid, 256, 0, st>>>(g, state, e_n, e_n1, e_slot, w, le, rep0); break;
-    case 2: state_closure_kernel<T, 2><<<grid, 256, 0, st>>>(g, state, e_n, e_n1, e_slot, w, le, rep0); break;
+    case 1: state_closure_kernel<T, 1><<<grid, 256, smem, st>>>(g, state, e_n, e_n1, e_slot, w, wt, le, rep0); break;
+    case 2: state_closure_kernel<T, 2><<<grid, 256, smem, st>>>(g, state, e_n, e_n1, e_slot, w, wt, le, rep0); break;
     default: return cudaErrorInvalidValue;
     }
+    return cudaGetLastError();
+}
+
+size_t closure_state_prepared_offset(int S) { return (sc_nweights(S) + 3) & ~(size_t)3; }  // 16-byte aligned
+
+size_t closure_state_prepared_floats(int S)
+{
+    return (size_t)sc_nin(S) * NH + 2 * (size_t)NH * NH + (size_t)NH * sc_nout(S);
+}
+
+cudaError_t launch_closure_state_prepare(int S, const float *w, float *wt, cudaStream_t st)
+{
+    if (S < 1 || S > 2) return cudaErrorInvalidValue;
+    static bool attr_set[3] = {false, false, false};
+    if (!attr_set[S]) {
+        const int smem = (int)(2 * SPTS * ILD * sizeof(float));
+        cudaError_t e = S == 1 ? cudaFuncSetAttribute(state_closure_kernel<double, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)
+                               : cudaFuncSetAttribute(state_closure_kernel<double, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e != cudaSuccess) return e;
+        attr_set[S] = true;
+    }
+    state_weights_prepare_kernel<<<256, 256, 0, st>>>(sc_nin(S), sc_nout(S), w, wt);
     return cudaGetLastError();
 }
 template cudaError_t launch_closure_state_fill<double>(const GridInfo &, double *, int, int, int, const float *, double,

@@ -206,6 +206,11 @@ cudaError_t launch_closure_infer(const GridInfo &g, double eta, const float *w_d
 // State-input closure (qhfpe_closure.cu): weights per S; fill the W^(N+1) slot of `state` from tiers
 // e_n, e_n1 of replicas rep0 .. rep0 + n_rep - 1; training samples of the tier e_t from e_t1, e_t2.
 size_t closure_state_n_weights(int S);
+// the fill reads w = the weights followed, at closure_state_prepared_offset(S) floats, by the
+// closure_state_prepared_floats(S) that launch_closure_state_prepare writes from them
+size_t closure_state_prepared_offset(int S);
+size_t closure_state_prepared_floats(int S);
+cudaError_t launch_closure_state_prepare(int S, const float *w, float *wt, cudaStream_t st);
 template <typename T>
 cudaError_t launch_closure_state_fill(const GridInfo &g, T *state, int e_n, int e_n1, int e_slot, const float *w,
                                       double eta, int rep0, int n_rep, cudaStream_t st);

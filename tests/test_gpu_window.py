@@ -29,8 +29,9 @@ def rel(a, b):
 def _models():
     two_k2 = qi.photoisomerization_two_state(nq=26, n_p=128, depth=3, n_matsubara=2)
     term = qi.harmonic_two_state(nq=30, n_p=128, pr=(-16.0, 16.0), depth=3)
+    # dt inside the RK4 stability bound (the quartic surface reaches ~900 at q + r/2 on this p grid)
     one = qi.single_state(lambda q: 0.5 * q * q + 0.02 * q ** 4, nq=37, n_p=128, pr=(-16.0, 16.0), depth=3,
-                          closure=1)
+                          closure=1, dt=0.001)
     per = qi.photoisomerization_two_state(nq=20, n_p=128, depth=2, n_matsubara=1)
     per["periodic_q"] = 1
     return {"two_state_K2": two_k2, "terminator": term, "one_state": one, "periodic": per}
@@ -64,11 +65,14 @@ def test_window_steps_against_oracle_and_other_kernel(name, monkeypatch):
     W = qi.random_state(m, seed=22, hermitian=True)
     ref_W, ref_tr = oracle.Oracle(m).step(W, 12)
     out = {}
+    # a pinned tile skips the timed choice between the forms, so that each form certainly runs
+    monkeypatch.setenv("QHFPE_TILE_ROWS", "2")
     for flag in ("1", "0"):
         monkeypatch.setenv("QHFPE_FUSED_WINDOW", flag)
         P = _P(m)
         P.set_state(W)
         tr = P.step(12, record_trace=True)[0]
+        assert P.stage_form() == int(flag)
         out[flag] = (P.get_state(0), tr)
         P.close()
     got, tr = out["1"]
@@ -91,14 +95,17 @@ def test_window_learned_closure_slot():
     res = {}
     for flag in ("1", "0"):
         os.environ["QHFPE_FUSED_WINDOW"] = flag
+        os.environ["QHFPE_TILE_ROWS"] = "2"
         try:
             P = Propagator(m, T, precision="mixed")
             P.closure_load(w)
             P.set_state(W)
             P.step(5)
+            assert P.stage_form() == int(flag)
             res[flag] = P.get_state(0)
             P.close()
         finally:
             os.environ.pop("QHFPE_FUSED_WINDOW", None)
+            os.environ.pop("QHFPE_TILE_ROWS", None)
     assert np.all(np.isfinite(res["1"]))
     assert rel(res["1"], res["0"]) < 2e-6
