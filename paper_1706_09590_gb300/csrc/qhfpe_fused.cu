@@ -159,29 +159,11 @@ cudaError_t launch_fused_t(const GridInfo &g, const ElemInfo *elems, const Fused
         if (form != 0 && fused_window_applies(g, terms, Pg != nullptr))
             return launch_window_t<S, MIXED>(g, elems, tab, v_in, y, y0, v_out, y0_out, h, mode, rep0, n_rep, st);
     }
-    int tq = tq_req > 0 ? tq_req : fused_rows_per_tile(NP, S, sizeof(T));
-    const int tmax = fused_max_rows(NP, S, sizeof(T));  // the shared-memory limit set at preparation
-    if (tq > tmax) tq = tmax;
-    if (tq > g.nq) tq = g.nq;
-    const size_t smem = fused_smem_bytes(tq, NP, S, sizeof(T));
-    const int tiles = (g.nq + tq - 1) / tq;
-    const long blocks = (long)tiles * n_rep * g.n_elem;
-    if (blocks <= 0) return cudaSuccess;
-    const StageScalars<T> sc = stage_scalars<T>(g, h);
-    // launched with programmatic stream serialisation: its blocks may be scheduled while the previous
-    // kernel drains (the kernel waits for it before reading the state)
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3((unsigned)blocks);
-    cfg.blockDim = dim3(FTHREADS);
-    cfg.dynamicSmemBytes = smem;
-    cfg.stream = st;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    attr[0].val.programmaticStreamSerializationAllowed = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, fused_stage_kernel<T, NP, S, MIXED, false>, g, elems, tab, sc, v_in, y, y0, v_out,
-                              y0_out, h, mode, terms, rep0, n_rep, tq, Pg, (const MultiMember<T> *)nullptr, 0, 0);
+    if (g.c2 != 0.0)  // the nonlinear coupling's terms: the instantiation of qhfpe_fused_nl.cu
+        return launch_fused_nl<T, MIXED>(g, elems, tab, v_in, y, y0, v_out, y0_out, h, mode, terms, rep0, n_rep, st, Pg,
+                                         tq_req);
+    return launch_general_t<T, NP, S, MIXED, false>(g, elems, tab, v_in, y, y0, v_out, y0_out, h, mode, terms, rep0,
+                                                    n_rep, st, Pg, tq_req);
 }
 
 template <typename T, int NP, int S, bool MIXED>
@@ -189,8 +171,9 @@ cudaError_t prepare_fused_t()
 {
     const int tq = fused_max_rows(NP, S, sizeof(T));
     const size_t smem = fused_smem_bytes(tq, NP, S, sizeof(T));
-    cudaError_t e = cudaFuncSetAttribute(fused_stage_kernel<T, NP, S, MIXED, false>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = prepare_general_t<T, NP, S, MIXED, false>();
+    if (e != cudaSuccess) return e;
+    e = prepare_fused_nl<T, MIXED>(NP, S);
     if (e != cudaSuccess) return e;
     if constexpr (sizeof(T) == 4 && NP == 128 && S <= 2) {
         constexpr int TQ = WinTile<S>::TQ;

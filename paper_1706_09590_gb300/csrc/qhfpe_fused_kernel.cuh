@@ -405,7 +405,9 @@ __device__ __forceinline__ void potential_in_place(typename V2<T>::type *X, cons
 // autotuner).  The other arguments are then taken from the member.
 // The block `bid` of a fused stage launch (see fused_stage_kernel below); also called in a loop by the
 // persistent kernel (a barrier must separate two calls of one block: shared memory is reused).
-template <typename T, int NP, int S, bool MIXED, bool MULTI>
+// NL: the terms of the nonlinear coupling (GridInfo::c2 != 0) are compiled in; NL = false requires
+// c2 = 0 (the linear coupling of every workload but the NEXT-3b one keeps their registers free).
+template <typename T, int NP, int S, bool MIXED, bool MULTI, bool NL>
 __device__ __forceinline__ void
 fused_stage_body(unsigned bid, GridInfo g, const ElemInfo *__restrict__ elems, FusedTables<T> tab, StageScalars<T> sc,
                  const T *__restrict__ v_in, const T *y, const double *y0, T *v_out, double *y0_out, double h, int mode,
@@ -486,7 +488,7 @@ fused_stage_body(unsigned bid, GridInfo g, const ElemInfo *__restrict__ elems, F
         }
         const int n_dn = (terms & 16) ? E.n_dn : 0;
         for (int pass = 0; pass < 2; ++pass) {
-            if (pass == 0 && (terms & 16)) {  // |m| = 2 couplings of the nonlinear coupling: G only
+            if (NL && pass == 0 && (terms & 16)) {  // |m| = 2 couplings of the nonlinear coupling: G only
                 for (int a = 0; a < E.n_d2; ++a, ++n) {
                     nb_off[n] = (long long)(E.d2[a] - e) * (long long)g.elem_stride;
                     nb_wg[n] = (T)E.w2[a];
@@ -502,7 +504,7 @@ fused_stage_body(unsigned bid, GridInfo g, const ElemInfo *__restrict__ elems, F
             }
             if (pass == 0) s_cnt[1] = n;
         }
-        const int n_mx = (terms & 16) ? E.n_mx : 0;
+        const int n_mx = NL && (terms & 16) ? E.n_mx : 0;
         for (int a = 0; a < n_mx; ++a) {
             mx_off[a] = (long long)(E.mx[a] - e) * (long long)g.elem_stride;
             mx_w[a] = (T)(E.wmx[a] / (12.0 * g.dq));
@@ -547,7 +549,7 @@ fused_stage_body(unsigned bid, GridInfo g, const ElemInfo *__restrict__ elems, F
         __syncthreads();
         potential_in_place<T, NP, S>(X, tw, tab, nq, i0, rows,
                                      ((terms & 4) ? sc.fdelta : (T)0) + ((s_cnt[3] != 0) ? sc.fterm : (T)0), s_ngam,
-                                     s_lpp, g.c2, g.q_min, g.dq);
+                                     s_lpp, NL ? g.c2 : 0.0, g.q_min, g.dq);
     }
 
     // ---- phase B: one warp per p-row ------------------------------------------------------------
@@ -706,7 +708,7 @@ fused_stage_body(unsigned bid, GridInfo g, const ElemInfo *__restrict__ elems, F
         }
         // nonlinear coupling V = q + c2 q^2: phi = 1 + 2 c2 q_i multiplies Phi = -phi d/dp and the
         // p phi part of Lambda^(1); its d2/dp dq part enters G below (block-uniform branches)
-        const T phi = g.c2 != 0.0 ? (T)(1.0 + 2.0 * g.c2 * (g.q_min + i * g.dq)) : (T)1;
+        const T phi = NL && g.c2 != 0.0 ? (T)(1.0 + 2.0 * g.c2 * (g.q_min + i * g.dq)) : (T)1;
         if (n_d0 < n_nb) {
             for (int a = n_d0; a < n_nb; ++a) {
                 const T *u = v_in + (long long)o + nb_off[a];
@@ -719,7 +721,7 @@ fused_stage_body(unsigned bid, GridInfo g, const ElemInfo *__restrict__ elems, F
                 v_axpy<VEC>(hr, wa, xr);
                 v_axpy<VEC>(hi, wa, xi);
             }
-            if (g.c2 != 0.0) {
+            if (NL && g.c2 != 0.0) {
 #pragma unroll
                 for (int v = 0; v < VEC; ++v) {
                     hr[v] *= phi;
@@ -729,8 +731,8 @@ fused_stage_body(unsigned bid, GridInfo g, const ElemInfo *__restrict__ elems, F
             v_fma<VEC>(ar, pcol, hr);
             v_fma<VEC>(ai, pcol, hi);
         }
-        const int n_mx = s_nmx;
-        if (g.c2 != 0.0) {
+        const int n_mx = NL ? s_nmx : 0;
+        if (NL && g.c2 != 0.0) {
             // G' = phi G + sum_a wmx_a d/dq W^(mx_a) (4th-order central in q, rows i-2..i+2), so that
             // d/dp G' = phi dG/dp + wmx d2/dp dq W: the p-stencil below covers both
 #pragma unroll
@@ -861,7 +863,7 @@ fused_stage_body(unsigned bid, GridInfo g, const ElemInfo *__restrict__ elems, F
     }
 }
 
-template <typename T, int NP, int S, bool MIXED, bool MULTI>
+template <typename T, int NP, int S, bool MIXED, bool MULTI, bool NL>
 __global__ void __launch_bounds__(FTHREADS, FusedOcc<T, NP, S>::blocks - (MULTI && FusedOcc<T, NP, S>::blocks > 2 ? 1 : 0))
 fused_stage_kernel(GridInfo g, const ElemInfo *__restrict__ elems, FusedTables<T> tab, StageScalars<T> sc, const T *__restrict__ v_in,
                    const T *y, const double *y0, T *v_out, double *y0_out, double h, int mode, int terms, int rep0,
@@ -871,8 +873,48 @@ fused_stage_kernel(GridInfo g, const ElemInfo *__restrict__ elems, FusedTables<T
     // block of this one has started; the body waits (griddepcontrol.wait) for this grid's completion
     // before touching the state.  Both are no-ops for a plain launch.
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
-    fused_stage_body<T, NP, S, MIXED, MULTI>(blockIdx.x, g, elems, tab, sc, v_in, y, y0, v_out, y0_out, h, mode, terms,
+    fused_stage_body<T, NP, S, MIXED, MULTI, NL>(blockIdx.x, g, elems, tab, sc, v_in, y, y0, v_out, y0_out, h, mode, terms,
                                              rep0, n_rep, tq, Pg, mem, n_mem, k);
+}
+
+
+// One stage of the single-model kernel at tile height tq_req (0: default), launched with programmatic
+// stream serialisation: its blocks may be scheduled while the previous kernel drains (the kernel waits
+// for it before reading the state).
+template <typename T, int NP, int S, bool MIXED, bool NL>
+cudaError_t launch_general_t(const GridInfo &g, const ElemInfo *elems, const FusedTables<T> &tab, const T *v_in,
+                             const T *y, const double *y0, T *v_out, double *y0_out, double h, int mode, int terms,
+                             int rep0, int n_rep, cudaStream_t st, const T *Pg, int tq_req)
+{
+    int tq = tq_req > 0 ? tq_req : fused_rows_per_tile(NP, S, sizeof(T));
+    const int tmax = fused_max_rows(NP, S, sizeof(T));  // the shared-memory limit set at preparation
+    if (tq > tmax) tq = tmax;
+    if (tq > g.nq) tq = g.nq;
+    const size_t smem = fused_smem_bytes(tq, NP, S, sizeof(T));
+    const int tiles = (g.nq + tq - 1) / tq;
+    const long blocks = (long)tiles * n_rep * g.n_elem;
+    if (blocks <= 0) return cudaSuccess;
+    const StageScalars<T> sc = stage_scalars<T>(g, h);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)blocks);
+    cfg.blockDim = dim3(FTHREADS);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, fused_stage_kernel<T, NP, S, MIXED, false, NL>, g, elems, tab, sc, v_in, y, y0,
+                              v_out, y0_out, h, mode, terms, rep0, n_rep, tq, Pg, (const MultiMember<T> *)nullptr, 0, 0);
+}
+
+template <typename T, int NP, int S, bool MIXED, bool NL>
+cudaError_t prepare_general_t()
+{
+    const size_t smem = fused_smem_bytes(fused_max_rows(NP, S, sizeof(T)), NP, S, sizeof(T));
+    return cudaFuncSetAttribute(fused_stage_kernel<T, NP, S, MIXED, false, NL>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
 }
 
 }  // namespace

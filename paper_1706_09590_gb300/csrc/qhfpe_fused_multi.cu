@@ -9,7 +9,7 @@ cudaError_t launch_fused_multi_t(const MultiMember<T> *mem, int n_mem, int k, in
 {
     if (blocks <= 0) return cudaSuccess;
     const size_t smem = fused_smem_bytes(tq, NP, S, sizeof(T));
-    fused_stage_kernel<T, NP, S, MIXED, true><<<(unsigned)blocks, FTHREADS, smem, st>>>(
+    fused_stage_kernel<T, NP, S, MIXED, true, true><<<(unsigned)blocks, FTHREADS, smem, st>>>(
         GridInfo{}, nullptr, FusedTables<T>{}, StageScalars<T>{}, nullptr, nullptr, nullptr, nullptr, nullptr, 0.0, 0, 0, 0,
         1, tq, nullptr, mem, n_mem, k);
     return cudaGetLastError();
@@ -18,7 +18,7 @@ cudaError_t launch_fused_multi_t(const MultiMember<T> *mem, int n_mem, int k, in
 template <typename T, int NP, int S, bool MIXED>
 cudaError_t prepare_fused_multi_t(size_t smem)
 {
-    return cudaFuncSetAttribute(fused_stage_kernel<T, NP, S, MIXED, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    return cudaFuncSetAttribute(fused_stage_kernel<T, NP, S, MIXED, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)smem);
 }
 

@@ -157,6 +157,14 @@ cudaError_t launch_fused_multi(int np, int S, const MultiMember<T> *mem, int n_m
 // shared-memory limit of the batch instantiation (called by prepare_fused)
 template <typename T, bool MIXED>
 cudaError_t prepare_fused_multi(int np, int S, size_t smem);
+// The single-model stage with the nonlinear coupling's terms compiled in (qhfpe_fused_nl.cu; launch_fused
+// takes it when GridInfo::c2 != 0), and its shared-memory limit (called by prepare_fused).
+template <typename T, bool MIXED>
+cudaError_t launch_fused_nl(const GridInfo &g, const ElemInfo *elems, const FusedTables<T> &tab, const T *v_in,
+                            const T *y, const double *y0, T *v_out, double *y0_out, double h, int mode, int terms,
+                            int rep0, int n_rep, cudaStream_t st, const T *Pg, int tq);
+template <typename T, bool MIXED>
+cudaError_t prepare_fused_nl(int np, int S);
 // Non-Condon dipole super-operator (side 1: mu^->, 2: mu^<-, 3: mu^x, times scale) on n_elem elements of
 // n_rep replicas (reps: device list or nullptr for 0..n_rep-1), in place, through an FFT along p.
 // TL, TR: [S][S][nq][np] r-space multipliers mu(q + r/2), mu(q - r/2) / np in the fused FFT's order;

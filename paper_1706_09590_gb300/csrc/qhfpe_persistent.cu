@@ -145,7 +145,7 @@ persistent_steps_kernel(const MultiMember<T> *__restrict__ mem, long n_items, in
         for (int k = 4; k >= 1; --k) {
             for (long it = blockIdx.x; it < n_items; it += gridDim.x) {
                 __syncthreads();  // the previous item's shared memory is free
-                fused_stage_body<T, NP, S, MIXED, true>((unsigned)it, GridInfo{}, nullptr, FusedTables<T>{},
+                fused_stage_body<T, NP, S, MIXED, true, true>((unsigned)it, GridInfo{}, nullptr, FusedTables<T>{},
                                                          StageScalars<T>{}, nullptr, nullptr, nullptr, nullptr, nullptr,
                                                          0.0, 0, 0, 0, 1, tq, nullptr, mem, 1, k);
             }
