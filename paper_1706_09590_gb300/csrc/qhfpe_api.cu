@@ -900,11 +900,11 @@ qhfpe_status run_persistent(qhfpe *h, Prop &P, long n_steps, double *trace_dev, 
         if (P.mixed)
             e = launch_persistent<float, true>(P.g.np, P.g.S, (const MultiMember<float> *)P.pdesc, n_items, P.pdesc_tq,
                                                len, ts, trs, P.m->mu, P.partial, nc, trace_dev, stride, 1 + done,
-                                               P.pbar, err, limit, st);
+                                               P.pbar, err, limit, P.g.c2 != 0.0, st);
         else
             e = launch_persistent<double, false>(P.g.np, P.g.S, (const MultiMember<double> *)P.pdesc, n_items,
                                                  P.pdesc_tq, len, ts, trs, P.m->mu, P.partial, nc, trace_dev, stride,
-                                                 1 + done, P.pbar, err, limit, st);
+                                                 1 + done, P.pbar, err, limit, P.g.c2 != 0.0, st);
         QH_CK(h, e);
         int bad = 0;
         QH_CK(h, cudaMemcpyAsync(&bad, err, sizeof(int), cudaMemcpyDeviceToHost, st));

@@ -412,24 +412,27 @@ __device__ __forceinline__ void
 fused_stage_body(unsigned bid, GridInfo g, const ElemInfo *__restrict__ elems, FusedTables<T> tab, StageScalars<T> sc,
                  const T *__restrict__ v_in, const T *y, const double *y0, T *v_out, double *y0_out, double h, int mode,
                  int terms, int rep0, int n_rep, int tq, const T *__restrict__ Pg, const MultiMember<T> *__restrict__ mem,
-                 int n_mem, int k)
+                 int n_mem, int k, bool warm = false)
 {
+    // warm: this block's previous call was for the same member and tile height (the persistent kernel's
+    // one-member loop), so the member's description, twiddles, p grid and r-space eigenvalues are still
+    // in shared memory
     if constexpr (MULTI) {
         __shared__ MultiMember<T> M;
         __shared__ int s_m;
-        if (threadIdx.x == 0) {
-            int m = 0;
-            while (m + 1 < n_mem && mem[m + 1].block0 <= (long)bid) ++m;
-            s_m = m;
-        }
-        __syncthreads();
-        {
+        if (!warm) {
+            if (threadIdx.x == 0) {
+                int m = 0;
+                while (m + 1 < n_mem && mem[m + 1].block0 <= (long)bid) ++m;
+                s_m = m;
+            }
+            __syncthreads();
             static_assert(sizeof(MultiMember<T>) % sizeof(int) == 0, "member size");
             const int *src = reinterpret_cast<const int *>(mem + s_m);
             int *dst = reinterpret_cast<int *>(&M);
             for (int w = threadIdx.x; w < (int)(sizeof(MultiMember<T>) / sizeof(int)); w += FTHREADS) dst[w] = src[w];
+            __syncthreads();
         }
-        __syncthreads();
         g = M.g;
         elems = M.elems;
         tab = M.tab;
@@ -515,11 +518,12 @@ fused_stage_body(unsigned bid, GridInfo g, const ElemInfo *__restrict__ elems, F
         s_cnt[3] = (terms & 8) && E.terminator;
         s_ngam = (terms & 4) ? (T)E.ngam : (T)0;
     }
-    for (int t = threadIdx.x; t < NP; t += FTHREADS) {
-        tw[t] = C{tab.tw[2 * t], tab.tw[2 * t + 1]};
-        pgrid[t] = (T)(g.p_min + t * g.dp);
-        s_lpp[t] = tab.lpp[t];
-    }
+    if (!warm)
+        for (int t = threadIdx.x; t < NP; t += FTHREADS) {
+            tw[t] = C{tab.tw[2 * t], tab.tw[2 * t + 1]};
+            pgrid[t] = (T)(g.p_min + t * g.dp);
+            s_lpp[t] = tab.lpp[t];
+        }
 
     // the previous launch on the stream (the stage whose output this one reads) has completed and its
     // writes are visible

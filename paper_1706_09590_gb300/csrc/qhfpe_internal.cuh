@@ -180,12 +180,13 @@ cudaError_t launch_dipole_fft(const GridInfo &g, const T *TL, const T *TR, const
 // grid barriers between stages (bar_words: two zeroed words, count and generation; *err set to 1 when a
 // wait exceeded limit_ns).  trace_out (device, may be nullptr): Tr{mu W^(0)} of every replica after
 // each step into slots slot0 .. slot0 + n_steps - 1 of [n_rep][trace_stride] complex, from the FP64
-// trace_state (Condon mu), chunk partials in `partial` ([n_rep][n_chunks][2]).
+// trace_state (Condon mu), chunk partials in `partial` ([n_rep][n_chunks][2]).  nonlinear: the member has
+// c2 != 0 (the instantiation with those terms).
 template <typename T, bool MIXED>
 cudaError_t launch_persistent(int np, int S, const MultiMember<T> *mem, long n_items, int tq, int n_steps,
                               const double *trace_state, size_t trace_rep_stride, const double *mu, double *partial,
                               int n_chunks, double *trace_out, long trace_stride, long slot0, unsigned *bar_words,
-                              int *err, unsigned long long limit_ns, cudaStream_t st);
+                              int *err, unsigned long long limit_ns, bool nonlinear, cudaStream_t st);
 // The barrier alone on four one-warp blocks; withhold = 1 keeps block 0 away, so the others give up.
 cudaError_t launch_barrier_selftest(unsigned *bar_words, int *err, unsigned long long limit_ns, int withhold,
                                     cudaStream_t st);

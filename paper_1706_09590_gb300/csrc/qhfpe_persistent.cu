@@ -135,19 +135,22 @@ __device__ bool trace_step(const GridInfo &g, const TraceJob &tj, long slot, con
     return true;
 }
 
-template <typename T, int NP, int S, bool MIXED>
+// NL: the nonlinear coupling's terms compiled in (the member's c2 != 0).
+template <typename T, int NP, int S, bool MIXED, bool NL>
 __global__ void __launch_bounds__(FTHREADS, FusedOcc<T, NP, S>::blocks - (FusedOcc<T, NP, S>::blocks > 2 ? 1 : 0))
 persistent_steps_kernel(const MultiMember<T> *__restrict__ mem, long n_items, int tq, int n_steps, TraceJob tj,
                         GridBarrier bar)
 {
     const GridInfo g = mem->g;
+    bool warm = false;  // the member's description and tables stay in shared memory after the first item
     for (int s = 0; s < n_steps; ++s) {
         for (int k = 4; k >= 1; --k) {
             for (long it = blockIdx.x; it < n_items; it += gridDim.x) {
                 __syncthreads();  // the previous item's shared memory is free
-                fused_stage_body<T, NP, S, MIXED, true, true>((unsigned)it, GridInfo{}, nullptr, FusedTables<T>{},
-                                                         StageScalars<T>{}, nullptr, nullptr, nullptr, nullptr, nullptr,
-                                                         0.0, 0, 0, 0, 1, tq, nullptr, mem, 1, k);
+                fused_stage_body<T, NP, S, MIXED, true, NL>((unsigned)it, GridInfo{}, nullptr, FusedTables<T>{},
+                                                           StageScalars<T>{}, nullptr, nullptr, nullptr, nullptr,
+                                                           nullptr, 0.0, 0, 0, 0, 1, tq, nullptr, mem, 1, k, warm);
+                warm = true;
             }
             if (!grid_barrier(bar)) return;
         }
@@ -165,11 +168,11 @@ __global__ void barrier_selftest_kernel(GridBarrier bar, int withhold)
     grid_barrier(bar);
 }
 
-template <typename T, int NP, int S, bool MIXED>
+template <typename T, int NP, int S, bool MIXED, bool NL>
 cudaError_t launch_persistent_t(const MultiMember<T> *mem, long n_items, int tq, int n_steps, const TraceJob &tj,
                                 const GridBarrier &bar, cudaStream_t st)
 {
-    auto kern = persistent_steps_kernel<T, NP, S, MIXED>;
+    auto kern = persistent_steps_kernel<T, NP, S, MIXED, NL>;
     const size_t smem = fused_smem_bytes(tq, NP, S, sizeof(T));
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
@@ -191,12 +194,14 @@ template <typename T, bool MIXED>
 cudaError_t launch_persistent(int np, int S, const MultiMember<T> *mem, long n_items, int tq, int n_steps,
                               const double *trace_state, size_t trace_rep_stride, const double *mu, double *partial,
                               int n_chunks, double *trace_out, long trace_stride, long slot0, unsigned *bar_words,
-                              int *err, unsigned long long limit_ns, cudaStream_t st)
+                              int *err, unsigned long long limit_ns, bool nonlinear, cudaStream_t st)
 {
     TraceJob tj{trace_out != nullptr, trace_state, trace_rep_stride, mu, partial, n_chunks, trace_out, trace_stride,
                 slot0};
     GridBarrier bar{bar_words, bar_words + 1, err, limit_ns};
-#define QH_CALL(NP_, S_) launch_persistent_t<T, NP_, S_, MIXED>(mem, n_items, tq, n_steps, tj, bar, st)
+#define QH_CALL(NP_, S_)                                                                              \
+    (nonlinear ? launch_persistent_t<T, NP_, S_, MIXED, true>(mem, n_items, tq, n_steps, tj, bar, st)   \
+               : launch_persistent_t<T, NP_, S_, MIXED, false>(mem, n_items, tq, n_steps, tj, bar, st))
     switch (np * 8 + S) {
     case 32 * 8 + 1: return QH_CALL(32, 1);
     case 32 * 8 + 2: return QH_CALL(32, 2);
@@ -225,7 +230,8 @@ cudaError_t launch_barrier_selftest(unsigned *bar_words, int *err, unsigned long
 
 template cudaError_t launch_persistent<float, true>(int, int, const MultiMember<float> *, long, int, int, const double *,
                                                     size_t, const double *, double *, int, double *, long, long,
-                                                    unsigned *, int *, unsigned long long, cudaStream_t);
+                                                    unsigned *, int *, unsigned long long, bool, cudaStream_t);
 template cudaError_t launch_persistent<double, false>(int, int, const MultiMember<double> *, long, int, int,
                                                       const double *, size_t, const double *, double *, int, double *,
-                                                      long, long, unsigned *, int *, unsigned long long, cudaStream_t);
+                                                      long, long, unsigned *, int *, unsigned long long, bool,
+                                                      cudaStream_t);

@@ -1,6 +1,7 @@
 """The nonlinear system-bath coupling V(q) = q + c2 q^2 (Sec. II) through the C ABI against the CPU
 oracle (whose operators are pinned against the density-matrix hierarchy): each right-hand-side term
-alone, RK4 steps with traces, the linear response, and a heterogeneous batch with a nonlinear member.
+alone, RK4 steps with traces, the linear response, a heterogeneous batch with a nonlinear member and
+persistent propagation.
 Tolerances as in the other parity tests: FP64 1e-12 (one right-hand side) / 1e-11 (steps) / 1e-10
 (response), mixed 2e-5 / 1e-5 / 1e-4."""
 import numpy as np
@@ -117,6 +118,22 @@ def test_nonlinear_member_in_a_heterogeneous_batch():
     B.close()
     for P in Ps:
         P.close()
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-11), ("mixed", 1e-5)])
+def test_nonlinear_persistent_steps(precision, tol):
+    """Persistent propagation (one cooperative launch over the batch kernel, which carries the nonlinear
+    terms) against the oracle, with the trace reduced in the same launch."""
+    m = MODELS["harmonic"]
+    W = qi.random_state(m, seed=35)
+    P = _P(m, precision)
+    P.set_persistent(True)
+    P.set_state(W)
+    tr = P.step(9, record_trace=True)[0]
+    got = P.get_state(0)
+    P.close()
+    ref_W, ref_tr = oracle.Oracle(m).step(W, 9)
+    assert rel(got, ref_W) < tol and rel(tr, ref_tr) < tol, (rel(got, ref_W), rel(tr, ref_tr))
 
 
 def test_nonlinear_coupling_rejects_closures():
