@@ -297,7 +297,7 @@ def linear_absorption_measure(stream):
 
 
 def learned_closure_measure(stream):
-    """Learned closures on the config-1 model at 96 x 128 (q, p in [-8, 8)): trained on depth-12 FP64 runs
+    """Learned closures on the two-state harmonic model at 96 x 128 (q, p in [-8, 8)): trained on depth-12 FP64 runs
     at eta in {0.2, 0.5, 1}, deployed at depth 4, judged at the held-out eta = 0.3 against depth 12: R1
     over 10 time units for the truncation, the Eq. (GMFP) terminator, the coefficient form (QHFPE_LEARNED)
     and the state-input network (QHFPE_LEARNED_STATE); their training times (device kernels), the wall
@@ -441,7 +441,7 @@ def paper_workload_measure(stream):
 
 
 def hetero_batch_measure(stream):
-    """Eight config-1-shaped models that differ in q grid, depth, closure, bath and dt (np = 32, two
+    """Eight two-state harmonic models that differ in q grid, depth, closure, bath and dt (np = 32, two
     states, FP32 mixed form), advanced together as one heterogeneous batch (every Horner stage of all
     eight one launch) and one after another on their own: wall time of the same RK4 steps, inputs
     resident on the device."""
@@ -602,11 +602,11 @@ def fp64_form_measure(stream, m, T, fp64_peak_tflops, peak_source):
                          "ms_per_launch": stage_ms, "flops_per_launch": fl}}
 
 
-CONFIG2_ETAS = (0.1, 1.0, 5.0)
-CONFIG2_COUPLINGS = (0.2, 0.5, 1.0, 2.0)
+SWEEP_ETAS = (0.1, 1.0, 5.0)
+SWEEP_COUPLINGS = (0.2, 0.5, 1.0, 2.0)
 
 
-def config2_sweep_measure(stream):
+def eta_coupling_sweep_measure(stream):
     """The benchmark model over its stated parameter ranges (eta in {0.1, 1, 5} x diabatic coupling in
     {0.2, 0.5, 1, 2}, 96 x 128, depth 8, two Matsubara terms + delta-term, dt = 0.8 x the stability
     bound): linear response over one time unit and the transient-absorption response (t1 = 0, waiting
@@ -617,8 +617,8 @@ def config2_sweep_measure(stream):
     import qhfpe_inputs as qi
     from paper_1706_09590_gb300 import Propagator
     rows = []
-    for eta in CONFIG2_ETAS:
-        for coupling in CONFIG2_COUPLINGS:
+    for eta in SWEEP_ETAS:
+        for coupling in SWEEP_COUPLINGS:
             m = qi.photoisomerization_two_state(eta=eta, coupling=coupling)
             T = qi.u_table(m)
             E = Propagator(m, T, precision="fp64", stream=stream)
@@ -726,8 +726,8 @@ def main():
     ap.add_argument("--no-forms", action="store_true",
                     help="skip the tensor-core and FP64 forms on the benchmark workload")
     ap.add_argument("--no-closure", action="store_true",
-                    help="skip the learned-closure measurement (config-5 shape)")
-    ap.add_argument("--no-config2-sweep", action="store_true",
+                    help="skip the learned-closure measurement (two-state harmonic model, 96 x 128)")
+    ap.add_argument("--no-sweep", action="store_true",
                     help="skip the eta x coupling sweep of the benchmark model (FP64 vs mixed spectra)")
     args = ap.parse_args()
     if args.impl == "reference":
@@ -900,8 +900,8 @@ def main():
     if args.precision == "mixed" and not args.no_forms:
         timed("tensor_core", tensor_core_measure, stream, m, T, tc_peak, tc_src)
         timed("fp64_form", fp64_form_measure, stream, m, T, fp64_peak, fp64_src)
-    if not args.no_config2_sweep:
-        timed("config2_sweep", config2_sweep_measure, stream)
+    if not args.no_sweep:
+        timed("eta_coupling_sweep", eta_coupling_sweep_measure, stream)
     if not args.no_closure:
         timed("learned_closure", learned_closure_measure, stream)
     if not args.no_spectrum:

@@ -373,7 +373,7 @@ qhfpe_status qhfpe_closure_loss_grad(const float *w, const double *X, const doub
 qhfpe_status qhfpe_closure_train(float *w, const double *X, const double *stats, int n_points, int n_iters,
                                  int batch, double lr, double ridge, unsigned seed, double *loss_history);
 
-/* ---- State-input learned closure (BASELINE's literal network; no counterpart in the paper) ---------
+/* ---- State-input learned closure (the network reads the state; no counterpart in the paper) ------
  * With closure = QHFPE_LEARNED_STATE the missing element W^(N+1) of the deepest tier (one Drude mode,
  * a chain) is predicted at every grid point (q_i, p_l) by a perceptron of the state itself: inputs
  * (q_i / 8, p_l / 8, ln eta) followed by the 3 x 3 patches (q_{i+a}, p_{l+b}), a, b in {-1, 0, 1} (q: zero

@@ -62,7 +62,7 @@ def train(X, stats, n_iters=3000, batch=4096, lr=1e-3, ridge=0.01, seed=1706, we
     return closure_train(w0, X, stats, n_iters, batch=batch, lr=lr, ridge=ridge, seed=seed)
 
 
-# ---- state-input network (BASELINE's literal closure; QHFPE_LEARNED_STATE) -------------------------
+# ---- state-input network (QHFPE_LEARNED_STATE): the network reads the deepest tiers' local values ------
 def initial_state_weights(S, seed=1706):
     """Glorot-uniform hidden layers, zero output layer (the untrained network predicts zero: truncation),
     unit scales."""

@@ -179,7 +179,7 @@ def random_state(model, seed=SEED, replicas=None, hermitian=False, zero_p_edges=
     return np.ascontiguousarray(W)
 
 
-CONFIGS = {
+WORKLOADS = {  # the named synthetic workloads at their full sizes
     "harmonic_32x32_d3": lambda: harmonic_two_state(),
     "photoiso_96x128_d8": lambda: photoisomerization_two_state(),
     "three_state_256x256_d10": lambda: three_state(),

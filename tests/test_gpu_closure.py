@@ -113,7 +113,7 @@ HELD_OUT_ETAS = (0.3, 0.7)
 
 
 def test_learned_closure_gains_over_truncation(torch):
-    """Config-1 model on 96 x 128: trained on depth-12 runs at eta in {0.1, 0.2, 0.5, 1}, deployed at
+    """The two-state harmonic model on 96 x 128: trained on depth-12 runs at eta in {0.1, 0.2, 0.5, 1}, deployed at
     depth 4, judged on held-out eta (0.3, 0.7) against the depth-12 hierarchy: linear response R1 and
     a small third-order schedule.  The learned closure must beat the plain depth-4 truncation; the
     terminator of Eq. (GMFP) is reported beside it.  (Depth-12 hierarchies of this model grow at

@@ -127,7 +127,7 @@ def test_state_closure_steps_match_oracle(torch):
 
 
 def test_state_closure_additivity_defect_and_error(torch):
-    """Trained on depth-10 runs of the config-1 model (32 x 32) at eta in {0.2, 0.5, 1}, deployed at depth
+    """Trained on depth-10 runs of the two-state harmonic model (32 x 32) at eta in {0.2, 0.5, 1}, deployed at depth
     4, judged at eta = 0.3 against depth 10: the additivity defect of the third-order response (ket +
     bra against the full commutator) of the state-input closure, against the coefficient form, where
     it is rounding only; and the R1 errors of both learned forms, the truncation and the terminator."""
