@@ -286,6 +286,26 @@ def test_full_size_rhs(precision, tol):
     assert rel(got, ref) < tol
 
 
+def test_isolated_system_decouples_the_hierarchy():
+    """eta = 0 (no bath): the couplings to lower tiers vanish (c_k = r_k = 0 in Eq. (heom)), so higher
+    tiers that start at zero are never sourced and the zeroth tier evolves as the depth-0 hierarchy,
+    i.e. the isolated system's Wigner-space equation of motion; against each other and the oracle."""
+    m = qi.harmonic_two_state(nq=20, n_p=32, depth=2, eta=0.0, closure=0)
+    W = qi.random_state(m, seed=41, hermitian=True)
+    W[1:] = 0
+    out = []
+    for mm, WW in ((m, W), (dict(m, depth=0), W[:1])):
+        P = _P(mm, "fp64")
+        P.set_state(WW)
+        P.step(20)
+        out.append(P.get_state(0))
+        P.close()
+    assert np.abs(out[0][1:]).max() == 0.0
+    assert rel(out[0][0], out[1][0]) < 1e-13
+    ref, _ = oracle.Oracle(m).step(W, 20)
+    assert rel(out[0], ref) < 1e-11
+
+
 def test_set_state_rejects_non_finite():
     from paper_1706_09590_gb300 import QhfpeError
     m = MODELS["harmonic"]
