@@ -374,16 +374,19 @@ qhfpe_status qhfpe_closure_train(float *w, const double *X, const double *stats,
                                  int batch, double lr, double ridge, unsigned seed, double *loss_history);
 
 /* ---- State-input learned closure (the network reads the state; no counterpart in the paper) ------
- * With closure = QHFPE_LEARNED_STATE the missing element W^(N+1) of the deepest tier (one Drude mode,
- * a chain) is predicted at every grid point (q_i, p_l) by a perceptron of the state itself: inputs
+ * With closure = QHFPE_LEARNED_STATE the deepest tier (one Drude mode, a chain) keeps the Eq. (GMFP)
+ * terminator, d/dp (r_0 p W^(N)) + c_0 d2W^(N)/dp2, and adds d/dp D, where D is the missing element
+ * W^(N+1) less the element the terminator stands for, r_0 p W^(N) + c_0 dW^(N)/dp (the derivatives the
+ * stencils of the right-hand side: 4th-order central, periodic p).  D is predicted at every grid
+ * point (q_i, p_l) by a perceptron of the state itself: inputs
  * (q_i / 8, p_l / 8, ln eta) followed by the 3 x 3 patches (q_{i+a}, p_{l+b}), a, b in {-1, 0, 1} (q: zero
  * outside the grid, or periodic; p periodic), of tiers N and N-1, pair by pair (j, k row-major), patch
  * row-major over (a, b), (re, im) innermost -- 36 S^2 + 3 values; three tanh layers of width 256 and a
- * linear output of 2 S^2 values, W^(N+1)_jk(q_i, p_l) (re, im) pair by pair.  The closed hierarchy is
+ * linear output of 2 S^2 values, D_jk(q_i, p_l) (re, im) pair by pair.  The closed hierarchy is
  * nonlinear in the state, so the step is classic RK4 (four right-hand sides, FP64) and pathway
  * additivity no longer holds exactly.  Inference runs in every right-hand side with bf16 weights and
- * activations and FP32 accumulation.  Until weights are loaded the slot is zero (the truncated
- * hierarchy).  The equilibrium (qhfpe_equilibrate) uses the Eq. (GMFP) terminator.  Weights (float):
+ * activations and FP32 accumulation.  Until weights are loaded D is zero (the terminator alone).  The
+ * equilibrium (qhfpe_equilibrate) uses the Eq. (GMFP) terminator.  Weights (float):
  * W1[256][36 S^2 + 3], b1[256], W2[256][256], b2, W3[256][256], b3, W4[2 S^2][256], b4, then three scales
  * (tier-N inputs, tier-(N-1) inputs, outputs: the network sees the values divided by them) --
  * qhfpe_closure_state_n_weights(S) floats. */
@@ -391,8 +394,9 @@ size_t qhfpe_closure_state_n_weights(int n_states);
 qhfpe_status qhfpe_closure_state_load(qhfpe_t *h, const float *weights, size_t n);
 /* Training samples from the handle's current state (FP64, n_matsubara = 0, any closure): for every
  * replica and grid point, the inputs of the target tier t (1 <= t <= depth; tiers t-1, t-2, unscaled) into
- * X_dev [..][36 S^2 + 3] and the tier-t values into Y_dev [..][2 S^2] (device, floats), starting at sample
- * `offset`, at most up to `capacity`; count_out: samples written. */
+ * X_dev [..][36 S^2 + 3] and the targets into Y_dev [..][2 S^2] (device, floats): the tier-t values less
+ * r_0 p W^(t-1) + c_0 dW^(t-1)/dp (4th-order central along the periodic p axis), i.e. the D of a depth
+ * t - 1 closure; starting at sample `offset`, at most up to `capacity`; count_out: samples written. */
 qhfpe_status qhfpe_closure_state_collect(qhfpe_t *h, int target_tier, float *X_dev, float *Y_dev, long offset,
                                          long capacity, long *count_out);
 /* The mean squared error over the n_points samples and all outputs, and its gradient (FP32 kernels),

@@ -224,14 +224,32 @@ def state_inputs(W, tier, model):
     return out
 
 
-def state_targets(W, tier):
-    """[nq][np][2 S^2] targets: (re, im) of W^(tier)_jk pair by pair."""
+def terminator_element(W_low, model, r0, c0):
+    """The element that the Eq. (GMFP) terminator stands for, r_0 p W + c_0 dW/dp, of one tier W_low
+    [S][S][nq][np]: its d/dp is the terminator's d/dp (r_0 p W) + c_0 d2W/dp2 up to the composition of
+    two first differences (the right-hand side's 4th-order central difference along the periodic p
+    axis, written out here as a sum over the four neighbours)."""
+    from qhfpe_inputs import axis
+    n_p = W_low.shape[-1]
+    p = axis(n_p, model["p_min"], model["p_max"])
+    dp = (model["p_max"] - model["p_min"]) / n_p
+    dW = (np.roll(W_low, 2, -1) - 8 * np.roll(W_low, 1, -1) + 8 * np.roll(W_low, -1, -1) - np.roll(W_low, -2, -1)) / (12 * dp)
+    return r0 * p * W_low + c0 * dW
+
+
+def state_targets(W, tier, model):
+    """[nq][np][2 S^2] targets: (re, im) pair by pair of D = W^(tier) less the terminator's element of
+    W^(tier-1) (the closure term of a depth tier-1 hierarchy is then the terminator plus d/dp D), with
+    the bath's r_0 and c_0 (one Drude mode)."""
+    import oracle
+    co = oracle.Oracle(dict(model, closure=0)).coefficients()
     n_elem, S, _, nq, n_p = W.shape
+    D = W[tier] - terminator_element(W[tier - 1], model, co["r"][0], co["c"][0])
     Y = np.zeros((nq, n_p, 2 * S * S))
     for j in range(S):
         for k in range(S):
-            Y[..., 2 * (j * S + k)] = W[tier, j, k].real
-            Y[..., 2 * (j * S + k) + 1] = W[tier, j, k].imag
+            Y[..., 2 * (j * S + k)] = D[j, k].real
+            Y[..., 2 * (j * S + k) + 1] = D[j, k].imag
     return Y
 
 

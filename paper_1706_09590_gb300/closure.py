@@ -64,7 +64,8 @@ def train(X, stats, n_iters=3000, batch=4096, lr=1e-3, ridge=0.01, seed=1706, we
 
 # ---- state-input network (QHFPE_LEARNED_STATE): the network reads the deepest tiers' local values ------
 def initial_state_weights(S, seed=1706):
-    """Glorot-uniform hidden layers, zero output layer (the untrained network predicts zero: truncation),
+    """Glorot-uniform hidden layers, zero output layer (the untrained network predicts a zero correction:
+    the Eq. (GMFP) terminator alone),
     unit scales."""
     from .qhfpe import closure_state_n_weights
     n_in, n_out = 36 * S * S + 3, 2 * S * S
@@ -83,8 +84,9 @@ def state_training_set(model, U_table, etas, deep_depth, target_tier, n_eq, n_pr
                        max_samples=400000, seed=1706):
     """Samples (X, Y) of the target tier from depth-`deep_depth` FP64 runs (Eq. (GMFP) terminator) at each
     eta, excited like the statistics of the coefficient form: every grid point of both replicas every
-    `every` steps, then at most max_samples of them drawn at random (seeded).  Returns host float32
-    arrays."""
+    `every` steps, then at most max_samples of them drawn at random (seeded).  Y is the target tier less
+    the element that the terminator of the tier below stands for (qhfpe_closure_state_collect).  Returns
+    host float32 arrays."""
     import torch
     S = model["S"]
     n_in, n_out = 36 * S * S + 3, 2 * S * S

@@ -416,7 +416,8 @@ qhfpe_status build_model(qhfpe *h, Model &M, int S, const double *U, const doubl
         }
         E.ngam = ngam;
         E.tier = tier;
-        E.terminator = ((p.closure == QHFPE_TERMINATOR || p.closure == QHFPE_LEARNED) && tier == p.depth) ? 1 : 0;  // not LEARNED_STATE
+        E.terminator = ((p.closure == QHFPE_TERMINATOR || p.closure == QHFPE_LEARNED || p.closure == QHFPE_LEARNED_STATE) &&
+                        tier == p.depth) ? 1 : 0;
         for (int k = 0; k < M.n_modes; ++k) {
             std::vector<int> v = n;
             v[k] += 1;

@@ -540,10 +540,11 @@ extern "C" qhfpe_status qhfpe_closure_train(float *w, const double *X, const dou
 // State-input closure: the network reads the state itself.  For the deepest element n (one Drude
 // mode, a chain), at grid point (q_i, p_l) the inputs are (q_i / 8, p_l / 8, ln eta) followed by the
 // 3 x 3 patches (q_{i+a}, p_{l+b}), a, b in {-1, 0, 1}, of tiers N and N-1 for every electronic pair
-// (re, im) -- 36 S^2 + 3 values -- and the outputs are W^(N+1)_jk(q_i, p_l) for every pair (re, im),
-// 2 S^2 values, written to the closure slot that the deepest element's tier-up term reads.  The closed
-// hierarchy is then nonlinear in the state (no terminator is added: the network predicts the whole
-// element).  Weights (float): W1[256][n_in], b1, W2[256][256], b2, W3[256][256], b3, W4[n_out][256],
+// (re, im) -- 36 S^2 + 3 values -- and the outputs are D_jk(q_i, p_l) for every pair (re, im), 2 S^2
+// values: the missing element W^(N+1) less the element that the Eq. (GMFP) terminator stands for,
+// r_0 p W^(N) + c_0 dW^(N)/dp.  They are written to the closure slot that the deepest element's tier-up
+// term reads; that element keeps the terminator, so an untrained (zero) network is the terminator.  The
+// closed hierarchy is nonlinear in the state.  Weights (float): W1[256][n_in], b1, W2[256][256], b2, W3[256][256], b3, W4[n_out][256],
 // b4, then three scales: tier-N inputs, tier-(N-1) inputs and outputs (the network works on the
 // values divided by them).
 // ===================================================================================================
@@ -721,7 +722,8 @@ __global__ void __launch_bounds__(256) state_closure_kernel(GridInfo g, T *state
 }
 
 // training samples of target tier t from every replica and grid point: X [n][n_in] unscaled inputs of
-// tiers t-1, t-2, Y [n][n_out] the tier-t values
+// tiers t-1, t-2, Y [n][n_out] the tier-t values less r_0 p W^(t-1) + c_0 dW^(t-1)/dp (4th-order central
+// difference, periodic p)
 template <typename T, int S>
 __global__ void state_collect_kernel(GridInfo g, const T *state, int e_t, int e_t1, int e_t2, double log_eta, float *X,
                                      float *Y, long offset, long capacity)
@@ -735,10 +737,18 @@ __global__ void state_collect_kernel(GridInfo g, const T *state, int e_t, int e_
         const int x = (int)(idx % g.blk);
         const T *rs = state + (size_t)rep * g.rep_stride;
         sc_gather<T>(g, rs, e_t1, e_t2, x / g.np, x % g.np, log_eta, X + (size_t)o * NI, 1.f, 1.f);
+        const int i = x / g.np, l = x % g.np, np = g.np;
+        const double p = g.p_min + l * g.dp, inv12dp = 1.0 / (12.0 * g.dp);
+        const int lm2 = (l + np - 2) % np, lm1 = (l + np - 1) % np, lp1 = (l + 1) % np, lp2 = (l + 2) % np;
         for (int pr = 0; pr < S2; ++pr) {
             const T *blk = rs + (size_t)e_t * g.elem_stride + (size_t)pr * 2 * g.blk;
-            Y[(size_t)o * NO + 2 * pr] = (float)blk[x];
-            Y[(size_t)o * NO + 2 * pr + 1] = (float)blk[g.blk + x];
+            const T *low = rs + (size_t)e_t1 * g.elem_stride + (size_t)pr * 2 * g.blk + (size_t)i * np;
+            for (int part = 0; part < 2; ++part) {
+                const T *w1 = low + (size_t)part * g.blk;
+                const double dw = (w1[lm2] - 8.0 * w1[lm1] + 8.0 * w1[lp1] - w1[lp2]) * inv12dp;
+                const double term = g.term_r0 * p * (double)w1[l] + g.term_c0 * dw;
+                Y[(size_t)o * NO + 2 * pr + part] = (float)((double)blk[(size_t)part * g.blk + x] - term);
+            }
         }
     }
 }

@@ -1,5 +1,5 @@
 """The state-input learned closure (QHFPE_LEARNED_STATE: the network reads 3 x 3 patches of tiers N and
-N-1 and predicts W^(N+1)) on the GPU: its training gradient and samples against the oracle, the
+N-1 and predicts the part of W^(N+1) that the Eq. (GMFP) terminator misses) on the GPU: its training gradient and samples against the oracle, the
 classic-RK4 propagation with the network inside every right-hand side against an oracle composition,
 and the measurement that decides between it and the coefficient form: the pathway-additivity defect of
 the third-order response (ket + bra - full) and the error against the deep hierarchy."""
@@ -69,16 +69,16 @@ def test_state_samples_match_oracle(torch):
     assert n == 2 * 12 * 32
     got_X, got_Y = X[5:].cpu().numpy(), Y[5:].cpu().numpy()
     ref_X = np.concatenate([ocl.state_inputs(W, 3, m).reshape(-1, n_in) for W in (W0, W1)])
-    ref_Y = np.concatenate([ocl.state_targets(W, 3).reshape(-1, n_out) for W in (W0, W1)])
+    ref_Y = np.concatenate([ocl.state_targets(W, 3, m).reshape(-1, n_out) for W in (W0, W1)])
     assert rel(got_X, ref_X) < 1e-6 and rel(got_Y, ref_Y) < 1e-6
     P.close()
 
 
 def _oracle_state_rk4(m, w, W, n_steps):
-    """Classic RK4 of the oracle's truncated right-hand side plus the closure term d/dp W^(N+1) at the
-    deepest tier, W^(N+1) from the oracle's forward of the network with bf16 inputs, weights and
+    """Classic RK4 of the oracle's right-hand side with the Eq. (GMFP) terminator plus the closure term
+    d/dp D at the deepest tier, D from the oracle's forward of the network with bf16 inputs, weights and
     activations (the library's inference precision)."""
-    O = oracle.Oracle(dict(m, closure=0))
+    O = oracle.Oracle(dict(m, closure=1))
     S, N = m["S"], m["depth"]
     dp = (m["p_max"] - m["p_min"]) / m["np"]
 
@@ -116,11 +116,11 @@ def test_state_closure_steps_match_oracle(torch):
     assert np.all(np.isfinite(got)) and np.all(np.isfinite(tr))
     # bf16 inference: a pre-activation at a rounding boundary may land one bf16 step apart
     assert rel(got, ref) < 1e-5
-    # without weights the closure slot is zero: the truncated hierarchy, classic RK4
+    # without weights the network's element is zero: the terminator alone, classic RK4
     Q = _P(m)
     Q.set_state(W)
     Q.step(4)
-    ref0, _ = oracle.Oracle(dict(m, closure=0)).step(W, 4)
+    ref0, _ = oracle.Oracle(dict(m, closure=1)).step(W, 4)
     assert rel(Q.get_state(0), ref0) < 1e-11
     Q.close()
     P.close()

@@ -138,6 +138,30 @@ def test_state_inputs_layout_on_an_impulse():
     assert X[0, 0, 0] == m["q_min"] / 8 and X[0, 1, 1] == (m["p_min"] + 2.0) / 8
 
 
+def test_state_targets_on_plane_waves():
+    """The target is W^(t) less r_0 p W^(t-1) + c_0 dW^(t-1)/dp.  With W^(t-1) = exp(i k p) (a plane wave of
+    the periodic p grid) the 4th-order central difference is multiplication by
+    i (8 sin(k dp) - sin(2 k dp)) / (6 dp), so W^(t) = r_0 p W^(t-1) + c_0 lambda W^(t-1) gives a zero target,
+    and W^(t) = 0 gives minus that element; r_0 = eta and c_0 = eta / beta (high temperature, Sec. II)."""
+    m = qi.harmonic_two_state(nq=5, n_p=16, depth=3, eta=0.7, beta=0.48)
+    n_p, dp = m["np"], (m["p_max"] - m["p_min"]) / m["np"]
+    p = m["p_min"] + dp * np.arange(n_p)
+    r0, c0 = 0.7, 0.7 / 0.48
+    W = np.zeros(qi.state_shape(m), complex)
+    for mode, (j, k) in ((3, (0, 1)), (5, (1, 1))):
+        kk = 2 * np.pi * mode / (n_p * dp)
+        wave = np.exp(1j * kk * (p - m["p_min"]))
+        lam = 1j * (8 * np.sin(kk * dp) - np.sin(2 * kk * dp)) / (6 * dp)
+        W[1, j, k] = wave[None, :] * (1.0 + np.arange(5))[:, None]
+        W[2, j, k] = (r0 * p + c0 * lam) * W[1, j, k]
+    Y = cl.state_targets(W, 2, m)
+    assert np.abs(Y).max() < 1e-12 * np.abs(W).max()
+    W[2] = 0
+    Y = cl.state_targets(W, 2, m)
+    ref = -(r0 * p + c0 * 1j * (8 * np.sin(2 * np.pi * 3 / n_p) - np.sin(4 * np.pi * 3 / n_p)) / (6 * dp)) * W[1, 0, 1]
+    assert np.allclose(Y[..., 2 * 1] + 1j * Y[..., 2 * 1 + 1], ref, rtol=1e-12, atol=1e-12)
+
+
 def test_state_gradient_matches_finite_differences():
     S = 1
     n_in, n_out = cl.state_sizes(S)
