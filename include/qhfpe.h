@@ -62,7 +62,13 @@ typedef enum {
     QHFPE_MIXED = 1,
     /* As QHFPE_MIXED, but the potential kernel is a DFT-as-GEMM on the tcgen05 tensor cores with
      * split bf16 (hi + lo, three products) operands and FP32 accumulation. */
-    QHFPE_MIXED_BF16X3 = 2
+    QHFPE_MIXED_BF16X3 = 2,
+    /* Reserved: the same DFT-as-GEMM with split TF32 operands.  Not built; qhfpe_create returns
+     * QHFPE_EUNSUPPORTED.  kind::tf32 runs at half the bf16 tensor rate with twice the operand bytes,
+     * so the resident cosine/sine operand tiles (hi and lo, 256 KB at np = 128) no longer fit in
+     * shared memory beside the streamed state; the split-bf16 form already meets the mixed forms'
+     * 1e-4 accuracy on the responses. */
+    QHFPE_MIXED_TF32X3 = 3
 } qhfpe_precision;
 
 typedef enum {

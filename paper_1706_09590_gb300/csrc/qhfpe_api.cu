@@ -1131,6 +1131,11 @@ qhfpe_status qhfpe_create(const qhfpe_params *params, void *stream, qhfpe_t **ou
     if (p.closure == QHFPE_LEARNED_STATE &&
         (p.n_matsubara != 0 || p.precision != QHFPE_FP64 || p.n_states > 2 || !fused_supported(p.np, p.n_states)))
         return bad("the state-input closure needs n_matsubara = 0, QHFPE_FP64, n_states <= 2 and np in {32, 64, 128, 256}");
+    if (p.precision == QHFPE_MIXED_TF32X3) {
+        create_err = "QHFPE_MIXED_TF32X3 is not built (its tf32 operand tiles do not fit in shared memory; "
+                     "use QHFPE_MIXED_BF16X3)";
+        return QHFPE_EUNSUPPORTED;
+    }
     if (p.precision != QHFPE_FP64 && p.precision != QHFPE_MIXED && p.precision != QHFPE_MIXED_BF16X3)
         return bad("unknown precision");
     if (p.precision == QHFPE_MIXED_BF16X3 && !tc_supported(p.np, p.n_states)) {

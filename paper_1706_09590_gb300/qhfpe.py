@@ -13,12 +13,12 @@ from . import build as _build
 
 LIB_PATH = _build.LIB
 
-FP64, MIXED, MIXED_BF16X3 = 0, 1, 2
+FP64, MIXED, MIXED_BF16X3, MIXED_TF32X3 = 0, 1, 2, 3  # TF32X3: declared, not built
 TRUNCATE, TERMINATOR, LEARNED = 0, 1, 2
 LEFT, RIGHT, COMMUTATOR = 1, 2, 3
 TERM_KINETIC, TERM_POTENTIAL, TERM_DAMPING, TERM_TIER_UP, TERM_TIER_DOWN, TERM_ALL = 1, 2, 4, 8, 16, 31
 LINEAR, THIRD_ORDER = 0, 1
-PRECISIONS = {"fp64": FP64, "mixed": MIXED, "bf16x3": MIXED_BF16X3}
+PRECISIONS = {"fp64": FP64, "mixed": MIXED, "bf16x3": MIXED_BF16X3, "tf32x3": MIXED_TF32X3}
 
 STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ENUMERIC", 5: "ETIMEOUT", 6: "EUNSUPPORTED",
           7: "ESTATE"}

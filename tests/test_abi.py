@@ -73,6 +73,17 @@ def test_create_rejects_invalid_parameters(over, msg):
     assert msg in L.qhfpe_last_error(None).decode()
 
 
+def test_split_tf32_precision_is_reserved():
+    """QHFPE_MIXED_TF32X3 is declared but not built: creation answers QHFPE_EUNSUPPORTED with a reason."""
+    import paper_1706_09590_gb300.qhfpe as q
+    L = q.lib()
+    p, keep = _params(precision=3)
+    h = ctypes.c_void_p()
+    assert L.qhfpe_create(ctypes.byref(p), None, ctypes.byref(h)) == 6  # EUNSUPPORTED
+    assert not h.value
+    assert "TF32X3" in L.qhfpe_last_error(None).decode()
+
+
 def test_create_rejects_non_finite_tables():
     import paper_1706_09590_gb300.qhfpe as q
     L = q.lib()
