@@ -10,7 +10,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libqhfpe.so")
-SOURCES = ["qhfpe_api.cu", "qhfpe_kernels.cu", "qhfpe_fused.cu", "qhfpe_fused_nl.cu", "qhfpe_fused_multi.cu", "qhfpe_closure.cu", "qhfpe_tc.cu", "qhfpe_static.cu", "qhfpe_persistent.cu"]
+SOURCES = ["qhfpe_api.cu", "qhfpe_kernels.cu", "qhfpe_fused.cu", "qhfpe_fused_nl.cu", "qhfpe_fused_multi.cu", "qhfpe_fused_multi_nl.cu", "qhfpe_closure.cu", "qhfpe_tc.cu", "qhfpe_static.cu", "qhfpe_persistent.cu", "qhfpe_persistent_nl.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-I" + os.path.join(HERE, "..", "include")]

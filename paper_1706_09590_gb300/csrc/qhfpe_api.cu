@@ -2218,12 +2218,14 @@ qhfpe_status batch_launch(qhfpe_batch *b, int k, cudaStream_t st)
 {
     qhfpe *h0 = b->mem[0];
     const int n = (int)b->mem.size();
+    bool nonlinear = false;
+    for (qhfpe *m : b->mem) nonlinear = nonlinear || m->main->g.c2 != 0.0;
     if (b->mixed)
         QH_CK(h0, (launch_fused_multi<float, true>(b->np, b->S, (const MultiMember<float> *)b->desc, n, k, b->tq,
-                                                   b->blocks, st)));
+                                                   b->blocks, nonlinear, st)));
     else
         QH_CK(h0, (launch_fused_multi<double, false>(b->np, b->S, (const MultiMember<double> *)b->desc, n, k, b->tq,
-                                                     b->blocks, st)));
+                                                     b->blocks, nonlinear, st)));
     return QHFPE_OK;
 }
 

@@ -150,10 +150,11 @@ StageScalars<T> stage_scalars(const GridInfo &g, double h);
 // blocks of one fused launch over all replicas at tile height tq
 long fused_blocks(const GridInfo &g, int tq);
 // Horner stage k (4..1; 0: the right-hand side into vB) of every member of mem (device array, n_mem
-// members sharing np and S, block0 ascending from 0, blocks in total) as one launch.
+// members sharing np and S, block0 ascending from 0, blocks in total) as one launch; nonlinear: some
+// member has c2 != 0 (the instantiation with those terms).
 template <typename T, bool MIXED>
 cudaError_t launch_fused_multi(int np, int S, const MultiMember<T> *mem, int n_mem, int k, int tq, long blocks,
-                               cudaStream_t st);
+                               bool nonlinear, cudaStream_t st);
 // shared-memory limit of the batch instantiation (called by prepare_fused)
 template <typename T, bool MIXED>
 cudaError_t prepare_fused_multi(int np, int S, size_t smem);
