@@ -81,6 +81,27 @@ def test_window_steps_against_oracle_and_other_kernel(name, monkeypatch):
     assert rel(got, out["0"][0]) < 2e-6
 
 
+def test_window_replicas_and_single_replica_rhs(monkeypatch):
+    """Three replicas with different states in one launch (replica index of each block), and the
+    right-hand side of one replica alone (the launch's first-replica offset), against the oracle."""
+    m = MODELS["two_state_K2"]
+    monkeypatch.setenv("QHFPE_TILE_ROWS", "2")
+    W = qi.random_state(m, seed=24, replicas=3, hermitian=True)
+    P = _P(m, n_replicas=3)
+    for r in range(3):
+        P.set_state(W[r], replica=r)
+    tr = P.step(6, record_trace=True)
+    assert P.stage_form() == 1
+    O = oracle.Oracle(m)
+    for r in range(3):
+        ref_W, ref_tr = O.step(W[r], 6)
+        assert rel(P.get_state(r), ref_W) < 1e-5 and rel(tr[r], ref_tr) < 1e-5
+    got = P.apply_rhs(1)
+    ref = O.rhs(P.get_state(1))
+    assert rel(got, ref) < 2e-5
+    P.close()
+
+
 def test_window_learned_closure_slot():
     """The learned closure's W^(N+1) slot is one more tier-up neighbour of the deepest element: with
     loaded weights the window kernel matches the other kernel."""
