@@ -8,6 +8,7 @@
 #include "qhfpe_internal.cuh"
 
 #include <algorithm>
+#include <cstdint>
 #include <mutex>
 
 namespace {
@@ -458,6 +459,102 @@ __global__ void from_canonical_kernel(GridInfo g, const H *__restrict__ src, T *
     }
 }
 
+// N consecutive floats or doubles (N x size a multiple of 16 bytes, 16-byte aligned) through 16-byte accesses
+template <typename V, int N> __device__ __forceinline__ void ld16(const V *p, V *out)
+{
+    static_assert((N * sizeof(V)) % 16 == 0, "16-byte chunks");
+#pragma unroll
+    for (int c = 0; c < (int)(N * sizeof(V) / 16); ++c) {
+        if constexpr (sizeof(V) == 4) {
+            const float4 a = reinterpret_cast<const float4 *>(p)[c];
+            out[4 * c] = a.x; out[4 * c + 1] = a.y; out[4 * c + 2] = a.z; out[4 * c + 3] = a.w;
+        } else {
+            const double2 a = reinterpret_cast<const double2 *>(p)[c];
+            out[2 * c] = a.x; out[2 * c + 1] = a.y;
+        }
+    }
+}
+template <typename V, int N> __device__ __forceinline__ void st16(V *p, const V *in)
+{
+    static_assert((N * sizeof(V)) % 16 == 0, "16-byte chunks");
+#pragma unroll
+    for (int c = 0; c < (int)(N * sizeof(V) / 16); ++c) {
+        if constexpr (sizeof(V) == 4)
+            reinterpret_cast<float4 *>(p)[c] = make_float4(in[4 * c], in[4 * c + 1], in[4 * c + 2], in[4 * c + 3]);
+        else
+            reinterpret_cast<double2 *>(p)[c] = make_double2(in[2 * c], in[2 * c + 1]);
+    }
+}
+
+// The same conversions four cells at a time (blk a multiple of 4, the canonical array 16-byte aligned):
+// one thread reads four interleaved complex values and writes four values of each plane.
+template <typename T, typename H>
+__global__ void from_canonical4_kernel(GridInfo g, const H *__restrict__ src, T *dst, double *y0, int rep0,
+                                       int *nonfinite)
+{
+    const size_t blk = g.blk, blk4 = blk / 4;
+    const size_t per4 = (size_t)g.n_elem * g.S * g.S * blk4;
+    const int rep = rep0 + blockIdx.y;
+    bool bad = false;
+    for (size_t qd = blockIdx.x * (size_t)blockDim.x + threadIdx.x; qd < per4; qd += (size_t)gridDim.x * blockDim.x) {
+        const size_t ep = qd / blk4, cell = (qd - ep * blk4) * 4;
+        H v[8];
+        ld16<H, 8>(src + 2 * (ep * blk + cell), v);
+        double re[4], im[4];
+        T tr[4], ti[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            re[j] = (double)v[2 * j];
+            im[j] = (double)v[2 * j + 1];
+            bad = bad || !(isfinite(re[j]) && isfinite(im[j]));
+            tr[j] = (T)re[j];
+            ti[j] = (T)im[j];
+        }
+        const size_t o = (size_t)rep * g.rep_stride + ep * 2 * blk + cell;
+        st16<T, 4>(dst + o, tr);
+        st16<T, 4>(dst + o + blk, ti);
+        if (y0 && ep < (size_t)(g.S * g.S)) {
+            const size_t o0 = (size_t)rep * g.tier0_rep_stride + ep * 2 * blk + cell;
+            st16<double, 4>(y0 + o0, re);
+            st16<double, 4>(y0 + o0 + blk, im);
+        }
+    }
+    if (bad && nonfinite) *nonfinite = 1;
+}
+
+template <typename T, typename H>
+__global__ void to_canonical4_kernel(GridInfo g, const T *__restrict__ src, const double *__restrict__ y0, H *dst, int rep)
+{
+    const size_t blk = g.blk, blk4 = blk / 4;
+    const size_t per4 = (size_t)g.n_elem * g.S * g.S * blk4;
+    for (size_t qd = blockIdx.x * (size_t)blockDim.x + threadIdx.x; qd < per4; qd += (size_t)gridDim.x * blockDim.x) {
+        const size_t ep = qd / blk4, cell = (qd - ep * blk4) * 4;
+        double re[4], im[4];
+        if (y0 && ep < (size_t)(g.S * g.S)) {
+            const size_t o0 = (size_t)rep * g.tier0_rep_stride + ep * 2 * blk + cell;
+            ld16<double, 4>(y0 + o0, re);
+            ld16<double, 4>(y0 + o0 + blk, im);
+        } else {
+            const size_t o = (size_t)rep * g.rep_stride + ep * 2 * blk + cell;
+            T tr[4], ti[4];
+            ld16<T, 4>(src + o, tr);
+            ld16<T, 4>(src + o + blk, ti);
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                re[j] = (double)tr[j];
+                im[j] = (double)ti[j];
+            }
+        }
+        H v[8];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            v[2 * j] = (H)re[j];
+            v[2 * j + 1] = (H)im[j];
+        }
+        st16<H, 8>(dst + 2 * (ep * blk + cell), v);
+    }
+}
+
 template <typename T, typename H>
 __global__ void to_canonical_kernel(GridInfo g, const T *__restrict__ src, const double *__restrict__ y0,
                                     H *dst, int rep)
@@ -717,8 +814,13 @@ cudaError_t launch_from_canonical(const GridInfo &g, const H *src, T *dst, doubl
                                   cudaStream_t st, int *nonfinite)
 {
     const size_t per = (size_t)g.n_elem * g.S * g.S * g.blk;
-    dim3 grid(grid_for(per, 256, 2048), n_rep);
-    from_canonical_kernel<T, H><<<grid, 256, 0, st>>>(g, src, dst, y0_dst, rep, nonfinite);
+    if (g.blk % 4 == 0 && reinterpret_cast<uintptr_t>(src) % 16 == 0) {
+        dim3 grid(grid_for(per / 4, 256, 2048), n_rep);
+        from_canonical4_kernel<T, H><<<grid, 256, 0, st>>>(g, src, dst, y0_dst, rep, nonfinite);
+    } else {
+        dim3 grid(grid_for(per, 256, 2048), n_rep);
+        from_canonical_kernel<T, H><<<grid, 256, 0, st>>>(g, src, dst, y0_dst, rep, nonfinite);
+    }
     return cudaGetLastError();
 }
 
@@ -727,7 +829,10 @@ cudaError_t launch_to_canonical(const GridInfo &g, const T *src, const double *y
                                 cudaStream_t st)
 {
     const size_t per = (size_t)g.n_elem * g.S * g.S * g.blk;
-    to_canonical_kernel<T, H><<<grid_for(per, 256, 2048), 256, 0, st>>>(g, src, y0_src, dst, rep);
+    if (g.blk % 4 == 0 && reinterpret_cast<uintptr_t>(dst) % 16 == 0)
+        to_canonical4_kernel<T, H><<<grid_for(per / 4, 256, 2048), 256, 0, st>>>(g, src, y0_src, dst, rep);
+    else
+        to_canonical_kernel<T, H><<<grid_for(per, 256, 2048), 256, 0, st>>>(g, src, y0_src, dst, rep);
     return cudaGetLastError();
 }
 

@@ -42,7 +42,23 @@ def test_complex64_state_io(precision):
     d_out = torch.empty(P.shape, dtype=torch.complex64, device="cuda")
     P.get_state(1, out=d_out)
     assert np.array_equal(d_out.cpu().numpy(), W32)
-    # non-finite input
+    # device buffers 8 bytes off a 16-byte boundary take the element-wise conversion (the four-cell
+    # conversion needs 16-byte aligned canonical arrays)
+    big_in = torch.zeros(W32.size + 1, dtype=torch.complex64, device="cuda")
+    off_in = big_in[1:].view(P.shape)
+    off_in.copy_(d_in)
+    assert off_in.data_ptr() % 16 == 8
+    P.set_state(off_in, 1)
+    big_out = torch.zeros(W32.size + 1, dtype=torch.complex64, device="cuda")
+    off_out = big_out[1:].view(P.shape)
+    P.get_state(1, out=off_out)
+    assert np.array_equal(off_out.cpu().numpy(), W32)
+    # non-finite input, at the first and the last cell too
+    for idx in ((0, 0, 0, 0, 0), tuple(d - 1 for d in W32.shape)):
+        bad = W32.copy()
+        bad[idx] = np.inf
+        with pytest.raises(QhfpeError):
+            P.set_state(bad, 0)
     bad = W32.copy()
     bad[1, 0, 1, 3, 5] = np.nan
     with pytest.raises(QhfpeError):
