@@ -189,8 +189,9 @@ class Clocks:
 
 
 SPEC2D = dict(n_t1=64, t1_stride=8, t2=[0, 100, 200, 300], n_t3=512)
-# FP64 stage kernel on the benchmark workload: (2 DFMA + DADD + DMUL) per cell per stage, ncu count
-FP64_FLOPS_PER_CELL_STAGE = (2 * 412277760 + 311639040 + 60825600) / 8110080
+# FP64 stage kernel on the benchmark workload: (2 DFMA + DADD + DMUL) per cell per stage, ncu count of
+# the current kernel (the p-diagonal bath terms in the r-space mixing)
+FP64_FLOPS_PER_CELL_STAGE = (2 * 348410880 + 287308800 + 61332480) / 8110080
 FP64_PEAK_TFLOPS = 2 * 2 * 152 * 2.07e9 / 1e12
 
 
